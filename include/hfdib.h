@@ -1,0 +1,195 @@
+/*
+ * hfdib.h -- C ABI of the GB300 (sm_103a) HFDIB steady-RANS SIMPLE solver.
+ *
+ * The library solves the steady RANS equations with the hybrid fictitious
+ * domain-immersed boundary (HFDIB) treatment on a uniform Cartesian grid:
+ * momentum with the immersed-boundary source f_ib and the lambda-masked
+ * continuity equation (Sec. 2.1, Eq. hfdibrans), k-epsilon or k-omega SST
+ * transport with wall-function values imposed at immersed-boundary cells
+ * (Sec. 2.5, Eqs. imval, kws, frictionvel, omegaws), iterated with the
+ * extended SIMPLE loop of Sec. 2.5.1 (Fig. simplehfdibrans).
+ *
+ * Conventions
+ *   - Cell arrays are [nz][ny][nx] with x fastest, FP64, on the device.
+ *     nz == 1 is a one-cell-thick 2D grid (dz is then taken as sqrt(dx*dy),
+ *     so that the cell size V^(1/3) is sqrt(dx*dy)).
+ *   - Every call returns an int status: HFDIB_OK (0) or a negative
+ *     hfdib_status.  No call aborts, traps or exits.  After an error the
+ *     handle stays valid (HFDIB_ERR_CUDA after a sticky CUDA error excepted).
+ *   - Device pointers passed in are read on the handle's stream; the caller
+ *     keeps ownership of every buffer it passes.  The handle owns its fields
+ *     and scratch (allocated at create, freed at destroy).
+ *   - All work is issued on the stream given at create (NULL = default).
+ */
+#ifndef HFDIB_H
+#define HFDIB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HFDIB_OK = 0,
+    HFDIB_ERR_INVALID_ARG = -1,   /* bad sizes, NaN / out-of-range lambda, bad enum */
+    HFDIB_ERR_CUDA = -2,          /* a CUDA runtime call failed                     */
+    HFDIB_ERR_OOM = -3,           /* device allocation failed                       */
+    HFDIB_ERR_NOT_CONVERGED = -4, /* max_iter reached above tol                     */
+    HFDIB_ERR_DIVERGED = -5,      /* NaN / Inf in a residual                        */
+    HFDIB_ERR_STATE_MISMATCH = -6 /* checkpoint from another grid / model           */
+} hfdib_status;
+
+typedef enum { HFDIB_LAMINAR = 0, HFDIB_KEPSILON = 1, HFDIB_KOMEGA_SST = 2 } hfdib_model;
+
+/* Domain boundary kinds (Sec. 3.1 "Boundary conditions"):
+ *  INLET  : Dirichlet u = u_in, k, eps/omega from Eq. (bcspkoein); zero-gradient p
+ *  OUTLET : p = p_out; zero-gradient u, k, eps/omega
+ *  SLIP   : zero normal velocity, zero-gradient tangential velocity and scalars
+ *  WALL   : no-slip u = 0; zero-gradient p and turbulence (Sec. 3.6)
+ *  EMPTY  : the two z sides of a 2D grid
+ * A wall or slip face whose cell has lambda > 0, and an inlet face whose cell
+ * has lambda >= 0.5, is closed: zero gradient for all variables, no flux
+ * (walls inside the solid phase, Sec. 3.1). */
+typedef enum {
+    HFDIB_BC_INLET = 0, HFDIB_BC_OUTLET = 1, HFDIB_BC_SLIP = 2, HFDIB_BC_WALL = 3,
+    HFDIB_BC_EMPTY = 4
+} hfdib_bc_kind;
+
+typedef struct {
+    int32_t nx, ny, nz;          /* cells; nz == 1 -> 2D                         */
+    double x0, y0, z0;           /* lower corner                                 */
+    double dx, dy, dz;           /* uniform spacings (2D: dz = sqrt(dx*dy))      */
+} hfdib_grid;
+
+typedef struct {
+    int32_t face[6];             /* hfdib_bc_kind for xmin,xmax,ymin,ymax,zmin,zmax */
+    double u_in[3];              /* inlet velocity                                */
+    double I_in;                 /* inlet turbulence intensity (Eq. bcspkoein)    */
+    double lt_in;                /* inlet turbulent length scale l_t              */
+    double p_out;                /* outlet kinematic pressure                     */
+    double u_ref, l_ref;         /* nu = u_ref * l_ref / Re                       */
+    double u_s[3];               /* velocity of the solid (Eq. imval)             */
+} hfdib_bc;
+
+typedef struct {
+    double urf_u;                /* momentum under-relaxation (default 0.7)       */
+    double urf_p;                /* pressure under-relaxation (default 0.3)       */
+    double urf_turb;             /* k, eps/omega under-relaxation (default 0.85)  */
+    int32_t n_u;                 /* red-black Gauss-Seidel sweeps, momentum (2)   */
+    int32_t n_turb;              /* red-black Gauss-Seidel sweeps, k and eps/omega (2) */
+    double p_reltol;             /* pressure solve: |r| <= p_reltol |r0| (0.01)   */
+    int32_t p_maxiter;           /* pressure solve iteration cap (200)            */
+    int32_t precision;           /* 0 = FP64 throughout                           */
+    int32_t precond;             /* pressure preconditioner: 0 Jacobi, 1 GMG V-cycle (1) */
+    int32_t p_check;             /* read |r| back every p_check CG iterations (1);
+                                    0 = run p_maxiter iterations without host reads */
+    int32_t mg_coarse_sweeps;    /* red-black sweeps (each way) on the coarsest level (20) */
+    int32_t reserved[5];
+} hfdib_options;
+
+typedef struct hfdib_ctx* hfdib_handle;
+
+/* Field identifiers for hfdib_get_field / hfdib_set_field. */
+enum {
+    HFDIB_FIELD_UX = 0, HFDIB_FIELD_UY = 1, HFDIB_FIELD_UZ = 2, HFDIB_FIELD_P = 3,
+    HFDIB_FIELD_K = 4, HFDIB_FIELD_EPS = 5, HFDIB_FIELD_OMEGA = 6, HFDIB_FIELD_NUT = 7,
+    HFDIB_FIELD_PHIX = 8, HFDIB_FIELD_PHIY = 9, HFDIB_FIELD_PHIZ = 10
+};
+
+/* Residual slots of the per-sweep residual vector (HFDIB_NRES doubles):
+ * scaled residuals sum|b-Ax| / (sum|Ax - xbar A1| + sum|b - xbar A1|) of the
+ * momentum components, pressure, eps or omega and k, evaluated at the start
+ * of each solve (App. D), then the continuity error sum over lambda<1 cells
+ * of |div phi| (App. D), then the number of pressure iterations. */
+enum { HFDIB_RES_UX = 0, HFDIB_RES_UY = 1, HFDIB_RES_UZ = 2, HFDIB_RES_P = 3,
+       HFDIB_RES_EPSW = 4, HFDIB_RES_K = 5, HFDIB_RES_CONT = 6, HFDIB_RES_PITER = 7,
+       HFDIB_NRES = 8 };
+
+/* Fill *opt with the defaults listed in hfdib_options. */
+void hfdib_default_options(hfdib_options* opt);
+
+/* hfdib_create -- set up a solver for one lambda field.
+ *   grid     : sizes and spacings; nx, ny >= 2; nz >= 1.
+ *   lambda   : device pointer, nx*ny*nz doubles in [0, 1] (Eq. lambda); copied.
+ *   ywall    : device pointer to the wall distance used by the SST blending
+ *              functions (nullable; required for HFDIB_KOMEGA_SST); copied.
+ *   model    : hfdib_model.
+ *   Re       : Reynolds number; nu = bc->u_ref * bc->l_ref / Re.
+ *   bc       : boundary description (not NULL).
+ *   opt      : options (NULL -> defaults).
+ *   stream   : cudaStream_t used for every call on the handle (NULL = default).
+ *   out      : receives the handle.
+ * At create the library classifies cells into ic/bc/fc (Sec. 2.3), builds
+ * the boundary-cell geometry -- normal, in-solid neighbour, y_perp, y_eff,
+ * interpolation stencils (Sec. 2.4-2.5) -- and sets the initial state: u_in
+ * outside the solid and u_s in it, p = 0, k and eps/omega at their inlet
+ * values (k = 0 in the solid).  Errors: INVALID_ARG for bad sizes / enums or
+ * lambda outside [0, 1] or NaN; OOM; CUDA. */
+int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywall,
+                 int model, double Re, const hfdib_bc* bc, const hfdib_options* opt,
+                 void* stream, hfdib_handle* out);
+
+/* hfdib_simple_sweep -- run n_sweeps iterations of the extended SIMPLE loop
+ * (Fig. simplehfdibrans, Sec. 2.5.1): set alpha_u and compute u_ib, momentum
+ * predictor, correction u += alpha_u (u_ib - u) (Eq. corru), pressure
+ * corrector with the lambda-masked continuity, velocity/flux update, omega_ib
+ * (eps_ib) and P_ib, the eps/omega equation with its imposed rows, k_ib, the
+ * k equation and the k correction.
+ *   residuals : host pointer to HFDIB_NRES doubles receiving the residuals of
+ *               the last sweep (nullable: then nothing is copied back and the
+ *               call returns without waiting for the GPU). */
+int hfdib_simple_sweep(hfdib_handle h, int n_sweeps, double* residuals);
+
+/* hfdib_solve_steady -- sweep until the largest scaled residual (momentum,
+ * pressure, turbulence) is <= tol, or max_iter sweeps.  Residuals are read
+ * back every check_every sweeps (<= 0 -> 10).  Returns HFDIB_OK,
+ * HFDIB_ERR_NOT_CONVERGED or HFDIB_ERR_DIVERGED.  iters_out and final_res
+ * (HFDIB_NRES doubles) are host pointers and nullable. */
+int hfdib_solve_steady(hfdib_handle h, double tol, int max_iter, int check_every,
+                       int* iters_out, double* final_res);
+
+/* Copy a field (HFDIB_FIELD_*) device-to-device into dst (caller-owned, sized
+ * like the field: cells, or faces (nx+1)*ny*nz / nx*(ny+1)*nz / nx*ny*(nz+1)). */
+int hfdib_get_field(hfdib_handle h, int field, double* dst);
+/* Overwrite a field from a caller device buffer (used to restart or to set a
+ * test state).  nu_t is recomputed by the next sweep. */
+int hfdib_set_field(hfdib_handle h, int field, const double* src);
+
+/* Cell groups and boundary-cell list (Sec. 2.3-2.4).
+ *   tags     : device, N bytes: 0 fc, 1 bc, 2 ic (nullable)
+ *   n_bc     : host, receives the number of bc cells (nullable)
+ * hfdib_get_bc_list copies, for the n_bc boundary cells in increasing cell
+ * order, device arrays (each nullable):
+ *   ints     : int64 [n_bc][8] = cell, in-solid neighbour (-1 none), y_perp
+ *              case (0,1,2), clamped flag, X1 base cell (i,j,k) -- then X2 base
+ *              (i,j,k) follows in ints2 ;
+ *   ints2    : int64 [n_bc][3] = X2 base (i,j,k)
+ *   reals    : double [n_bc][14] = n (3), y_perp, y_eff, wS, w1, w2,
+ *              t1 (3), t2 (3). */
+int hfdib_get_tags(hfdib_handle h, uint8_t* tags, int64_t* n_bc);
+int hfdib_get_bc_list(hfdib_handle h, int64_t* ints, int64_t* ints2, double* reals);
+
+/* Residual history: copies the residual vectors of the last `count` sweeps
+ * (at most 1024 are kept) into host memory, oldest first; *n_out = rows. */
+int hfdib_get_history(hfdib_handle h, int count, double* host, int* n_out);
+
+/* Checkpoint: the complete FP64 state (u, p, phi, k, eps, omega, nu_t and the
+ * sweep counter).  hfdib_get_state with buf == NULL returns the size in
+ * *bytes.  Buffers are host memory.  Resuming from a saved state reproduces
+ * the uninterrupted run bit for bit. */
+int hfdib_get_state(hfdib_handle h, void* buf, size_t* bytes);
+int hfdib_set_state(hfdib_handle h, const void* buf, size_t bytes);
+
+/* Number of sweeps run so far and of kernel launches issued by the last
+ * hfdib_simple_sweep / hfdib_solve_steady call. */
+int hfdib_get_counters(hfdib_handle h, int64_t* sweeps, int64_t* launches);
+
+const char* hfdib_error_string(int code);
+void hfdib_destroy(hfdib_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HFDIB_H */

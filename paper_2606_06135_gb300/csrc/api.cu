@@ -1,0 +1,613 @@
+// api.cu -- C ABI of the HFDIB SIMPLE solver: handle set-up, the sweep
+// schedule (Fig. simplehfdibrans), steady solve, field access, checkpoints.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+using namespace hf;
+
+namespace {
+
+constexpr int HIST = 1024;
+constexpr uint64_t STATE_MAGIC = 0x48464449425354ull;  // "HFDIBST"
+
+struct Ctx {
+    Grid g;
+    Params P;
+    hfdib_options opt;
+    hfdib_bc bc;
+    int model = 0;
+    cudaStream_t stream = nullptr;
+    Fields F;
+    BcList bl;
+    MgLevels mg;
+    int tail_from = 1;
+    double* lam = nullptr;
+    double* hist = nullptr;      // device [HIST][HFDIB_NRES]
+    double* res_dev = nullptr;   // device [HFDIB_NRES]
+    int* cnt_scratch = nullptr;  // compaction scratch
+    std::vector<void*> allocs;
+    long long sweeps = 0;
+    long long launches = 0;
+    int last_piters = 0;
+    double* pinned = nullptr;    // host pinned scratch (64 doubles)
+};
+
+#define CK(x)                                         \
+    do {                                              \
+        cudaError_t e_ = (x);                         \
+        if (e_ != cudaSuccess) return HFDIB_ERR_CUDA; \
+    } while (0)
+
+int dalloc(Ctx* h, void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? HFDIB_ERR_OOM : HFDIB_ERR_CUDA;
+    }
+    h->allocs.push_back(*p);
+    if (cudaMemsetAsync(*p, 0, bytes, h->stream) != cudaSuccess) return HFDIB_ERR_CUDA;
+    return HFDIB_OK;
+}
+
+template <typename T>
+int dalloc_n(Ctx* h, T** p, long long n) {
+    return dalloc(h, (void**)p, (size_t)n * sizeof(T));
+}
+
+void free_all(Ctx* h) {
+    for (void* p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+    if (h->pinned) cudaFreeHost(h->pinned);
+    h->pinned = nullptr;
+}
+
+__global__ void k_check_lambda(long long N, const double* lam, double* partials, unsigned int* counter,
+                               double* out) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double v[1] = {0.0};
+    if (c < N) {
+        double l = lam[c];
+        if (!(l >= 0.0 && l <= 1.0)) v[0] = 1.0;
+    }
+    grid_reduce<1, false>(v, partials, counter, out);
+}
+
+__global__ void k_init_state(Grid g, Params P, Fields F, int model) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    bool ic = tag_of(F.flags[c]) == TAG_IC;
+    for (int q = 0; q < 3; ++q) F.u[q][c] = ic ? g.u_s[q] : g.u_in[q];
+    F.p[c] = 0.0;
+    if (model != HFDIB_LAMINAR) {
+        double k = ic ? 0.0 : P.k_in;
+        F.k[c] = k;
+        F.w[c] = P.w_in;
+        // nu_t = C_mu k^2/eps = k/omega for the inlet pair
+        double eps = model == HFDIB_KEPSILON ? P.w_in : C_MU * P.k_in * P.w_in;
+        F.nut[c] = ic ? 0.0 : C_MU * k * k / eps;
+        F.w2[c] = model == HFDIB_KEPSILON ? P.w_in / (C_MU * fmax(k, K_MIN)) : C_MU * k * P.w_in;
+    }
+}
+
+__global__ void k_write_hist(const double* res, double* hist, int slot) {
+    int t = threadIdx.x;
+    if (t < HFDIB_NRES) hist[slot * HFDIB_NRES + t] = res[t];
+}
+
+int sync_read(Ctx* h, const double* dev, double* host, int n) {
+    CK(cudaMemcpyAsync(h->pinned, dev, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    memcpy(host, h->pinned, n * sizeof(double));
+    return HFDIB_OK;
+}
+
+// pressure equation: coefficients, PCG initialisation, iterations
+int pressure_solve(Ctx* h, long long* L) {
+    const Grid& g = h->g;
+    Fields& F = h->F;
+    cudaStream_t s = h->stream;
+    const MgLevels& M = h->mg;
+    int jac = h->opt.precond == 0;
+    int cs = h->opt.mg_coarse_sweeps > 0 ? h->opt.mg_coarse_sweeps : 20;
+    launch_p_coef(g, M, F.rAU, h->tail_from, s);
+    *L += 1 + (h->tail_from - 1) + (h->tail_from < M.nl ? 1 : 0);
+    launch_pcg_init(g, F, M, jac, s);
+    *L += 1;
+    if (!jac) {
+        launch_vcycle(g, M, h->tail_from, F, F.scal + SC_PCG_INIT, cs, s);
+        *L += 6 * h->tail_from + 1;
+    }
+    int check = h->opt.p_check;
+    double rr0 = 1.0, tol2 = 0.0;
+    if (check > 0) {
+        double tmp[2];
+        int rc = sync_read(h, F.scal + SC_PCG_INIT, tmp, 2);
+        if (rc) return rc;
+        rr0 = tmp[1];
+        tol2 = h->opt.p_reltol * h->opt.p_reltol * rr0;
+    }
+    int it = 0;
+    if (rr0 > 0.0 && isfinite(rr0)) {
+        while (it < h->opt.p_maxiter) {
+            launch_pcg_A(g, F, M, it, s);
+            launch_pcg_update(g, F, M, it, jac, s);
+            *L += 2;
+            int slot = SC_PCG_RZRR + 2 * ((it + 1) & 1);
+            if (!jac) {
+                launch_vcycle(g, M, h->tail_from, F, F.scal + slot, cs, s);
+                *L += 6 * h->tail_from + 1;
+            }
+            ++it;
+            if (check > 0 && it % check == 0) {
+                double rr;
+                int rc = sync_read(h, F.scal + slot + 1, &rr, 1);
+                if (rc) return rc;
+                if (!(rr > tol2)) break;
+            }
+        }
+    }
+    h->last_piters = it;
+    return HFDIB_OK;
+}
+
+// one iteration of the extended SIMPLE loop
+int run_sweep(Ctx* h) {
+    const Grid& g = h->g;
+    const Params& P = h->P;
+    Fields& F = h->F;
+    cudaStream_t s = h->stream;
+    bool turb = h->model != HFDIB_LAMINAR;
+    long long L = 0;
+    // a1: omega_ib (eps_ib) of ic cells = max over bc u fc of the old field
+    if (turb) { launch_max_not_ic(g, F.flags, F.w, F.partials, F.counters + 0, F.scal + SC_WMAX, s); L++; }
+    // a2: set alpha_u, compute u_ib, k_ib, omega_ib
+    launch_imposed(g, h->model, h->bl, F.flags, F.u[0], F.u[1], F.u[2], F.k, F.uib[0], F.uib[1], F.uib[2],
+                   F.kib, F.wib, s);
+    L++;
+    launch_means(g, P, F, s); L++;
+    // a3: momentum assembly; a4: predictor; a5: correction (imposed rows)
+    launch_grad_u(g, F, s); L++;
+    launch_mom_asm(g, P, F, s); L++;
+    for (int n = 0; n < h->opt.n_u; ++n) {
+        launch_mom_smooth(g, P, F, 0, s);
+        launch_mom_smooth(g, P, F, 1, s);
+        L += 2;
+    }
+    // a6: rAU, HbyA, phiHbyA
+    launch_hbya(g, P, F, s); L++;
+    launch_phiH(g, F, s); L++;
+    // a7: pressure equation, PCG with a Jacobi or multigrid preconditioner
+    int rc = pressure_solve(h, &L);
+    if (rc) return rc;
+    int it = h->last_piters;
+    // a8: flux, pressure relaxation, velocity update
+    launch_update(g, P, F, h->mg.lv[0], s); L++;
+    std::swap(F.p, F.pr);
+    if (turb) {
+        // a9: production with the updated velocity, P_ib
+        launch_grad_u(g, F, s); L++;
+        launch_turb_prep(g, P, F, s); L++;
+        launch_bc_prod(g, h->bl, F, s); L++;
+        // a10: eps / omega with imposed rows
+        launch_scal_asm(g, P, F, 0, s); L++;
+        for (int n = 0; n < h->opt.n_turb; ++n) {
+            launch_scal_smooth(g, P, F, 0, 0, s);
+            launch_scal_smooth(g, P, F, 0, 1, s);
+            L += 2;
+        }
+        // a11: k with imposed rows, then the correction; a12 nu_t
+        launch_k_prep(g, P, F, s); L++;
+        launch_scal_asm(g, P, F, 1, s); L++;
+        for (int n = 0; n < h->opt.n_turb; ++n) {
+            launch_scal_smooth(g, P, F, 1, 0, s);
+            launch_scal_smooth(g, P, F, 1, 1, s);
+            L += 2;
+        }
+        launch_turb_final(g, P, F, s); L++;
+    }
+    launch_sweep_end(P, F, g.dims, (double)it, h->res_dev, s); L++;
+    k_write_hist<<<1, 32, 0, s>>>(h->res_dev, h->hist, (int)(h->sweeps % HIST)); L++;
+    CK(cudaGetLastError());
+    h->sweeps++;
+    h->launches += L;
+    return HFDIB_OK;
+}
+
+double* field_ptr(Ctx* h, int field, long long* n) {
+    *n = h->g.N;
+    switch (field) {
+        case HFDIB_FIELD_UX: return h->F.u[0];
+        case HFDIB_FIELD_UY: return h->F.u[1];
+        case HFDIB_FIELD_UZ: return h->g.dims == 3 ? h->F.u[2] : nullptr;
+        case HFDIB_FIELD_P: return h->F.p;
+        case HFDIB_FIELD_K: return h->model ? h->F.k : nullptr;
+        case HFDIB_FIELD_EPS: return h->model == HFDIB_KEPSILON ? h->F.w : (h->model ? h->F.w2 : nullptr);
+        case HFDIB_FIELD_OMEGA: return h->model == HFDIB_KOMEGA_SST ? h->F.w : (h->model ? h->F.w2 : nullptr);
+        case HFDIB_FIELD_NUT: return h->F.nut;
+        case HFDIB_FIELD_PHIX: *n = h->g.nface[0]; return h->F.phi[0];
+        case HFDIB_FIELD_PHIY: *n = h->g.nface[1]; return h->F.phi[1];
+        case HFDIB_FIELD_PHIZ: *n = h->g.nface[2]; return h->g.dims == 3 ? h->F.phi[2] : nullptr;
+        default: return nullptr;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+void hfdib_default_options(hfdib_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->urf_u = 0.7;
+    o->urf_p = 0.3;
+    o->urf_turb = 0.85;
+    o->n_u = 2;
+    o->n_turb = 2;
+    o->p_reltol = 0.01;
+    o->p_maxiter = 200;
+    o->precision = 0;
+    o->precond = 1;
+    o->p_check = 1;
+    o->mg_coarse_sweeps = 20;
+}
+
+const char* hfdib_error_string(int code) {
+    switch (code) {
+        case HFDIB_OK: return "ok";
+        case HFDIB_ERR_INVALID_ARG: return "invalid argument";
+        case HFDIB_ERR_CUDA: return "CUDA runtime error";
+        case HFDIB_ERR_OOM: return "device out of memory";
+        case HFDIB_ERR_NOT_CONVERGED: return "not converged";
+        case HFDIB_ERR_DIVERGED: return "diverged (non-finite residual)";
+        case HFDIB_ERR_STATE_MISMATCH: return "checkpoint does not match the handle";
+        default: return "unknown error";
+    }
+}
+
+int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywall, int model, double Re,
+                 const hfdib_bc* bc, const hfdib_options* opt, void* stream, hfdib_handle* out) {
+    if (!out) return HFDIB_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!grid || !lambda || !bc) return HFDIB_ERR_INVALID_ARG;
+    if (grid->nx < 2 || grid->ny < 2 || grid->nz < 1) return HFDIB_ERR_INVALID_ARG;
+    if (!(grid->dx > 0 && grid->dy > 0 && grid->dz > 0)) return HFDIB_ERR_INVALID_ARG;
+    if (model < HFDIB_LAMINAR || model > HFDIB_KOMEGA_SST) return HFDIB_ERR_INVALID_ARG;
+    if (model == HFDIB_KOMEGA_SST && !ywall) return HFDIB_ERR_INVALID_ARG;
+    if (!(Re > 0) || !(bc->u_ref > 0) || !(bc->l_ref > 0)) return HFDIB_ERR_INVALID_ARG;
+    long long N = (long long)grid->nx * grid->ny * grid->nz;
+    if (N > (1ll << 31) - 1) return HFDIB_ERR_INVALID_ARG;
+    for (int s = 0; s < 6; ++s)
+        if (bc->face[s] < HFDIB_BC_INLET || bc->face[s] > HFDIB_BC_EMPTY) return HFDIB_ERR_INVALID_ARG;
+    if (grid->nz == 1) {
+        if (bc->face[4] != HFDIB_BC_EMPTY || bc->face[5] != HFDIB_BC_EMPTY) return HFDIB_ERR_INVALID_ARG;
+    }
+    hfdib_options o;
+    if (opt) o = *opt; else hfdib_default_options(&o);
+    if (!(o.urf_u > 0 && o.urf_u <= 1) || !(o.urf_p > 0 && o.urf_p <= 1) || !(o.urf_turb > 0 && o.urf_turb <= 1))
+        return HFDIB_ERR_INVALID_ARG;
+    if (o.n_u < 1 || o.n_turb < 1 || o.p_maxiter < 0 || !(o.p_reltol >= 0)) return HFDIB_ERR_INVALID_ARG;
+    if (o.precond < 0 || o.precond > 1 || o.p_check < 0 || o.mg_coarse_sweeps < 0) return HFDIB_ERR_INVALID_ARG;
+
+    Ctx* h = new (std::nothrow) Ctx();
+    if (!h) return HFDIB_ERR_OOM;
+    h->stream = (cudaStream_t)stream;
+    h->opt = o;
+    h->bc = *bc;
+    h->model = model;
+    Grid& g = h->g;
+    g.nx = grid->nx; g.ny = grid->ny; g.nz = grid->nz;
+    g.dims = grid->nz == 1 ? 2 : 3;
+    g.N = N;
+    g.n[0] = g.nx; g.n[1] = g.ny; g.n[2] = g.nz;
+    g.D[0] = grid->dx; g.D[1] = grid->dy; g.D[2] = grid->dz;
+    g.o[0] = grid->x0; g.o[1] = grid->y0; g.o[2] = grid->z0;
+    g.S[0] = g.D[1] * g.D[2]; g.S[1] = g.D[0] * g.D[2]; g.S[2] = g.D[0] * g.D[1];
+    g.V = g.D[0] * g.D[1] * g.D[2];
+    // V^(1/3): sqrt(dx*dy) on one-cell-thick 2D grids
+    g.h = g.dims == 2 ? sqrt(g.D[0] * g.D[1]) : pow(g.D[0] * g.D[1] * g.D[2], 1.0 / 3.0);
+    for (int s = 0; s < 6; ++s) g.kind[s] = bc->face[s];
+    for (int q = 0; q < 3; ++q) { g.u_in[q] = bc->u_in[q]; g.u_s[q] = bc->u_s[q]; }
+    g.p_out = bc->p_out;
+    g.nu = bc->u_ref * bc->l_ref / Re;
+    g.stride[0] = 1; g.stride[1] = g.nx; g.stride[2] = (long long)g.nx * g.ny;
+    g.nface[0] = (long long)(g.nx + 1) * g.ny * g.nz;
+    g.nface[1] = (long long)g.nx * (g.ny + 1) * g.nz;
+    g.nface[2] = (long long)g.nx * g.ny * (g.nz + 1);
+    Params& P = h->P;
+    P.model = model;
+    P.urf_u = o.urf_u; P.urf_p = o.urf_p; P.urf_turb = o.urf_turb;
+    // inlet turbulence, Eq. (bcspkoein): k = 1.5 (U I)^2, eps = C_nu k^1.5 / l_t, omega = eps/(C_nu k)
+    double U = sqrt(bc->u_in[0] * bc->u_in[0] + bc->u_in[1] * bc->u_in[1] + bc->u_in[2] * bc->u_in[2]);
+    double kin = 1.5 * (U * bc->I_in) * (U * bc->I_in);
+    double ein = C_MU * pow(kin, 1.5) / bc->lt_in;
+    double win = ein / (C_MU * kin);
+    P.k_in = kin;
+    P.w_in = model == HFDIB_KOMEGA_SST ? win : ein;
+    if (model != HFDIB_LAMINAR && !(kin > 0 && bc->lt_in > 0)) { delete h; return HFDIB_ERR_INVALID_ARG; }
+
+    int rc = HFDIB_OK;
+    Fields& F = h->F;
+    memset(&F, 0, sizeof(F));
+    unsigned int nb = nblocks(N);
+    long long maxf = g.nface[0] > g.nface[1] ? g.nface[0] : g.nface[1];
+    if (g.nface[2] > maxf) maxf = g.nface[2];
+#define A(ptr, n) if (!rc) rc = dalloc_n(h, &(ptr), (n))
+    A(h->lam, N);
+    for (int q = 0; q < 3; ++q) {
+        A(F.u[q], N); A(F.us[q], N); A(F.HbyA[q], N); A(F.bm[q], N); A(F.uib[q], N);
+        A(F.phi[q], g.nface[q]); A(F.phiH[q], g.nface[q]);
+    }
+    A(F.p, N); A(F.pn, N); A(F.pr, N); A(F.rAU, N);
+    A(F.k, N); A(F.w, N); A(F.w2, N); A(F.nut, N); A(F.kib, N); A(F.wib, N);
+    A(F.G, 9 * N); A(F.Pk, N); A(F.S2, N); A(F.gam, N); A(F.gamk, N); A(F.sp, N); A(F.src, N);
+    A(F.bt, N); A(F.diag, N); A(F.ywall, N); A(F.flags, N);
+    A(F.prhs, N); A(F.pdiag, N); A(F.r, N); A(F.z, N); A(F.d[0], N); A(F.d[1], N); A(F.q, N);
+    A(F.scal, SC_NSCAL); A(F.partials, 16 * (long long)nb + 64); A(F.counters, 64);
+    A(h->hist, HIST * HFDIB_NRES); A(h->res_dev, HFDIB_NRES);
+    A(h->cnt_scratch, (long long)nb + 2);
+    // multigrid hierarchy of the pressure operator: level 0 is the grid
+    // itself (x = z, b = r); coarsen by 2 while every dimension is >= 4
+    if (!rc) {
+        MgLevels& M = h->mg;
+        memset(&M, 0, sizeof(M));
+        Level& l0 = M.lv[0];
+        l0.nx = g.nx; l0.ny = g.ny; l0.nz = g.nz; l0.N = N;
+        for (int d = 0; d < 3; ++d) A(l0.cf[d], g.nface[d]);
+        A(l0.diag, N);
+        l0.x = F.z;
+        l0.b = F.r;
+        M.nl = 1;
+        while (!rc && M.nl < MAX_LEVELS) {
+            const Level& f = M.lv[M.nl - 1];
+            int mn = f.nx < f.ny ? f.nx : f.ny;
+            if (g.dims == 3 && f.nz < mn) mn = f.nz;
+            if (mn < 4) break;
+            Level c;
+            c.nx = (f.nx + 1) / 2; c.ny = (f.ny + 1) / 2; c.nz = g.dims == 3 ? (f.nz + 1) / 2 : 1;
+            c.N = (long long)c.nx * c.ny * c.nz;
+            A(c.cf[0], (long long)(c.nx + 1) * c.ny * c.nz);
+            A(c.cf[1], (long long)c.nx * (c.ny + 1) * c.nz);
+            A(c.cf[2], (long long)c.nx * c.ny * (c.nz + 1));
+            A(c.diag, c.N); A(c.x, c.N); A(c.b, c.N);
+            M.lv[M.nl++] = c;
+        }
+        h->tail_from = M.nl;
+        for (int l = 1; l < M.nl; ++l)
+            if (M.lv[l].N <= TAIL_CELLS) { h->tail_from = l; break; }
+    }
+#undef A
+    if (!rc && cudaMallocHost((void**)&h->pinned, 64 * sizeof(double)) != cudaSuccess) rc = HFDIB_ERR_OOM;
+    if (rc) { free_all(h); delete h; return rc; }
+    cudaStream_t s = h->stream;
+    if (cudaMemcpyAsync(h->lam, lambda, N * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        (ywall && cudaMemcpyAsync(F.ywall, ywall, N * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)) {
+        free_all(h); delete h; return HFDIB_ERR_CUDA;
+    }
+    // lambda must be finite and in [0, 1]
+    k_check_lambda<<<nb, BLOCK, 0, s>>>(N, h->lam, F.partials, F.counters + 8, F.scal + 63);
+    double bad = 0.0;
+    if (sync_read(h, F.scal + 63, &bad, 1) != HFDIB_OK) { free_all(h); delete h; return HFDIB_ERR_CUDA; }
+    if (bad != 0.0) { free_all(h); delete h; return HFDIB_ERR_INVALID_ARG; }
+
+    // a0: groups, boundary-cell list and geometry
+    launch_classify(g, h->lam, F.flags, s);
+    launch_compact_bc(g, F.flags, h->cnt_scratch, h->cnt_scratch + nb, (int*)F.bt, s);
+    int nbc = 0;
+    if (cudaMemcpyAsync(&nbc, h->cnt_scratch + nb, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        free_all(h); delete h; return HFDIB_ERR_CUDA;
+    }
+    BcList& bl = h->bl;
+    bl.nbc = nbc;
+#define A(ptr, n) if (!rc) rc = dalloc_n(h, &(ptr), (n))
+    A(bl.cell, nbc); A(bl.nbr, nbc); A(bl.cas, nbc); A(bl.clamped, nbc); A(bl.b1, 3 * (long long)nbc);
+    A(bl.b2, 3 * (long long)nbc); A(bl.lamb, nbc); A(bl.n, 3 * (long long)nbc); A(bl.yp, nbc);
+    A(bl.ye, nbc); A(bl.wS, nbc); A(bl.w1, nbc); A(bl.w2, nbc); A(bl.t1, 3 * (long long)nbc);
+    A(bl.t2, 3 * (long long)nbc); A(bl.yplus, nbc);
+#undef A
+    if (rc) { free_all(h); delete h; return rc; }
+    if (nbc > 0 && cudaMemcpyAsync(bl.cell, F.bt, nbc * sizeof(int), cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+        free_all(h); delete h; return HFDIB_ERR_CUDA;
+    }
+    launch_bc_geometry(g, h->lam, F.flags, bl, s);
+    // initial state and face fluxes
+    k_init_state<<<nb, BLOCK, 0, s>>>(g, P, F, model);
+    launch_init_flux(g, F, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        free_all(h); delete h; return HFDIB_ERR_CUDA;
+    }
+    *out = (hfdib_handle)h;
+    return HFDIB_OK;
+}
+
+int hfdib_simple_sweep(hfdib_handle hh, int n_sweeps, double* residuals) {
+    Ctx* h = (Ctx*)hh;
+    if (!h || n_sweeps < 0) return HFDIB_ERR_INVALID_ARG;
+    h->launches = 0;
+    for (int n = 0; n < n_sweeps; ++n) {
+        int rc = run_sweep(h);
+        if (rc) return rc;
+    }
+    if (residuals) {
+        int rc = sync_read(h, h->res_dev, residuals, HFDIB_NRES);
+        if (rc) return rc;
+        for (int q = 0; q < HFDIB_NRES; ++q)
+            if (!isfinite(residuals[q])) return HFDIB_ERR_DIVERGED;
+    }
+    return HFDIB_OK;
+}
+
+int hfdib_solve_steady(hfdib_handle hh, double tol, int max_iter, int check_every, int* iters_out,
+                       double* final_res) {
+    Ctx* h = (Ctx*)hh;
+    if (!h || max_iter < 0 || !(tol >= 0)) return HFDIB_ERR_INVALID_ARG;
+    if (check_every <= 0) check_every = 10;
+    h->launches = 0;
+    double res[HFDIB_NRES] = {0};
+    int it = 0;
+    int status = HFDIB_ERR_NOT_CONVERGED;
+    while (it < max_iter) {
+        int rc = run_sweep(h);
+        if (rc) return rc;
+        ++it;
+        if (it % check_every == 0 || it == max_iter) {
+            rc = sync_read(h, h->res_dev, res, HFDIB_NRES);
+            if (rc) return rc;
+            double mx = 0.0;
+            bool bad = false;
+            for (int q = 0; q <= HFDIB_RES_K; ++q) {
+                if (!isfinite(res[q])) bad = true;
+                mx = fmax(mx, res[q]);
+            }
+            if (bad) { status = HFDIB_ERR_DIVERGED; break; }
+            if (mx <= tol) { status = HFDIB_OK; break; }
+        }
+    }
+    if (iters_out) *iters_out = it;
+    if (final_res) memcpy(final_res, res, sizeof(res));
+    return status;
+}
+
+int hfdib_get_field(hfdib_handle hh, int field, double* dst) {
+    Ctx* h = (Ctx*)hh;
+    if (!h || !dst) return HFDIB_ERR_INVALID_ARG;
+    long long n;
+    double* src = field_ptr(h, field, &n);
+    if (!src) return HFDIB_ERR_INVALID_ARG;
+    CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    return HFDIB_OK;
+}
+
+int hfdib_set_field(hfdib_handle hh, int field, const double* srcp) {
+    Ctx* h = (Ctx*)hh;
+    if (!h || !srcp) return HFDIB_ERR_INVALID_ARG;
+    long long n;
+    double* dst = field_ptr(h, field, &n);
+    if (!dst) return HFDIB_ERR_INVALID_ARG;
+    CK(cudaMemcpyAsync(dst, srcp, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    return HFDIB_OK;
+}
+
+int hfdib_get_tags(hfdib_handle hh, uint8_t* tags, int64_t* n_bc) {
+    Ctx* h = (Ctx*)hh;
+    if (!h) return HFDIB_ERR_INVALID_ARG;
+    if (n_bc) *n_bc = h->bl.nbc;
+    if (tags) {
+        // low byte of the flags holds the group in bits 0-1
+        std::vector<uint16_t> f(h->g.N);
+        CK(cudaMemcpyAsync(f.data(), h->F.flags, h->g.N * sizeof(uint16_t), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        std::vector<uint8_t> t(h->g.N);
+        for (long long c = 0; c < h->g.N; ++c) t[c] = (uint8_t)(f[c] & F_TAG);
+        CK(cudaMemcpyAsync(tags, t.data(), h->g.N, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    return HFDIB_OK;
+}
+
+int hfdib_get_bc_list(hfdib_handle hh, int64_t* ints, int64_t* ints2, double* reals) {
+    Ctx* h = (Ctx*)hh;
+    if (!h) return HFDIB_ERR_INVALID_ARG;
+    launch_export_bc(h->bl, (long long*)ints, (long long*)ints2, reals, h->stream);
+    CK(cudaGetLastError());
+    return HFDIB_OK;
+}
+
+int hfdib_get_history(hfdib_handle hh, int count, double* host, int* n_out) {
+    Ctx* h = (Ctx*)hh;
+    if (!h || !host || count < 0) return HFDIB_ERR_INVALID_ARG;
+    long long avail = h->sweeps < HIST ? h->sweeps : HIST;
+    int n = (int)(count < avail ? count : avail);
+    std::vector<double> all(HIST * HFDIB_NRES);
+    CK(cudaMemcpyAsync(all.data(), h->hist, all.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int r = 0; r < n; ++r) {
+        long long sw = h->sweeps - n + r;
+        memcpy(host + (size_t)r * HFDIB_NRES, all.data() + (sw % HIST) * HFDIB_NRES, HFDIB_NRES * sizeof(double));
+    }
+    if (n_out) *n_out = n;
+    return HFDIB_OK;
+}
+
+// checkpoint layout: header (8 x int64) then the FP64 arrays in a fixed order
+static void state_arrays(Ctx* h, std::vector<std::pair<double*, long long>>& v) {
+    const Grid& g = h->g;
+    for (int q = 0; q < g.dims; ++q) v.push_back({h->F.u[q], g.N});
+    v.push_back({h->F.p, g.N});
+    for (int q = 0; q < g.dims; ++q) v.push_back({h->F.phi[q], g.nface[q]});
+    v.push_back({h->F.k, g.N});
+    v.push_back({h->F.w, g.N});
+    v.push_back({h->F.w2, g.N});
+    v.push_back({h->F.nut, g.N});
+}
+
+int hfdib_get_state(hfdib_handle hh, void* buf, size_t* bytes) {
+    Ctx* h = (Ctx*)hh;
+    if (!h || !bytes) return HFDIB_ERR_INVALID_ARG;
+    std::vector<std::pair<double*, long long>> v;
+    state_arrays(h, v);
+    size_t total = 8 * sizeof(int64_t);
+    for (auto& a : v) total += a.second * sizeof(double);
+    if (!buf) { *bytes = total; return HFDIB_OK; }
+    if (*bytes < total) return HFDIB_ERR_INVALID_ARG;
+    int64_t* hd = (int64_t*)buf;
+    hd[0] = (int64_t)STATE_MAGIC; hd[1] = h->g.nx; hd[2] = h->g.ny; hd[3] = h->g.nz; hd[4] = h->model;
+    hd[5] = h->sweeps; hd[6] = (int64_t)total; hd[7] = 0;
+    char* p = (char*)buf + 8 * sizeof(int64_t);
+    for (auto& a : v) {
+        CK(cudaMemcpyAsync(p, a.first, a.second * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        p += a.second * sizeof(double);
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    *bytes = total;
+    return HFDIB_OK;
+}
+
+int hfdib_set_state(hfdib_handle hh, const void* buf, size_t bytes) {
+    Ctx* h = (Ctx*)hh;
+    if (!h || !buf) return HFDIB_ERR_INVALID_ARG;
+    std::vector<std::pair<double*, long long>> v;
+    state_arrays(h, v);
+    size_t total = 8 * sizeof(int64_t);
+    for (auto& a : v) total += a.second * sizeof(double);
+    if (bytes != total) return HFDIB_ERR_STATE_MISMATCH;
+    const int64_t* hd = (const int64_t*)buf;
+    if (hd[0] != (int64_t)STATE_MAGIC || hd[1] != h->g.nx || hd[2] != h->g.ny || hd[3] != h->g.nz ||
+        hd[4] != h->model || hd[6] != (int64_t)total)
+        return HFDIB_ERR_STATE_MISMATCH;
+    const char* p = (const char*)buf + 8 * sizeof(int64_t);
+    for (auto& a : v) {
+        CK(cudaMemcpyAsync(a.first, p, a.second * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        p += a.second * sizeof(double);
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    h->sweeps = hd[5];
+    return HFDIB_OK;
+}
+
+int hfdib_get_counters(hfdib_handle hh, int64_t* sweeps, int64_t* launches) {
+    Ctx* h = (Ctx*)hh;
+    if (!h) return HFDIB_ERR_INVALID_ARG;
+    if (sweeps) *sweeps = h->sweeps;
+    if (launches) *launches = h->launches;
+    return HFDIB_OK;
+}
+
+void hfdib_destroy(hfdib_handle hh) {
+    Ctx* h = (Ctx*)hh;
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,154 @@
+// common.cuh -- shared device definitions of the HFDIB SIMPLE kernels.
+//
+// Layout: cell arrays [nz][ny][nx], x fastest, cell index c = (k*ny + j)*nx + i.
+// Face arrays (volumetric flux in the +d direction):
+//   x faces [(nx+1) per row]: (k*ny + j)*(nx+1) + i is the face on the low-x side of cell i
+//   y faces: (k*(ny+1) + j)*nx + i is the face on the low-y side of cell j
+//   z faces: (k*ny + j)*nx + i     is the face on the low-z side of cell k
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hfdib.h"
+
+namespace hf {
+
+// wall-function constants (Sec. 2.5; standard published values)
+constexpr double C_MU = 0.09;       // C_nu of Eq. (frictionvel)
+constexpr double KAPPA = 0.41;
+constexpr double E_WF = 9.8;
+constexpr double BETA1_WF = 0.075;  // beta_1 of Eq. (omegaws)
+constexpr double C_WF = 11.0;       // C of Eq. (kws)
+constexpr double C_EPS2 = 1.9;      // C_eps2 of Eq. (kws)
+constexpr double YPLUS_LAM = 11.0;  // Sec. 2.3
+
+// standard k-epsilon
+constexpr double KE_C1 = 1.44, KE_C2 = 1.92, KE_SIGK = 1.0, KE_SIGE = 1.3;
+// k-omega SST (Menter) coefficients
+constexpr double SST_AK1 = 0.85, SST_AK2 = 1.0, SST_AW1 = 0.5, SST_AW2 = 0.856;
+constexpr double SST_G1 = 5.0 / 9.0, SST_G2 = 0.44, SST_B1 = 0.075, SST_B2 = 0.0828;
+constexpr double SST_BSTAR = 0.09, SST_A1 = 0.31, SST_BB1 = 1.0, SST_C1 = 10.0;
+
+constexpr double K_MIN = 1e-14, EPS_MIN = 1e-14, OMEGA_MIN = 1e-14;
+
+enum { TAG_FC = 0, TAG_BC = 1, TAG_IC = 2 };
+
+// per-cell uint16 flags
+constexpr uint16_t F_TAG = 3;           // bits 0-1: cell group
+constexpr int F_CLOSED_SHIFT = 2;       // bits 2-7: closed boundary face on side s
+constexpr uint16_t F_M = 1u << 8;       // lambda < 1: continuity enforced
+constexpr uint16_t F_AU = 1u << 9;      // alpha_u = alpha_k = 1 (dynamic)
+
+constexpr int BLOCK = 256;
+
+struct Grid {
+    int nx, ny, nz, dims;
+    long long N;
+    int n[3];
+    double D[3];     // spacings
+    double o[3];     // origin
+    double S[3];     // face areas
+    double V, h;     // cell volume, V^(1/3)
+    int kind[6];     // hfdib_bc_kind per side
+    double u_in[3], u_s[3], p_out;
+    double nu;
+    long long stride[3];
+    long long nface[3];
+};
+
+__host__ __device__ inline int tag_of(uint16_t f) { return f & F_TAG; }
+__host__ __device__ inline bool closed_side(uint16_t f, int s) { return (f >> (F_CLOSED_SHIFT + s)) & 1u; }
+
+__device__ inline void cell_ijk(const Grid& g, long long c, int& i, int& j, int& k) {
+    i = (int)(c % g.nx);
+    long long r = c / g.nx;
+    j = (int)(r % g.ny);
+    k = (int)(r / g.ny);
+}
+
+// index of the low face of cell (i,j,k) in direction d; the high face is +fstride
+__device__ inline long long face_lo(const Grid& g, int d, int i, int j, int k) {
+    if (d == 0) return ((long long)k * g.ny + j) * (g.nx + 1) + i;
+    if (d == 1) return ((long long)k * (g.ny + 1) + j) * g.nx + i;
+    return ((long long)k * g.ny + j) * g.nx + i;
+}
+__device__ inline long long face_stride(const Grid& g, int d) {
+    if (d == 0) return 1;
+    if (d == 1) return g.nx;
+    return (long long)g.nx * g.ny;
+}
+
+__device__ inline int coord(int d, int i, int j, int k) { return d == 0 ? i : (d == 1 ? j : k); }
+
+// ---- boundary conditions -------------------------------------------------
+// velocity component c on side s: true + value if the face is fixed-value
+__device__ inline bool vel_fixed(const Grid& g, uint16_t f, int s, int c, double& val) {
+    if (closed_side(f, s)) return false;
+    int kind = g.kind[s];
+    if (kind == HFDIB_BC_INLET) { val = g.u_in[c]; return true; }
+    if (kind == HFDIB_BC_WALL) { val = 0.0; return true; }
+    if (kind == HFDIB_BC_SLIP) { val = 0.0; return c == (s >> 1); }
+    return false;
+}
+// scalar (k, eps, omega): fixed only on open inlet faces
+__device__ inline bool scal_fixed(const Grid& g, uint16_t f, int s) {
+    return !closed_side(f, s) && g.kind[s] == HFDIB_BC_INLET;
+}
+__device__ inline bool p_fixed(const Grid& g, int s) { return g.kind[s] == HFDIB_BC_OUTLET; }
+
+// ---- deterministic grid reduction (last block finishes) -------------------
+template <bool MAX>
+__device__ inline double rop(double a, double b) { return MAX ? fmax(a, b) : a + b; }
+
+// Reduce v[NV] over the whole grid.  Every block writes its partials; the
+// block that finishes last combines all partials in a fixed order, so the
+// result does not depend on scheduling.  blockDim.x must be BLOCK.
+template <int NV, bool MAX>
+__device__ void grid_reduce(double (&v)[NV], double* partials, unsigned int* counter, double* out) {
+    __shared__ double sm[NV][BLOCK / 32];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double x = v[q];
+        for (int o = 16; o > 0; o >>= 1) x = rop<MAX>(x, __shfl_down_sync(0xffffffffu, x, o));
+        if (lane == 0) sm[q][warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double x = sm[q][0];
+            for (int w = 1; w < BLOCK / 32; ++w) x = rop<MAX>(x, sm[q][w]);
+            partials[(long long)q * gridDim.x + blockIdx.x] = x;
+        }
+        __threadfence();
+        unsigned int t = atomicAdd(counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double x = MAX ? -1.0e308 : 0.0;
+        for (unsigned int b = threadIdx.x; b < gridDim.x; b += BLOCK)
+            x = rop<MAX>(x, __ldcg(&partials[(long long)q * gridDim.x + b]));
+        for (int o = 16; o > 0; o >>= 1) x = rop<MAX>(x, __shfl_down_sync(0xffffffffu, x, o));
+        if (lane == 0) sm[q][warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double x = sm[q][0];
+            for (int w = 1; w < BLOCK / 32; ++w) x = rop<MAX>(x, sm[q][w]);
+            out[q] = x;
+        }
+        *counter = 0u;
+    }
+}
+
+inline unsigned int nblocks(long long n) { return (unsigned int)((n + BLOCK - 1) / BLOCK); }
+
+}  // namespace hf

@@ -1,0 +1,411 @@
+// flow.cu -- momentum predictor, pressure corrector and velocity update of
+// the extended SIMPLE sweep (Sec. 2.5.1, Fig. simplehfdibrans), FP64.
+//
+// Rows are matrix-free: every kernel rebuilds the coefficients of a cell from
+// the face fluxes phi and nu_eff = nu + nu_t, so the only stored per-cell
+// operator data are right-hand sides.  Discretisation (Sec. 3.1 "Numerical
+// schemes"): upwind convection in bounded form, central diffusion with the
+// arithmetic mean of the face diffusivity, Gauss-linear gradients, explicit
+// div(nu_eff (grad u)^T), implicit under-relaxation of the momentum rows.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace hf {
+
+__device__ inline long long nbr_cell(const Grid& g, long long c, int d, int side) {
+    return side ? c + g.stride[d] : c - g.stride[d];
+}
+__device__ inline bool interior(const Grid& g, int d, int side, int i, int j, int k) {
+    int pos = coord(d, i, j, k);
+    return side ? pos < g.n[d] - 1 : pos > 0;
+}
+
+// fixed value of velocity component cpt imposed by the row of cell c (if any)
+__device__ inline bool vel_row_fixed(const Grid& g, const Fields& F, long long c, int cpt, double& v) {
+    uint16_t f = F.flags[c];
+    if (tag_of(f) == TAG_IC) { v = g.u_s[cpt]; return true; }
+    if (f & F_AU) { v = F.uib[cpt][c]; return true; }
+    return false;
+}
+
+// momentum row of cell c (unrelaxed): aP per component, neighbour
+// coefficients and the boundary right-hand side per component
+struct MomRow {
+    double aP[3];
+    double a[6];
+    long long nb[6];
+    bool has[6];
+    double bnd[3];
+};
+
+__device__ void mom_row(const Grid& g, const Fields& F, long long c, int i, int j, int k, uint16_t f,
+                        MomRow& R) {
+    double nuP = g.nu + F.nut[c];
+    for (int q = 0; q < 3; ++q) { R.aP[q] = 0.0; R.bnd[q] = 0.0; }
+    for (int d = 0; d < g.dims; ++d) {
+        long long fl = face_lo(g, d, i, j, k);
+        long long fs = face_stride(g, d);
+        for (int side = 0; side < 2; ++side) {
+            int s = 2 * d + side;
+            double Fb = F.phi[d][fl + side * fs];
+            double Fout = side ? Fb : -Fb;
+            if (interior(g, d, side, i, j, k)) {
+                long long nc = nbr_cell(g, c, d, side);
+                double nuN = g.nu + F.nut[nc];
+                double Dif = 0.5 * (nuP + nuN) * g.S[d] / g.D[d];
+                R.a[s] = fmin(Fout, 0.0) - Dif;
+                R.nb[s] = nc;
+                R.has[s] = true;
+                double add = fmax(-Fout, 0.0) + Dif;
+                for (int q = 0; q < g.dims; ++q) R.aP[q] += add;
+            } else {
+                R.a[s] = 0.0;
+                R.nb[s] = c;
+                R.has[s] = false;
+                for (int q = 0; q < g.dims; ++q) {
+                    double val;
+                    if (vel_fixed(g, f, s, q, val)) {
+                        double coef = nuP * g.S[d] / (0.5 * g.D[d]) + fmax(-Fout, 0.0);
+                        R.aP[q] += coef;
+                        R.bnd[q] += coef * val;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Gauss-linear gradient of the pressure-like field p at cell c (outlet faces
+// carry p_out, the rest zero gradient)
+__device__ inline double grad_p(const Grid& g, const double* p, long long c, int d, int i, int j, int k) {
+    double pP = p[c];
+    double lo, hi;
+    if (interior(g, d, 0, i, j, k)) lo = 0.5 * (p[c - g.stride[d]] + pP);
+    else lo = p_fixed(g, 2 * d) ? g.p_out : pP;
+    if (interior(g, d, 1, i, j, k)) hi = 0.5 * (pP + p[c + g.stride[d]]);
+    else hi = p_fixed(g, 2 * d + 1) ? g.p_out : pP;
+    return (hi - lo) / g.D[d];
+}
+
+// relaxed pressure p + a (pn - p), evaluated on the fly
+__device__ inline double prelax(const double* p, const double* pn, long long c, double a) {
+    double po = p[c];
+    return po + a * (pn[c] - po);
+}
+
+// ---------------------------------------------------------------- initial flux
+// phi of the current velocity: linear interpolation inside, inlet u_in S,
+// outlet u_P S, zero on walls, slip and closed faces.
+__device__ inline double bnd_flux_hbya(const Grid& g, uint16_t f, int s, double vP) {
+    if (closed_side(f, s)) return 0.0;
+    int d = s >> 1;
+    int kind = g.kind[s];
+    if (kind == HFDIB_BC_INLET) return g.u_in[d] * g.S[d];
+    if (kind == HFDIB_BC_OUTLET) return vP * g.S[d];
+    return 0.0;
+}
+
+__global__ void k_face_flux(Grid g, const uint16_t* __restrict__ flags, const double* vx, const double* vy,
+                            const double* vz, double* fx, double* fy, double* fz) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    int i, j, k;
+    cell_ijk(g, c, i, j, k);
+    uint16_t f = flags[c];
+    const double* v[3] = {vx, vy, vz};
+    double* out[3] = {fx, fy, fz};
+    for (int d = 0; d < g.dims; ++d) {
+        long long fl = face_lo(g, d, i, j, k);
+        if (interior(g, d, 0, i, j, k))
+            out[d][fl] = 0.5 * (v[d][c - g.stride[d]] + v[d][c]) * g.S[d];
+        else
+            out[d][fl] = bnd_flux_hbya(g, f, 2 * d, v[d][c]);
+        if (!interior(g, d, 1, i, j, k))
+            out[d][fl + face_stride(g, d)] = bnd_flux_hbya(g, f, 2 * d + 1, v[d][c]);
+    }
+}
+
+// ---------------------------------------------------------------- means
+// Sums of the fields the residual normalisation needs, with imposed rows
+// replaced by their imposed values.
+__global__ void k_means(Grid g, Params P, Fields F) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    if (c < g.N) {
+        uint16_t f = F.flags[c];
+        int tag = tag_of(f);
+        for (int q = 0; q < g.dims; ++q) {
+            double x;
+            if (!vel_row_fixed(g, F, c, q, x)) x = F.u[q][c];
+            v[q] = x;
+        }
+        v[3] = F.p[c];
+        if (P.model != HFDIB_LAMINAR) {
+            v[4] = tag == TAG_IC ? 0.0 : ((f & F_AU) ? F.kib[c] : F.k[c]);
+            v[5] = tag == TAG_IC ? F.scal[SC_WMAX] : (tag == TAG_BC ? F.wib[c] : F.w[c]);
+        }
+    }
+    grid_reduce<6, false>(v, F.partials, F.counters + 1, F.scal + SC_SUM_U);
+}
+
+// ---------------------------------------------------------------- grad u
+__global__ void k_grad_u(Grid g, Fields F) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    int i, j, k;
+    cell_ijk(g, c, i, j, k);
+    uint16_t f = F.flags[c];
+    for (int b = 0; b < g.dims; ++b) {
+        const double* u = F.u[b];
+        double uP = u[c];
+        for (int a = 0; a < g.dims; ++a) {
+            double lo, hi, val;
+            if (interior(g, a, 0, i, j, k)) lo = 0.5 * (u[c - g.stride[a]] + uP);
+            else lo = vel_fixed(g, f, 2 * a, b, val) ? val : uP;
+            if (interior(g, a, 1, i, j, k)) hi = 0.5 * (uP + u[c + g.stride[a]]);
+            else hi = vel_fixed(g, f, 2 * a + 1, b, val) ? val : uP;
+            F.G[(long long)(3 * a + b) * g.N + c] = (hi - lo) / g.D[a];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- a3 assembly
+__global__ void k_mom_asm(Grid g, Params P, Fields F) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double red[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (c < g.N) {
+        int i, j, k;
+        cell_ijk(g, c, i, j, k);
+        uint16_t f = F.flags[c];
+        MomRow R;
+        mom_row(g, F, c, i, j, k, f, R);
+        double nuP = g.nu + F.nut[c];
+        bool fixed_row = (tag_of(f) == TAG_IC) || (f & F_AU);
+        for (int q = 0; q < g.dims; ++q) {
+            // explicit div(nu_eff (grad u)^T), component q: face flux nu_f (d u_a/d x_q)_f S_a
+            double T = 0.0;
+            for (int a = 0; a < g.dims; ++a) {
+                const double* Gq = F.G + (long long)(3 * q + a) * g.N;
+                double GP = Gq[c];
+                double flo, fhi;
+                if (interior(g, a, 0, i, j, k)) {
+                    long long nc = c - g.stride[a];
+                    flo = (0.5 * (nuP + g.nu + F.nut[nc])) * (0.5 * (GP + Gq[nc])) * g.S[a];
+                } else {
+                    flo = nuP * GP * g.S[a];
+                }
+                if (interior(g, a, 1, i, j, k)) {
+                    long long nc = c + g.stride[a];
+                    fhi = (0.5 * (nuP + g.nu + F.nut[nc])) * (0.5 * (GP + Gq[nc])) * g.S[a];
+                } else {
+                    fhi = nuP * GP * g.S[a];
+                }
+                T += fhi - flo;
+            }
+            double b0 = R.bnd[q] + T;
+            double gp = grad_p(g, F.p, c, q, i, j, k);
+            double uold = F.u[q][c];
+            double bfull = b0 - gp * g.V;
+            F.bm[q][c] = b0 + (1.0 - P.urf_u) / P.urf_u * R.aP[q] * uold - gp * g.V;
+            // initial guess of the predictor: u_old, with the imposed rows
+            // already at their imposed values (so an exact solution of the
+            // sweep's system is left unchanged by the smoother)
+            double fv;
+            F.us[q][c] = vel_row_fixed(g, F, c, q, fv) ? fv : uold;
+            if (!fixed_row) {
+                double xP = uold;
+                double Ax = R.aP[q] * xP, A1 = R.aP[q];
+                for (int s = 0; s < 2 * g.dims; ++s) {
+                    if (!R.has[s]) continue;
+                    double xN;
+                    long long nc = R.nb[s];
+                    if (!vel_row_fixed(g, F, nc, q, xN)) xN = F.u[q][nc];
+                    Ax += R.a[s] * xN;
+                    A1 += R.a[s];
+                }
+                double xbar = F.scal[SC_SUM_U + q] / (double)g.N;
+                red[3 * q + 0] = fabs(bfull - Ax);
+                red[3 * q + 1] = fabs(Ax - A1 * xbar);
+                red[3 * q + 2] = fabs(bfull - A1 * xbar);
+            }
+        }
+    }
+    grid_reduce<9, false>(red, F.partials, F.counters + 2, F.scal + SC_RES_U);
+}
+
+// ---------------------------------------------------------------- a4 smoother
+// Red-black Gauss-Seidel on the relaxed momentum rows; rows with alpha_u = 1
+// hold u = u_ib (ic: u_s), which realises the correction of Eq. (corru).
+__global__ void k_mom_smooth(Grid g, Params P, Fields F, int colour) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    int i, j, k;
+    cell_ijk(g, c, i, j, k);
+    if (((i + j + k) & 1) != colour) return;
+    uint16_t f = F.flags[c];
+    if (tag_of(f) == TAG_IC) {
+        for (int q = 0; q < g.dims; ++q) F.us[q][c] = g.u_s[q];
+        return;
+    }
+    if (f & F_AU) {
+        for (int q = 0; q < g.dims; ++q) F.us[q][c] = F.uib[q][c];
+        return;
+    }
+    MomRow R;
+    mom_row(g, F, c, i, j, k, f, R);
+    for (int q = 0; q < g.dims; ++q) {
+        double acc = F.bm[q][c];
+        for (int s = 0; s < 2 * g.dims; ++s)
+            if (R.has[s]) acc -= R.a[s] * F.us[q][R.nb[s]];
+        F.us[q][c] = acc / (R.aP[q] / P.urf_u);
+    }
+}
+
+// ---------------------------------------------------------------- a6 HbyA
+__global__ void k_hbya(Grid g, Params P, Fields F) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    int i, j, k;
+    cell_ijk(g, c, i, j, k);
+    uint16_t f = F.flags[c];
+    MomRow R;
+    mom_row(g, F, c, i, j, k, f, R);
+    double aavg = 0.0;
+    double aPr[3];
+    for (int q = 0; q < g.dims; ++q) { aPr[q] = R.aP[q] / P.urf_u; aavg += aPr[q]; }
+    aavg = aavg / (double)g.dims;
+    for (int q = 0; q < g.dims; ++q) {
+        double br = F.bm[q][c] + grad_p(g, F.p, c, q, i, j, k) * g.V;
+        double off = 0.0;
+        for (int s = 0; s < 2 * g.dims; ++s)
+            if (R.has[s]) off += R.a[s] * F.us[q][R.nb[s]];
+        double H = br - off - (aPr[q] - aavg) * F.us[q][c];
+        F.HbyA[q][c] = H / aavg;
+    }
+    F.rAU[c] = g.V / aavg;
+}
+
+// ---------------------------------------------------------------- phiHbyA
+__global__ void k_phiH(Grid g, Fields F) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    int i, j, k;
+    cell_ijk(g, c, i, j, k);
+    uint16_t f = F.flags[c];
+    for (int d = 0; d < g.dims; ++d) {
+        long long fl = face_lo(g, d, i, j, k);
+        const double* H = F.HbyA[d];
+        if (interior(g, d, 0, i, j, k))
+            F.phiH[d][fl] = 0.5 * (H[c - g.stride[d]] + H[c]) * g.S[d];
+        else
+            F.phiH[d][fl] = bnd_flux_hbya(g, f, 2 * d, H[c]);
+        if (!interior(g, d, 1, i, j, k))
+            F.phiH[d][fl + face_stride(g, d)] = bnd_flux_hbya(g, f, 2 * d + 1, H[c]);
+    }
+}
+
+// ---------------------------------------------------------------- a8 update
+// phi = phiHbyA - rAU_f (p_N - p_P)/Delta S with the new (unrelaxed) pressure;
+// p <- p + urf_p (p_new - p); u = HbyA - rAU grad(p_relaxed); continuity error.
+__global__ void k_update(Grid g, Params P, Fields F, Level L0) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double red[1] = {0.0};
+    if (c < g.N) {
+        int i, j, k;
+        cell_ijk(g, c, i, j, k);
+        uint16_t f = F.flags[c];
+        double pnP = F.pn[c];
+        double div = 0.0;
+        for (int d = 0; d < g.dims; ++d) {
+            long long fl = face_lo(g, d, i, j, k);
+            long long fs = face_stride(g, d);
+            double flo, fhi;
+            // L0.cf holds rAU_f S/Delta (inside) and rAU_P S/(Delta/2) (outlet)
+            if (interior(g, d, 0, i, j, k)) {
+                long long nc = c - g.stride[d];
+                flo = F.phiH[d][fl] - L0.cf[d][fl] * (pnP - F.pn[nc]);
+            } else if (p_fixed(g, 2 * d)) {
+                flo = F.phiH[d][fl] - L0.cf[d][fl] * (pnP - g.p_out);
+            } else {
+                flo = F.phiH[d][fl];
+            }
+            if (interior(g, d, 1, i, j, k)) {
+                long long nc = c + g.stride[d];
+                fhi = F.phiH[d][fl + fs] - L0.cf[d][fl + fs] * (F.pn[nc] - pnP);
+            } else if (p_fixed(g, 2 * d + 1)) {
+                fhi = F.phiH[d][fl + fs] - L0.cf[d][fl + fs] * (g.p_out - pnP);
+            } else {
+                fhi = F.phiH[d][fl + fs];
+            }
+            F.phi[d][fl] = flo;
+            if (!interior(g, d, 1, i, j, k)) F.phi[d][fl + fs] = fhi;
+            div += fhi - flo;
+        }
+        red[0] = (f & F_M) ? fabs(div) : 0.0;
+        // relaxed pressure and the velocity update
+        double a = P.urf_p;
+        double prP = prelax(F.p, F.pn, c, a);
+        for (int d = 0; d < g.dims; ++d) {
+            double lo, hi;
+            if (interior(g, d, 0, i, j, k)) lo = 0.5 * (prelax(F.p, F.pn, c - g.stride[d], a) + prP);
+            else lo = p_fixed(g, 2 * d) ? g.p_out : prP;
+            if (interior(g, d, 1, i, j, k)) hi = 0.5 * (prP + prelax(F.p, F.pn, c + g.stride[d], a));
+            else hi = p_fixed(g, 2 * d + 1) ? g.p_out : prP;
+            double gp = (hi - lo) / g.D[d];
+            F.u[d][c] = F.HbyA[d][c] - F.rAU[c] * gp;
+        }
+        F.pr[c] = prP;
+    }
+    grid_reduce<1, false>(red, F.partials, F.counters + 6, F.scal + SC_CONT);
+}
+
+// ---------------------------------------------------------------- sweep end
+__global__ void k_sweep_end(Fields F, int dims, int model, double p_iters, double* res_out) {
+    double* s = F.scal;
+    auto sc = [](double r, double n1, double n2) { return r / ((n1 + n2) + 1e-20); };
+    for (int q = 0; q < 3; ++q)
+        res_out[HFDIB_RES_UX + q] = q < dims ? sc(s[SC_RES_U + 3 * q], s[SC_RES_U + 3 * q + 1], s[SC_RES_U + 3 * q + 2]) : 0.0;
+    res_out[HFDIB_RES_P] = sc(s[SC_PCG_INIT + 3], s[SC_PCG_INIT + 4], s[SC_PCG_INIT + 5]);
+    if (model != HFDIB_LAMINAR) {
+        res_out[HFDIB_RES_EPSW] = sc(s[SC_RES_W], s[SC_RES_W + 1], s[SC_RES_W + 2]);
+        res_out[HFDIB_RES_K] = sc(s[SC_RES_K], s[SC_RES_K + 1], s[SC_RES_K + 2]);
+    } else {
+        res_out[HFDIB_RES_EPSW] = 0.0;
+        res_out[HFDIB_RES_K] = 0.0;
+    }
+    res_out[HFDIB_RES_CONT] = s[SC_CONT];
+    res_out[HFDIB_RES_PITER] = p_iters;
+}
+
+// ---------------------------------------------------------------- launchers
+void launch_init_flux(const Grid& g, const Fields& F, cudaStream_t s) {
+    k_face_flux<<<nblocks(g.N), BLOCK, 0, s>>>(g, F.flags, F.u[0], F.u[1], F.u[2], F.phi[0], F.phi[1],
+                                                F.phi[2]);
+}
+void launch_means(const Grid& g, const Params& P, const Fields& F, cudaStream_t s) {
+    k_means<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F);
+}
+void launch_grad_u(const Grid& g, const Fields& F, cudaStream_t s) {
+    k_grad_u<<<nblocks(g.N), BLOCK, 0, s>>>(g, F);
+}
+void launch_mom_asm(const Grid& g, const Params& P, const Fields& F, cudaStream_t s) {
+    k_mom_asm<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F);
+}
+void launch_mom_smooth(const Grid& g, const Params& P, const Fields& F, int colour, cudaStream_t s) {
+    k_mom_smooth<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F, colour);
+}
+void launch_hbya(const Grid& g, const Params& P, const Fields& F, cudaStream_t s) {
+    k_hbya<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F);
+}
+void launch_phiH(const Grid& g, const Fields& F, cudaStream_t s) {
+    k_phiH<<<nblocks(g.N), BLOCK, 0, s>>>(g, F);
+}
+void launch_update(const Grid& g, const Params& P, const Fields& F, const Level& L0, cudaStream_t s) {
+    k_update<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F, L0);
+}
+void launch_sweep_end(const Params& P, const Fields& F, int dims, double p_iters, double* res_out,
+                      cudaStream_t s) {
+    k_sweep_end<<<1, 1, 0, s>>>(F, dims, P.model, p_iters, res_out);
+}
+
+}  // namespace hf

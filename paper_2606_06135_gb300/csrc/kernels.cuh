@@ -1,0 +1,147 @@
+// kernels.cuh -- device data structures and kernel launchers of the sweep.
+#pragma once
+#include "common.cuh"
+
+namespace hf {
+
+// compacted boundary-cell list (bc cells in increasing cell order)
+struct BcList {
+    int nbc;
+    int* cell;      // cell index
+    int* nbr;       // in-solid neighbour (-1: none)
+    int* cas;       // y_perp case 0 (a), 1 (b), 2 (c)
+    int* clamped;   // y_perp clamped at 1e-3 h
+    int* b1;        // [3*nbc] base cell of the X1 stencil
+    int* b2;        // [3*nbc] base cell of the X2 stencil
+    int* lamb;      // per sweep: 1 if y+ <= y+_lam (laminar branch)
+    double* n;      // [3*nbc] outer unit normal
+    double* yp;     // y_perp
+    double* ye;     // y_eff
+    double *wS, *w1, *w2;  // quadratic weights
+    double* t1;     // [3*nbc]
+    double* t2;     // [3*nbc]
+    double* yplus;  // per sweep
+};
+
+// device scalar slots
+enum {
+    SC_WMAX = 0,                 // max over bc u fc of omega_old / eps_old
+    SC_SUM_U = 1,                // sums of substituted u_x, u_y, u_z, p, k, eps|omega (6)
+    SC_SUM_P = 4, SC_SUM_K = 5, SC_SUM_W = 6,
+    SC_RES_U = 8,                // 9: |r|, |Ax-A1 xbar|, |b-A1 xbar| per component
+    SC_RES_W = 20,               // 3
+    SC_RES_K = 23,               // 3
+    SC_CONT = 26,
+    SC_PCG_RZRR = 28,            // [r.z, r.r] ping-pong pair at 28/29 and 30/31
+    SC_PCG_DQ = 32,
+    SC_PCG_INIT = 40,            // r0.z0, r0.r0, b.b, then the 3 scaled-residual sums of p
+    SC_NSCAL = 64
+};
+
+struct Fields {
+    double* u[3];
+    double* us[3];     // predictor output u*
+    double* p;
+    double* pn;        // pressure-equation solution
+    double* pr;        // relaxed pressure (swap buffer)
+    double* phi[3];
+    double* phiH[3];
+    double* HbyA[3];
+    double* rAU;
+    double* bm[3];
+    double* k;
+    double* w;         // eps (k-epsilon) or omega (SST)
+    double* w2;        // the other one (omega for k-eps, eps for SST), diagnostic
+    double* nut;
+    double* uib[3];
+    double* kib;
+    double* wib;
+    double* G;         // 9*N velocity gradient, G[(3a+b)N + c] = d u_b / d x_a
+    double* Pk;
+    double* S2;
+    double* gam;       // scalar equation diffusivity
+    double* gamk;
+    double* sp;        // extra implicit diagonal (integrated)
+    double* src;       // explicit source (integrated)
+    double* bt;        // relaxed right-hand side
+    double* diag;      // relaxed diagonal
+    double* ywall;
+    uint16_t* flags;
+    // pressure solver
+    double* prhs;
+    double* pdiag;
+    double* r;
+    double* z;
+    double* d[2];
+    double* q;
+    // scalars and reductions
+    double* scal;
+    double* partials;
+    unsigned int* counters;
+};
+
+// one multigrid level of the pressure operator (level 0 = the fine grid)
+struct Level {
+    int nx, ny, nz;
+    long long N;
+    double* cf[3];   // face coefficients, face layout of the level
+    double* diag;
+    double* x;       // correction (level 0: z)
+    double* b;       // right-hand side (level 0: r)
+};
+constexpr int MAX_LEVELS = 16;
+constexpr long long TAIL_CELLS = 16384;
+struct MgLevels {
+    int nl;
+    Level lv[MAX_LEVELS];
+};
+
+struct Params {
+    int model;
+    double urf_u, urf_p, urf_turb;
+    double k_in, w_in;   // inlet k and eps (k-eps) or omega (SST)
+};
+
+// ib.cu
+void launch_classify(const Grid& g, const double* lam, uint16_t* flags, cudaStream_t s);
+void launch_compact_bc(const Grid& g, const uint16_t* flags, int* counts, int* total, int* cells,
+                       cudaStream_t s);
+void launch_bc_geometry(const Grid& g, const double* lam, const uint16_t* flags, const BcList& bl,
+                        cudaStream_t s);
+void launch_max_not_ic(const Grid& g, const uint16_t* flags, const double* w, double* partials,
+                       unsigned int* counter, double* out, cudaStream_t s);
+void launch_imposed(const Grid& g, int model, const BcList& bl, uint16_t* flags, const double* ux,
+                    const double* uy, const double* uz, const double* k, double* uibx, double* uiby,
+                    double* uibz, double* kib, double* wib, cudaStream_t s);
+void launch_export_bc(const BcList& bl, long long* ints, long long* ints2, double* reals, cudaStream_t s);
+
+// flow.cu
+void launch_init_flux(const Grid& g, const Fields& F, cudaStream_t s);
+void launch_means(const Grid& g, const Params& P, const Fields& F, cudaStream_t s);
+void launch_grad_u(const Grid& g, const Fields& F, cudaStream_t s);
+void launch_mom_asm(const Grid& g, const Params& P, const Fields& F, cudaStream_t s);
+void launch_mom_smooth(const Grid& g, const Params& P, const Fields& F, int colour, cudaStream_t s);
+void launch_hbya(const Grid& g, const Params& P, const Fields& F, cudaStream_t s);
+void launch_phiH(const Grid& g, const Fields& F, cudaStream_t s);
+void launch_update(const Grid& g, const Params& P, const Fields& F, const Level& L0, cudaStream_t s);
+
+// pressure.cu
+void launch_p_coef(const Grid& g, const MgLevels& M, const double* rAU, int ntail_from, cudaStream_t s);
+void launch_vcycle(const Grid& g, const MgLevels& M, int ntail_from, const Fields& F, double* dot_out,
+                   int coarse_sweeps, cudaStream_t s);
+void launch_pcg_init(const Grid& g, const Fields& F, const MgLevels& M, int jacobi, cudaStream_t s);
+void launch_pcg_A(const Grid& g, const Fields& F, const MgLevels& M, int it, cudaStream_t s);
+void launch_pcg_update(const Grid& g, const Fields& F, const MgLevels& M, int it, int jacobi, cudaStream_t s);
+void launch_sweep_end(const Params& P, const Fields& F, int dims, double p_iters, double* res_out,
+                      cudaStream_t s);
+
+// turb.cu
+void launch_turb_prep(const Grid& g, const Params& P, const Fields& F, cudaStream_t s);
+void launch_bc_prod(const Grid& g, const BcList& bl, const Fields& F, cudaStream_t s);
+void launch_scal_asm(const Grid& g, const Params& P, const Fields& F, int eq, cudaStream_t s);
+void launch_scal_smooth(const Grid& g, const Params& P, const Fields& F, int eq, int colour,
+                        cudaStream_t s);
+void launch_k_prep(const Grid& g, const Params& P, const Fields& F, cudaStream_t s);
+void launch_turb_final(const Grid& g, const Params& P, const Fields& F, cudaStream_t s);
+
+}  // namespace hf

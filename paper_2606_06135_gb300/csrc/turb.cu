@@ -1,0 +1,283 @@
+// turb.cu -- two-equation turbulence part of the sweep (Fig. simplehfdibrans):
+// production and the P_ib assignment (Eq. omegaws), the eps / omega equation
+// with its rows fixed to eps_ib / omega_ib where alpha_omega = 1 (Eq.
+// alphaomega, "matrix manipulation"), the k equation with its rows fixed to
+// k_ib where alpha_k = 1 followed by the k correction, and nu_t.
+//
+// Models: standard k-epsilon (Launder-Spalding) and k-omega SST (Menter),
+// both with their published coefficients; the paper cites them without
+// printing the equations.  eq = 0 is eps (k-epsilon) or omega (SST), eq = 1 is k.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace hf {
+
+__device__ inline bool interior_t(const Grid& g, int d, int side, int i, int j, int k) {
+    int pos = coord(d, i, j, k);
+    return side ? pos < g.n[d] - 1 : pos > 0;
+}
+
+// Gauss-linear gradient of a turbulence scalar (open inlet faces carry xin)
+__device__ inline double grad_s(const Grid& g, const double* x, uint16_t f, double xin, long long c, int d,
+                                int i, int j, int k) {
+    double xP = x[c];
+    double lo, hi;
+    if (interior_t(g, d, 0, i, j, k)) lo = 0.5 * (x[c - g.stride[d]] + xP);
+    else lo = scal_fixed(g, f, 2 * d) ? xin : xP;
+    if (interior_t(g, d, 1, i, j, k)) hi = 0.5 * (xP + x[c + g.stride[d]]);
+    else hi = scal_fixed(g, f, 2 * d + 1) ? xin : xP;
+    return (hi - lo) / g.D[d];
+}
+
+__device__ inline double sst_F2(double kk, double ww, double y, double nu) {
+    double sk = sqrt(kk);
+    double arg2 = fmin(fmax(2.0 * sk / (SST_BSTAR * ww * y), 500.0 * nu / (y * y * ww)), 100.0);
+    return tanh(arg2 * arg2);
+}
+
+// ---------------------------------------------------------------- a9 production
+__global__ void k_turb_prep(Grid g, Params P, Fields F) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    int i, j, k;
+    cell_ijk(g, c, i, j, k);
+    uint16_t f = F.flags[c];
+    double S2 = 0.0;
+    for (int a = 0; a < g.dims; ++a)
+        for (int b = 0; b < g.dims; ++b) {
+            double s = 0.5 * (F.G[(long long)(3 * a + b) * g.N + c] + F.G[(long long)(3 * b + a) * g.N + c]);
+            S2 += s * s;
+        }
+    S2 = 2.0 * S2;
+    double nut = F.nut[c];
+    double Pk = tag_of(f) == TAG_IC ? 0.0 : nut * S2;
+    F.S2[c] = S2;
+    F.Pk[c] = Pk;
+    double kold = F.k[c], wold = F.w[c];
+    double V = g.V;
+    if (P.model == HFDIB_KEPSILON) {
+        double ratio = wold / fmax(kold, K_MIN);
+        F.gam[c] = g.nu + nut / KE_SIGE;
+        F.sp[c] = KE_C2 * ratio * V;
+        F.src[c] = KE_C1 * (nut * S2) * ratio * V;
+        F.gamk[c] = g.nu + nut / KE_SIGK;
+    } else {
+        double gk = 0.0;
+        for (int d = 0; d < g.dims; ++d)
+            gk += grad_s(g, F.k, f, P.k_in, c, d, i, j, k) * grad_s(g, F.w, f, P.w_in, c, d, i, j, k);
+        double y = fmax(F.ywall[c], 1e-3 * g.h);
+        double kk = fmax(kold, K_MIN), ww = wold;
+        double CDkw = 2.0 * SST_AW2 * gk / ww;
+        double CDp = fmax(CDkw, 1e-10);
+        double sk = sqrt(kk);
+        double arg1 = fmin(fmax(sk / (SST_BSTAR * ww * y), 500.0 * g.nu / (y * y * ww)),
+                           4.0 * SST_AW2 * kk / (CDp * y * y));
+        double F1 = tanh(arg1 * arg1 * arg1 * arg1);
+        double F2 = sst_F2(kk, ww, y, g.nu);
+        double gamma = F1 * SST_G1 + (1.0 - F1) * SST_G2;
+        double beta = F1 * SST_B1 + (1.0 - F1) * SST_B2;
+        double GbyNu = fmin(S2, (SST_C1 / SST_A1) * SST_BSTAR * wold * fmax(SST_A1 * wold, SST_BB1 * F2 * sqrt(S2)));
+        double cdc = (F1 - 1.0) * CDkw / wold;
+        F.gam[c] = g.nu + (F1 * SST_AW1 + (1.0 - F1) * SST_AW2) * nut;
+        F.sp[c] = beta * wold * V + (cdc > 0.0 ? cdc : 0.0) * V;
+        F.src[c] = gamma * GbyNu * V - (cdc > 0.0 ? 0.0 : cdc) * wold * V;
+        F.gamk[c] = g.nu + (F1 * SST_AK1 + (1.0 - F1) * SST_AK2) * nut;
+    }
+}
+
+// P_ib in the log branch of bc cells: kappa nu y+ |n.grad u|^2 / ln^2(E y+)
+__global__ void k_bc_prod(Grid g, BcList bl, Fields F) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= bl.nbc) return;
+    if (bl.lamb[q]) return;
+    long long c = bl.cell[q];
+    double dudn2 = 0.0;
+    for (int b = 0; b < g.dims; ++b) {
+        double comp = 0.0;
+        for (int a = 0; a < g.dims; ++a) comp += bl.n[3 * q + a] * F.G[(long long)(3 * a + b) * g.N + c];
+        dudn2 += comp * comp;
+    }
+    double yp = bl.yplus[q];
+    double L = log(E_WF * yp);
+    F.Pk[c] = KAPPA * g.nu * yp * dudn2 / (L * L);
+}
+
+// ---------------------------------------------------------------- scalar rows
+__device__ inline bool scal_row_fixed(const Grid& g, const Fields& F, int eq, long long c, double& v) {
+    uint16_t f = F.flags[c];
+    int tag = tag_of(f);
+    if (eq == 0) {
+        if (tag == TAG_IC) { v = F.scal[SC_WMAX]; return true; }
+        if (tag == TAG_BC) { v = F.wib[c]; return true; }
+        return false;
+    }
+    if (tag == TAG_IC) { v = 0.0; return true; }
+    if (f & F_AU) { v = F.kib[c]; return true; }
+    return false;
+}
+
+struct ScalRow {
+    double aP, bnd;
+    double a[6];
+    long long nb[6];
+    bool has[6];
+};
+
+__device__ void scal_row(const Grid& g, const Fields& F, const double* gam, double xin, long long c, int i,
+                         int j, int k, uint16_t f, ScalRow& R) {
+    double gP = gam[c];
+    R.aP = 0.0;
+    R.bnd = 0.0;
+    for (int d = 0; d < g.dims; ++d) {
+        long long fl = face_lo(g, d, i, j, k);
+        long long fs = face_stride(g, d);
+        for (int side = 0; side < 2; ++side) {
+            int s = 2 * d + side;
+            double Fb = F.phi[d][fl + side * fs];
+            double Fout = side ? Fb : -Fb;
+            if (interior_t(g, d, side, i, j, k)) {
+                long long nc = side ? c + g.stride[d] : c - g.stride[d];
+                double Dif = 0.5 * (gP + gam[nc]) * g.S[d] / g.D[d];
+                R.a[s] = fmin(Fout, 0.0) - Dif;
+                R.nb[s] = nc;
+                R.has[s] = true;
+                R.aP += fmax(-Fout, 0.0) + Dif;
+            } else {
+                R.a[s] = 0.0;
+                R.nb[s] = c;
+                R.has[s] = false;
+                if (scal_fixed(g, f, s)) {
+                    double coef = gP * g.S[d] / (0.5 * g.D[d]) + fmax(-Fout, 0.0);
+                    R.aP += coef;
+                    R.bnd += coef * xin;
+                }
+            }
+        }
+    }
+}
+
+__global__ void k_scal_asm(Grid g, Params P, Fields F, int eq) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double red[3] = {0.0, 0.0, 0.0};
+    double* x = eq == 0 ? F.w : F.k;
+    const double* gam = eq == 0 ? F.gam : F.gamk;
+    double xin = eq == 0 ? P.w_in : P.k_in;
+    if (c < g.N) {
+        int i, j, k;
+        cell_ijk(g, c, i, j, k);
+        uint16_t f = F.flags[c];
+        ScalRow R;
+        scal_row(g, F, gam, xin, c, i, j, k, f, R);
+        double aP = R.aP + F.sp[c];
+        double b = R.bnd + F.src[c];
+        double xold = x[c];
+        F.bt[c] = b + (1.0 - P.urf_turb) / P.urf_turb * aP * xold;
+        F.diag[c] = aP / P.urf_turb;
+        double fv;
+        if (scal_row_fixed(g, F, eq, c, fv)) {
+            // imposed rows start at their imposed values (only neighbours'
+            // substituted values are read below, so this write is race-free)
+            x[c] = fv;
+        } else {
+            double Ax = aP * xold, A1 = aP;
+            for (int s = 0; s < 2 * g.dims; ++s) {
+                if (!R.has[s]) continue;
+                double xN;
+                if (!scal_row_fixed(g, F, eq, R.nb[s], xN)) xN = x[R.nb[s]];
+                Ax += R.a[s] * xN;
+                A1 += R.a[s];
+            }
+            double xbar = F.scal[eq == 0 ? SC_SUM_W : SC_SUM_K] / (double)g.N;
+            red[0] = fabs(b - Ax);
+            red[1] = fabs(Ax - A1 * xbar);
+            red[2] = fabs(b - A1 * xbar);
+        }
+    }
+    grid_reduce<3, false>(red, F.partials, F.counters + 7, F.scal + (eq == 0 ? SC_RES_W : SC_RES_K));
+}
+
+__global__ void k_scal_smooth(Grid g, Params P, Fields F, int eq, int colour) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    int i, j, k;
+    cell_ijk(g, c, i, j, k);
+    if (((i + j + k) & 1) != colour) return;
+    double* x = eq == 0 ? F.w : F.k;
+    double fv;
+    if (scal_row_fixed(g, F, eq, c, fv)) {
+        x[c] = fv;
+        return;
+    }
+    const double* gam = eq == 0 ? F.gam : F.gamk;
+    double xin = eq == 0 ? P.w_in : P.k_in;
+    uint16_t f = F.flags[c];
+    ScalRow R;
+    scal_row(g, F, gam, xin, c, i, j, k, f, R);
+    double acc = F.bt[c];
+    for (int s = 0; s < 2 * g.dims; ++s)
+        if (R.has[s]) acc -= R.a[s] * x[R.nb[s]];
+    x[c] = acc / F.diag[c];
+}
+
+// after the eps/omega solve: bound it, set the k-equation sink and source
+__global__ void k_k_prep(Grid g, Params P, Fields F) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    double w = F.w[c];
+    double wmin = P.model == HFDIB_KEPSILON ? EPS_MIN : OMEGA_MIN;
+    w = fmax(w, wmin);
+    F.w[c] = w;
+    double kold = F.k[c];
+    if (P.model == HFDIB_KEPSILON) {
+        F.sp[c] = w / fmax(kold, K_MIN) * g.V;
+        F.src[c] = F.Pk[c] * g.V;
+    } else {
+        F.sp[c] = SST_BSTAR * w * g.V;
+        F.src[c] = fmin(F.Pk[c], SST_C1 * SST_BSTAR * kold * w) * g.V;
+    }
+}
+
+// bound k, apply the k correction (Eq. corru for k), update nu_t
+__global__ void k_turb_final(Grid g, Params P, Fields F) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    uint16_t f = F.flags[c];
+    double k = fmax(F.k[c], K_MIN);
+    if (tag_of(f) == TAG_IC) k = k + (0.0 - k);
+    else if (f & F_AU) k = k + (F.kib[c] - k);
+    F.k[c] = k;
+    double w = F.w[c];
+    if (P.model == HFDIB_KEPSILON) {
+        F.nut[c] = C_MU * k * k / w;
+        F.w2[c] = w / (C_MU * fmax(k, K_MIN));
+    } else {
+        double y = fmax(F.ywall[c], 1e-3 * g.h);
+        double F2 = sst_F2(fmax(k, K_MIN), w, y, g.nu);
+        F.nut[c] = SST_A1 * k / fmax(SST_A1 * w, SST_BB1 * F2 * sqrt(F.S2[c]));
+        F.w2[c] = C_MU * k * w;
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+void launch_turb_prep(const Grid& g, const Params& P, const Fields& F, cudaStream_t s) {
+    k_turb_prep<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F);
+}
+void launch_bc_prod(const Grid& g, const BcList& bl, const Fields& F, cudaStream_t s) {
+    if (bl.nbc == 0) return;
+    k_bc_prod<<<nblocks(bl.nbc), BLOCK, 0, s>>>(g, bl, F);
+}
+void launch_scal_asm(const Grid& g, const Params& P, const Fields& F, int eq, cudaStream_t s) {
+    k_scal_asm<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F, eq);
+}
+void launch_scal_smooth(const Grid& g, const Params& P, const Fields& F, int eq, int colour,
+                        cudaStream_t s) {
+    k_scal_smooth<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F, eq, colour);
+}
+void launch_k_prep(const Grid& g, const Params& P, const Fields& F, cudaStream_t s) {
+    k_k_prep<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F);
+}
+void launch_turb_final(const Grid& g, const Params& P, const Fields& F, cudaStream_t s) {
+    k_turb_final<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F);
+}
+
+}  // namespace hf

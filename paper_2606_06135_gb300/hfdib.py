@@ -1,0 +1,261 @@
+"""ctypes binding of libhfdib.so (the C ABI declared in include/hfdib.h).
+
+Argument marshalling only: every step of the SIMPLE sweep runs in the CUDA
+kernels of the library.  PyTorch provides device memory and the stream.  The
+library must have been built (paper_2606_06135_gb300.build); there is no
+fallback -- load_library() raises when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "lib", "libhfdib.so")
+
+LAMINAR, KEPSILON, KOMEGA_SST = 0, 1, 2
+MODELS = {"laminar": LAMINAR, "kepsilon": KEPSILON, "komegasst": KOMEGA_SST}
+BC_KIND = {"inlet": 0, "outlet": 1, "slip": 2, "wall": 3, "empty": 4}
+SIDES = ("xmin", "xmax", "ymin", "ymax", "zmin", "zmax")
+FIELDS = {"ux": 0, "uy": 1, "uz": 2, "p": 3, "k": 4, "eps": 5, "omega": 6, "nut": 7,
+          "phix": 8, "phiy": 9, "phiz": 10}
+RES_NAMES = ("Ux", "Uy", "Uz", "p", "epsw", "k", "cont", "p_iters")
+NRES = 8
+STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "out of memory",
+          -4: "not converged", -5: "diverged", -6: "state mismatch"}
+
+ERR_NOT_CONVERGED = -4
+
+
+class HfdibError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__("%s: %s (%d)" % (where, STATUS.get(code, "error"), code))
+        self.code = code
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double)]
+
+
+class Bc(C.Structure):
+    _fields_ = [("face", C.c_int32 * 6), ("u_in", C.c_double * 3), ("I_in", C.c_double),
+                ("lt_in", C.c_double), ("p_out", C.c_double), ("u_ref", C.c_double),
+                ("l_ref", C.c_double), ("u_s", C.c_double * 3)]
+
+
+class Options(C.Structure):
+    _fields_ = [("urf_u", C.c_double), ("urf_p", C.c_double), ("urf_turb", C.c_double),
+                ("n_u", C.c_int32), ("n_turb", C.c_int32), ("p_reltol", C.c_double),
+                ("p_maxiter", C.c_int32), ("precision", C.c_int32), ("precond", C.c_int32),
+                ("p_check", C.c_int32), ("mg_coarse_sweeps", C.c_int32), ("reserved", C.c_int32 * 5)]
+
+
+_LIB = None
+
+EXPORTED = ("hfdib_default_options", "hfdib_create", "hfdib_simple_sweep", "hfdib_solve_steady",
+            "hfdib_get_field", "hfdib_set_field", "hfdib_get_tags", "hfdib_get_bc_list",
+            "hfdib_get_history", "hfdib_get_state", "hfdib_set_state", "hfdib_get_counters",
+            "hfdib_error_string", "hfdib_destroy")
+
+
+def load_library(path=LIBPATH):
+    """Load libhfdib.so once and declare the C signatures."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise RuntimeError("libhfdib.so not built (%s); run paper_2606_06135_gb300.build" % path)
+    lib = C.CDLL(path)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_int64, C.c_double
+    lib.hfdib_default_options.argtypes = [C.POINTER(Options)]
+    lib.hfdib_default_options.restype = None
+    lib.hfdib_create.argtypes = [C.POINTER(Grid), vp, vp, i32, dbl, C.POINTER(Bc), C.POINTER(Options),
+                                 vp, C.POINTER(vp)]
+    lib.hfdib_simple_sweep.argtypes = [vp, i32, vp]
+    lib.hfdib_solve_steady.argtypes = [vp, dbl, i32, i32, C.POINTER(i32), vp]
+    lib.hfdib_get_field.argtypes = [vp, i32, vp]
+    lib.hfdib_set_field.argtypes = [vp, i32, vp]
+    lib.hfdib_get_tags.argtypes = [vp, vp, C.POINTER(i64)]
+    lib.hfdib_get_bc_list.argtypes = [vp, vp, vp, vp]
+    lib.hfdib_get_history.argtypes = [vp, i32, vp, C.POINTER(i32)]
+    lib.hfdib_get_state.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
+    lib.hfdib_set_state.argtypes = [vp, vp, C.c_size_t]
+    lib.hfdib_get_counters.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
+    lib.hfdib_error_string.argtypes = [i32]
+    lib.hfdib_error_string.restype = C.c_char_p
+    lib.hfdib_destroy.argtypes = [vp]
+    lib.hfdib_destroy.restype = None
+    for name in EXPORTED:
+        f = getattr(lib, name)
+        if f.restype is C.c_int or name in ("hfdib_create", "hfdib_simple_sweep", "hfdib_solve_steady",
+                                             "hfdib_get_field", "hfdib_set_field", "hfdib_get_tags",
+                                             "hfdib_get_bc_list", "hfdib_get_history", "hfdib_get_state",
+                                             "hfdib_set_state", "hfdib_get_counters"):
+            f.restype = C.c_int
+    _LIB = lib
+    return lib
+
+
+def default_options(**kw):
+    lib = load_library()
+    o = Options()
+    lib.hfdib_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise HfdibError(rc, where)
+
+
+def grid_struct(g):
+    return Grid(g["nx"], g["ny"], g["nz"], g["x0"], g["y0"], g["z0"], g["dx"], g["dy"], g["dz"])
+
+
+def bc_struct(case):
+    b = Bc()
+    for s, name in enumerate(SIDES):
+        b.face[s] = BC_KIND[case["bc"][name]]
+    for q in range(3):
+        b.u_in[q] = case["u_in"][q]
+        b.u_s[q] = case["u_s"][q]
+    b.I_in = case["I_in"]
+    b.lt_in = case["lt_in"]
+    b.p_out = case["p_out"]
+    b.u_ref = case["u_ref"]
+    b.l_ref = case["l_ref"]
+    return b
+
+
+class Solver:
+    """One HFDIB steady-RANS problem on the GPU (wraps one hfdib handle)."""
+
+    def __init__(self, case, device="cuda:0", stream=None, **opts):
+        import torch
+        self.torch = torch
+        self.lib = load_library()
+        self.case = case
+        self.device = torch.device(device)
+        g = case["grid"]
+        self.shape = (g["nz"], g["ny"], g["nx"])
+        self.N = g["nx"] * g["ny"] * g["nz"]
+        self.dims = 2 if g["nz"] == 1 else 3
+        self.face_counts = ((g["nx"] + 1) * g["ny"] * g["nz"], g["nx"] * (g["ny"] + 1) * g["nz"],
+                            g["nx"] * g["ny"] * (g["nz"] + 1))
+        self.model = MODELS[case["model"]]
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        lam = torch.as_tensor(np.ascontiguousarray(case["lam"], dtype=np.float64)).to(self.device)
+        ywall = case.get("ywall")
+        yw = (torch.as_tensor(np.ascontiguousarray(ywall, dtype=np.float64)).to(self.device)
+              if ywall is not None else None)
+        torch.cuda.synchronize(self.device)
+        self._opts = default_options(**opts)
+        h = C.c_void_p()
+        rc = self.lib.hfdib_create(C.byref(grid_struct(g)), C.c_void_p(lam.data_ptr()),
+                                   C.c_void_p(yw.data_ptr()) if yw is not None else None,
+                                   self.model, float(case["Re"]), C.byref(bc_struct(case)),
+                                   C.byref(self._opts), C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        _check(rc, "hfdib_create")
+        self.h = h
+
+    # ------------------------------------------------------------------ sweeps
+    def sweep(self, n=1, read=True):
+        res = np.zeros(NRES) if read else None
+        rc = self.lib.hfdib_simple_sweep(self.h, int(n), res.ctypes.data if read else None)
+        _check(rc, "hfdib_simple_sweep")
+        return res
+
+    def solve(self, tol=1e-6, max_iter=1000, check_every=10, raise_on_fail=False):
+        it = C.c_int(0)
+        res = np.zeros(NRES)
+        rc = self.lib.hfdib_solve_steady(self.h, float(tol), int(max_iter), int(check_every),
+                                         C.byref(it), res.ctypes.data)
+        if rc not in (0, ERR_NOT_CONVERGED) or (raise_on_fail and rc != 0):
+            _check(rc, "hfdib_solve_steady")
+        return rc, it.value, res
+
+    # ------------------------------------------------------------------ data
+    def field(self, name):
+        torch = self.torch
+        fid = FIELDS[name]
+        n = self.face_counts[fid - 8] if fid >= 8 else self.N
+        out = torch.empty(n, dtype=torch.float64, device=self.device)
+        _check(self.lib.hfdib_get_field(self.h, fid, C.c_void_p(out.data_ptr())), "hfdib_get_field")
+        self.stream.synchronize()
+        return out
+
+    def set_field(self, name, values):
+        torch = self.torch
+        t = torch.as_tensor(values, dtype=torch.float64).to(self.device).contiguous().reshape(-1)
+        fid = FIELDS[name]
+        self.stream.synchronize()
+        _check(self.lib.hfdib_set_field(self.h, fid, C.c_void_p(t.data_ptr())), "hfdib_set_field")
+        self.stream.synchronize()
+
+    def fields(self):
+        names = ["ux", "uy", "uz"][: self.dims] + ["p", "nut"]
+        if self.model != LAMINAR:
+            names += ["k", "eps", "omega"]
+        return {n: self.field(n).cpu().numpy().reshape(self.shape) for n in names}
+
+    def tags(self):
+        torch = self.torch
+        t = torch.empty(self.N, dtype=torch.uint8, device=self.device)
+        nbc = C.c_int64(0)
+        _check(self.lib.hfdib_get_tags(self.h, C.c_void_p(t.data_ptr()), C.byref(nbc)), "hfdib_get_tags")
+        return t.cpu().numpy().reshape(self.shape), nbc.value
+
+    def bc_list(self):
+        torch = self.torch
+        _, nbc = self.tags()
+        ints = torch.zeros((max(nbc, 1), 8), dtype=torch.int64, device=self.device)
+        ints2 = torch.zeros((max(nbc, 1), 3), dtype=torch.int64, device=self.device)
+        reals = torch.zeros((max(nbc, 1), 14), dtype=torch.float64, device=self.device)
+        _check(self.lib.hfdib_get_bc_list(self.h, C.c_void_p(ints.data_ptr()), C.c_void_p(ints2.data_ptr()),
+                                          C.c_void_p(reals.data_ptr())), "hfdib_get_bc_list")
+        self.stream.synchronize()
+        a = ints.cpu().numpy()[:nbc]
+        a2 = ints2.cpu().numpy()[:nbc]
+        r = reals.cpu().numpy()[:nbc]
+        return dict(cell=a[:, 0], nbr=a[:, 1], case=a[:, 2], clamped=a[:, 3].astype(bool),
+                    base1=a[:, 4:7], base2=a2, n=r[:, 0:3], y_perp=r[:, 3], y_eff=r[:, 4],
+                    wS=r[:, 5], w1=r[:, 6], w2=r[:, 7], t1=r[:, 8:11], t2=r[:, 11:14])
+
+    def history(self, count=1024):
+        buf = np.zeros((count, NRES))
+        n = C.c_int(0)
+        _check(self.lib.hfdib_get_history(self.h, int(count), buf.ctypes.data, C.byref(n)), "hfdib_get_history")
+        return buf[: n.value]
+
+    def counters(self):
+        s, l = C.c_int64(0), C.c_int64(0)
+        _check(self.lib.hfdib_get_counters(self.h, C.byref(s), C.byref(l)), "hfdib_get_counters")
+        return s.value, l.value
+
+    def get_state(self):
+        n = C.c_size_t(0)
+        _check(self.lib.hfdib_get_state(self.h, None, C.byref(n)), "hfdib_get_state")
+        buf = np.zeros(n.value, dtype=np.uint8)
+        _check(self.lib.hfdib_get_state(self.h, buf.ctypes.data, C.byref(n)), "hfdib_get_state")
+        return buf
+
+    def set_state(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        _check(self.lib.hfdib_set_state(self.h, buf.ctypes.data, buf.nbytes), "hfdib_set_state")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hfdib_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,62 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry
+point include/hfdib.h declares (no compute calls: no GPU needed)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hfdib.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hfdib_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2606_06135_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_path():
+    names = declared_functions()
+    for need in ("hfdib_create", "hfdib_simple_sweep", "hfdib_solve_steady", "hfdib_get_field",
+                 "hfdib_destroy"):
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (hfdib_[a-z_0-9]+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_binds(libpath):
+    from paper_2606_06135_gb300 import hfdib
+    lib = hfdib.load_library(libpath)
+    for n in declared_functions():
+        assert hasattr(lib, n)
+    o = hfdib.default_options()
+    assert o.urf_u == 0.7 and o.urf_p == 0.3 and o.urf_turb == 0.85 and o.n_u == 2
+    assert lib.hfdib_error_string(-1) == b"invalid argument"
+
+
+def test_create_rejects_bad_arguments_without_touching_the_gpu(libpath):
+    import ctypes as C
+    from paper_2606_06135_gb300 import hfdib
+    lib = hfdib.load_library(libpath)
+    h = C.c_void_p()
+    g = hfdib.Grid(1, 4, 1, 0, 0, 0, 1, 1, 1)      # nx < 2
+    bc = hfdib.Bc()
+    rc = lib.hfdib_create(C.byref(g), C.c_void_p(8), None, 1, 100.0, C.byref(bc), None, None, C.byref(h))
+    assert rc == -1
+    g = hfdib.Grid(4, 4, 1, 0, 0, 0, 1, 1, 1)
+    rc = lib.hfdib_create(C.byref(g), C.c_void_p(8), None, 7, 100.0, C.byref(bc), None, None, C.byref(h))
+    assert rc == -1                                   # bad model
+    rc = lib.hfdib_create(C.byref(g), C.c_void_p(8), None, 2, 100.0, C.byref(bc), None, None, C.byref(h))
+    assert rc == -1                                   # SST without wall distance

@@ -1,0 +1,157 @@
+"""GPU path (through the C ABI) against the FP64 CPU oracle.
+
+* a0 integer work -- cell groups, boundary-cell list, in-solid neighbour,
+  y_perp case, interpolation cells -- must match bit for bit; the normal and
+  the interpolation fractions too (no transcendental on their path); y_perp,
+  y_eff and the quadratic weights (atanh on their path) within 1e-13.
+* A few sweeps with the inner solves driven to convergence must match the
+  oracle's sweeps (exact sparse solves) within 1e-9 relative L2.
+* The converged steady state (scaled residual <= 1e-12) must match the
+  oracle's converged state within relative L2 <= 1e-9 (FP64), whatever the
+  inner solvers: the SIMPLE fixed point is independent of them.
+"""
+import numpy as np
+import pytest
+
+from paper_2606_06135_gb300 import geometry as G
+from oracle import hfdib_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+def make_solver(case, **opts):
+    from paper_2606_06135_gb300.hfdib import Solver
+    return Solver(case, **opts)
+
+
+def relL2(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+TAG_CASES = {
+    "cylinder64": lambda: G.case_cylinder(64, 32),
+    "cylinder128": lambda: G.case_cylinder(128, 64),
+    "channel": lambda: G.case_channel(16, 48),
+    "channel_shift": lambda: G.case_channel(16, 48, wall_offset=0.37),
+    "bfs_small": lambda: G.case_bfs(128, 32),
+    "bfs_full": lambda: G.case_bfs(1024, 256),
+    "grf": lambda: G.case_grf(64, 32, seed=3),
+    "box15": lambda: G.case_rotated_box(15.0, 48),
+    "box45": lambda: G.case_rotated_box(45.0, 48),
+    "naca4": lambda: G.case_naca(256, 128, aoa_deg=4.0),
+    "ahmed_small": lambda: G.case_ahmed(64, 24, 24),
+}
+
+
+@pytest.mark.parametrize("name", sorted(TAG_CASES))
+def test_ib_tags_and_geometry_bit_exact(name):
+    case = TAG_CASES[name]()
+    m = O.Mesh(case["grid"])
+    otag = O.classify(m, case["lam"])
+    ogeo = O.ib_geometry(m, case["lam"], otag)
+    s = make_solver(case)
+    tags, nbc = s.tags()
+    np.testing.assert_array_equal(tags, otag)
+    assert nbc == len(ogeo["cell"])
+    if nbc == 0:
+        return
+    bl = s.bc_list()
+    for key in ("cell", "nbr", "case", "clamped", "base1", "base2"):
+        np.testing.assert_array_equal(bl[key], ogeo[key], err_msg=key)
+    for key in ("n", "t1", "t2"):
+        np.testing.assert_array_equal(bl[key], ogeo[key], err_msg=key)
+    for key in ("y_perp", "y_eff", "wS", "w1", "w2"):
+        np.testing.assert_allclose(bl[key], ogeo[key], rtol=1e-13, atol=1e-15, err_msg=key)
+    s.close()
+
+
+FIELD_MAP = {"ux": lambda o: o.u[0], "uy": lambda o: o.u[1], "p": lambda o: o.p,
+             "k": lambda o: o.k, "eps": lambda o: o.eps, "omega": lambda o: o.omega,
+             "nut": lambda o: o.nut}
+
+
+def compare_fields(s, o, tol, names=None):
+    got = s.fields()
+    names = names or [n for n in FIELD_MAP if n in got]
+    errs = {n: relL2(got[n], FIELD_MAP[n](o)) for n in names}
+    bad = {n: e for n, e in errs.items() if not e <= tol}
+    assert not bad, (errs, tol)
+    return errs
+
+
+SWEEP_CASES = {
+    "channel_laminar": lambda: G.case_channel(8, 24, Re=10.0),
+    "cylinder_keps": lambda: G.case_cylinder(48, 24),
+    "bfs_sst": lambda: G.case_bfs(64, 16),
+    "bfs_keps": lambda: G.case_bfs(64, 16, model="kepsilon"),
+}
+
+EXACT = dict(n_u=600, n_turb=600, p_reltol=1e-15, p_maxiter=4000)
+
+
+@pytest.mark.parametrize("name", sorted(SWEEP_CASES))
+def test_sweeps_match_oracle_with_exact_inner_solves(name):
+    case = SWEEP_CASES[name]()
+    o = O.Oracle(case)
+    s = make_solver(case, **EXACT)
+    for n in range(3):
+        o.sweep()
+        s.sweep()
+    compare_fields(s, o, 1e-9)
+    s.close()
+
+
+CONVERGED = {
+    "channel_laminar": (lambda: G.case_channel(8, 24, Re=10.0), 3000),
+    "cylinder_keps": (lambda: G.case_cylinder(64, 32), 6000),
+    "bfs_sst": (lambda: G.case_bfs(128, 32), 8000),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CONVERGED))
+def test_converged_state_matches_oracle_fp64(name):
+    mk, maxit = CONVERGED[name]
+    case = mk()
+    o = O.Oracle(case)
+    _, ores = o.solve(tol=1e-12, max_iter=2000)
+    assert o.max_residual(ores) <= 1e-12
+    s = make_solver(case)
+    rc, it, res = s.solve(tol=1e-12, max_iter=maxit, check_every=20)
+    assert rc == 0, (rc, it, res)
+    compare_fields(s, o, 1e-9)
+    s.close()
+
+
+def test_deterministic_and_checkpoint_resume():
+    case = G.case_cylinder(64, 32)
+    a = make_solver(case)
+    b = make_solver(case)
+    a.sweep(30)
+    b.sweep(30)
+    fa, fb = a.fields(), b.fields()
+    for n in fa:
+        np.testing.assert_array_equal(fa[n], fb[n], err_msg=n)
+    st = a.get_state()
+    a.sweep(20)
+    b.set_state(st)
+    b.sweep(20)
+    fa, fb = a.fields(), b.fields()
+    for n in fa:
+        np.testing.assert_array_equal(fa[n], fb[n], err_msg=n)
+    a.close()
+    b.close()
+
+
+def test_invalid_lambda_rejected():
+    from paper_2606_06135_gb300.hfdib import HfdibError
+    case = G.case_cylinder(32, 16)
+    case["lam"] = case["lam"].copy()
+    case["lam"][0, 3, 3] = np.nan
+    with pytest.raises(HfdibError) as e:
+        make_solver(case)
+    assert e.value.code == -1
+    case["lam"][0, 3, 3] = 1.5
+    with pytest.raises(HfdibError):
+        make_solver(case)
