@@ -1,0 +1,336 @@
+#!/usr/bin/env python3
+"""Benchmark: HFDIB steady-RANS SIMPLE sweep on one GB300 (sm_103a).
+
+Workload: 2D immersed backward-facing step, h = 1, expansion 9/8, uniform
+1024 x 256 grid over 30h x 9h, inlet plug U = 1 with I = 5 %, Re_h = 36000,
+k-omega SST with immersed-boundary wall functions (synthetic lambda field
+from the analytic step geometry).
+
+A step is one extended SIMPLE sweep (Fig. simplehfdibrans: imposed fields,
+momentum predictor, pressure corrector with multigrid-preconditioned CG,
+flux/velocity update, omega and k transport), issued as one CUDA graph.
+`value` = cell-updates/s = cells x timed sweeps / device time, with L2
+flushed (a 512 MB write) between timed steps because the working set fits
+in L2.  Also reported: converged solves/s to max scaled residual 1e-6, the
+end-to-end rate through the public API from host arrays, the roofline of the
+dominant kernel class, and the CPU oracle on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SIMPLE cell-updates/s & solves/s to residual 1e-6 (% HBM roofline), mixed vs FP64"
+WORKLOAD = "bfs_1024x256_sst"
+NX, NY = 1024, 256
+TOL = 1e-6
+FREEZE = 300           # one-way y+ switch from sweep 300 (limit cycles otherwise)
+MAX_SOLVE_SWEEPS = 20000
+
+# Algorithmic bytes per cell for one launch group of each kernel class
+# (2D, FP64 words of 8 B, minimum traffic with perfect neighbour reuse,
+# face arrays counted as one word per cell and direction, flags 2 B).
+BYTES_PER_CELL = {
+    # u, v, p, nut, phi_x, phi_y, 4 gradient comps read; bm x2, u* x2 written
+    "mom_asm": 8 * (10 + 4) + 2,
+    # one colour: bm x2 (half the cells), u* x2, phi x2, nut read; u* x2 (half) written
+    "mom_smooth": 8 * (1 + 2 + 2 + 1 + 1) + 2,
+    # u*, bm x2, p, phi x2, nut read; HbyA x2, rAU, phiH x2 written
+    "hbya": 8 * (7 + 5) + 2,
+    # one CG iteration + one V-cycle: A-product (z, d, cf x2, diag; d, q) +
+    # update (pn, d, r, q; pn, r) + fine-level V-cycle (~26 words) x 4/3
+    "pcg": 8 * (7 + 6) + int(8 * 26 * 4 / 3),
+    "vcycle0": int(8 * 26 * 4 / 3),
+    # phiH x2, pn, p, HbyA x2, rAU, cf x2 read; phi x2, u x2, p written
+    "update": 8 * (9 + 5) + 2,
+    "grad_u": 8 * (2 + 4) + 2,
+    "turb_prep": 8 * (4 + 4 + 2 + 1 + 6) + 2,
+    "scal_asm": 8 * (2 + 1 + 2 + 2 + 2) + 2,
+    "scal_smooth": 8 * (1 + 1 + 2 + 1 + 1) + 2,
+    "imposed": 8 * 8 + 2,
+    "p_coef": 8 * (1 + 3),
+    "turb_final": 8 * (5 + 4) + 2,
+    "sweep_end": 0,
+}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while timing."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_rate(seconds=15.0, min_sweeps=1, max_sweeps=1000):
+    """Time the FP64 oracle sweeping the same workload on this host (one
+    thread).  Run in a child process so the thread-count variables apply."""
+    code = r"""
+import json, sys, time
+sys.path.insert(0, %r)
+from paper_2606_06135_gb300 import geometry as G
+from oracle import hfdib_oracle as O
+case = G.case_bfs(%d, %d)
+o = O.Oracle(case, dict(freeze_switch=%d))
+n = 0; t0 = time.perf_counter()
+while True:
+    o.sweep(); n += 1
+    el = time.perf_counter() - t0
+    if (el >= %f and n >= %d) or n >= %d:
+        break
+print(json.dumps({"sweeps": n, "seconds": el, "cells": %d}))
+""" % (ROOT, NX, NY, FREEZE, seconds, min_sweeps, max_sweeps, NX * NY)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError("oracle run failed: " + out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def run_reference(args, rank):
+    """Reference arm: the CPU oracle as it stands, on this host's cores; each
+    step is one full-size oracle sweep of the same workload."""
+    if rank != 0:
+        return 0
+    code = r"""
+import json, sys, time
+sys.path.insert(0, %r)
+from paper_2606_06135_gb300 import geometry as G
+from oracle import hfdib_oracle as O
+case = G.case_bfs(%d, %d)
+o = O.Oracle(case, dict(freeze_switch=%d))
+for _ in range(%d):
+    o.sweep()
+t0 = time.perf_counter()
+for _ in range(%d):
+    o.sweep()
+print(json.dumps({"seconds": time.perf_counter() - t0}))
+""" % (ROOT, NX, NY, FREEZE, args.warmup, args.steps)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if out.returncode != 0:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle failed: " + out.stderr[-300:].replace("\n", " ")}))
+        return 0
+    sec = json.loads(out.stdout.strip().splitlines()[-1])["seconds"]
+    value = NX * NY * args.steps / sec
+    line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "grid": [NX, NY], "model": "komega_sst", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d full-size FP64 oracle sweeps after %d warm-up sweeps" % (args.steps, args.warmup)},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-solve", action="store_true", help="skip the converged-solve and e2e legs")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import numpy as np
+    import torch
+    from paper_2606_06135_gb300 import build as B
+    from paper_2606_06135_gb300 import geometry as G
+    from paper_2606_06135_gb300 import hfdib
+
+    if not os.path.exists(hfdib.LIBPATH):
+        B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    case = G.case_bfs(NX, NY)
+    N = NX * NY
+    opts = dict(freeze_switch=FREEZE, precision=1 if args.precision == "mixed" else 0)
+    stream = torch.cuda.Stream(dev)
+    s = hfdib.Solver(case, device=str(dev), stream=stream, **opts)
+    for _ in range(args.warmup):
+        s.sweep(1, read=False)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    stream.synchronize()
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    n0 = s.counters()[0]
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+        ev[k][0].record(stream)
+        s.sweep(1, read=False)
+        ev[k][1].record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize(dev)
+    barrier()
+    clk = clocks.stop()
+    t_dev = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    hist = s.history(args.steps)
+    piters = hist[:, 7]
+    fixed, per_it = s.launch_counts()
+    gpu_launches = int(args.steps * fixed + per_it * piters.sum())
+    if dist is not None:
+        t = torch.tensor([t_dev], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev = float(t.item())
+    value = world * N * args.steps / t_dev
+    ms_per_step = 1e3 * t_dev / args.steps
+
+    # roofline of the dominant kernel class (host-driven sweeps, event pairs)
+    prof = s.profile(3)
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dname, (dus, dcalls) = dom
+    avg_us = dus / max(dcalls, 1)
+    bpc = BYTES_PER_CELL.get(dname, 0)
+    achieved = bpc * N / (avg_us * 1e-6) / 1e9
+    peak, peak_kind = measured_peaks()
+    roofline = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                "algorithmic_bytes_per_launch": bpc * N, "avg_launch_us": avg_us,
+                "class_share": {k: round(v[0] / sum(x[0] for x in prof.values()), 4) for k, v in prof.items()}}
+    s.close()
+
+    out = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "grid": [NX, NY], "cells": N, "model": "komega_sst",
+                      "Re_h": 36000, "precision": args.precision, "l2": "flushed (512 MB write) between timed steps",
+                      "parallelism": "replicas" if world > 1 else "single",
+                      "freeze_switch": FREEZE, "pcg_iters_mean": float(piters.mean())},
+           "gpu_launches": gpu_launches, "clocks": clk, "roofline": roofline}
+
+    # converged solve and end-to-end leg (public API from host arrays)
+    if not args.no_solve:
+        lam_h = torch.from_numpy(np.ascontiguousarray(case["lam"])).pin_memory()
+        yw_h = torch.from_numpy(np.ascontiguousarray(case["ywall"])).pin_memory()
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            lam_d = lam_h.to(dev, non_blocking=True)
+            yw_d = yw_h.to(dev, non_blocking=True)
+        s2 = hfdib.Solver(dict(case, lam=lam_d, ywall=yw_d), device=str(dev), stream=stream, **opts)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc, iters, res = s2.solve(tol=TOL, max_iter=MAX_SOLVE_SWEEPS, check_every=100)
+        e1.record(stream)
+        host = {n: s2.field(n).cpu() for n in ("ux", "uy", "p", "k", "omega")}
+        torch.cuda.synchronize(dev)
+        t_e2e = time.perf_counter() - t0
+        t_solve = e0.elapsed_time(e1) / 1e3
+        s2.close()
+        converged = rc == 0
+        out["solves_per_s"] = (world / t_solve) if converged else 0.0
+        out["solve"] = {"converged": converged, "sweeps": iters, "seconds": t_solve,
+                        "final_max_residual": float(max(res[:6])), "tol": TOL}
+        d2h = sum(v.numel() * 8 for v in host.values()) + 8 * hfdib.NRES * ((iters + 99) // 100)
+        out["e2e"] = {"value": world * N * iters / t_e2e, "unit": "cell-updates/s",
+                      "h2d_bytes_per_step": 2 * N * 8, "d2h_bytes_per_step": d2h,
+                      "step": "host lambda/ywall -> create (IB geometry) -> solve to 1e-6 -> host fields",
+                      "solves_per_s": (world / t_e2e) if converged else 0.0}
+    if rank == 0 and not args.no_cpu:
+        r = oracle_rate(seconds=15.0)
+        out["cpu_baseline"] = {"value": r["cells"] * r["sweeps"] / r["seconds"], "unit": "cell-updates/s",
+                               "cores": 1, "kind": "oracle",
+                               "sample": "%d full-size FP64 oracle sweeps of the same workload" % r["sweeps"]}
+    if rank == 0:
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

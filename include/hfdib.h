@@ -19,7 +19,8 @@
  *   - Device pointers passed in are read on the handle's stream; the caller
  *     keeps ownership of every buffer it passes.  The handle owns its fields
  *     and scratch (allocated at create, freed at destroy).
- *   - All work is issued on the stream given at create (NULL = default).
+ *   - All work is issued on the handle's stream (see hfdib_create); calls
+ *     that return data to host memory synchronise that stream.
  */
 #ifndef HFDIB_H
 #define HFDIB_H
@@ -80,13 +81,23 @@ typedef struct {
     int32_t n_u;                 /* red-black Gauss-Seidel sweeps, momentum (2)   */
     int32_t n_turb;              /* red-black Gauss-Seidel sweeps, k and eps/omega (2) */
     double p_reltol;             /* pressure solve: |r| <= p_reltol |r0| (0.01)   */
-    int32_t p_maxiter;           /* pressure solve iteration cap (200)            */
+    int32_t p_maxiter;           /* pressure solve iteration cap (50)             */
     int32_t precision;           /* 0 = FP64 throughout                           */
     int32_t precond;             /* pressure preconditioner: 0 Jacobi, 1 GMG V-cycle (1) */
-    int32_t p_check;             /* read |r| back every p_check CG iterations (1);
-                                    0 = run p_maxiter iterations without host reads */
-    int32_t mg_coarse_sweeps;    /* red-black sweeps (each way) on the coarsest level (20) */
-    int32_t reserved[5];
+    int32_t p_check;             /* host-driven solve: read the convergence flag every
+                                    p_check CG iterations; 0 = no host reads: the loop
+                                    stops on the device (0) */
+    int32_t mg_coarse_sweeps;    /* red-black sweeps (each way) on the coarsest level (4) */
+    int32_t graph;               /* 1: run each sweep as one CUDA graph, the pressure
+                                    iterations in a device-controlled while node (1);
+                                    needs p_check == 0 */
+    int32_t freeze_switch;       /* 0: the y+ <= y+_lam branch of every bc cell is
+                                    re-evaluated each sweep (Eq. alphauk, default);
+                                    n > 0: from sweep n on a bc cell may leave the
+                                    laminar branch but not re-enter it, which ends
+                                    limit cycles of the discrete switch (not part
+                                    of the paper)                                  */
+    int32_t reserved[3];
 } hfdib_options;
 
 typedef struct hfdib_ctx* hfdib_handle;
@@ -102,10 +113,13 @@ enum {
  * scaled residuals sum|b-Ax| / (sum|Ax - xbar A1| + sum|b - xbar A1|) of the
  * momentum components, pressure, eps or omega and k, evaluated at the start
  * of each solve (App. D), then the continuity error sum over lambda<1 cells
- * of |div phi| (App. D), then the number of pressure iterations. */
+ * of |div phi| (App. D), the number of pressure iterations, the number of
+ * bc cells in the laminar branch y+ <= y+_lam (Eq. alphauk) and the number
+ * of bc cells whose branch changed since the previous sweep -- a non-zero
+ * count late in a solve marks a limit cycle of the discrete switch. */
 enum { HFDIB_RES_UX = 0, HFDIB_RES_UY = 1, HFDIB_RES_UZ = 2, HFDIB_RES_P = 3,
        HFDIB_RES_EPSW = 4, HFDIB_RES_K = 5, HFDIB_RES_CONT = 6, HFDIB_RES_PITER = 7,
-       HFDIB_NRES = 8 };
+       HFDIB_RES_NLAM = 8, HFDIB_RES_NSWITCH = 9, HFDIB_NRES = 10 };
 
 /* Fill *opt with the defaults listed in hfdib_options. */
 void hfdib_default_options(hfdib_options* opt);
@@ -119,7 +133,9 @@ void hfdib_default_options(hfdib_options* opt);
  *   Re       : Reynolds number; nu = bc->u_ref * bc->l_ref / Re.
  *   bc       : boundary description (not NULL).
  *   opt      : options (NULL -> defaults).
- *   stream   : cudaStream_t used for every call on the handle (NULL = default).
+ *   stream   : cudaStream_t used for every call on the handle.  NULL: the
+ *              handle creates and owns a non-blocking stream (the legacy
+ *              default stream cannot be captured into a CUDA graph).
  *   out      : receives the handle.
  * At create the library classifies cells into ic/bc/fc (Sec. 2.3), builds
  * the boundary-cell geometry -- normal, in-solid neighbour, y_perp, y_eff,
@@ -182,9 +198,37 @@ int hfdib_get_history(hfdib_handle h, int count, double* host, int* n_out);
 int hfdib_get_state(hfdib_handle h, void* buf, size_t* bytes);
 int hfdib_set_state(hfdib_handle h, const void* buf, size_t bytes);
 
+/* Kernel launches of one sweep outside the pressure iterations, and of one
+ * pressure (CG + V-cycle) iteration. */
+int hfdib_get_launch_counts(hfdib_handle h, int64_t* per_sweep, int64_t* per_pcg_iteration);
+
 /* Number of sweeps run so far and of kernel launches issued by the last
  * hfdib_simple_sweep / hfdib_solve_steady call. */
 int hfdib_get_counters(hfdib_handle h, int64_t* sweeps, int64_t* launches);
+
+/* Kernel classes timed by hfdib_profile_sweeps. */
+enum { HFDIB_K_IMPOSED = 0,   /* a1, a2 and the residual means                */
+       HFDIB_K_GRAD_U = 1,    /* velocity gradient (a3, a9)                   */
+       HFDIB_K_MOM_ASM = 2,   /* a3 momentum assembly + momentum residual      */
+       HFDIB_K_MOM_SMOOTH = 3,/* a4 red-black sweeps of the predictor         */
+       HFDIB_K_HBYA = 4,      /* a6 rAU, HbyA, phiHbyA                        */
+       HFDIB_K_P_COEF = 5,    /* a7 pressure operator on all levels           */
+       HFDIB_K_PCG = 6,       /* a7 CG kernels (init, products, updates)      */
+       HFDIB_K_VCYCLE = 7,    /* a7 initial multigrid V-cycle                 */
+       HFDIB_K_UPDATE = 8,    /* a8 flux / pressure / velocity update         */
+       HFDIB_K_TURB_PREP = 9, /* a9 production, P_ib, blending, k sources     */
+       HFDIB_K_SCAL_ASM = 10, /* a10/a11 assembly + residuals                 */
+       HFDIB_K_SCAL_SMOOTH = 11, /* a10/a11 red-black sweeps                  */
+       HFDIB_K_TURB_FINAL = 12,  /* a11 k bound + correction, a12 nu_t         */
+       HFDIB_K_SWEEP_END = 13,   /* a12 residual record                       */
+       HFDIB_K_COUNT = 14 };
+
+/* Run n_sweeps host-driven sweeps with a CUDA event pair around every
+ * launch group and return, per kernel class, the summed device time in
+ * microseconds (total_us) and the number of timed launch groups (calls).
+ * Arrays are host memory of n_classes >= HFDIB_K_COUNT entries.  The sweeps
+ * advance the solution exactly like hfdib_simple_sweep. */
+int hfdib_profile_sweeps(hfdib_handle h, int n_sweeps, double* total_us, int64_t* calls, int n_classes);
 
 const char* hfdib_error_string(int code);
 void hfdib_destroy(hfdib_handle h);

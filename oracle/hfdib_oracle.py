@@ -68,7 +68,7 @@ OMEGA_MIN = 1e-14
 
 TAG_FC, TAG_BC, TAG_IC = 0, 1, 2
 
-DEFAULT_OPTS = dict(urf_u=0.7, urf_p=0.3, urf_turb=0.85)
+DEFAULT_OPTS = dict(urf_u=0.7, urf_p=0.3, urf_turb=0.85, freeze_switch=0)
 
 
 def _sl(ax, a, b):
@@ -639,6 +639,14 @@ class Oracle:
         ut = C_MU ** 0.25 * np.sqrt(kP)
         yplus = geo["y_eff"] * ut / self.nu
         lamb = (yplus <= YPLUS_LAM) if turb else np.ones(len(cells), bool)
+        # reading (opt-in, not in the paper): from sweep `freeze_switch` on, a
+        # bc cell may leave the laminar branch but never re-enter it.  The
+        # laminar branch feeds k_P back through k_ib ~ k_vis(y+) C_mu^1/2 k_P,
+        # a gain above 1 for y+ above ~5, so cells between ~5 and y+_lam
+        # cycle between the branches; the one-way rule ends such cycles.
+        fz = self.opts.get("freeze_switch", 0)
+        if turb and fz > 0 and self.iteration >= fz and getattr(self, "lam_branch", None) is not None:
+            lamb = self.lam_branch & lamb
         self.yplus_bc = yplus
         self.lam_branch = lamb
         af = alpha_u.ravel()
@@ -859,7 +867,9 @@ class Oracle:
             for a in range(m.dims):
                 comp += nvec[:, a] * G[a][b].ravel()[cells]
             dudn2 += comp * comp
-        yp = self.yplus_bc
+        # log branch of Eq. omegaws; y+ > y+_lam there, so max(y+, y+_lam) only
+        # matters for cells kept in the log branch by the one-way switch
+        yp = np.maximum(self.yplus_bc, YPLUS_LAM)
         with np.errstate(divide="ignore", invalid="ignore"):
             plog = KAPPA * self.nu * yp * dudn2 / np.log(E_WF * yp) ** 2
         Gf = Gk.ravel().copy()

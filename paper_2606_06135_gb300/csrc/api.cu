@@ -17,6 +17,15 @@ namespace {
 constexpr int HIST = 1024;
 constexpr uint64_t STATE_MAGIC = 0x48464449425354ull;  // "HFDIBST"
 
+// Optional per-class kernel timing (host-driven sweeps only): an event pair
+// around each launch, read back after the sweeps.
+struct Prof {
+    bool on = false;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+};
+
 struct Ctx {
     Grid g;
     Params P;
@@ -24,10 +33,18 @@ struct Ctx {
     hfdib_bc bc;
     int model = 0;
     cudaStream_t stream = nullptr;
+    bool own_stream = false;
     Fields F;
     BcList bl;
     MgLevels mg;
     int tail_from = 1;
+    int coarse_sweeps = 20;
+    int use_graph = 0;
+    int parity = 0;              // which of the two sweep graphs matches the p / pr buffers
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    long long graph_launches = 0, graph_body_launches = 0;
+    Prof prof;
     double* lam = nullptr;
     double* hist = nullptr;      // device [HIST][HFDIB_NRES]
     double* res_dev = nullptr;   // device [HFDIB_NRES]
@@ -64,10 +81,21 @@ int dalloc_n(Ctx* h, T** p, long long n) {
 }
 
 void free_all(Ctx* h) {
+    for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
+    h->prof.pool.clear();
+    for (int q = 0; q < 2; ++q) {
+        if (h->gexec[q]) cudaGraphExecDestroy(h->gexec[q]);
+        if (h->graph[q]) cudaGraphDestroy(h->graph[q]);
+        h->gexec[q] = nullptr;
+        h->graph[q] = nullptr;
+    }
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
     if (h->pinned) cudaFreeHost(h->pinned);
     h->pinned = nullptr;
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    h->stream = nullptr;
+    h->own_stream = false;
 }
 
 __global__ void k_check_lambda(long long N, const double* lam, double* partials, unsigned int* counter,
@@ -98,11 +126,6 @@ __global__ void k_init_state(Grid g, Params P, Fields F, int model) {
     }
 }
 
-__global__ void k_write_hist(const double* res, double* hist, int slot) {
-    int t = threadIdx.x;
-    if (t < HFDIB_NRES) hist[slot * HFDIB_NRES + t] = res[t];
-}
-
 int sync_read(Ctx* h, const double* dev, double* host, int n) {
     CK(cudaMemcpyAsync(h->pinned, dev, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -110,115 +133,199 @@ int sync_read(Ctx* h, const double* dev, double* host, int n) {
     return HFDIB_OK;
 }
 
-// pressure equation: coefficients, PCG initialisation, iterations
-int pressure_solve(Ctx* h, long long* L) {
-    const Grid& g = h->g;
-    Fields& F = h->F;
-    cudaStream_t s = h->stream;
-    const MgLevels& M = h->mg;
-    int jac = h->opt.precond == 0;
-    int cs = h->opt.mg_coarse_sweeps > 0 ? h->opt.mg_coarse_sweeps : 20;
-    launch_p_coef(g, M, F.rAU, h->tail_from, s);
-    *L += 1 + (h->tail_from - 1) + (h->tail_from < M.nl ? 1 : 0);
-    launch_pcg_init(g, F, M, jac, s);
-    *L += 1;
-    if (!jac) {
-        launch_vcycle(g, M, h->tail_from, F, F.scal + SC_PCG_INIT, cs, s);
-        *L += 6 * h->tail_from + 1;
+// ---------------------------------------------------------------- profiling
+cudaEvent_t prof_event(Prof& p) {
+    if (p.used == p.pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        p.pool.push_back(e);
     }
-    int check = h->opt.p_check;
-    double rr0 = 1.0, tol2 = 0.0;
-    if (check > 0) {
-        double tmp[2];
-        int rc = sync_read(h, F.scal + SC_PCG_INIT, tmp, 2);
-        if (rc) return rc;
-        rr0 = tmp[1];
-        tol2 = h->opt.p_reltol * h->opt.p_reltol * rr0;
-    }
-    int it = 0;
-    if (rr0 > 0.0 && isfinite(rr0)) {
-        while (it < h->opt.p_maxiter) {
-            launch_pcg_A(g, F, M, it, s);
-            launch_pcg_update(g, F, M, it, jac, s);
-            *L += 2;
-            int slot = SC_PCG_RZRR + 2 * ((it + 1) & 1);
-            if (!jac) {
-                launch_vcycle(g, M, h->tail_from, F, F.scal + slot, cs, s);
-                *L += 6 * h->tail_from + 1;
-            }
-            ++it;
-            if (check > 0 && it % check == 0) {
-                double rr;
-                int rc = sync_read(h, F.scal + slot + 1, &rr, 1);
-                if (rc) return rc;
-                if (!(rr > tol2)) break;
-            }
-        }
-    }
-    h->last_piters = it;
-    return HFDIB_OK;
+    return p.pool[p.used++];
 }
 
-// one iteration of the extended SIMPLE loop
-int run_sweep(Ctx* h) {
+#define PROF(h, id, call)                                               \
+    do {                                                                \
+        if ((h)->prof.on) {                                             \
+            cudaEvent_t a_ = prof_event((h)->prof), b_ = prof_event((h)->prof); \
+            cudaEventRecord(a_, (h)->stream);                           \
+            call;                                                       \
+            cudaEventRecord(b_, (h)->stream);                           \
+            (h)->prof.marks.push_back({(id), {a_, b_}});                \
+        } else {                                                        \
+            call;                                                       \
+        }                                                               \
+    } while (0)
+
+// ---------------------------------------------------------------- sweep schedule
+// Part A: a1-a6 of Fig. simplehfdibrans and the set-up of the pressure solve.
+void enqueue_part_a(Ctx* h, long long* L) {
     const Grid& g = h->g;
     const Params& P = h->P;
     Fields& F = h->F;
     cudaStream_t s = h->stream;
     bool turb = h->model != HFDIB_LAMINAR;
-    long long L = 0;
     // a1: omega_ib (eps_ib) of ic cells = max over bc u fc of the old field
-    if (turb) { launch_max_not_ic(g, F.flags, F.w, F.partials, F.counters + 0, F.scal + SC_WMAX, s); L++; }
+    if (turb) { PROF(h, HFDIB_K_IMPOSED, launch_max_not_ic(g, F.flags, F.w, F.partials, F.counters + 0, F.scal + SC_WMAX, s)); (*L)++; }
     // a2: set alpha_u, compute u_ib, k_ib, omega_ib
-    launch_imposed(g, h->model, h->bl, F.flags, F.u[0], F.u[1], F.u[2], F.k, F.uib[0], F.uib[1], F.uib[2],
-                   F.kib, F.wib, s);
-    L++;
-    launch_means(g, P, F, s); L++;
+    PROF(h, HFDIB_K_IMPOSED, launch_imposed(g, h->model, h->opt.freeze_switch, h->bl, F.flags, F.scal, F.u[0], F.u[1],
+                                            F.u[2], F.k, F.uib[0], F.uib[1], F.uib[2], F.kib, F.wib, s));
+    PROF(h, HFDIB_K_IMPOSED, launch_means(g, P, F, s));
     // a3: momentum assembly; a4: predictor; a5: correction (imposed rows)
-    launch_grad_u(g, F, s); L++;
-    launch_mom_asm(g, P, F, s); L++;
+    PROF(h, HFDIB_K_GRAD_U, launch_grad_u(g, F, s));
+    PROF(h, HFDIB_K_MOM_ASM, launch_mom_asm(g, P, F, s));
+    *L += 4;
     for (int n = 0; n < h->opt.n_u; ++n) {
-        launch_mom_smooth(g, P, F, 0, s);
-        launch_mom_smooth(g, P, F, 1, s);
-        L += 2;
+        PROF(h, HFDIB_K_MOM_SMOOTH, launch_mom_smooth(g, P, F, 0, s));
+        PROF(h, HFDIB_K_MOM_SMOOTH, launch_mom_smooth(g, P, F, 1, s));
+        *L += 2;
     }
     // a6: rAU, HbyA, phiHbyA
-    launch_hbya(g, P, F, s); L++;
-    launch_phiH(g, F, s); L++;
-    // a7: pressure equation, PCG with a Jacobi or multigrid preconditioner
-    int rc = pressure_solve(h, &L);
-    if (rc) return rc;
-    int it = h->last_piters;
-    // a8: flux, pressure relaxation, velocity update
-    launch_update(g, P, F, h->mg.lv[0], s); L++;
-    std::swap(F.p, F.pr);
+    PROF(h, HFDIB_K_HBYA, launch_hbya(g, P, F, s));
+    PROF(h, HFDIB_K_HBYA, launch_phiH(g, F, s));
+    *L += 2;
+    // a7 set-up: operator, r0, initial preconditioning, loop state
+    const MgLevels& M = h->mg;
+    int jac = h->opt.precond == 0;
+    PROF(h, HFDIB_K_P_COEF, launch_p_coef(g, M, F.rAU, h->tail_from, s));
+    *L += 1 + (h->tail_from - 1) + (h->tail_from < M.nl ? 1 : 0);
+    PROF(h, HFDIB_K_PCG, launch_pcg_init(g, F, M, jac, s));
+    (*L)++;
+    if (!jac) {
+        PROF(h, HFDIB_K_VCYCLE, launch_vcycle(g, M, h->tail_from, F, F.scal + SC_PCG_RZN, h->coarse_sweeps, s));
+        *L += 5 * h->tail_from + 1;
+    }
+}
+
+void enqueue_pcg_start(Ctx* h, cudaGraphConditionalHandle hc, int use_cond, long long* L) {
+    launch_pcg_start(h->F, h->opt.precond == 0, h->opt.p_reltol, h->opt.p_maxiter, hc, use_cond, h->stream);
+    (*L)++;
+}
+
+void enqueue_pcg_body(Ctx* h, cudaGraphConditionalHandle hc, int use_cond, long long* L) {
+    int jac = h->opt.precond == 0;
+    PROF(h, HFDIB_K_PCG, launch_pcg_body(h->g, h->F, h->mg, h->tail_from, jac, h->coarse_sweeps, h->opt.p_maxiter,
+                                         hc, use_cond, h->stream));
+    *L += 3 + (jac ? 0 : 5 * h->tail_from + 1);
+}
+
+// Part B: a8-a12 and the residual record.
+void enqueue_part_b(Ctx* h, long long* L) {
+    const Grid& g = h->g;
+    const Params& P = h->P;
+    Fields& F = h->F;
+    cudaStream_t s = h->stream;
+    bool turb = h->model != HFDIB_LAMINAR;
+    // a8: flux, pressure relaxation, velocity update (writes the relaxed p to pr)
+    PROF(h, HFDIB_K_UPDATE, launch_update(g, P, F, h->mg.lv[0], s));
+    (*L)++;
     if (turb) {
         // a9: production with the updated velocity, P_ib
-        launch_grad_u(g, F, s); L++;
-        launch_turb_prep(g, P, F, s); L++;
-        launch_bc_prod(g, h->bl, F, s); L++;
+        const Fields& G = F;
+        PROF(h, HFDIB_K_GRAD_U, launch_grad_u(g, G, s));
+        PROF(h, HFDIB_K_TURB_PREP, launch_turb_prep(g, P, G, s));
+        PROF(h, HFDIB_K_TURB_PREP, launch_bc_prod(g, h->bl, G, s));
         // a10: eps / omega with imposed rows
-        launch_scal_asm(g, P, F, 0, s); L++;
+        PROF(h, HFDIB_K_SCAL_ASM, launch_scal_asm(g, P, G, 0, s));
+        *L += 4;
         for (int n = 0; n < h->opt.n_turb; ++n) {
-            launch_scal_smooth(g, P, F, 0, 0, s);
-            launch_scal_smooth(g, P, F, 0, 1, s);
-            L += 2;
+            PROF(h, HFDIB_K_SCAL_SMOOTH, launch_scal_smooth(g, P, G, 0, 0, s));
+            PROF(h, HFDIB_K_SCAL_SMOOTH, launch_scal_smooth(g, P, G, 0, 1, s));
+            *L += 2;
         }
         // a11: k with imposed rows, then the correction; a12 nu_t
-        launch_k_prep(g, P, F, s); L++;
-        launch_scal_asm(g, P, F, 1, s); L++;
+        PROF(h, HFDIB_K_TURB_PREP, launch_k_prep(g, P, G, s));
+        PROF(h, HFDIB_K_SCAL_ASM, launch_scal_asm(g, P, G, 1, s));
+        *L += 2;
         for (int n = 0; n < h->opt.n_turb; ++n) {
-            launch_scal_smooth(g, P, F, 1, 0, s);
-            launch_scal_smooth(g, P, F, 1, 1, s);
-            L += 2;
+            PROF(h, HFDIB_K_SCAL_SMOOTH, launch_scal_smooth(g, P, G, 1, 0, s));
+            PROF(h, HFDIB_K_SCAL_SMOOTH, launch_scal_smooth(g, P, G, 1, 1, s));
+            *L += 2;
         }
-        launch_turb_final(g, P, F, s); L++;
+        PROF(h, HFDIB_K_TURB_FINAL, launch_turb_final(g, P, G, s));
+        (*L)++;
     }
-    launch_sweep_end(P, F, g.dims, (double)it, h->res_dev, s); L++;
-    k_write_hist<<<1, 32, 0, s>>>(h->res_dev, h->hist, (int)(h->sweeps % HIST)); L++;
+    PROF(h, HFDIB_K_SWEEP_END, launch_sweep_end(P, F, g.dims, h->res_dev, h->hist, HIST, s));
+    (*L)++;
+}
+
+// one iteration of the extended SIMPLE loop, host-driven
+int run_sweep_host(Ctx* h) {
+    long long L = 0;
+    cudaGraphConditionalHandle none = 0;
+    enqueue_part_a(h, &L);
+    PROF(h, HFDIB_K_PCG, enqueue_pcg_start(h, none, 0, &L));
+    int check = h->opt.p_check;
+    for (int it = 0; it < h->opt.p_maxiter; ++it) {
+        enqueue_pcg_body(h, none, 0, &L);
+        if (check > 0 && (it + 1) % check == 0) {
+            double done;
+            int rc = sync_read(h, h->F.scal + SC_PCG_DONE, &done, 1);
+            if (rc) return rc;
+            if (done != 0.0) break;
+        }
+    }
+    enqueue_part_b(h, &L);
     CK(cudaGetLastError());
+    std::swap(h->F.p, h->F.pr);
+    h->parity ^= 1;
     h->sweeps++;
     h->launches += L;
+    return HFDIB_OK;
+}
+
+// The sweep as one CUDA graph: part A, a conditional while-node whose body is
+// one PCG iteration (ended from the device when |r| <= p_reltol |r0| or at
+// p_maxiter), part B.  Two graphs alternate the p / pr buffers.
+int build_graph(Ctx* h, int which) {
+    cudaStream_t s = h->stream;
+    cudaGraph_t graph;
+    CK(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle hc;
+    CK(cudaGraphConditionalHandleCreate(&hc, graph, 1, cudaGraphCondAssignDefault));
+    long long L = 0;
+    CK(cudaStreamBeginCaptureToGraph(s, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    enqueue_part_a(h, &L);
+    enqueue_pcg_start(h, hc, 1, &L);
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    CK(cudaStreamGetCaptureInfo(s, &st, nullptr, nullptr, &deps, nullptr, &ndeps));
+    std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
+    CK(cudaStreamEndCapture(s, &graph));
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = hc;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    CK(cudaGraphAddNode(&cnode, graph, dv.data(), nullptr, dv.size(), &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    long long Lb = 0;
+    enqueue_pcg_body(h, hc, 1, &Lb);
+    CK(cudaStreamEndCapture(s, &body));
+    CK(cudaStreamBeginCaptureToGraph(s, graph, &cnode, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+    enqueue_part_b(h, &L);
+    CK(cudaStreamEndCapture(s, &graph));
+    cudaGraphExec_t exec;
+    CK(cudaGraphInstantiate(&exec, graph, 0));
+    h->graph[which] = graph;
+    h->gexec[which] = exec;
+    h->graph_launches = L;
+    h->graph_body_launches = Lb;
+    return HFDIB_OK;
+}
+
+int run_sweep(Ctx* h) {
+    if (!h->use_graph) return run_sweep_host(h);
+    if (!h->gexec[h->parity]) {
+        int rc = build_graph(h, h->parity);
+        if (rc) { cudaGetLastError(); return rc; }
+    }
+    CK(cudaGraphLaunch(h->gexec[h->parity], h->stream));
+    std::swap(h->F.p, h->F.pr);
+    h->parity ^= 1;
+    h->sweeps++;
+    h->launches += h->graph_launches;
     return HFDIB_OK;
 }
 
@@ -253,11 +360,13 @@ void hfdib_default_options(hfdib_options* o) {
     o->n_u = 2;
     o->n_turb = 2;
     o->p_reltol = 0.01;
-    o->p_maxiter = 200;
+    o->p_maxiter = 50;
     o->precision = 0;
     o->precond = 1;
-    o->p_check = 1;
-    o->mg_coarse_sweeps = 20;
+    o->p_check = 0;
+    o->mg_coarse_sweeps = 4;
+    o->graph = 1;
+    o->freeze_switch = 0;
 }
 
 const char* hfdib_error_string(int code) {
@@ -296,22 +405,37 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
         return HFDIB_ERR_INVALID_ARG;
     if (o.n_u < 1 || o.n_turb < 1 || o.p_maxiter < 0 || !(o.p_reltol >= 0)) return HFDIB_ERR_INVALID_ARG;
     if (o.precond < 0 || o.precond > 1 || o.p_check < 0 || o.mg_coarse_sweeps < 0) return HFDIB_ERR_INVALID_ARG;
+    if (o.precision != 0) return HFDIB_ERR_INVALID_ARG;
+    if (o.p_maxiter > 100000 || o.freeze_switch < 0) return HFDIB_ERR_INVALID_ARG;
 
     Ctx* h = new (std::nothrow) Ctx();
     if (!h) return HFDIB_ERR_OOM;
     h->stream = (cudaStream_t)stream;
+    if (!h->stream) {
+        // graph capture needs a real stream: own a non-blocking one
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) { delete h; return HFDIB_ERR_CUDA; }
+        h->own_stream = true;
+    }
     h->opt = o;
     h->bc = *bc;
+    h->coarse_sweeps = o.mg_coarse_sweeps > 0 ? o.mg_coarse_sweeps : 4;
+    h->use_graph = (o.graph != 0 && o.p_check == 0) ? 1 : 0;
     h->model = model;
     Grid& g = h->g;
     g.nx = grid->nx; g.ny = grid->ny; g.nz = grid->nz;
     g.dims = grid->nz == 1 ? 2 : 3;
     g.N = N;
+    g.iN = 1.0 / (double)N;
     g.n[0] = g.nx; g.n[1] = g.ny; g.n[2] = g.nz;
     g.D[0] = grid->dx; g.D[1] = grid->dy; g.D[2] = grid->dz;
     g.o[0] = grid->x0; g.o[1] = grid->y0; g.o[2] = grid->z0;
     g.S[0] = g.D[1] * g.D[2]; g.S[1] = g.D[0] * g.D[2]; g.S[2] = g.D[0] * g.D[1];
     g.V = g.D[0] * g.D[1] * g.D[2];
+    for (int d = 0; d < 3; ++d) {
+        g.SoD[d] = g.S[d] / g.D[d];
+        g.SoHD[d] = g.S[d] / (0.5 * g.D[d]);
+        g.iD[d] = 1.0 / g.D[d];
+    }
     // V^(1/3): sqrt(dx*dy) on one-cell-thick 2D grids
     g.h = g.dims == 2 ? sqrt(g.D[0] * g.D[1]) : pow(g.D[0] * g.D[1] * g.D[2], 1.0 / 3.0);
     for (int s = 0; s < 6; ++s) g.kind[s] = bc->face[s];
@@ -325,6 +449,8 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
     Params& P = h->P;
     P.model = model;
     P.urf_u = o.urf_u; P.urf_p = o.urf_p; P.urf_turb = o.urf_turb;
+    P.iurf_u = 1.0 / o.urf_u; P.iurf_t = 1.0 / o.urf_turb;
+    P.rlx_u = (1.0 - o.urf_u) / o.urf_u; P.rlx_t = (1.0 - o.urf_turb) / o.urf_turb;
     // inlet turbulence, Eq. (bcspkoein): k = 1.5 (U I)^2, eps = C_nu k^1.5 / l_t, omega = eps/(C_nu k)
     double U = sqrt(bc->u_in[0] * bc->u_in[0] + bc->u_in[1] * bc->u_in[1] + bc->u_in[2] * bc->u_in[2]);
     double kin = 1.5 * (U * bc->I_in) * (U * bc->I_in);
@@ -362,7 +488,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
         Level& l0 = M.lv[0];
         l0.nx = g.nx; l0.ny = g.ny; l0.nz = g.nz; l0.N = N;
         for (int d = 0; d < 3; ++d) A(l0.cf[d], g.nface[d]);
-        A(l0.diag, N);
+        A(l0.diag, N); A(l0.idg, N);
         l0.x = F.z;
         l0.b = F.r;
         M.nl = 1;
@@ -377,7 +503,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
             A(c.cf[0], (long long)(c.nx + 1) * c.ny * c.nz);
             A(c.cf[1], (long long)c.nx * (c.ny + 1) * c.nz);
             A(c.cf[2], (long long)c.nx * c.ny * (c.nz + 1));
-            A(c.diag, c.N); A(c.x, c.N); A(c.b, c.N);
+            A(c.diag, c.N); A(c.idg, c.N); A(c.x, c.N); A(c.b, c.N);
             M.lv[M.nl++] = c;
         }
         h->tail_from = M.nl;
@@ -589,8 +715,49 @@ int hfdib_set_state(hfdib_handle hh, const void* buf, size_t bytes) {
         CK(cudaMemcpyAsync(a.first, p, a.second * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         p += a.second * sizeof(double);
     }
+    double ns = (double)hd[5];
+    CK(cudaMemcpyAsync(h->F.scal + SC_NSWEEP, &ns, sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->sweeps = hd[5];
+    return HFDIB_OK;
+}
+
+int hfdib_profile_sweeps(hfdib_handle hh, int n_sweeps, double* total_us, int64_t* calls, int n_classes) {
+    Ctx* h = (Ctx*)hh;
+    if (!h || n_sweeps < 0 || !total_us || !calls || n_classes < HFDIB_K_COUNT) return HFDIB_ERR_INVALID_ARG;
+    for (int q = 0; q < n_classes; ++q) { total_us[q] = 0.0; calls[q] = 0; }
+    h->prof.on = true;
+    h->prof.used = 0;
+    h->prof.marks.clear();
+    int rc = HFDIB_OK;
+    for (int n = 0; n < n_sweeps && rc == HFDIB_OK; ++n) rc = run_sweep_host(h);
+    h->prof.on = false;
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(h->stream));
+    for (auto& m : h->prof.marks) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, m.second.first, m.second.second));
+        total_us[m.first] += 1e3 * (double)ms;
+        calls[m.first] += 1;
+    }
+    h->prof.marks.clear();
+    return HFDIB_OK;
+}
+
+int hfdib_get_launch_counts(hfdib_handle hh, int64_t* per_sweep, int64_t* per_pcg_iteration) {
+    Ctx* h = (Ctx*)hh;
+    if (!h) return HFDIB_ERR_INVALID_ARG;
+    long long La = 0, Lb = 0, Lp = 0;
+    // count by enqueueing nothing: replicate the schedule's arithmetic
+    bool turb = h->model != HFDIB_LAMINAR;
+    int jac = h->opt.precond == 0;
+    int tf = h->tail_from;
+    La = (turb ? 1 : 0) + 4 + 2 * h->opt.n_u + 2 + (1 + (tf - 1) + (tf < h->mg.nl ? 1 : 0)) + 1 +
+         (jac ? 0 : 5 * tf + 1) + 1;
+    Lb = 1 + (turb ? 4 + 2 * h->opt.n_turb + 2 + 2 * h->opt.n_turb + 1 : 0) + 1;
+    Lp = 3 + (jac ? 0 : 5 * tf + 1);
+    if (per_sweep) *per_sweep = La + Lb;
+    if (per_pcg_iteration) *per_pcg_iteration = Lp;
     return HFDIB_OK;
 }
 

@@ -44,10 +44,14 @@ constexpr int BLOCK = 256;
 struct Grid {
     int nx, ny, nz, dims;
     long long N;
+    double iN;       // 1/N
     int n[3];
     double D[3];     // spacings
     double o[3];     // origin
     double S[3];     // face areas
+    double SoD[3];   // S/Delta (interior face diffusion factor)
+    double SoHD[3];  // S/(Delta/2) (boundary face diffusion factor)
+    double iD[3];    // 1/Delta
     double V, h;     // cell volume, V^(1/3)
     int kind[6];     // hfdib_bc_kind per side
     double u_in[3], u_s[3], p_out;
@@ -59,11 +63,16 @@ struct Grid {
 __host__ __device__ inline int tag_of(uint16_t f) { return f & F_TAG; }
 __host__ __device__ inline bool closed_side(uint16_t f, int s) { return (f >> (F_CLOSED_SHIFT + s)) & 1u; }
 
+// cell counts stay below 2^31 (checked at create), so 32-bit division suffices
 __device__ inline void cell_ijk(const Grid& g, long long c, int& i, int& j, int& k) {
-    i = (int)(c % g.nx);
-    long long r = c / g.nx;
-    j = (int)(r % g.ny);
-    k = (int)(r / g.ny);
+    unsigned int cc = (unsigned int)c, nx = (unsigned int)g.nx;
+    unsigned int r = cc / nx;
+    i = (int)(cc - r * nx);
+    if (g.nz == 1) { j = (int)r; k = 0; return; }
+    unsigned int ny = (unsigned int)g.ny;
+    unsigned int kk = r / ny;
+    j = (int)(r - kk * ny);
+    k = (int)kk;
 }
 
 // index of the low face of cell (i,j,k) in direction d; the high face is +fstride

@@ -52,7 +52,7 @@ __device__ void mom_row(const Grid& g, const Fields& F, long long c, int i, int 
             if (interior(g, d, side, i, j, k)) {
                 long long nc = nbr_cell(g, c, d, side);
                 double nuN = g.nu + F.nut[nc];
-                double Dif = 0.5 * (nuP + nuN) * g.S[d] / g.D[d];
+                double Dif = 0.5 * (nuP + nuN) * g.SoD[d];
                 R.a[s] = fmin(Fout, 0.0) - Dif;
                 R.nb[s] = nc;
                 R.has[s] = true;
@@ -65,7 +65,7 @@ __device__ void mom_row(const Grid& g, const Fields& F, long long c, int i, int 
                 for (int q = 0; q < g.dims; ++q) {
                     double val;
                     if (vel_fixed(g, f, s, q, val)) {
-                        double coef = nuP * g.S[d] / (0.5 * g.D[d]) + fmax(-Fout, 0.0);
+                        double coef = nuP * g.SoHD[d] + fmax(-Fout, 0.0);
                         R.aP[q] += coef;
                         R.bnd[q] += coef * val;
                     }
@@ -84,7 +84,7 @@ __device__ inline double grad_p(const Grid& g, const double* p, long long c, int
     else lo = p_fixed(g, 2 * d) ? g.p_out : pP;
     if (interior(g, d, 1, i, j, k)) hi = 0.5 * (pP + p[c + g.stride[d]]);
     else hi = p_fixed(g, 2 * d + 1) ? g.p_out : pP;
-    return (hi - lo) / g.D[d];
+    return (hi - lo) * g.iD[d];
 }
 
 // relaxed pressure p + a (pn - p), evaluated on the fly
@@ -164,7 +164,7 @@ __global__ void k_grad_u(Grid g, Fields F) {
             else lo = vel_fixed(g, f, 2 * a, b, val) ? val : uP;
             if (interior(g, a, 1, i, j, k)) hi = 0.5 * (uP + u[c + g.stride[a]]);
             else hi = vel_fixed(g, f, 2 * a + 1, b, val) ? val : uP;
-            F.G[(long long)(3 * a + b) * g.N + c] = (hi - lo) / g.D[a];
+            F.G[(long long)(3 * a + b) * g.N + c] = (hi - lo) * g.iD[a];
         }
     }
 }
@@ -206,7 +206,7 @@ __global__ void k_mom_asm(Grid g, Params P, Fields F) {
             double gp = grad_p(g, F.p, c, q, i, j, k);
             double uold = F.u[q][c];
             double bfull = b0 - gp * g.V;
-            F.bm[q][c] = b0 + (1.0 - P.urf_u) / P.urf_u * R.aP[q] * uold - gp * g.V;
+            F.bm[q][c] = b0 + P.rlx_u * R.aP[q] * uold - gp * g.V;
             // initial guess of the predictor: u_old, with the imposed rows
             // already at their imposed values (so an exact solution of the
             // sweep's system is left unchanged by the smoother)
@@ -223,7 +223,7 @@ __global__ void k_mom_asm(Grid g, Params P, Fields F) {
                     Ax += R.a[s] * xN;
                     A1 += R.a[s];
                 }
-                double xbar = F.scal[SC_SUM_U + q] / (double)g.N;
+                double xbar = F.scal[SC_SUM_U + q] * g.iN;
                 red[3 * q + 0] = fabs(bfull - Ax);
                 red[3 * q + 1] = fabs(Ax - A1 * xbar);
                 red[3 * q + 2] = fabs(bfull - A1 * xbar);
@@ -257,7 +257,7 @@ __global__ void k_mom_smooth(Grid g, Params P, Fields F, int colour) {
         double acc = F.bm[q][c];
         for (int s = 0; s < 2 * g.dims; ++s)
             if (R.has[s]) acc -= R.a[s] * F.us[q][R.nb[s]];
-        F.us[q][c] = acc / (R.aP[q] / P.urf_u);
+        F.us[q][c] = acc * P.urf_u / R.aP[q];
     }
 }
 
@@ -272,17 +272,18 @@ __global__ void k_hbya(Grid g, Params P, Fields F) {
     mom_row(g, F, c, i, j, k, f, R);
     double aavg = 0.0;
     double aPr[3];
-    for (int q = 0; q < g.dims; ++q) { aPr[q] = R.aP[q] / P.urf_u; aavg += aPr[q]; }
-    aavg = aavg / (double)g.dims;
+    for (int q = 0; q < g.dims; ++q) { aPr[q] = R.aP[q] * P.iurf_u; aavg += aPr[q]; }
+    aavg = aavg * (g.dims == 2 ? 0.5 : (1.0 / 3.0));
+    double ia = 1.0 / aavg;
     for (int q = 0; q < g.dims; ++q) {
         double br = F.bm[q][c] + grad_p(g, F.p, c, q, i, j, k) * g.V;
         double off = 0.0;
         for (int s = 0; s < 2 * g.dims; ++s)
             if (R.has[s]) off += R.a[s] * F.us[q][R.nb[s]];
         double H = br - off - (aPr[q] - aavg) * F.us[q][c];
-        F.HbyA[q][c] = H / aavg;
+        F.HbyA[q][c] = H * ia;
     }
-    F.rAU[c] = g.V / aavg;
+    F.rAU[c] = g.V * ia;
 }
 
 // ---------------------------------------------------------------- phiHbyA
@@ -351,7 +352,7 @@ __global__ void k_update(Grid g, Params P, Fields F, Level L0) {
             else lo = p_fixed(g, 2 * d) ? g.p_out : prP;
             if (interior(g, d, 1, i, j, k)) hi = 0.5 * (prP + prelax(F.p, F.pn, c + g.stride[d], a));
             else hi = p_fixed(g, 2 * d + 1) ? g.p_out : prP;
-            double gp = (hi - lo) / g.D[d];
+            double gp = (hi - lo) * g.iD[d];
             F.u[d][c] = F.HbyA[d][c] - F.rAU[c] * gp;
         }
         F.pr[c] = prP;
@@ -360,21 +361,33 @@ __global__ void k_update(Grid g, Params P, Fields F, Level L0) {
 }
 
 // ---------------------------------------------------------------- sweep end
-__global__ void k_sweep_end(Fields F, int dims, int model, double p_iters, double* res_out) {
+__global__ void k_sweep_end(Fields F, int dims, int model, double* res_out, double* hist, int nhist) {
     double* s = F.scal;
     auto sc = [](double r, double n1, double n2) { return r / ((n1 + n2) + 1e-20); };
+    double res[HFDIB_NRES];
     for (int q = 0; q < 3; ++q)
-        res_out[HFDIB_RES_UX + q] = q < dims ? sc(s[SC_RES_U + 3 * q], s[SC_RES_U + 3 * q + 1], s[SC_RES_U + 3 * q + 2]) : 0.0;
-    res_out[HFDIB_RES_P] = sc(s[SC_PCG_INIT + 3], s[SC_PCG_INIT + 4], s[SC_PCG_INIT + 5]);
+        res[HFDIB_RES_UX + q] = q < dims ? sc(s[SC_RES_U + 3 * q], s[SC_RES_U + 3 * q + 1], s[SC_RES_U + 3 * q + 2]) : 0.0;
+    res[HFDIB_RES_P] = sc(s[SC_PCG_INIT + 3], s[SC_PCG_INIT + 4], s[SC_PCG_INIT + 5]);
     if (model != HFDIB_LAMINAR) {
-        res_out[HFDIB_RES_EPSW] = sc(s[SC_RES_W], s[SC_RES_W + 1], s[SC_RES_W + 2]);
-        res_out[HFDIB_RES_K] = sc(s[SC_RES_K], s[SC_RES_K + 1], s[SC_RES_K + 2]);
+        res[HFDIB_RES_EPSW] = sc(s[SC_RES_W], s[SC_RES_W + 1], s[SC_RES_W + 2]);
+        res[HFDIB_RES_K] = sc(s[SC_RES_K], s[SC_RES_K + 1], s[SC_RES_K + 2]);
     } else {
-        res_out[HFDIB_RES_EPSW] = 0.0;
-        res_out[HFDIB_RES_K] = 0.0;
+        res[HFDIB_RES_EPSW] = 0.0;
+        res[HFDIB_RES_K] = 0.0;
     }
-    res_out[HFDIB_RES_CONT] = s[SC_CONT];
-    res_out[HFDIB_RES_PITER] = p_iters;
+    res[HFDIB_RES_CONT] = s[SC_CONT];
+    res[HFDIB_RES_PITER] = s[SC_PCG_ITERS];
+    res[HFDIB_RES_NLAM] = s[SC_NLAM];
+    res[HFDIB_RES_NSWITCH] = s[SC_NSWITCH];
+    s[SC_NLAM] = 0.0;
+    s[SC_NSWITCH] = 0.0;
+    long long n = (long long)s[SC_NSWEEP];
+    int slot = (int)(n % nhist);
+    for (int q = 0; q < HFDIB_NRES; ++q) {
+        res_out[q] = res[q];
+        hist[slot * HFDIB_NRES + q] = res[q];
+    }
+    s[SC_NSWEEP] = (double)(n + 1);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -403,9 +416,9 @@ void launch_phiH(const Grid& g, const Fields& F, cudaStream_t s) {
 void launch_update(const Grid& g, const Params& P, const Fields& F, const Level& L0, cudaStream_t s) {
     k_update<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F, L0);
 }
-void launch_sweep_end(const Params& P, const Fields& F, int dims, double p_iters, double* res_out,
+void launch_sweep_end(const Params& P, const Fields& F, int dims, double* res_out, double* hist, int nhist,
                       cudaStream_t s) {
-    k_sweep_end<<<1, 1, 0, s>>>(F, dims, P.model, p_iters, res_out);
+    k_sweep_end<<<1, 1, 0, s>>>(F, dims, P.model, res_out, hist, nhist);
 }
 
 }  // namespace hf

@@ -306,7 +306,7 @@ __device__ inline double interp_cell(const Grid& g, const double* f, const int* 
     return val;
 }
 
-__global__ void k_imposed(Grid g, int model, BcList bl, uint16_t* __restrict__ flags,
+__global__ void k_imposed(Grid g, int model, int freeze, BcList bl, uint16_t* __restrict__ flags, double* scal,
                           const double* __restrict__ ux, const double* __restrict__ uy,
                           const double* __restrict__ uz, const double* __restrict__ kf,
                           double* __restrict__ uibx, double* __restrict__ uiby, double* __restrict__ uibz,
@@ -324,8 +324,16 @@ __global__ void k_imposed(Grid g, int model, BcList bl, uint16_t* __restrict__ f
     double ut = pow(C_MU, 0.25) * sqrt(kP);
     double yplus = ye * ut / g.nu;
     bool lamb = turb ? (yplus <= YPLUS_LAM) : true;
+    int old = bl.lamb[q];
+    // opt-in (not in the paper): from sweep `freeze` on a cell may leave the
+    // laminar branch but not re-enter it (ends limit cycles of the switch)
+    if (turb && freeze > 0 && scal[SC_NSWEEP] >= (double)freeze) lamb = lamb && (old != 0);
     bl.yplus[q] = yplus;
     bl.lamb[q] = lamb ? 1 : 0;
+    // diagnostics: branch population and changes (integer-valued sums are
+    // exact in any order)
+    if (lamb) atomicAdd(scal + SC_NLAM, 1.0);
+    if (old != (lamb ? 1 : 0)) atomicAdd(scal + SC_NSWITCH, 1.0);
     uint16_t f = flags[c];
     f = lamb ? (uint16_t)(f | F_AU) : (uint16_t)(f & ~F_AU);
     flags[c] = f;
@@ -392,11 +400,11 @@ void launch_max_not_ic(const Grid& g, const uint16_t* flags, const double* w, do
                        unsigned int* counter, double* out, cudaStream_t s) {
     k_max_not_ic<<<nblocks(g.N), BLOCK, 0, s>>>(g, flags, w, partials, counter, out);
 }
-void launch_imposed(const Grid& g, int model, const BcList& bl, uint16_t* flags, const double* ux,
+void launch_imposed(const Grid& g, int model, int freeze, const BcList& bl, uint16_t* flags, double* scal, const double* ux,
                     const double* uy, const double* uz, const double* k, double* uibx, double* uiby,
                     double* uibz, double* kib, double* wib, cudaStream_t s) {
     if (bl.nbc == 0) return;
-    k_imposed<<<nblocks(bl.nbc), BLOCK, 0, s>>>(g, model, bl, flags, ux, uy, uz, k, uibx, uiby, uibz,
+    k_imposed<<<nblocks(bl.nbc), BLOCK, 0, s>>>(g, model, freeze, bl, flags, scal, ux, uy, uz, k, uibx, uiby, uibz,
                                                 kib, wib);
 }
 void launch_export_bc(const BcList& bl, long long* ints, long long* ints2, double* reals, cudaStream_t s) {

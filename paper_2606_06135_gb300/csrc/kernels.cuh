@@ -32,8 +32,18 @@ enum {
     SC_RES_W = 20,               // 3
     SC_RES_K = 23,               // 3
     SC_CONT = 26,
-    SC_PCG_RZRR = 28,            // [r.z, r.r] ping-pong pair at 28/29 and 30/31
+    SC_PCG_RZ = 28,              // r.z of the current iterate
+    SC_PCG_RZP = 29,             // previous r.z
+    SC_PCG_RZN = 30,             // r.z of the new residual   (RZN, RR adjacent)
+    SC_PCG_RR = 31,              // r.r of the new residual
     SC_PCG_DQ = 32,
+    SC_PCG_IT = 33,              // iteration counter
+    SC_PCG_DONE = 34,            // 1: converged or capped
+    SC_PCG_TOL2 = 35,            // p_reltol^2 |r0|^2
+    SC_PCG_ITERS = 36,           // iterations of the last solve
+    SC_NSWEEP = 37,              // sweeps run (history slot)
+    SC_NLAM = 38,                // bc cells in the laminar branch this sweep
+    SC_NSWITCH = 39,             // bc cells whose branch changed
     SC_PCG_INIT = 40,            // r0.z0, r0.r0, b.b, then the 3 scaled-residual sums of p
     SC_NSCAL = 64
 };
@@ -86,11 +96,12 @@ struct Level {
     long long N;
     double* cf[3];   // face coefficients, face layout of the level
     double* diag;
+    double* idg;     // 1/diag (0 where diag is 0)
     double* x;       // correction (level 0: z)
     double* b;       // right-hand side (level 0: r)
 };
 constexpr int MAX_LEVELS = 16;
-constexpr long long TAIL_CELLS = 16384;
+constexpr long long TAIL_CELLS = 4096;
 struct MgLevels {
     int nl;
     Level lv[MAX_LEVELS];
@@ -99,6 +110,8 @@ struct MgLevels {
 struct Params {
     int model;
     double urf_u, urf_p, urf_turb;
+    double iurf_u, iurf_t;   // 1/urf
+    double rlx_u, rlx_t;     // (1 - urf)/urf
     double k_in, w_in;   // inlet k and eps (k-eps) or omega (SST)
 };
 
@@ -110,7 +123,7 @@ void launch_bc_geometry(const Grid& g, const double* lam, const uint16_t* flags,
                         cudaStream_t s);
 void launch_max_not_ic(const Grid& g, const uint16_t* flags, const double* w, double* partials,
                        unsigned int* counter, double* out, cudaStream_t s);
-void launch_imposed(const Grid& g, int model, const BcList& bl, uint16_t* flags, const double* ux,
+void launch_imposed(const Grid& g, int model, int freeze, const BcList& bl, uint16_t* flags, double* scal, const double* ux,
                     const double* uy, const double* uz, const double* k, double* uibx, double* uiby,
                     double* uibz, double* kib, double* wib, cudaStream_t s);
 void launch_export_bc(const BcList& bl, long long* ints, long long* ints2, double* reals, cudaStream_t s);
@@ -124,16 +137,18 @@ void launch_mom_smooth(const Grid& g, const Params& P, const Fields& F, int colo
 void launch_hbya(const Grid& g, const Params& P, const Fields& F, cudaStream_t s);
 void launch_phiH(const Grid& g, const Fields& F, cudaStream_t s);
 void launch_update(const Grid& g, const Params& P, const Fields& F, const Level& L0, cudaStream_t s);
+void launch_sweep_end(const Params& P, const Fields& F, int dims, double* res_out, double* hist, int nhist,
+                      cudaStream_t s);
 
 // pressure.cu
 void launch_p_coef(const Grid& g, const MgLevels& M, const double* rAU, int ntail_from, cudaStream_t s);
 void launch_vcycle(const Grid& g, const MgLevels& M, int ntail_from, const Fields& F, double* dot_out,
                    int coarse_sweeps, cudaStream_t s);
 void launch_pcg_init(const Grid& g, const Fields& F, const MgLevels& M, int jacobi, cudaStream_t s);
-void launch_pcg_A(const Grid& g, const Fields& F, const MgLevels& M, int it, cudaStream_t s);
-void launch_pcg_update(const Grid& g, const Fields& F, const MgLevels& M, int it, int jacobi, cudaStream_t s);
-void launch_sweep_end(const Params& P, const Fields& F, int dims, double p_iters, double* res_out,
-                      cudaStream_t s);
+void launch_pcg_start(const Fields& F, int jacobi, double reltol, int maxit, cudaGraphConditionalHandle h,
+                      int use_cond, cudaStream_t s);
+void launch_pcg_body(const Grid& g, const Fields& F, const MgLevels& M, int ntail_from, int jacobi,
+                     int coarse_sweeps, int maxit, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s);
 
 // turb.cu
 void launch_turb_prep(const Grid& g, const Params& P, const Fields& F, cudaStream_t s);

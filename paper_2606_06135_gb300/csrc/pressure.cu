@@ -34,10 +34,14 @@ __device__ inline long long lv_cstride(const Level& L, int d) {
     return d == 0 ? 1 : (d == 1 ? L.nx : (long long)L.nx * L.ny);
 }
 __device__ inline void lv_ijk(const Level& L, long long c, int& i, int& j, int& k) {
-    i = (int)(c % L.nx);
-    long long r = c / L.nx;
-    j = (int)(r % L.ny);
-    k = (int)(r / L.ny);
+    unsigned int cc = (unsigned int)c, nx = (unsigned int)L.nx;
+    unsigned int r = cc / nx;
+    i = (int)(cc - r * nx);
+    if (L.nz == 1) { j = (int)r; k = 0; return; }
+    unsigned int ny = (unsigned int)L.ny;
+    unsigned int kk = r / ny;
+    j = (int)(r - kk * ny);
+    k = (int)kk;
 }
 
 // (A x)_P = diag x_P - sum over interior faces cf x_N
@@ -66,15 +70,16 @@ __global__ void k_p_coef(Grid g, Level L, const double* __restrict__ rAU) {
         long long fl = lv_face(L, d, i, j, k);
         long long fs = lv_fstride(L, d);
         double clo, chi;
-        if (idx[d] > 0) clo = 0.5 * (rAU[c] + rAU[c - g.stride[d]]) * g.S[d] / g.D[d];
-        else clo = p_fixed(g, 2 * d) ? rAU[c] * g.S[d] / (0.5 * g.D[d]) : 0.0;
-        if (idx[d] < g.n[d] - 1) chi = 0.5 * (rAU[c] + rAU[c + g.stride[d]]) * g.S[d] / g.D[d];
-        else chi = p_fixed(g, 2 * d + 1) ? rAU[c] * g.S[d] / (0.5 * g.D[d]) : 0.0;
+        if (idx[d] > 0) clo = 0.5 * (rAU[c] + rAU[c - g.stride[d]]) * g.SoD[d];
+        else clo = p_fixed(g, 2 * d) ? rAU[c] * g.SoHD[d] : 0.0;
+        if (idx[d] < g.n[d] - 1) chi = 0.5 * (rAU[c] + rAU[c + g.stride[d]]) * g.SoD[d];
+        else chi = p_fixed(g, 2 * d + 1) ? rAU[c] * g.SoHD[d] : 0.0;
         L.cf[d][fl] = clo;
         if (idx[d] == g.n[d] - 1) L.cf[d][fl + fs] = chi;
         diag += clo + chi;
     }
     L.diag[c] = diag;
+    L.idg[c] = diag > 0.0 ? 1.0 / diag : 0.0;
 }
 
 // coarse level coefficients: half the sum of the covered fine faces
@@ -125,6 +130,7 @@ __device__ void coarsen_cell(const Level& F, const Level& Cc, int dims, long lon
             diag += 0.5 * sum;
         }
     Cc.diag[C] = diag;
+    Cc.idg[C] = diag > 0.0 ? 1.0 / diag : 0.0;
 }
 
 __global__ void k_coarsen(Level F, Level Cc, int dims) {
@@ -139,10 +145,36 @@ __device__ inline void smooth_cell(const Level& L, int dims, long long c, int co
     int i, j, k;
     lv_ijk(L, c, i, j, k);
     if (((i + j + k) & 1) != colour) return;
-    double dg = L.diag[c];
     double v = L.b[c];
     if (!zero_init) v += lv_offsum(L, dims, L.x, c, i, j, k);
-    L.x[c] = dg > 0.0 ? v / dg : 0.0;
+    L.x[c] = v * L.idg[c];
+}
+
+// prolongation fused with the first (black) post-smoothing half sweep: a
+// black cell reads red neighbours corrected on the fly; red cells keep stale
+// values that the following red half sweep overwrites without reading them
+__device__ inline void prolong_smooth_black(const Level& L, const Level& Cc, int dims, long long c) {
+    int i, j, k;
+    lv_ijk(L, c, i, j, k);
+    if (((i + j + k) & 1) != 1) return;
+    int idx[3] = {i, j, k};
+    int nn[3] = {L.nx, L.ny, L.nz};
+    double acc = L.b[c];
+    for (int d = 0; d < dims; ++d) {
+        long long fl = lv_face(L, d, i, j, k);
+        long long cs = lv_cstride(L, d);
+        for (int side = 0; side < 2; ++side) {
+            if (side == 0 && idx[d] == 0) continue;
+            if (side == 1 && idx[d] == nn[d] - 1) continue;
+            int ni[3] = {i, j, k};
+            ni[d] += side ? 1 : -1;
+            long long nc = side ? c + cs : c - cs;
+            long long C = ((long long)(ni[2] >> 1) * Cc.ny + (ni[1] >> 1)) * Cc.nx + (ni[0] >> 1);
+            double cfv = L.cf[d][fl + (side ? lv_fstride(L, d) : 0)];
+            acc += cfv * (L.x[nc] + Cc.x[C]);
+        }
+    }
+    L.x[c] = acc * L.idg[c];
 }
 
 // residual of the children, summed into the parent's right-hand side
@@ -169,7 +201,8 @@ __device__ inline void prolong_cell(const Level& F, const Level& Cc, long long c
     F.x[c] += Cc.x[C];
 }
 
-__global__ void k_smooth(Level L, int dims, int colour, int zero_init) {
+__global__ void k_smooth(Level L, int dims, int colour, int zero_init, const double* done) {
+    if (*done != 0.0) return;
     long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= L.N) return;
     smooth_cell(L, dims, c, colour, zero_init != 0);
@@ -177,7 +210,8 @@ __global__ void k_smooth(Level L, int dims, int colour, int zero_init) {
 
 // last post-smoothing half sweep of the finest level, fused with r.z
 __global__ void k_smooth_dot(Level L, int dims, int colour, const double* __restrict__ r, double* partials,
-                             unsigned int* counter, double* out) {
+                             unsigned int* counter, double* out, const double* done) {
+    if (*done != 0.0) return;
     long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double v[1] = {0.0};
     if (c < L.N) {
@@ -187,13 +221,22 @@ __global__ void k_smooth_dot(Level L, int dims, int colour, const double* __rest
     grid_reduce<1, false>(v, partials, counter, out);
 }
 
-__global__ void k_restrict(Level F, Level Cc, int dims) {
+__global__ void k_prolong_black(Level L, Level Cc, int dims, const double* done) {
+    if (*done != 0.0) return;
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= L.N) return;
+    prolong_smooth_black(L, Cc, dims, c);
+}
+
+__global__ void k_restrict(Level F, Level Cc, int dims, const double* done) {
+    if (*done != 0.0) return;
     long long C = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (C >= Cc.N) return;
     restrict_cell(F, Cc, dims, C);
 }
 
-__global__ void k_prolong(Level F, Level Cc) {
+__global__ void k_prolong(Level F, Level Cc, const double* done) {
+    if (*done != 0.0) return;
     long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= F.N) return;
     prolong_cell(F, Cc, c);
@@ -212,7 +255,9 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_coarsen(MgLevels M, int d
     }
 }
 
-__global__ void __launch_bounds__(TAIL_THREADS) k_tail_cycle(MgLevels M, int dims, int l0, int coarse_sweeps) {
+__global__ void __launch_bounds__(TAIL_THREADS) k_tail_cycle(MgLevels M, int dims, int l0, int coarse_sweeps,
+                                                             const double* done) {
+    if (*done != 0.0) return;
     const int T = blockDim.x;
     // l0 is entered with b set (restricted by the caller); x is computed here
     for (int l = l0; l < M.nl - 1; ++l) {
@@ -243,9 +288,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_cycle(MgLevels M, int dim
     for (int l = M.nl - 2; l >= l0; --l) {
         const Level& L = M.lv[l];
         const Level& Cc = M.lv[l + 1];
-        for (long long c = threadIdx.x; c < L.N; c += T) prolong_cell(L, Cc, c);
-        __syncthreads();
-        for (long long c = threadIdx.x; c < L.N; c += T) smooth_cell(L, dims, c, 1, false);
+        for (long long c = threadIdx.x; c < L.N; c += T) prolong_smooth_black(L, Cc, dims, c);
         __syncthreads();
         for (long long c = threadIdx.x; c < L.N; c += T) smooth_cell(L, dims, c, 0, false);
         __syncthreads();
@@ -253,6 +296,11 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_cycle(MgLevels M, int dim
 }
 
 // ---------------------------------------------------------------- PCG
+// The iteration counter, r.z history and the convergence flag live in device
+// scalars, so the same kernels run host-driven or as the body of a graph
+// while-loop (k_pcg_next ends the loop through the conditional handle).
+__device__ inline bool pcg_done(const Fields& F) { return F.scal[SC_PCG_DONE] != 0.0; }
+
 // r = rhs - A p with rhs = -m div(phiHbyA) + outlet terms; Jacobi z; sums
 __global__ void k_pcg_init(Grid g, Fields F, Level L0, int jacobi) {
     long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -279,10 +327,11 @@ __global__ void k_pcg_init(Grid g, Fields F, Level L0, int jacobi) {
         double r = rhs - Ap;
         F.r[c] = r;
         F.d[0][c] = 0.0;
+        F.d[1][c] = 0.0;
         F.pn[c] = F.p[c];
         double z = 0.0;
         if (jacobi) { z = dg > 0.0 ? r / dg : 0.0; F.z[c] = z; }
-        double pbar = F.scal[SC_SUM_P] / (double)g.N;
+        double pbar = F.scal[SC_SUM_P] * g.iN;
         red[0] = r * z;
         red[1] = r * r;
         red[2] = rhs * rhs;
@@ -290,18 +339,33 @@ __global__ void k_pcg_init(Grid g, Fields F, Level L0, int jacobi) {
         red[4] = fabs(Ap - A1 * pbar);
         red[5] = fabs(rhs - A1 * pbar);
     }
+    // the initial V-cycle that follows must run: clear the flag of the last solve
+    if (blockIdx.x == 0 && threadIdx.x == 0) F.scal[SC_PCG_DONE] = 0.0;
     grid_reduce<6, false>(red, F.partials, F.counters + 3, F.scal + SC_PCG_INIT);
 }
 
-__device__ inline double pcg_rz(const Fields& F, int it) {
-    return it == 0 ? F.scal[SC_PCG_INIT] : F.scal[SC_PCG_RZRR + 2 * (it & 1)];
+// loop state after the initial preconditioning
+__global__ void k_pcg_start(Fields F, int jacobi, double reltol, int maxit, cudaGraphConditionalHandle hcond,
+                            int use_cond) {
+    double* s = F.scal;
+    double rr0 = s[SC_PCG_INIT + 1];
+    s[SC_PCG_RZ] = jacobi ? s[SC_PCG_INIT] : s[SC_PCG_RZN];
+    s[SC_PCG_RZP] = 1.0;
+    s[SC_PCG_IT] = 0.0;
+    s[SC_PCG_ITERS] = 0.0;
+    s[SC_PCG_TOL2] = reltol * reltol * rr0;
+    bool done = !(rr0 > 0.0) || maxit <= 0 || !isfinite(rr0);
+    s[SC_PCG_DONE] = done ? 1.0 : 0.0;
+    if (use_cond && done) cudaGraphSetConditional(hcond, 0);
 }
 
 // d = z + beta d_old (neighbours on the fly); q = A d; d.q
-__global__ void k_pcg_A(Grid g, Fields F, Level L0, int it) {
+__global__ void k_pcg_A(Grid g, Fields F, Level L0) {
+    if (pcg_done(F)) return;
     long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double red[1] = {0.0};
-    double beta = it == 0 ? 0.0 : pcg_rz(F, it) / pcg_rz(F, it - 1);
+    int it = (int)F.scal[SC_PCG_IT];
+    double beta = it == 0 ? 0.0 : F.scal[SC_PCG_RZ] / F.scal[SC_PCG_RZP];
     const double* dold = F.d[it & 1];
     double* dnew = F.d[(it + 1) & 1];
     if (c < g.N) {
@@ -329,12 +393,13 @@ __global__ void k_pcg_A(Grid g, Fields F, Level L0, int it) {
 }
 
 // alpha = r.z/d.q; p += alpha d; r -= alpha q; r.r (and Jacobi z, r.z)
-__global__ void k_pcg_update(Grid g, Fields F, Level L0, int it, int jacobi) {
+__global__ void k_pcg_update(Grid g, Fields F, Level L0, int jacobi) {
+    if (pcg_done(F)) return;
     long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double red[2] = {0.0, 0.0};
-    double rz = pcg_rz(F, it);
+    int it = (int)F.scal[SC_PCG_IT];
     double dq = F.scal[SC_PCG_DQ];
-    double alpha = dq != 0.0 ? rz / dq : 0.0;
+    double alpha = dq != 0.0 ? F.scal[SC_PCG_RZ] / dq : 0.0;
     const double* dn = F.d[(it + 1) & 1];
     if (c < g.N) {
         F.pn[c] += alpha * dn[c];
@@ -348,12 +413,32 @@ __global__ void k_pcg_update(Grid g, Fields F, Level L0, int it, int jacobi) {
             red[0] = r * z;
         }
     }
-    int slot = SC_PCG_RZRR + 2 * ((it + 1) & 1);
+    // [RZN, RR] are adjacent slots
     if (jacobi) {
-        grid_reduce<2, false>(red, F.partials, F.counters + 5, F.scal + slot);
+        grid_reduce<2, false>(red, F.partials, F.counters + 5, F.scal + SC_PCG_RZN);
     } else {
         double v[1] = {red[1]};
-        grid_reduce<1, false>(v, F.partials, F.counters + 5, F.scal + slot + 1);
+        grid_reduce<1, false>(v, F.partials, F.counters + 5, F.scal + SC_PCG_RR);
+    }
+}
+
+// shift r.z, count the iteration, test |r|^2 <= tol^2 |r0|^2 or the cap
+__global__ void k_pcg_next(Fields F, int maxit, cudaGraphConditionalHandle hcond, int use_cond) {
+    double* s = F.scal;
+    if (s[SC_PCG_DONE] != 0.0) {
+        if (use_cond) cudaGraphSetConditional(hcond, 0);
+        return;
+    }
+    s[SC_PCG_RZP] = s[SC_PCG_RZ];
+    s[SC_PCG_RZ] = s[SC_PCG_RZN];
+    double it = s[SC_PCG_IT] + 1.0;
+    s[SC_PCG_IT] = it;
+    s[SC_PCG_ITERS] = it;
+    double rr = s[SC_PCG_RR];
+    bool done = !(rr > s[SC_PCG_TOL2]) || it >= (double)maxit;
+    if (done) {
+        s[SC_PCG_DONE] = 1.0;
+        if (use_cond) cudaGraphSetConditional(hcond, 0);
     }
 }
 
@@ -365,45 +450,53 @@ void launch_p_coef(const Grid& g, const MgLevels& M, const double* rAU, int ntai
     if (ntail_from < M.nl) k_tail_coarsen<<<1, TAIL_THREADS, 0, s>>>(M, g.dims, ntail_from);
 }
 
-// z = B r (one V-cycle) with r.z written to *dot_out
+// z = B r (one V-cycle) with r.z written to *dot_out; skipped once the
+// solve has converged (device flag)
 void launch_vcycle(const Grid& g, const MgLevels& M, int ntail_from, const Fields& F, double* dot_out,
                    int coarse_sweeps, cudaStream_t s) {
     int dims = g.dims;
+    const double* done = F.scal + SC_PCG_DONE;
     if (M.nl == 1) {
         const Level& L = M.lv[0];
-        k_smooth<<<nblocks(L.N), BLOCK, 0, s>>>(L, dims, 0, 1);
-        k_smooth<<<nblocks(L.N), BLOCK, 0, s>>>(L, dims, 1, 0);
-        k_smooth<<<nblocks(L.N), BLOCK, 0, s>>>(L, dims, 1, 0);
-        k_smooth_dot<<<nblocks(L.N), BLOCK, 0, s>>>(L, dims, 0, F.r, F.partials, F.counters + 9, dot_out);
+        k_smooth<<<nblocks(L.N), BLOCK, 0, s>>>(L, dims, 0, 1, done);
+        k_smooth<<<nblocks(L.N), BLOCK, 0, s>>>(L, dims, 1, 0, done);
+        k_smooth<<<nblocks(L.N), BLOCK, 0, s>>>(L, dims, 1, 0, done);
+        k_smooth_dot<<<nblocks(L.N), BLOCK, 0, s>>>(L, dims, 0, F.r, F.partials, F.counters + 9, dot_out, done);
         return;
     }
     int lf = ntail_from;  // levels 0 .. lf-1 by grid launches
     for (int l = 0; l < lf; ++l) {
         const Level& L = M.lv[l];
-        k_smooth<<<nblocks(L.N), BLOCK, 0, s>>>(L, dims, 0, 1);
-        k_smooth<<<nblocks(L.N), BLOCK, 0, s>>>(L, dims, 1, 0);
-        if (l + 1 < M.nl) k_restrict<<<nblocks(M.lv[l + 1].N), BLOCK, 0, s>>>(L, M.lv[l + 1], dims);
+        k_smooth<<<nblocks(L.N), BLOCK, 0, s>>>(L, dims, 0, 1, done);
+        k_smooth<<<nblocks(L.N), BLOCK, 0, s>>>(L, dims, 1, 0, done);
+        if (l + 1 < M.nl) k_restrict<<<nblocks(M.lv[l + 1].N), BLOCK, 0, s>>>(L, M.lv[l + 1], dims, done);
     }
-    if (lf < M.nl) k_tail_cycle<<<1, TAIL_THREADS, 0, s>>>(M, dims, lf, coarse_sweeps);
+    if (lf < M.nl) k_tail_cycle<<<1, TAIL_THREADS, 0, s>>>(M, dims, lf, coarse_sweeps, done);
     for (int l = lf - 1; l >= 0; --l) {
         const Level& L = M.lv[l];
-        if (l + 1 < M.nl) k_prolong<<<nblocks(L.N), BLOCK, 0, s>>>(L, M.lv[l + 1]);
-        k_smooth<<<nblocks(L.N), BLOCK, 0, s>>>(L, dims, 1, 0);
+        if (l + 1 < M.nl) k_prolong_black<<<nblocks(L.N), BLOCK, 0, s>>>(L, M.lv[l + 1], dims, done);
+        else k_smooth<<<nblocks(L.N), BLOCK, 0, s>>>(L, dims, 1, 0, done);
         if (l == 0)
-            k_smooth_dot<<<nblocks(L.N), BLOCK, 0, s>>>(L, dims, 0, F.r, F.partials, F.counters + 9, dot_out);
+            k_smooth_dot<<<nblocks(L.N), BLOCK, 0, s>>>(L, dims, 0, F.r, F.partials, F.counters + 9, dot_out,
+                                                        done);
         else
-            k_smooth<<<nblocks(L.N), BLOCK, 0, s>>>(L, dims, 0, 0);
+            k_smooth<<<nblocks(L.N), BLOCK, 0, s>>>(L, dims, 0, 0, done);
     }
 }
 
 void launch_pcg_init(const Grid& g, const Fields& F, const MgLevels& M, int jacobi, cudaStream_t s) {
     k_pcg_init<<<nblocks(g.N), BLOCK, 0, s>>>(g, F, M.lv[0], jacobi);
 }
-void launch_pcg_A(const Grid& g, const Fields& F, const MgLevels& M, int it, cudaStream_t s) {
-    k_pcg_A<<<nblocks(g.N), BLOCK, 0, s>>>(g, F, M.lv[0], it);
+void launch_pcg_start(const Fields& F, int jacobi, double reltol, int maxit, cudaGraphConditionalHandle h,
+                      int use_cond, cudaStream_t s) {
+    k_pcg_start<<<1, 1, 0, s>>>(F, jacobi, reltol, maxit, h, use_cond);
 }
-void launch_pcg_update(const Grid& g, const Fields& F, const MgLevels& M, int it, int jacobi, cudaStream_t s) {
-    k_pcg_update<<<nblocks(g.N), BLOCK, 0, s>>>(g, F, M.lv[0], it, jacobi);
+void launch_pcg_body(const Grid& g, const Fields& F, const MgLevels& M, int ntail_from, int jacobi,
+                     int coarse_sweeps, int maxit, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
+    k_pcg_A<<<nblocks(g.N), BLOCK, 0, s>>>(g, F, M.lv[0]);
+    k_pcg_update<<<nblocks(g.N), BLOCK, 0, s>>>(g, F, M.lv[0], jacobi);
+    if (!jacobi) launch_vcycle(g, M, ntail_from, F, F.scal + SC_PCG_RZN, coarse_sweeps, s);
+    k_pcg_next<<<1, 1, 0, s>>>(F, maxit, h, use_cond);
 }
 
 }  // namespace hf

@@ -26,7 +26,7 @@ __device__ inline double grad_s(const Grid& g, const double* x, uint16_t f, doub
     else lo = scal_fixed(g, f, 2 * d) ? xin : xP;
     if (interior_t(g, d, 1, i, j, k)) hi = 0.5 * (xP + x[c + g.stride[d]]);
     else hi = scal_fixed(g, f, 2 * d + 1) ? xin : xP;
-    return (hi - lo) / g.D[d];
+    return (hi - lo) * g.iD[d];
 }
 
 __device__ inline double sst_F2(double kk, double ww, double y, double nu) {
@@ -97,7 +97,9 @@ __global__ void k_bc_prod(Grid g, BcList bl, Fields F) {
         for (int a = 0; a < g.dims; ++a) comp += bl.n[3 * q + a] * F.G[(long long)(3 * a + b) * g.N + c];
         dudn2 += comp * comp;
     }
-    double yp = bl.yplus[q];
+    // y+ > y+_lam in the log branch; the max only matters for cells kept
+    // there by the one-way switch option
+    double yp = fmax(bl.yplus[q], YPLUS_LAM);
     double L = log(E_WF * yp);
     F.Pk[c] = KAPPA * g.nu * yp * dudn2 / (L * L);
 }
@@ -137,7 +139,7 @@ __device__ void scal_row(const Grid& g, const Fields& F, const double* gam, doub
             double Fout = side ? Fb : -Fb;
             if (interior_t(g, d, side, i, j, k)) {
                 long long nc = side ? c + g.stride[d] : c - g.stride[d];
-                double Dif = 0.5 * (gP + gam[nc]) * g.S[d] / g.D[d];
+                double Dif = 0.5 * (gP + gam[nc]) * g.SoD[d];
                 R.a[s] = fmin(Fout, 0.0) - Dif;
                 R.nb[s] = nc;
                 R.has[s] = true;
@@ -147,7 +149,7 @@ __device__ void scal_row(const Grid& g, const Fields& F, const double* gam, doub
                 R.nb[s] = c;
                 R.has[s] = false;
                 if (scal_fixed(g, f, s)) {
-                    double coef = gP * g.S[d] / (0.5 * g.D[d]) + fmax(-Fout, 0.0);
+                    double coef = gP * g.SoHD[d] + fmax(-Fout, 0.0);
                     R.aP += coef;
                     R.bnd += coef * xin;
                 }
@@ -171,8 +173,8 @@ __global__ void k_scal_asm(Grid g, Params P, Fields F, int eq) {
         double aP = R.aP + F.sp[c];
         double b = R.bnd + F.src[c];
         double xold = x[c];
-        F.bt[c] = b + (1.0 - P.urf_turb) / P.urf_turb * aP * xold;
-        F.diag[c] = aP / P.urf_turb;
+        F.bt[c] = b + P.rlx_t * aP * xold;
+        F.diag[c] = aP * P.iurf_t;
         double fv;
         if (scal_row_fixed(g, F, eq, c, fv)) {
             // imposed rows start at their imposed values (only neighbours'
@@ -187,7 +189,7 @@ __global__ void k_scal_asm(Grid g, Params P, Fields F, int eq) {
                 Ax += R.a[s] * xN;
                 A1 += R.a[s];
             }
-            double xbar = F.scal[eq == 0 ? SC_SUM_W : SC_SUM_K] / (double)g.N;
+            double xbar = F.scal[eq == 0 ? SC_SUM_W : SC_SUM_K] * g.iN;
             red[0] = fabs(b - Ax);
             red[1] = fabs(Ax - A1 * xbar);
             red[2] = fabs(b - A1 * xbar);

@@ -21,8 +21,8 @@ BC_KIND = {"inlet": 0, "outlet": 1, "slip": 2, "wall": 3, "empty": 4}
 SIDES = ("xmin", "xmax", "ymin", "ymax", "zmin", "zmax")
 FIELDS = {"ux": 0, "uy": 1, "uz": 2, "p": 3, "k": 4, "eps": 5, "omega": 6, "nut": 7,
           "phix": 8, "phiy": 9, "phiz": 10}
-RES_NAMES = ("Ux", "Uy", "Uz", "p", "epsw", "k", "cont", "p_iters")
-NRES = 8
+RES_NAMES = ("Ux", "Uy", "Uz", "p", "epsw", "k", "cont", "p_iters", "n_lam", "n_switch")
+NRES = 10
 STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "out of memory",
           -4: "not converged", -5: "diverged", -6: "state mismatch"}
 
@@ -51,7 +51,8 @@ class Options(C.Structure):
     _fields_ = [("urf_u", C.c_double), ("urf_p", C.c_double), ("urf_turb", C.c_double),
                 ("n_u", C.c_int32), ("n_turb", C.c_int32), ("p_reltol", C.c_double),
                 ("p_maxiter", C.c_int32), ("precision", C.c_int32), ("precond", C.c_int32),
-                ("p_check", C.c_int32), ("mg_coarse_sweeps", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("p_check", C.c_int32), ("mg_coarse_sweeps", C.c_int32), ("graph", C.c_int32),
+                ("freeze_switch", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 _LIB = None
@@ -59,7 +60,9 @@ _LIB = None
 EXPORTED = ("hfdib_default_options", "hfdib_create", "hfdib_simple_sweep", "hfdib_solve_steady",
             "hfdib_get_field", "hfdib_set_field", "hfdib_get_tags", "hfdib_get_bc_list",
             "hfdib_get_history", "hfdib_get_state", "hfdib_set_state", "hfdib_get_counters",
-            "hfdib_error_string", "hfdib_destroy")
+            "hfdib_error_string", "hfdib_destroy", "hfdib_profile_sweeps", "hfdib_get_launch_counts")
+KERNEL_CLASSES = ("imposed", "grad_u", "mom_asm", "mom_smooth", "hbya", "p_coef", "pcg", "vcycle0",
+                  "update", "turb_prep", "scal_asm", "scal_smooth", "turb_final", "sweep_end")
 
 
 def load_library(path=LIBPATH):
@@ -85,6 +88,10 @@ def load_library(path=LIBPATH):
     lib.hfdib_get_state.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
     lib.hfdib_set_state.argtypes = [vp, vp, C.c_size_t]
     lib.hfdib_get_counters.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
+    lib.hfdib_profile_sweeps.argtypes = [vp, i32, vp, vp, i32]
+    lib.hfdib_profile_sweeps.restype = C.c_int
+    lib.hfdib_get_launch_counts.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
+    lib.hfdib_get_launch_counts.restype = C.c_int
     lib.hfdib_error_string.argtypes = [i32]
     lib.hfdib_error_string.restype = C.c_char_p
     lib.hfdib_destroy.argtypes = [vp]
@@ -149,11 +156,17 @@ class Solver:
         self.face_counts = ((g["nx"] + 1) * g["ny"] * g["nz"], g["nx"] * (g["ny"] + 1) * g["nz"],
                             g["nx"] * g["ny"] * (g["nz"] + 1))
         self.model = MODELS[case["model"]]
-        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        lam = torch.as_tensor(np.ascontiguousarray(case["lam"], dtype=np.float64)).to(self.device)
-        ywall = case.get("ywall")
-        yw = (torch.as_tensor(np.ascontiguousarray(ywall, dtype=np.float64)).to(self.device)
-              if ywall is not None else None)
+        # a dedicated stream: sweeps are captured as CUDA graphs, which the
+        # legacy default stream does not allow
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        def dev_array(x):
+            if x is None:
+                return None
+            if isinstance(x, torch.Tensor):
+                return x.to(self.device, torch.float64).contiguous()
+            return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64)).to(self.device)
+        lam = dev_array(case["lam"])
+        yw = dev_array(case.get("ywall"))
         torch.cuda.synchronize(self.device)
         self._opts = default_options(**opts)
         h = C.c_void_p()
@@ -237,6 +250,21 @@ class Solver:
         s, l = C.c_int64(0), C.c_int64(0)
         _check(self.lib.hfdib_get_counters(self.h, C.byref(s), C.byref(l)), "hfdib_get_counters")
         return s.value, l.value
+
+    def profile(self, n_sweeps=3):
+        """Per kernel class: (total device microseconds, timed launch groups)."""
+        k = len(KERNEL_CLASSES)
+        us = np.zeros(k)
+        calls = np.zeros(k, dtype=np.int64)
+        _check(self.lib.hfdib_profile_sweeps(self.h, int(n_sweeps), us.ctypes.data, calls.ctypes.data, k),
+               "hfdib_profile_sweeps")
+        return {name: (float(us[i]), int(calls[i])) for i, name in enumerate(KERNEL_CLASSES)}
+
+    def launch_counts(self):
+        """(launches per sweep outside the pressure loop, launches per pressure iteration)."""
+        a, b = C.c_int64(0), C.c_int64(0)
+        _check(self.lib.hfdib_get_launch_counts(self.h, C.byref(a), C.byref(b)), "hfdib_get_launch_counts")
+        return a.value, b.value
 
     def get_state(self):
         n = C.c_size_t(0)
