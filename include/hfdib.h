@@ -39,7 +39,8 @@ typedef enum {
     HFDIB_ERR_OOM = -3,           /* device allocation failed                       */
     HFDIB_ERR_NOT_CONVERGED = -4, /* max_iter reached above tol                     */
     HFDIB_ERR_DIVERGED = -5,      /* NaN / Inf in a residual                        */
-    HFDIB_ERR_STATE_MISMATCH = -6 /* checkpoint from another grid / model           */
+    HFDIB_ERR_STATE_MISMATCH = -6,/* checkpoint from another grid / model           */
+    HFDIB_ERR_TOO_LARGE = -7      /* problem exceeds a fixed capacity (see below)   */
 } hfdib_status;
 
 typedef enum { HFDIB_LAMINAR = 0, HFDIB_KEPSILON = 1, HFDIB_KOMEGA_SST = 2 } hfdib_model;
@@ -229,6 +230,30 @@ enum { HFDIB_K_IMPOSED = 0,   /* a1, a2 and the residual means                */
  * Arrays are host memory of n_classes >= HFDIB_K_COUNT entries.  The sweeps
  * advance the solution exactly like hfdib_simple_sweep. */
 int hfdib_profile_sweeps(hfdib_handle h, int n_sweeps, double* total_us, int64_t* calls, int n_classes);
+
+/* hfdib_classify_noalloc -- cell groups and the ordered boundary-cell list
+ * for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is the allocation-free form of the classification step
+ * of hfdib_create, for callers whose device memory belongs to another
+ * framework's pool, that run under a fixed memory budget, or that must not
+ * enter the driver's allocator.  It allocates nothing: the compaction's
+ * per-block counts live in a fixed array inside the library (room for
+ * 2^24 cells; every GPU that loads the library keeps it until exit).
+ *   grid      : sizes (spacings are not used).
+ *   lambda    : device, nx*ny*nz doubles in [0, 1].
+ *   tags      : device, nx*ny*nz bytes out: 0 fc, 1 bc, 2 ic (Sec. 2.3),
+ *               identical to hfdib_get_tags of a handle made from lambda.
+ *   bc_cells  : device, bc_capacity int32 out: the bc cells in increasing
+ *               cell order, identical to the cell column of hfdib_get_bc_list.
+ *   n_bc      : host, receives the number of bc cells.
+ *   stream    : cudaStream_t; the call synchronises it before returning.
+ * Errors: INVALID_ARG; TOO_LARGE when nx*ny*nz > 2^24, or when n_bc >
+ * bc_capacity (*n_bc is then set and the list is truncated); CUDA.
+ * The first call on a device looks up the fixed array's device address and
+ * should not be made inside a stream capture.  Calls share the array: two
+ * calls that overlap on the GPU (unordered streams) race. */
+int hfdib_classify_noalloc(const hfdib_grid* grid, const double* lambda, uint8_t* tags, int32_t* bc_cells,
+                           int64_t bc_capacity, int64_t* n_bc, void* stream);
 
 const char* hfdib_error_string(int code);
 void hfdib_destroy(hfdib_handle h);

@@ -378,6 +378,7 @@ const char* hfdib_error_string(int code) {
         case HFDIB_ERR_NOT_CONVERGED: return "not converged";
         case HFDIB_ERR_DIVERGED: return "diverged (non-finite residual)";
         case HFDIB_ERR_STATE_MISMATCH: return "checkpoint does not match the handle";
+        case HFDIB_ERR_TOO_LARGE: return "problem exceeds a fixed capacity of the call";
         default: return "unknown error";
     }
 }

@@ -24,9 +24,10 @@ FIELDS = {"ux": 0, "uy": 1, "uz": 2, "p": 3, "k": 4, "eps": 5, "omega": 6, "nut"
 RES_NAMES = ("Ux", "Uy", "Uz", "p", "epsw", "k", "cont", "p_iters", "n_lam", "n_switch")
 NRES = 10
 STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "out of memory",
-          -4: "not converged", -5: "diverged", -6: "state mismatch"}
+          -4: "not converged", -5: "diverged", -6: "state mismatch", -7: "too large"}
 
 ERR_NOT_CONVERGED = -4
+STATUS_TOO_LARGE = -7
 
 
 class HfdibError(RuntimeError):
@@ -60,7 +61,8 @@ _LIB = None
 EXPORTED = ("hfdib_default_options", "hfdib_create", "hfdib_simple_sweep", "hfdib_solve_steady",
             "hfdib_get_field", "hfdib_set_field", "hfdib_get_tags", "hfdib_get_bc_list",
             "hfdib_get_history", "hfdib_get_state", "hfdib_set_state", "hfdib_get_counters",
-            "hfdib_error_string", "hfdib_destroy", "hfdib_profile_sweeps", "hfdib_get_launch_counts")
+            "hfdib_error_string", "hfdib_destroy", "hfdib_profile_sweeps", "hfdib_get_launch_counts",
+            "hfdib_classify_noalloc")
 KERNEL_CLASSES = ("imposed", "grad_u", "mom_asm", "mom_smooth", "hbya", "p_coef", "pcg", "vcycle0",
                   "update", "turb_prep", "scal_asm", "scal_smooth", "turb_final", "sweep_end")
 
@@ -92,6 +94,8 @@ def load_library(path=LIBPATH):
     lib.hfdib_profile_sweeps.restype = C.c_int
     lib.hfdib_get_launch_counts.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
     lib.hfdib_get_launch_counts.restype = C.c_int
+    lib.hfdib_classify_noalloc.argtypes = [C.POINTER(Grid), vp, vp, vp, i64, C.POINTER(i64), vp]
+    lib.hfdib_classify_noalloc.restype = C.c_int
     lib.hfdib_error_string.argtypes = [i32]
     lib.hfdib_error_string.restype = C.c_char_p
     lib.hfdib_destroy.argtypes = [vp]
