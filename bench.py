@@ -39,6 +39,11 @@ MAX_SOLVE_SWEEPS = 20000
 # Algorithmic bytes per cell for one launch group of each kernel class
 # (2D, FP64 words of 8 B, minimum traffic with perfect neighbour reuse,
 # face arrays counted as one word per cell and direction, flags 2 B).
+def PCG_ITERS_FACTOR(piters):
+    """The 'pcg' class is one launch of the whole pressure solve."""
+    return max(float(piters.mean()), 1.0)
+
+
 BYTES_PER_CELL = {
     # u, v, p, nut, phi_x, phi_y, 4 gradient comps read; bm x2, u* x2 written
     "mom_asm": 8 * (10 + 4) + 2,
@@ -46,8 +51,9 @@ BYTES_PER_CELL = {
     "mom_smooth": 8 * (1 + 2 + 2 + 1 + 1) + 2,
     # u*, bm x2, p, phi x2, nut read; HbyA x2, rAU, phiH x2 written
     "hbya": 8 * (7 + 5) + 2,
-    # one CG iteration + one V-cycle: A-product (z, d, cf x2, diag; d, q) +
-    # update (pn, d, r, q; pn, r) + fine-level V-cycle (~26 words) x 4/3
+    # per CG iteration (x iterations per launch): A-product (z, d, cf x2,
+    # diag; d, q) + update (pn, d, r, q; pn, r) + fine-level V-cycle (~26
+    # words) x 4/3 for the coarser levels
     "pcg": 8 * (7 + 6) + int(8 * 26 * 4 / 3),
     "vcycle0": int(8 * 26 * 4 / 3),
     # phiH x2, pn, p, HbyA x2, rAU, cf x2 read; phi x2, u x2, p written
@@ -197,7 +203,6 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-solve", action="store_true", help="skip the converged-solve and e2e legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     args = ap.parse_args()
@@ -230,68 +235,78 @@ def main():
 
     case = G.case_bfs(NX, NY)
     N = NX * NY
-    opts = dict(freeze_switch=FREEZE, precision=1 if args.precision == "mixed" else 0)
-    stream = torch.cuda.Stream(dev)
-    s = hfdib.Solver(case, device=str(dev), stream=stream, **opts)
-    for _ in range(args.warmup):
-        s.sweep(1, read=False)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    stream.synchronize()
-    barrier()
-    torch.cuda.synchronize(dev)
-    clocks.start()
-    n0 = s.counters()[0]
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(float(k))
-        ev[k][0].record(stream)
-        s.sweep(1, read=False)
-        ev[k][1].record(stream)
-    stream.synchronize()
-    torch.cuda.synchronize(dev)
-    barrier()
-    clk = clocks.stop()
-    t_dev = sum(a.elapsed_time(b) for a, b in ev) / 1e3
-    hist = s.history(args.steps)
-    piters = hist[:, 7]
-    fixed, per_it = s.launch_counts()
-    gpu_launches = int(args.steps * fixed + per_it * piters.sum())
-    if dist is not None:
-        t = torch.tensor([t_dev], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev = float(t.item())
-    value = world * N * args.steps / t_dev
-    ms_per_step = 1e3 * t_dev / args.steps
-
-    # roofline of the dominant kernel class (host-driven sweeps, event pairs)
-    prof = s.profile(3)
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
-    dname, (dus, dcalls) = dom
-    avg_us = dus / max(dcalls, 1)
-    bpc = BYTES_PER_CELL.get(dname, 0)
-    achieved = bpc * N / (avg_us * 1e-6) / 1e9
     peak, peak_kind = measured_peaks()
-    roofline = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(dev)
+
+    def timed_sweeps(precision):
+        """W warm-up + K timed sweeps; L2 flushed between timed sweeps."""
+        opts = dict(freeze_switch=FREEZE, precision=1 if precision == "mixed" else 0)
+        s = hfdib.Solver(case, device=str(dev), stream=stream, **opts)
+        for _ in range(args.warmup):
+            s.sweep(1, read=False)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        clocks = ClockSampler(local)
+        stream.synchronize()
+        barrier()
+        torch.cuda.synchronize(dev)
+        clocks.start()
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))
+            ev[k][0].record(stream)
+            s.sweep(1, read=False)
+            ev[k][1].record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize(dev)
+        barrier()
+        clk = clocks.stop()
+        t_dev = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+        hist = s.history(args.steps)
+        piters = hist[:, 7]
+        fixed, per_it = s.launch_counts()
+        launches = int(args.steps * fixed + per_it * piters.sum())
+        if dist is not None:
+            t = torch.tensor([t_dev], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_dev = float(t.item())
+        # roofline of the dominant kernel class (host-driven sweeps, event pairs)
+        prof = s.profile(3)
+        dname, (dus, dcalls) = max(prof.items(), key=lambda kv: kv[1][0])
+        avg_us = dus / max(dcalls, 1)
+        bpc = BYTES_PER_CELL.get(dname, 0) * (PCG_ITERS_FACTOR(piters) if dname == "pcg" else 1)
+        achieved = bpc * N / (avg_us * 1e-6) / 1e9
+        total = sum(x[0] for x in prof.values())
+        roof = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
                 "algorithmic_bytes_per_launch": bpc * N, "avg_launch_us": avg_us,
-                "class_share": {k: round(v[0] / sum(x[0] for x in prof.values()), 4) for k, v in prof.items()}}
-    s.close()
+                "class_share": {k: round(v[0] / total, 4) for k, v in prof.items()}}
+        s.close()
+        return dict(value=world * N * args.steps / t_dev, ms=1e3 * t_dev / args.steps, clocks=clk,
+                    launches=launches, piters=float(piters.mean()), roofline=roof)
 
-    out = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+    res = {p: timed_sweeps(p) for p in ("mixed", "fp64")}
+    head = res["mixed"]
+    out = {"metric": METRIC, "value": head["value"], "unit": "cell-updates/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if args.precision == "fp64" else "f32+f64",
-           "data": "synthetic",
+           "dtype": "f32+f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "grid": [NX, NY], "cells": N, "model": "komega_sst",
-                      "Re_h": 36000, "precision": args.precision, "l2": "flushed (512 MB write) between timed steps",
+                      "Re_h": 36000, "precision": "mixed (FP32 inner sweeps + FP32 multigrid, FP64 defects)",
+                      "l2": "flushed (512 MB write) between timed steps",
                       "parallelism": "replicas" if world > 1 else "single",
-                      "freeze_switch": FREEZE, "pcg_iters_mean": float(piters.mean())},
-           "gpu_launches": gpu_launches, "clocks": clk, "roofline": roofline}
+                      "freeze_switch": FREEZE, "pcg_iters_mean": head["piters"]},
+           "gpu_launches": head["launches"], "clocks": head["clocks"], "roofline": head["roofline"],
+           "fp64": {"value": res["fp64"]["value"], "ms_per_step": res["fp64"]["ms"],
+                    "roofline": res["fp64"]["roofline"], "clocks": res["fp64"]["clocks"],
+                    "pcg_iters_mean": res["fp64"]["piters"]}}
 
-    # converged solve and end-to-end leg (public API from host arrays)
-    if not args.no_solve:
+
+    # converged solves (both precisions) and the end-to-end leg (mixed, public
+    # API from host arrays)
+    def solve_leg(precision, e2e):
+        o = dict(freeze_switch=FREEZE, precision=1 if precision == "mixed" else 0)
         lam_h = torch.from_numpy(np.ascontiguousarray(case["lam"])).pin_memory()
         yw_h = torch.from_numpy(np.ascontiguousarray(case["ywall"])).pin_memory()
         barrier()
@@ -300,26 +315,36 @@ def main():
         with torch.cuda.stream(stream):
             lam_d = lam_h.to(dev, non_blocking=True)
             yw_d = yw_h.to(dev, non_blocking=True)
-        s2 = hfdib.Solver(dict(case, lam=lam_d, ywall=yw_d), device=str(dev), stream=stream, **opts)
+        s2 = hfdib.Solver(dict(case, lam=lam_d, ywall=yw_d), device=str(dev), stream=stream, **o)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        rc, iters, res = s2.solve(tol=TOL, max_iter=MAX_SOLVE_SWEEPS, check_every=100)
+        rc, iters, r = s2.solve(tol=TOL, max_iter=MAX_SOLVE_SWEEPS, check_every=100)
         e1.record(stream)
         host = {n: s2.field(n).cpu() for n in ("ux", "uy", "p", "k", "omega")}
         torch.cuda.synchronize(dev)
-        t_e2e = time.perf_counter() - t0
+        t_wall = time.perf_counter() - t0
         t_solve = e0.elapsed_time(e1) / 1e3
         s2.close()
-        converged = rc == 0
-        out["solves_per_s"] = (world / t_solve) if converged else 0.0
-        out["solve"] = {"converged": converged, "sweeps": iters, "seconds": t_solve,
-                        "final_max_residual": float(max(res[:6])), "tol": TOL}
-        d2h = sum(v.numel() * 8 for v in host.values()) + 8 * hfdib.NRES * ((iters + 99) // 100)
-        out["e2e"] = {"value": world * N * iters / t_e2e, "unit": "cell-updates/s",
-                      "h2d_bytes_per_step": 2 * N * 8, "d2h_bytes_per_step": d2h,
-                      "step": "host lambda/ywall -> create (IB geometry) -> solve to 1e-6 -> host fields",
-                      "solves_per_s": (world / t_e2e) if converged else 0.0}
+        conv = rc == 0
+        leg = {"converged": conv, "sweeps": iters, "seconds": t_solve, "solves_per_s": (world / t_solve) if conv else 0.0,
+               "final_max_residual": float(max(r[:6])), "tol": TOL}
+        if e2e:
+            d2h = sum(v.numel() * 8 for v in host.values()) + 8 * hfdib.NRES * ((iters + 99) // 100)
+            leg["e2e"] = {"value": world * N * iters / t_wall, "unit": "cell-updates/s",
+                          "h2d_bytes_per_step": 2 * N * 8, "d2h_bytes_per_step": d2h,
+                          "step": "host lambda/ywall -> create (IB geometry) -> solve to 1e-6 -> host fields",
+                          "solves_per_s": (world / t_wall) if conv else 0.0}
+        return leg
+
+    if not args.no_solve:
+        lm = solve_leg("mixed", True)
+        lf = solve_leg("fp64", False)
+        out["solves_per_s"] = lm["solves_per_s"]
+        out["e2e"] = lm.pop("e2e")
+        out["solve"] = lm
+        out["fp64"]["solve"] = lf
+        out["fp64"]["solves_per_s"] = lf["solves_per_s"]
     if rank == 0 and not args.no_cpu:
         r = oracle_rate(seconds=15.0)
         out["cpu_baseline"] = {"value": r["cells"] * r["sweeps"] / r["seconds"], "unit": "cell-updates/s",

@@ -40,7 +40,8 @@ typedef enum {
     HFDIB_ERR_NOT_CONVERGED = -4, /* max_iter reached above tol                     */
     HFDIB_ERR_DIVERGED = -5,      /* NaN / Inf in a residual                        */
     HFDIB_ERR_STATE_MISMATCH = -6,/* checkpoint from another grid / model           */
-    HFDIB_ERR_TOO_LARGE = -7      /* problem exceeds a fixed capacity (see below)   */
+    HFDIB_ERR_TOO_LARGE = -7,     /* problem exceeds a fixed capacity (see below)   */
+    HFDIB_ERR_TIMEOUT = -8        /* a device-wide barrier gave up (should not occur) */
 } hfdib_status;
 
 typedef enum { HFDIB_LAMINAR = 0, HFDIB_KEPSILON = 1, HFDIB_KOMEGA_SST = 2 } hfdib_model;
@@ -83,7 +84,13 @@ typedef struct {
     int32_t n_turb;              /* red-black Gauss-Seidel sweeps, k and eps/omega (2) */
     double p_reltol;             /* pressure solve: |r| <= p_reltol |r0| (0.01)   */
     int32_t p_maxiter;           /* pressure solve iteration cap (50)             */
-    int32_t precision;           /* 0 = FP64 throughout                           */
+    int32_t precision;           /* 0: FP64 throughout (default).  1: mixed -- FP64
+                                    state, assembly, defects (residuals), CG vectors
+                                    and reductions; the red-black inner sweeps of the
+                                    momentum and turbulence equations and the
+                                    multigrid preconditioner run in FP32 on FP32
+                                    corrections (needs p_persistent = 1, precond = 1);
+                                    the steady state solves the FP64 equations      */
     int32_t precond;             /* pressure preconditioner: 0 Jacobi, 1 GMG V-cycle (1) */
     int32_t p_check;             /* host-driven solve: read the convergence flag every
                                     p_check CG iterations; 0 = no host reads: the loop
@@ -92,13 +99,15 @@ typedef struct {
     int32_t graph;               /* 1: run each sweep as one CUDA graph, the pressure
                                     iterations in a device-controlled while node (1);
                                     needs p_check == 0 */
+    int32_t p_persistent;        /* 1: the whole pressure solve is one persistent
+                                    cooperative kernel (1); 0: one launch per step */
     int32_t freeze_switch;       /* 0: the y+ <= y+_lam branch of every bc cell is
                                     re-evaluated each sweep (Eq. alphauk, default);
                                     n > 0: from sweep n on a bc cell may leave the
                                     laminar branch but not re-enter it, which ends
                                     limit cycles of the discrete switch (not part
                                     of the paper)                                  */
-    int32_t reserved[3];
+    int32_t reserved[2];
 } hfdib_options;
 
 typedef struct hfdib_ctx* hfdib_handle;

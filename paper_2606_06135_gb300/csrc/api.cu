@@ -37,6 +37,7 @@ struct Ctx {
     Fields F;
     BcList bl;
     MgLevels mg;
+    MgLevels32 mg32;
     int tail_from = 1;
     int coarse_sweeps = 20;
     int use_graph = 0;
@@ -45,6 +46,10 @@ struct Ctx {
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     long long graph_launches = 0, graph_body_launches = 0;
     Prof prof;
+    int pblocks = 0;             // persistent pressure kernel grid (0: not used)
+    double* ppart = nullptr;     // its block partials
+    unsigned int* pbar = nullptr;
+    int* perr = nullptr;
     double* lam = nullptr;
     double* hist = nullptr;      // device [HIST][HFDIB_NRES]
     double* res_dev = nullptr;   // device [HFDIB_NRES]
@@ -109,6 +114,11 @@ __global__ void k_check_lambda(long long N, const double* lam, double* partials,
     grid_reduce<1, false>(v, partials, counter, out);
 }
 
+__global__ void k_to_f32(long long n, const double* __restrict__ a, float* __restrict__ b) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
 __global__ void k_init_state(Grid g, Params P, Fields F, int model) {
     long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.N) return;
@@ -131,6 +141,16 @@ int sync_read(Ctx* h, const double* dev, double* host, int n) {
     CK(cudaStreamSynchronize(h->stream));
     memcpy(host, h->pinned, n * sizeof(double));
     return HFDIB_OK;
+}
+
+// FP32 mirrors of phi and nu_t (mixed path) after the FP64 fields changed
+// outside a sweep (create, set_field, set_state)
+void refresh_mirrors(Ctx* h) {
+    if (!h->F.mixed) return;
+    const Grid& g = h->g;
+    for (int d = 0; d < g.dims; ++d)
+        k_to_f32<<<nblocks(g.nface[d]), BLOCK, 0, h->stream>>>(g.nface[d], h->F.phi[d], h->F.phi32[d]);
+    k_to_f32<<<nblocks(g.N), BLOCK, 0, h->stream>>>(g.N, h->F.nut, h->F.nut32);
 }
 
 // ---------------------------------------------------------------- profiling
@@ -175,8 +195,13 @@ void enqueue_part_a(Ctx* h, long long* L) {
     PROF(h, HFDIB_K_MOM_ASM, launch_mom_asm(g, P, F, s));
     *L += 4;
     for (int n = 0; n < h->opt.n_u; ++n) {
-        PROF(h, HFDIB_K_MOM_SMOOTH, launch_mom_smooth(g, P, F, 0, s));
-        PROF(h, HFDIB_K_MOM_SMOOTH, launch_mom_smooth(g, P, F, 1, s));
+        if (F.mixed) {
+            PROF(h, HFDIB_K_MOM_SMOOTH, launch_mom_smooth32(g, P, F, 0, n == 0, s));
+            PROF(h, HFDIB_K_MOM_SMOOTH, launch_mom_smooth32(g, P, F, 1, 0, s));
+        } else {
+            PROF(h, HFDIB_K_MOM_SMOOTH, launch_mom_smooth(g, P, F, 0, s));
+            PROF(h, HFDIB_K_MOM_SMOOTH, launch_mom_smooth(g, P, F, 1, s));
+        }
         *L += 2;
     }
     // a6: rAU, HbyA, phiHbyA
@@ -188,6 +213,23 @@ void enqueue_part_a(Ctx* h, long long* L) {
     int jac = h->opt.precond == 0;
     PROF(h, HFDIB_K_P_COEF, launch_p_coef(g, M, F.rAU, h->tail_from, s));
     *L += 1 + (h->tail_from - 1) + (h->tail_from < M.nl ? 1 : 0);
+    if (h->pblocks > 0) {
+        // the whole solve in one cooperative launch
+        cudaMemsetAsync(h->pbar, 0, sizeof(unsigned int), s);
+        if (F.mixed) {
+            PROF(h, HFDIB_K_P_COEF, launch_p_coef32(g, M, h->mg32, s));
+            PROF(h, HFDIB_K_PCG, launch_pressure_persistent32(g, F, M, h->mg32, h->coarse_sweeps,
+                                                               h->opt.p_reltol, h->opt.p_maxiter, h->pblocks,
+                                                               h->ppart, h->pbar, h->perr, s));
+            *L += 2 + (h->tail_from - 1) + (h->tail_from < M.nl ? 1 : 0);
+        } else {
+            PROF(h, HFDIB_K_PCG, launch_pressure_persistent(g, F, M, jac, h->coarse_sweeps, h->opt.p_reltol,
+                                                             h->opt.p_maxiter, h->pblocks, h->ppart, h->pbar,
+                                                             h->perr, s));
+            (*L)++;
+        }
+        return;
+    }
     PROF(h, HFDIB_K_PCG, launch_pcg_init(g, F, M, jac, s));
     (*L)++;
     if (!jac) {
@@ -228,8 +270,13 @@ void enqueue_part_b(Ctx* h, long long* L) {
         PROF(h, HFDIB_K_SCAL_ASM, launch_scal_asm(g, P, G, 0, s));
         *L += 4;
         for (int n = 0; n < h->opt.n_turb; ++n) {
-            PROF(h, HFDIB_K_SCAL_SMOOTH, launch_scal_smooth(g, P, G, 0, 0, s));
-            PROF(h, HFDIB_K_SCAL_SMOOTH, launch_scal_smooth(g, P, G, 0, 1, s));
+            if (F.mixed) {
+                PROF(h, HFDIB_K_SCAL_SMOOTH, launch_scal_smooth32(g, P, G, 0, 0, n == 0, s));
+                PROF(h, HFDIB_K_SCAL_SMOOTH, launch_scal_smooth32(g, P, G, 0, 1, 0, s));
+            } else {
+                PROF(h, HFDIB_K_SCAL_SMOOTH, launch_scal_smooth(g, P, G, 0, 0, s));
+                PROF(h, HFDIB_K_SCAL_SMOOTH, launch_scal_smooth(g, P, G, 0, 1, s));
+            }
             *L += 2;
         }
         // a11: k with imposed rows, then the correction; a12 nu_t
@@ -237,8 +284,13 @@ void enqueue_part_b(Ctx* h, long long* L) {
         PROF(h, HFDIB_K_SCAL_ASM, launch_scal_asm(g, P, G, 1, s));
         *L += 2;
         for (int n = 0; n < h->opt.n_turb; ++n) {
-            PROF(h, HFDIB_K_SCAL_SMOOTH, launch_scal_smooth(g, P, G, 1, 0, s));
-            PROF(h, HFDIB_K_SCAL_SMOOTH, launch_scal_smooth(g, P, G, 1, 1, s));
+            if (F.mixed) {
+                PROF(h, HFDIB_K_SCAL_SMOOTH, launch_scal_smooth32(g, P, G, 1, 0, n == 0, s));
+                PROF(h, HFDIB_K_SCAL_SMOOTH, launch_scal_smooth32(g, P, G, 1, 1, 0, s));
+            } else {
+                PROF(h, HFDIB_K_SCAL_SMOOTH, launch_scal_smooth(g, P, G, 1, 0, s));
+                PROF(h, HFDIB_K_SCAL_SMOOTH, launch_scal_smooth(g, P, G, 1, 1, s));
+            }
             *L += 2;
         }
         PROF(h, HFDIB_K_TURB_FINAL, launch_turb_final(g, P, G, s));
@@ -253,9 +305,9 @@ int run_sweep_host(Ctx* h) {
     long long L = 0;
     cudaGraphConditionalHandle none = 0;
     enqueue_part_a(h, &L);
-    PROF(h, HFDIB_K_PCG, enqueue_pcg_start(h, none, 0, &L));
+    if (h->pblocks == 0) PROF(h, HFDIB_K_PCG, enqueue_pcg_start(h, none, 0, &L));
     int check = h->opt.p_check;
-    for (int it = 0; it < h->opt.p_maxiter; ++it) {
+    for (int it = 0; h->pblocks == 0 && it < h->opt.p_maxiter; ++it) {
         enqueue_pcg_body(h, none, 0, &L);
         if (check > 0 && (it + 1) % check == 0) {
             double done;
@@ -280,6 +332,20 @@ int build_graph(Ctx* h, int which) {
     cudaStream_t s = h->stream;
     cudaGraph_t graph;
     CK(cudaGraphCreate(&graph, 0));
+    if (h->pblocks > 0) {
+        long long L = 0;
+        CK(cudaStreamBeginCaptureToGraph(s, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        enqueue_part_a(h, &L);
+        enqueue_part_b(h, &L);
+        CK(cudaStreamEndCapture(s, &graph));
+        cudaGraphExec_t exec;
+        CK(cudaGraphInstantiate(&exec, graph, 0));
+        h->graph[which] = graph;
+        h->gexec[which] = exec;
+        h->graph_launches = L;
+        h->graph_body_launches = 0;
+        return HFDIB_OK;
+    }
     cudaGraphConditionalHandle hc;
     CK(cudaGraphConditionalHandleCreate(&hc, graph, 1, cudaGraphCondAssignDefault));
     long long L = 0;
@@ -319,7 +385,18 @@ int run_sweep(Ctx* h) {
     if (!h->use_graph) return run_sweep_host(h);
     if (!h->gexec[h->parity]) {
         int rc = build_graph(h, h->parity);
-        if (rc) { cudaGetLastError(); return rc; }
+        if (rc) {
+            // capture not possible here: abandon it and run host-driven
+            cudaStreamCaptureStatus st;
+            if (cudaStreamIsCapturing(h->stream, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(h->stream, &g);
+                if (g) cudaGraphDestroy(g);
+            }
+            cudaGetLastError();
+            h->use_graph = 0;
+            return run_sweep_host(h);
+        }
     }
     CK(cudaGraphLaunch(h->gexec[h->parity], h->stream));
     std::swap(h->F.p, h->F.pr);
@@ -366,6 +443,7 @@ void hfdib_default_options(hfdib_options* o) {
     o->p_check = 0;
     o->mg_coarse_sweeps = 4;
     o->graph = 1;
+    o->p_persistent = 1;
     o->freeze_switch = 0;
 }
 
@@ -379,6 +457,7 @@ const char* hfdib_error_string(int code) {
         case HFDIB_ERR_DIVERGED: return "diverged (non-finite residual)";
         case HFDIB_ERR_STATE_MISMATCH: return "checkpoint does not match the handle";
         case HFDIB_ERR_TOO_LARGE: return "problem exceeds a fixed capacity of the call";
+        case HFDIB_ERR_TIMEOUT: return "a device-wide barrier timed out";
         default: return "unknown error";
     }
 }
@@ -406,7 +485,9 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
         return HFDIB_ERR_INVALID_ARG;
     if (o.n_u < 1 || o.n_turb < 1 || o.p_maxiter < 0 || !(o.p_reltol >= 0)) return HFDIB_ERR_INVALID_ARG;
     if (o.precond < 0 || o.precond > 1 || o.p_check < 0 || o.mg_coarse_sweeps < 0) return HFDIB_ERR_INVALID_ARG;
-    if (o.precision != 0) return HFDIB_ERR_INVALID_ARG;
+    if (o.precision < 0 || o.precision > 1) return HFDIB_ERR_INVALID_ARG;
+    // the mixed path runs its FP32 V-cycle inside the persistent CG kernel
+    if (o.precision == 1 && (o.p_persistent == 0 || o.precond != 1)) return HFDIB_ERR_INVALID_ARG;
     if (o.p_maxiter > 100000 || o.freeze_switch < 0) return HFDIB_ERR_INVALID_ARG;
 
     Ctx* h = new (std::nothrow) Ctx();
@@ -511,6 +592,34 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
         for (int l = 1; l < M.nl; ++l)
             if (M.lv[l].N <= TAIL_CELLS) { h->tail_from = l; break; }
     }
+    F.mixed = o.precision == 1 ? 1 : 0;
+    if (!rc && F.mixed) {
+        for (int d = 0; d < 3; ++d) { A(F.phi32[d], g.nface[d]); A(F.r32[d], N); A(F.d32[d], N); }
+        A(F.nut32, N); A(F.gam32, N); A(F.gamk32, N); A(F.diag32, N); A(F.z32, N);
+        // FP32 preconditioner hierarchy, same shapes as the FP64 one
+        MgLevels32& M32 = h->mg32;
+        memset(&M32, 0, sizeof(M32));
+        M32.nl = h->mg.nl;
+        for (int l = 0; l < M32.nl && !rc; ++l) {
+            const Level& Ld = h->mg.lv[l];
+            Level32& Lf = M32.lv[l];
+            Lf.nx = Ld.nx; Lf.ny = Ld.ny; Lf.nz = Ld.nz; Lf.N = Ld.N;
+            A(Lf.cf[0], (long long)(Lf.nx + 1) * Lf.ny * Lf.nz);
+            A(Lf.cf[1], (long long)Lf.nx * (Lf.ny + 1) * Lf.nz);
+            A(Lf.cf[2], (long long)Lf.nx * Lf.ny * (Lf.nz + 1));
+            A(Lf.diag, Lf.N); A(Lf.idg, Lf.N); A(Lf.b, Lf.N);
+            if (l == 0) Lf.x = F.z32;
+            else A(Lf.x, Lf.N);
+        }
+    }
+    if (!rc && o.p_persistent) {
+        int nbk = 0;
+        if (pcgp_blocks(&nbk) != 0 || nbk <= 0) rc = HFDIB_ERR_CUDA;
+        h->pblocks = nbk;
+        A(h->ppart, 8 * (long long)nbk + 8);
+        A(h->pbar, 2);
+        A(h->perr, 1);
+    }
 #undef A
     if (!rc && cudaMallocHost((void**)&h->pinned, 64 * sizeof(double)) != cudaSuccess) rc = HFDIB_ERR_OOM;
     if (rc) { free_all(h); delete h; return rc; }
@@ -549,6 +658,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
     // initial state and face fluxes
     k_init_state<<<nb, BLOCK, 0, s>>>(g, P, F, model);
     launch_init_flux(g, F, s);
+    refresh_mirrors(h);
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
         free_all(h); delete h; return HFDIB_ERR_CUDA;
     }
@@ -621,6 +731,7 @@ int hfdib_set_field(hfdib_handle hh, int field, const double* srcp) {
     double* dst = field_ptr(h, field, &n);
     if (!dst) return HFDIB_ERR_INVALID_ARG;
     CK(cudaMemcpyAsync(dst, srcp, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    refresh_mirrors(h);
     return HFDIB_OK;
 }
 
@@ -716,6 +827,7 @@ int hfdib_set_state(hfdib_handle hh, const void* buf, size_t bytes) {
         CK(cudaMemcpyAsync(a.first, p, a.second * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         p += a.second * sizeof(double);
     }
+    refresh_mirrors(h);
     double ns = (double)hd[5];
     CK(cudaMemcpyAsync(h->F.scal + SC_NSWEEP, &ns, sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -753,10 +865,10 @@ int hfdib_get_launch_counts(hfdib_handle hh, int64_t* per_sweep, int64_t* per_pc
     bool turb = h->model != HFDIB_LAMINAR;
     int jac = h->opt.precond == 0;
     int tf = h->tail_from;
-    La = (turb ? 1 : 0) + 4 + 2 * h->opt.n_u + 2 + (1 + (tf - 1) + (tf < h->mg.nl ? 1 : 0)) + 1 +
-         (jac ? 0 : 5 * tf + 1) + 1;
+    La = (turb ? 1 : 0) + 4 + 2 * h->opt.n_u + 2 + (1 + (tf - 1) + (tf < h->mg.nl ? 1 : 0)) +
+         (h->pblocks > 0 ? 1 : 1 + (jac ? 0 : 5 * tf + 1) + 1);
     Lb = 1 + (turb ? 4 + 2 * h->opt.n_turb + 2 + 2 * h->opt.n_turb + 1 : 0) + 1;
-    Lp = 3 + (jac ? 0 : 5 * tf + 1);
+    Lp = h->pblocks > 0 ? 0 : 3 + (jac ? 0 : 5 * tf + 1);
     if (per_sweep) *per_sweep = La + Lb;
     if (per_pcg_iteration) *per_pcg_iteration = Lp;
     return HFDIB_OK;

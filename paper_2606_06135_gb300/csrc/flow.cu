@@ -29,50 +29,66 @@ __device__ inline bool vel_row_fixed(const Grid& g, const Fields& F, long long c
 }
 
 // momentum row of cell c (unrelaxed): aP per component, neighbour
-// coefficients and the boundary right-hand side per component
-struct MomRow {
-    double aP[3];
-    double a[6];
+// coefficients and the boundary right-hand side per component.  T = double
+// for the FP64 operator, float for the FP32 smoother of the mixed path
+// (from FP32 mirrors of phi and nu_t).
+template <typename T>
+struct MomRowT {
+    T aP[3];
+    T a[6];
     long long nb[6];
     bool has[6];
-    double bnd[3];
+    T bnd[3];
 };
+using MomRow = MomRowT<double>;
 
-__device__ void mom_row(const Grid& g, const Fields& F, long long c, int i, int j, int k, uint16_t f,
-                        MomRow& R) {
-    double nuP = g.nu + F.nut[c];
-    for (int q = 0; q < 3; ++q) { R.aP[q] = 0.0; R.bnd[q] = 0.0; }
+template <typename T>
+__device__ void mom_row_t(const Grid& g, T* const* phi, const T* nut, long long c, int i, int j, int k, uint16_t f,
+                          MomRowT<T>& R) {
+    const T nu = (T)g.nu;
+    T nuP = nu + nut[c];
+    for (int q = 0; q < 3; ++q) { R.aP[q] = T(0); R.bnd[q] = T(0); }
     for (int d = 0; d < g.dims; ++d) {
         long long fl = face_lo(g, d, i, j, k);
         long long fs = face_stride(g, d);
         for (int side = 0; side < 2; ++side) {
             int s = 2 * d + side;
-            double Fb = F.phi[d][fl + side * fs];
-            double Fout = side ? Fb : -Fb;
+            T Fb = phi[d][fl + side * fs];
+            T Fout = side ? Fb : -Fb;
             if (interior(g, d, side, i, j, k)) {
                 long long nc = nbr_cell(g, c, d, side);
-                double nuN = g.nu + F.nut[nc];
-                double Dif = 0.5 * (nuP + nuN) * g.SoD[d];
-                R.a[s] = fmin(Fout, 0.0) - Dif;
+                T nuN = nu + nut[nc];
+                T Dif = T(0.5) * (nuP + nuN) * (T)g.SoD[d];
+                R.a[s] = fmin(Fout, T(0)) - Dif;
                 R.nb[s] = nc;
                 R.has[s] = true;
-                double add = fmax(-Fout, 0.0) + Dif;
+                T add = fmax(-Fout, T(0)) + Dif;
                 for (int q = 0; q < g.dims; ++q) R.aP[q] += add;
             } else {
-                R.a[s] = 0.0;
+                R.a[s] = T(0);
                 R.nb[s] = c;
                 R.has[s] = false;
                 for (int q = 0; q < g.dims; ++q) {
                     double val;
                     if (vel_fixed(g, f, s, q, val)) {
-                        double coef = nuP * g.SoHD[d] + fmax(-Fout, 0.0);
+                        T coef = nuP * (T)g.SoHD[d] + fmax(-Fout, T(0));
                         R.aP[q] += coef;
-                        R.bnd[q] += coef * val;
+                        R.bnd[q] += coef * (T)val;
                     }
                 }
             }
         }
     }
+}
+
+__device__ inline void mom_row(const Grid& g, const Fields& F, long long c, int i, int j, int k, uint16_t f,
+                               MomRow& R) {
+    mom_row_t<double>(g, F.phi, F.nut, c, i, j, k, f, R);
+}
+
+// predictor value u* = initial guess + (mixed path) FP32 correction
+__device__ inline double ustar(const Fields& F, int q, long long c) {
+    return F.mixed ? F.us[q][c] + (double)F.d32[q][c] : F.us[q][c];
 }
 
 // Gauss-linear gradient of the pressure-like field p at cell c (outlet faces
@@ -227,6 +243,11 @@ __global__ void k_mom_asm(Grid g, Params P, Fields F) {
                 red[3 * q + 0] = fabs(bfull - Ax);
                 red[3 * q + 1] = fabs(Ax - A1 * xbar);
                 red[3 * q + 2] = fabs(bfull - A1 * xbar);
+                // defect of the relaxed system at the initial guess: with
+                // x_P = u_old the relaxation terms cancel, leaving b - A x
+                if (F.mixed) F.r32[q][c] = (float)(bfull - Ax);
+            } else if (F.mixed) {
+                F.r32[q][c] = 0.0f;
             }
         }
     }
@@ -261,6 +282,32 @@ __global__ void k_mom_smooth(Grid g, Params P, Fields F, int colour) {
     }
 }
 
+// FP32 red-black sweep on the correction of the predictor (mixed path):
+// (aP/urf) d_P + sum a_N d_N = r (FP64 defect rounded), d = 0 on imposed rows.
+// zero_init: the other colour is taken as 0 (first half sweep).
+__global__ void k_mom_smooth32(Grid g, Params P, Fields F, int colour, int zero_init) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    int i, j, k;
+    cell_ijk(g, c, i, j, k);
+    if (((i + j + k) & 1) != colour) return;
+    uint16_t f = F.flags[c];
+    if (tag_of(f) == TAG_IC || (f & F_AU)) {
+        for (int q = 0; q < g.dims; ++q) F.d32[q][c] = 0.0f;
+        return;
+    }
+    MomRowT<float> R;
+    mom_row_t<float>(g, F.phi32, F.nut32, c, i, j, k, f, R);
+    const float urf = (float)P.urf_u;
+    for (int q = 0; q < g.dims; ++q) {
+        float acc = F.r32[q][c];
+        if (!zero_init)
+            for (int s = 0; s < 2 * g.dims; ++s)
+                if (R.has[s]) acc -= R.a[s] * F.d32[q][R.nb[s]];
+        F.d32[q][c] = acc * urf / R.aP[q];
+    }
+}
+
 // ---------------------------------------------------------------- a6 HbyA
 __global__ void k_hbya(Grid g, Params P, Fields F) {
     long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -279,8 +326,8 @@ __global__ void k_hbya(Grid g, Params P, Fields F) {
         double br = F.bm[q][c] + grad_p(g, F.p, c, q, i, j, k) * g.V;
         double off = 0.0;
         for (int s = 0; s < 2 * g.dims; ++s)
-            if (R.has[s]) off += R.a[s] * F.us[q][R.nb[s]];
-        double H = br - off - (aPr[q] - aavg) * F.us[q][c];
+            if (R.has[s]) off += R.a[s] * ustar(F, q, R.nb[s]);
+        double H = br - off - (aPr[q] - aavg) * ustar(F, q, c);
         F.HbyA[q][c] = H * ia;
     }
     F.rAU[c] = g.V * ia;
@@ -340,6 +387,10 @@ __global__ void k_update(Grid g, Params P, Fields F, Level L0) {
             }
             F.phi[d][fl] = flo;
             if (!interior(g, d, 1, i, j, k)) F.phi[d][fl + fs] = fhi;
+            if (F.mixed) {
+                F.phi32[d][fl] = (float)flo;
+                if (!interior(g, d, 1, i, j, k)) F.phi32[d][fl + fs] = (float)fhi;
+            }
             div += fhi - flo;
         }
         red[0] = (f & F_M) ? fabs(div) : 0.0;
@@ -406,6 +457,9 @@ void launch_mom_asm(const Grid& g, const Params& P, const Fields& F, cudaStream_
 }
 void launch_mom_smooth(const Grid& g, const Params& P, const Fields& F, int colour, cudaStream_t s) {
     k_mom_smooth<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F, colour);
+}
+void launch_mom_smooth32(const Grid& g, const Params& P, const Fields& F, int colour, int zero_init, cudaStream_t s) {
+    k_mom_smooth32<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F, colour, zero_init);
 }
 void launch_hbya(const Grid& g, const Params& P, const Fields& F, cudaStream_t s) {
     k_hbya<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F);

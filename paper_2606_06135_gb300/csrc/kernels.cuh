@@ -44,6 +44,7 @@ enum {
     SC_NSWEEP = 37,              // sweeps run (history slot)
     SC_NLAM = 38,                // bc cells in the laminar branch this sweep
     SC_NSWITCH = 39,             // bc cells whose branch changed
+    SC_TIMEOUT = 46,             // 1 once a persistent kernel's grid barrier gave up
     SC_PCG_INIT = 40,            // r0.z0, r0.r0, b.b, then the 3 scaled-residual sums of p
     SC_NSCAL = 64
 };
@@ -84,28 +85,47 @@ struct Fields {
     double* z;
     double* d[2];
     double* q;
+    // FP32 mirrors and corrections of the mixed-precision path (precision = 1):
+    // the inner red-black sweeps solve for corrections in FP32, the defects
+    // (right-hand sides) come from the FP64 assembly
+    float* phi32[3];
+    float* nut32;
+    float* gam32;
+    float* gamk32;
+    float* r32[3];     // FP64 defect of each momentum component / scalar, rounded
+    float* d32[3];     // FP32 correction
+    float* diag32;     // relaxed diagonal of the scalar equation
+    float* z32;        // preconditioned residual of the CG (mixed path)
+    int mixed;
     // scalars and reductions
     double* scal;
     double* partials;
     unsigned int* counters;
 };
 
-// one multigrid level of the pressure operator (level 0 = the fine grid)
-struct Level {
+// one multigrid level of the pressure operator (level 0 = the fine grid),
+// in FP64 (the plain path) or FP32 (the preconditioner of the mixed path)
+template <typename T>
+struct LevelT {
     int nx, ny, nz;
     long long N;
-    double* cf[3];   // face coefficients, face layout of the level
-    double* diag;
-    double* idg;     // 1/diag (0 where diag is 0)
-    double* x;       // correction (level 0: z)
-    double* b;       // right-hand side (level 0: r)
+    T* cf[3];   // face coefficients, face layout of the level
+    T* diag;
+    T* idg;     // 1/diag (0 where diag is 0)
+    T* x;       // correction (level 0: z)
+    T* b;       // right-hand side (level 0: r)
 };
+using Level = LevelT<double>;
+using Level32 = LevelT<float>;
 constexpr int MAX_LEVELS = 16;
 constexpr long long TAIL_CELLS = 4096;
-struct MgLevels {
+template <typename T>
+struct MgLevelsT {
     int nl;
-    Level lv[MAX_LEVELS];
+    LevelT<T> lv[MAX_LEVELS];
 };
+using MgLevels = MgLevelsT<double>;
+using MgLevels32 = MgLevelsT<float>;
 
 struct Params {
     int model;
@@ -149,6 +169,19 @@ void launch_pcg_start(const Fields& F, int jacobi, double reltol, int maxit, cud
                       int use_cond, cudaStream_t s);
 void launch_pcg_body(const Grid& g, const Fields& F, const MgLevels& M, int ntail_from, int jacobi,
                      int coarse_sweeps, int maxit, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s);
+
+// pcgp.cu
+int pcgp_blocks(int* out);
+cudaError_t launch_pressure_persistent(const Grid& g, const Fields& F, const MgLevels& M, int jacobi,
+                                       int coarse_sweeps, double reltol, int maxit, int nblk, double* part,
+                                       unsigned int* bar, int* err, cudaStream_t s);
+cudaError_t launch_pressure_persistent32(const Grid& g, const Fields& F, const MgLevels& M, const MgLevels32& M32,
+                                         int coarse_sweeps, double reltol, int maxit, int nblk, double* part,
+                                         unsigned int* bar, int* err, cudaStream_t s);
+void launch_p_coef32(const Grid& g, const MgLevels& M, const MgLevels32& M32, cudaStream_t s);
+void launch_mom_smooth32(const Grid& g, const Params& P, const Fields& F, int colour, int zero_init, cudaStream_t s);
+void launch_scal_smooth32(const Grid& g, const Params& P, const Fields& F, int eq, int colour, int zero_init,
+                          cudaStream_t s);
 
 // turb.cu
 void launch_turb_prep(const Grid& g, const Params& P, const Fields& F, cudaStream_t s);

@@ -1,0 +1,509 @@
+// pcgp.cu -- the pressure corrector (a7) as one persistent cooperative
+// kernel: PCG with one multigrid V-cycle per iteration (or Jacobi), the
+// whole loop inside a single launch.
+//
+// Operator and preconditioner are those of pressure.cu (same face
+// coefficients, same V-cycle: red-black Gauss-Seidel, piecewise-constant
+// transfers, coarse coefficients half the covered fine faces); only the
+// execution differs: phases separated by a grid barrier instead of kernel
+// boundaries.  The launch is cooperative (all blocks resident), the barrier
+// spins with an iteration limit and records a timeout in the error word
+// instead of waiting forever.  Reductions: every block writes its partial;
+// after the barrier every block sums all partials in the same order, so all
+// blocks hold the same bit-identical value (deterministic, no atomics on
+// floating point).  Levels of at most PT_TAIL_CELLS cells run inside block 0.
+//
+// Mixed precision (pattern "FP32 sweeps inside FP64 refinement"): the CG
+// vectors, dot products, scalars and the defect r = rhs - A p stay FP64; the
+// V-cycle that preconditions them runs in FP32 on an FP32 copy of the
+// operator (level 0 rounded from the FP64 face coefficients, coarse levels
+// coarsened in FP32).  The converged pressure solves the FP64 equation.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace hf {
+
+constexpr int PT_THREADS = 512;
+constexpr long long PT_TAIL_CELLS = 1024;
+constexpr long long PT_SPIN_LIMIT = 1ll << 26;   // ~0.1-1 s of polling
+
+template <typename MT>
+struct PcgpArgs {
+    Grid g;
+    Fields F;
+    Level L0d;           // FP64 operator of the CG product (level 0)
+    MgLevelsT<MT> M;     // preconditioner hierarchy (level 0 = the grid)
+    MT* zp;              // preconditioned residual z (= M.lv[0].x)
+    int lf;              // levels 0..lf-1 by the whole grid, lf..nl-1 by block 0
+    int coarse_sweeps;
+    int jacobi;
+    double reltol;
+    int maxit;
+    double* part;        // [8][gridDim.x] block partials
+    unsigned int* bar;   // [2] barrier arrival count, generation
+    int* err;            // barrier timeout flag
+};
+
+// ---------------------------------------------------------------- barrier
+template <typename AT>
+__device__ inline void grid_sync(const AT& A) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* gen = A.bar + 1;
+        unsigned int g0 = *gen;
+        __threadfence();
+        unsigned int arrived = atomicAdd(A.bar, 1u);
+        if (arrived == gridDim.x - 1) {
+            A.bar[0] = 0u;
+            __threadfence();
+            atomicAdd(A.bar + 1, 1u);
+        } else {
+            long long spins = 0;
+            while (*gen == g0) {
+                if (++spins > PT_SPIN_LIMIT) { atomicExch(A.err, 1); break; }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// block partial of v into slot q; returns nothing (combined after a barrier)
+template <typename AT>
+__device__ inline void block_partial(const AT& A, int q, double v) {
+    __shared__ double sm[PT_THREADS / 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = sm[0];
+        for (int w = 1; w < PT_THREADS / 32; ++w) x += sm[w];
+        A.part[(long long)q * gridDim.x + blockIdx.x] = x;
+    }
+}
+
+// sum of slot q over all blocks, same order in every block
+template <typename AT>
+__device__ inline double grid_total(const AT& A, int q) {
+    __shared__ double sm[PT_THREADS / 32];
+    __shared__ double res;
+    double x = 0.0;
+    for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) x += __ldcg(&A.part[(long long)q * gridDim.x + b]);
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sm[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double y = sm[0];
+        for (int w = 1; w < PT_THREADS / 32; ++w) y += sm[w];
+        res = y;
+    }
+    __syncthreads();
+    return res;
+}
+
+// ---------------------------------------------------------------- level ops
+template <typename T>
+__device__ inline long long pl_face(const LevelT<T>& L, int d, int i, int j, int k) {
+    if (d == 0) return ((long long)k * L.ny + j) * (L.nx + 1) + i;
+    if (d == 1) return ((long long)k * (L.ny + 1) + j) * L.nx + i;
+    return ((long long)k * L.ny + j) * L.nx + i;
+}
+template <typename T>
+__device__ inline long long pl_fstride(const LevelT<T>& L, int d) {
+    return d == 0 ? 1 : (d == 1 ? L.nx : (long long)L.nx * L.ny);
+}
+template <typename T>
+__device__ inline void pl_ijk(const LevelT<T>& L, long long c, int& i, int& j, int& k) {
+    unsigned int cc = (unsigned int)c, nx = (unsigned int)L.nx;
+    unsigned int r = cc / nx;
+    i = (int)(cc - r * nx);
+    if (L.nz == 1) { j = (int)r; k = 0; return; }
+    unsigned int ny = (unsigned int)L.ny;
+    unsigned int kk = r / ny;
+    j = (int)(r - kk * ny);
+    k = (int)kk;
+}
+template <typename T, typename X>
+__device__ inline T pl_offsum(const LevelT<T>& L, int dims, const X* x, long long c, int i, int j, int k) {
+    T acc = T(0);
+    int idx[3] = {i, j, k};
+    int nn[3] = {L.nx, L.ny, L.nz};
+    for (int d = 0; d < dims; ++d) {
+        long long fl = pl_face(L, d, i, j, k);
+        long long cs = d == 0 ? 1 : (d == 1 ? L.nx : (long long)L.nx * L.ny);
+        if (idx[d] > 0) acc += L.cf[d][fl] * (T)x[c - cs];
+        if (idx[d] < nn[d] - 1) acc += L.cf[d][fl + pl_fstride(L, d)] * (T)x[c + cs];
+    }
+    return acc;
+}
+
+template <typename T>
+__device__ inline void pl_smooth(const LevelT<T>& L, int dims, int colour, long long t0, long long TT) {
+    for (long long c = t0; c < L.N; c += TT) {
+        int i, j, k;
+        pl_ijk(L, c, i, j, k);
+        if (((i + j + k) & 1) != colour) continue;
+        L.x[c] = (L.b[c] + pl_offsum(L, dims, L.x, c, i, j, k)) * L.idg[c];
+    }
+}
+
+// b_C = sum of the children's residuals; fuse_red: also the zero-start red
+// half sweep of the coarse level (x_C = b_C / diag_C on red cells)
+template <typename T>
+__device__ inline void pl_restrict(const LevelT<T>& F, const LevelT<T>& Cc, int dims, bool fuse_red, long long t0,
+                                   long long TT) {
+    for (long long C = t0; C < Cc.N; C += TT) {
+        int I, J, K;
+        pl_ijk(Cc, C, I, J, K);
+        T sum = T(0);
+        for (int oz = 0; oz < (dims == 3 ? 2 : 1); ++oz)
+            for (int oy = 0; oy < 2; ++oy)
+                for (int ox = 0; ox < 2; ++ox) {
+                    int i = 2 * I + ox, j = 2 * J + oy, k = 2 * K + oz;
+                    if (i >= F.nx || j >= F.ny || k >= F.nz) continue;
+                    long long c = ((long long)k * F.ny + j) * F.nx + i;
+                    sum += F.b[c] - (F.diag[c] * F.x[c] - pl_offsum(F, dims, F.x, c, i, j, k));
+                }
+        Cc.b[C] = sum;
+        if (fuse_red && ((I + J + K) & 1) == 0) Cc.x[C] = sum * Cc.idg[C];
+    }
+}
+
+// prolongation fused with the black half sweep (red cells are overwritten by
+// the following red half sweep without being read)
+template <typename T>
+__device__ inline void pl_prolong_black(const LevelT<T>& L, const LevelT<T>& Cc, int dims, long long t0, long long TT) {
+    for (long long c = t0; c < L.N; c += TT) {
+        int i, j, k;
+        pl_ijk(L, c, i, j, k);
+        if (((i + j + k) & 1) != 1) continue;
+        int idx[3] = {i, j, k};
+        int nn[3] = {L.nx, L.ny, L.nz};
+        T acc = L.b[c];
+        for (int d = 0; d < dims; ++d) {
+            long long fl = pl_face(L, d, i, j, k);
+            long long cs = d == 0 ? 1 : (d == 1 ? L.nx : (long long)L.nx * L.ny);
+            for (int side = 0; side < 2; ++side) {
+                if (side == 0 && idx[d] == 0) continue;
+                if (side == 1 && idx[d] == nn[d] - 1) continue;
+                int ni[3] = {i, j, k};
+                ni[d] += side ? 1 : -1;
+                long long nc = side ? c + cs : c - cs;
+                long long C = ((long long)(ni[2] >> 1) * Cc.ny + (ni[1] >> 1)) * Cc.nx + (ni[0] >> 1);
+                acc += L.cf[d][fl + (side ? pl_fstride(L, d) : 0)] * (L.x[nc] + Cc.x[C]);
+            }
+        }
+        L.x[c] = acc * L.idg[c];
+    }
+}
+
+// levels l0..nl-1 inside one block: b of level l0 is set on entry
+template <typename T>
+__device__ void pl_tail(const MgLevelsT<T>& M, int dims, int l0, int sweeps) {
+    const long long t0 = threadIdx.x, TT = blockDim.x;
+    for (int l = l0; l < M.nl - 1; ++l) {
+        const LevelT<T>& L = M.lv[l];
+        for (long long c = t0; c < L.N; c += TT) {
+            int i, j, k;
+            pl_ijk(L, c, i, j, k);
+            if (((i + j + k) & 1) == 0) L.x[c] = L.b[c] * L.idg[c];
+        }
+        __syncthreads();
+        pl_smooth(L, dims, 1, t0, TT);
+        __syncthreads();
+        pl_restrict(L, M.lv[l + 1], dims, false, t0, TT);
+        __syncthreads();
+    }
+    const LevelT<T>& Lc = M.lv[M.nl - 1];
+    for (int s = 0; s < sweeps; ++s) {
+        if (s == 0) {
+            for (long long c = t0; c < Lc.N; c += TT) {
+                int i, j, k;
+                pl_ijk(Lc, c, i, j, k);
+                if (((i + j + k) & 1) == 0) Lc.x[c] = Lc.b[c] * Lc.idg[c];
+            }
+        } else {
+            pl_smooth(Lc, dims, 0, t0, TT);
+        }
+        __syncthreads();
+        pl_smooth(Lc, dims, 1, t0, TT);
+        __syncthreads();
+    }
+    for (int s = 0; s < sweeps; ++s) {
+        pl_smooth(Lc, dims, 1, t0, TT);
+        __syncthreads();
+        pl_smooth(Lc, dims, 0, t0, TT);
+        __syncthreads();
+    }
+    for (int l = M.nl - 2; l >= l0; --l) {
+        const LevelT<T>& L = M.lv[l];
+        pl_prolong_black(L, M.lv[l + 1], dims, t0, TT);
+        __syncthreads();
+        pl_smooth(L, dims, 0, t0, TT);
+        __syncthreads();
+    }
+}
+
+// z = B r: the level-0 zero-start red half sweep has been done by the caller;
+// the final red half sweep of level 0 accumulates r.z (r in FP64) into slot qdot
+template <typename MT>
+__device__ void pl_vcycle_rest(const PcgpArgs<MT>& A, int qdot) {
+    const MgLevelsT<MT>& M = A.M;
+    const int dims = A.g.dims;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long TT = (long long)gridDim.x * blockDim.x;
+    const int lf = A.lf;
+    pl_smooth(M.lv[0], dims, 1, t0, TT);
+    grid_sync(A);
+    for (int l = 0; l + 1 < lf; ++l) {
+        pl_restrict(M.lv[l], M.lv[l + 1], dims, true, t0, TT);
+        grid_sync(A);
+        pl_smooth(M.lv[l + 1], dims, 1, t0, TT);
+        grid_sync(A);
+    }
+    if (lf < M.nl) {
+        pl_restrict(M.lv[lf - 1], M.lv[lf], dims, false, t0, TT);
+        grid_sync(A);
+        if (blockIdx.x == 0) pl_tail(M, dims, lf, A.coarse_sweeps);
+        grid_sync(A);
+    }
+    for (int l = lf - 1; l >= 0; --l) {
+        const LevelT<MT>& L = M.lv[l];
+        if (l + 1 < M.nl) pl_prolong_black(L, M.lv[l + 1], dims, t0, TT);
+        else pl_smooth(L, dims, 1, t0, TT);
+        grid_sync(A);
+        if (l > 0) {
+            pl_smooth(L, dims, 0, t0, TT);
+            grid_sync(A);
+        }
+    }
+    // final red half sweep of level 0 with r.z
+    const LevelT<MT>& L0 = M.lv[0];
+    const double* r = A.F.r;
+    double rz = 0.0;
+    for (long long c = t0; c < L0.N; c += TT) {
+        int i, j, k;
+        pl_ijk(L0, c, i, j, k);
+        if (((i + j + k) & 1) == 0) L0.x[c] = (L0.b[c] + pl_offsum(L0, dims, L0.x, c, i, j, k)) * L0.idg[c];
+        rz += r[c] * (double)L0.x[c];
+    }
+    block_partial(A, qdot, rz);
+    grid_sync(A);
+}
+
+// ---------------------------------------------------------------- the solver
+enum { Q_RZ = 0, Q_RR = 1, Q_BB = 2, Q_R1 = 3, Q_R2 = 4, Q_R3 = 5, Q_DQ = 6 };
+
+template <typename MT>
+__global__ void __launch_bounds__(PT_THREADS) k_pressure_persistent(PcgpArgs<MT> A) {
+    const Grid& g = A.g;
+    const Fields& F = A.F;
+    const Level& L0 = A.L0d;             // FP64 operator
+    const LevelT<MT>& P0 = A.M.lv[0];    // preconditioner level 0 (z, b)
+    MT* z = A.zp;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long T = (long long)gridDim.x * blockDim.x;
+    const bool jac = A.jacobi != 0;
+    // ---- r = rhs - A p, residual sums; z0 (Jacobi, or the level-0 red start)
+    double s_rz = 0, s_rr = 0, s_bb = 0, s1 = 0, s2 = 0, s3 = 0;
+    double pbar = F.scal[SC_SUM_P] * g.iN;
+    for (long long c = t0; c < g.N; c += T) {
+        int i, j, k;
+        cell_ijk(g, c, i, j, k);
+        uint16_t f = F.flags[c];
+        int idx[3] = {i, j, k};
+        double div = 0.0, bout = 0.0, A1 = 0.0;
+        for (int d = 0; d < g.dims; ++d) {
+            long long fl = face_lo(g, d, i, j, k);
+            long long fs = face_stride(g, d);
+            div += F.phiH[d][fl + fs] - F.phiH[d][fl];
+            if (idx[d] == 0 && p_fixed(g, 2 * d)) { bout += L0.cf[d][fl] * g.p_out; A1 += L0.cf[d][fl]; }
+            if (idx[d] == g.n[d] - 1 && p_fixed(g, 2 * d + 1)) {
+                bout += L0.cf[d][fl + fs] * g.p_out;
+                A1 += L0.cf[d][fl + fs];
+            }
+        }
+        double rhs = -((f & F_M) ? div : 0.0) + bout;
+        double Ap = L0.diag[c] * F.p[c] - pl_offsum(L0, g.dims, F.p, c, i, j, k);
+        double r = rhs - Ap;
+        F.r[c] = r;
+        F.d[0][c] = 0.0;
+        F.pn[c] = F.p[c];
+        if (jac) {
+            double zz = r * L0.idg[c];
+            z[c] = (MT)zz;
+            s_rz += r * zz;
+        } else {
+            MT rb = (MT)r;
+            if ((void*)P0.b != (void*)F.r) P0.b[c] = rb;
+            if (((i + j + k) & 1) == 0) z[c] = rb * P0.idg[c];
+        }
+        s_rr += r * r;
+        s_bb += rhs * rhs;
+        s1 += fabs(r);
+        s2 += fabs(Ap - A1 * pbar);
+        s3 += fabs(rhs - A1 * pbar);
+    }
+    block_partial(A, Q_RZ, s_rz);
+    block_partial(A, Q_RR, s_rr);
+    block_partial(A, Q_BB, s_bb);
+    block_partial(A, Q_R1, s1);
+    block_partial(A, Q_R2, s2);
+    block_partial(A, Q_R3, s3);
+    grid_sync(A);
+    double rr0 = grid_total(A, Q_RR);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        F.scal[SC_PCG_INIT + 1] = rr0;
+        F.scal[SC_PCG_INIT + 3] = 0.0;
+    }
+    double r1 = grid_total(A, Q_R1), r2 = grid_total(A, Q_R2), r3 = grid_total(A, Q_R3);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        F.scal[SC_PCG_INIT + 3] = r1;
+        F.scal[SC_PCG_INIT + 4] = r2;
+        F.scal[SC_PCG_INIT + 5] = r3;
+    }
+    double tol2 = A.reltol * A.reltol * rr0;
+    int it = 0;
+    if (rr0 > 0.0 && isfinite(rr0) && A.maxit > 0) {
+        double rz;
+        if (jac) {
+            rz = grid_total(A, Q_RZ);
+        } else {
+            pl_vcycle_rest(A, Q_RZ);
+            rz = grid_total(A, Q_RZ);
+        }
+        double rz_prev = 1.0;
+        while (it < A.maxit) {
+            if (*A.err) break;
+            double beta = it == 0 ? 0.0 : rz / rz_prev;
+            const double* dold = F.d[it & 1];
+            double* dnew = F.d[(it + 1) & 1];
+            // d = z + beta d_old; q = A d; d.q
+            double s_dq = 0.0;
+            for (long long c = t0; c < g.N; c += T) {
+                int i, j, k;
+                cell_ijk(g, c, i, j, k);
+                int idx[3] = {i, j, k};
+                double dP = (double)z[c] + beta * dold[c];
+                double acc = L0.diag[c] * dP;
+                for (int d = 0; d < g.dims; ++d) {
+                    long long fl = face_lo(g, d, i, j, k);
+                    if (idx[d] > 0) {
+                        long long nc = c - g.stride[d];
+                        acc -= L0.cf[d][fl] * ((double)z[nc] + beta * dold[nc]);
+                    }
+                    if (idx[d] < g.n[d] - 1) {
+                        long long nc = c + g.stride[d];
+                        acc -= L0.cf[d][fl + face_stride(g, d)] * ((double)z[nc] + beta * dold[nc]);
+                    }
+                }
+                dnew[c] = dP;
+                F.q[c] = acc;
+                s_dq += dP * acc;
+            }
+            block_partial(A, Q_DQ, s_dq);
+            grid_sync(A);
+            double dq = grid_total(A, Q_DQ);
+            double alpha = dq != 0.0 ? rz / dq : 0.0;
+            // p += alpha d; r -= alpha q; r.r; z start
+            double s_r2 = 0.0, s_z = 0.0;
+            for (long long c = t0; c < g.N; c += T) {
+                F.pn[c] += alpha * dnew[c];
+                double r = F.r[c] - alpha * F.q[c];
+                F.r[c] = r;
+                s_r2 += r * r;
+                if (jac) {
+                    double zz = r * L0.idg[c];
+                    z[c] = (MT)zz;
+                    s_z += r * zz;
+                } else {
+                    MT rb = (MT)r;
+                    if ((void*)P0.b != (void*)F.r) P0.b[c] = rb;
+                    int i, j, k;
+                    cell_ijk(g, c, i, j, k);
+                    if (((i + j + k) & 1) == 0) z[c] = rb * P0.idg[c];
+                }
+            }
+            block_partial(A, Q_RR, s_r2);
+            if (jac) block_partial(A, Q_RZ, s_z);
+            grid_sync(A);
+            double rr = grid_total(A, Q_RR);
+            rz_prev = rz;
+            if (jac) {
+                rz = grid_total(A, Q_RZ);
+            } else {
+                pl_vcycle_rest(A, Q_RZ);
+                rz = grid_total(A, Q_RZ);
+            }
+            ++it;
+            if (!(rr > tol2)) break;
+            grid_sync(A);   // partial slots are rewritten next iteration
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        F.scal[SC_PCG_ITERS] = (double)it;
+        F.scal[SC_PCG_DONE] = 1.0;
+        if (*A.err) F.scal[SC_TIMEOUT] = 1.0;
+    }
+}
+
+// ---------------------------------------------------------------- launcher
+int pcgp_blocks(int* out) {
+    int dev = 0, sms = 0, occ = 0, occ32 = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pressure_persistent<double>, PT_THREADS, 0) !=
+        cudaSuccess)
+        return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ32, k_pressure_persistent<float>, PT_THREADS, 0) !=
+        cudaSuccess)
+        return -1;
+    if (occ < 1 || occ32 < 1) return -1;
+    *out = sms;   // one block per SM: fewer arrivals per grid barrier
+    return 0;
+}
+
+template <typename MT>
+static cudaError_t launch_pp(PcgpArgs<MT>& A, int nblk, cudaStream_t s) {
+    A.lf = A.M.nl;
+    for (int l = 1; l < A.M.nl; ++l)
+        if (A.M.lv[l].N <= PT_TAIL_CELLS) { A.lf = l; break; }
+    void* args[] = {&A};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nblk);
+    cfg.blockDim = dim3(PT_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, (const void*)k_pressure_persistent<MT>, args);
+}
+
+cudaError_t launch_pressure_persistent(const Grid& g, const Fields& F, const MgLevels& M, int jacobi,
+                                       int coarse_sweeps, double reltol, int maxit, int nblk, double* part,
+                                       unsigned int* bar, int* err, cudaStream_t s) {
+    PcgpArgs<double> A;
+    A.g = g; A.F = F; A.L0d = M.lv[0]; A.M = M; A.zp = M.lv[0].x;
+    A.coarse_sweeps = coarse_sweeps; A.jacobi = jacobi; A.reltol = reltol; A.maxit = maxit;
+    A.part = part; A.bar = bar; A.err = err;
+    return launch_pp(A, nblk, s);
+}
+
+cudaError_t launch_pressure_persistent32(const Grid& g, const Fields& F, const MgLevels& M, const MgLevels32& M32,
+                                         int coarse_sweeps, double reltol, int maxit, int nblk, double* part,
+                                         unsigned int* bar, int* err, cudaStream_t s) {
+    PcgpArgs<float> A;
+    A.g = g; A.F = F; A.L0d = M.lv[0]; A.M = M32; A.zp = M32.lv[0].x;
+    A.coarse_sweeps = coarse_sweeps; A.jacobi = 0; A.reltol = reltol; A.maxit = maxit;
+    A.part = part; A.bar = bar; A.err = err;
+    return launch_pp(A, nblk, s);
+}
+
+}  // namespace hf

@@ -22,18 +22,22 @@
 namespace hf {
 
 // ---------------------------------------------------------------- level helpers
-__device__ inline long long lv_face(const Level& L, int d, int i, int j, int k) {
+template <typename T>
+__device__ inline long long lv_face(const LevelT<T>& L, int d, int i, int j, int k) {
     if (d == 0) return ((long long)k * L.ny + j) * (L.nx + 1) + i;
     if (d == 1) return ((long long)k * (L.ny + 1) + j) * L.nx + i;
     return ((long long)k * L.ny + j) * L.nx + i;
 }
-__device__ inline long long lv_fstride(const Level& L, int d) {
+template <typename T>
+__device__ inline long long lv_fstride(const LevelT<T>& L, int d) {
     return d == 0 ? 1 : (d == 1 ? L.nx : (long long)L.nx * L.ny);
 }
-__device__ inline long long lv_cstride(const Level& L, int d) {
+template <typename T>
+__device__ inline long long lv_cstride(const LevelT<T>& L, int d) {
     return d == 0 ? 1 : (d == 1 ? L.nx : (long long)L.nx * L.ny);
 }
-__device__ inline void lv_ijk(const Level& L, long long c, int& i, int& j, int& k) {
+template <typename T>
+__device__ inline void lv_ijk(const LevelT<T>& L, long long c, int& i, int& j, int& k) {
     unsigned int cc = (unsigned int)c, nx = (unsigned int)L.nx;
     unsigned int r = cc / nx;
     i = (int)(cc - r * nx);
@@ -83,18 +87,19 @@ __global__ void k_p_coef(Grid g, Level L, const double* __restrict__ rAU) {
 }
 
 // coarse level coefficients: half the sum of the covered fine faces
-__device__ void coarsen_cell(const Level& F, const Level& Cc, int dims, long long C) {
+template <typename T>
+__device__ void coarsen_cell(const LevelT<T>& F, const LevelT<T>& Cc, int dims, long long C) {
     int I, J, K;
     lv_ijk(Cc, C, I, J, K);
     int idx[3] = {I, J, K};
     int nc[3] = {Cc.nx, Cc.ny, Cc.nz};
     int nf[3] = {F.nx, F.ny, F.nz};
-    double diag = 0.0;
+    T diag = T(0);
     for (int d = 0; d < dims; ++d) {
         for (int side = 0; side < 2; ++side) {
             if (side == 1 && idx[d] != nc[d] - 1) continue;  // high faces: boundary only (owner writes low faces)
             int fpos = side == 0 ? 2 * idx[d] : nf[d];
-            double sum = 0.0;
+            T sum = T(0);
             // the fine faces at position fpos along d covered by this coarse face
             int a1 = (d + 1) % 3, a2 = (d + 2) % 3;
             for (int o1 = 0; o1 < 2; ++o1)
@@ -107,7 +112,7 @@ __device__ void coarsen_cell(const Level& F, const Level& Cc, int dims, long lon
                     sum += F.cf[d][lv_face(F, d, fi[0], fi[1], fi[2])];
                 }
             long long cfi = lv_face(Cc, d, I, J, K) + (side ? lv_fstride(Cc, d) : 0);
-            Cc.cf[d][cfi] = 0.5 * sum;
+            Cc.cf[d][cfi] = T(0.5) * sum;
         }
     }
     // diagonal: all faces of the coarse cell (low faces of this cell and the
@@ -117,7 +122,7 @@ __device__ void coarsen_cell(const Level& F, const Level& Cc, int dims, long lon
         for (int side = 0; side < 2; ++side) {
             int fpos = side == 0 ? 2 * idx[d] : (idx[d] == nc[d] - 1 ? nf[d] : 2 * idx[d] + 2);
             int a1 = (d + 1) % 3, a2 = (d + 2) % 3;
-            double sum = 0.0;
+            T sum = T(0);
             for (int o1 = 0; o1 < 2; ++o1)
                 for (int o2 = 0; o2 < 2; ++o2) {
                     int fi[3];
@@ -127,13 +132,14 @@ __device__ void coarsen_cell(const Level& F, const Level& Cc, int dims, long lon
                     if (fi[a1] >= nf[a1] || fi[a2] >= nf[a2]) continue;
                     sum += F.cf[d][lv_face(F, d, fi[0], fi[1], fi[2])];
                 }
-            diag += 0.5 * sum;
+            diag += T(0.5) * sum;
         }
     Cc.diag[C] = diag;
-    Cc.idg[C] = diag > 0.0 ? 1.0 / diag : 0.0;
+    Cc.idg[C] = diag > T(0) ? T(1) / diag : T(0);
 }
 
-__global__ void k_coarsen(Level F, Level Cc, int dims) {
+template <typename T>
+__global__ void k_coarsen(LevelT<T> F, LevelT<T> Cc, int dims) {
     long long C = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (C >= Cc.N) return;
     coarsen_cell(F, Cc, dims, C);
@@ -246,10 +252,11 @@ __global__ void k_prolong(Level F, Level Cc, const double* done) {
 // Levels l0 .. nl-1 of one V-cycle inside one thread block.
 constexpr int TAIL_THREADS = 1024;
 
-__global__ void __launch_bounds__(TAIL_THREADS) k_tail_coarsen(MgLevels M, int dims, int l0) {
+template <typename T>
+__global__ void __launch_bounds__(TAIL_THREADS) k_tail_coarsen(MgLevelsT<T> M, int dims, int l0) {
     for (int l = l0; l < M.nl; ++l) {
-        const Level& F = M.lv[l - 1];
-        const Level& Cc = M.lv[l];
+        const LevelT<T>& F = M.lv[l - 1];
+        const LevelT<T>& Cc = M.lv[l];
         for (long long C = threadIdx.x; C < Cc.N; C += blockDim.x) coarsen_cell(F, Cc, dims, C);
         __syncthreads();
     }
@@ -446,8 +453,37 @@ __global__ void k_pcg_next(Fields F, int maxit, cudaGraphConditionalHandle hcond
 void launch_p_coef(const Grid& g, const MgLevels& M, const double* rAU, int ntail_from, cudaStream_t s) {
     k_p_coef<<<nblocks(g.N), BLOCK, 0, s>>>(g, M.lv[0], rAU);
     for (int l = 1; l < M.nl && l < ntail_from; ++l)
-        k_coarsen<<<nblocks(M.lv[l].N), BLOCK, 0, s>>>(M.lv[l - 1], M.lv[l], g.dims);
-    if (ntail_from < M.nl) k_tail_coarsen<<<1, TAIL_THREADS, 0, s>>>(M, g.dims, ntail_from);
+        k_coarsen<double><<<nblocks(M.lv[l].N), BLOCK, 0, s>>>(M.lv[l - 1], M.lv[l], g.dims);
+    if (ntail_from < M.nl) k_tail_coarsen<double><<<1, TAIL_THREADS, 0, s>>>(M, g.dims, ntail_from);
+}
+
+// FP32 copy of the level-0 operator, then FP32 coarsening (mixed path)
+__global__ void k_p_coef32(Grid g, Level L, Level32 P) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    int i, j, k;
+    cell_ijk(g, c, i, j, k);
+    int idx[3] = {i, j, k};
+    for (int d = 0; d < g.dims; ++d) {
+        long long fl = lv_face(L, d, i, j, k);
+        P.cf[d][fl] = (float)L.cf[d][fl];
+        if (idx[d] == g.n[d] - 1) {
+            long long fh = fl + lv_fstride(L, d);
+            P.cf[d][fh] = (float)L.cf[d][fh];
+        }
+    }
+    P.diag[c] = (float)L.diag[c];
+    P.idg[c] = (float)L.idg[c];
+}
+
+void launch_p_coef32(const Grid& g, const MgLevels& M, const MgLevels32& M32, cudaStream_t s) {
+    k_p_coef32<<<nblocks(g.N), BLOCK, 0, s>>>(g, M.lv[0], M32.lv[0]);
+    int tail = M32.nl;
+    for (int l = 1; l < M32.nl; ++l)
+        if (M32.lv[l].N <= TAIL_CELLS) { tail = l; break; }
+    for (int l = 1; l < M32.nl && l < tail; ++l)
+        k_coarsen<float><<<nblocks(M32.lv[l].N), BLOCK, 0, s>>>(M32.lv[l - 1], M32.lv[l], g.dims);
+    if (tail < M32.nl) k_tail_coarsen<float><<<1, TAIL_THREADS, 0, s>>>(M32, g.dims, tail);
 }
 
 // z = B r (one V-cycle) with r.z written to *dot_out; skipped once the

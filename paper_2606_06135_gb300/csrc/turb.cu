@@ -61,6 +61,7 @@ __global__ void k_turb_prep(Grid g, Params P, Fields F) {
         F.sp[c] = KE_C2 * ratio * V;
         F.src[c] = KE_C1 * (nut * S2) * ratio * V;
         F.gamk[c] = g.nu + nut / KE_SIGK;
+        if (F.mixed) { F.gam32[c] = (float)F.gam[c]; F.gamk32[c] = (float)F.gamk[c]; }
     } else {
         double gk = 0.0;
         for (int d = 0; d < g.dims; ++d)
@@ -82,6 +83,7 @@ __global__ void k_turb_prep(Grid g, Params P, Fields F) {
         F.sp[c] = beta * wold * V + (cdc > 0.0 ? cdc : 0.0) * V;
         F.src[c] = gamma * GbyNu * V - (cdc > 0.0 ? 0.0 : cdc) * wold * V;
         F.gamk[c] = g.nu + (F1 * SST_AK1 + (1.0 - F1) * SST_AK2) * nut;
+        if (F.mixed) { F.gam32[c] = (float)F.gam[c]; F.gamk32[c] = (float)F.gamk[c]; }
     }
 }
 
@@ -118,44 +120,54 @@ __device__ inline bool scal_row_fixed(const Grid& g, const Fields& F, int eq, lo
     return false;
 }
 
-struct ScalRow {
-    double aP, bnd;
-    double a[6];
+template <typename T>
+struct ScalRowT {
+    T aP, bnd;
+    T a[6];
     long long nb[6];
     bool has[6];
 };
+using ScalRow = ScalRowT<double>;
 
-__device__ void scal_row(const Grid& g, const Fields& F, const double* gam, double xin, long long c, int i,
-                         int j, int k, uint16_t f, ScalRow& R) {
-    double gP = gam[c];
-    R.aP = 0.0;
-    R.bnd = 0.0;
+// transport row of a turbulence scalar; T = double (operator) or float
+// (FP32 smoother of the mixed path, from FP32 mirrors)
+template <typename T>
+__device__ void scal_row_t(const Grid& g, T* const* phi, const T* gam, double xin, long long c, int i, int j,
+                           int k, uint16_t f, ScalRowT<T>& R) {
+    T gP = gam[c];
+    R.aP = T(0);
+    R.bnd = T(0);
     for (int d = 0; d < g.dims; ++d) {
         long long fl = face_lo(g, d, i, j, k);
         long long fs = face_stride(g, d);
         for (int side = 0; side < 2; ++side) {
             int s = 2 * d + side;
-            double Fb = F.phi[d][fl + side * fs];
-            double Fout = side ? Fb : -Fb;
+            T Fb = phi[d][fl + side * fs];
+            T Fout = side ? Fb : -Fb;
             if (interior_t(g, d, side, i, j, k)) {
                 long long nc = side ? c + g.stride[d] : c - g.stride[d];
-                double Dif = 0.5 * (gP + gam[nc]) * g.SoD[d];
-                R.a[s] = fmin(Fout, 0.0) - Dif;
+                T Dif = T(0.5) * (gP + gam[nc]) * (T)g.SoD[d];
+                R.a[s] = fmin(Fout, T(0)) - Dif;
                 R.nb[s] = nc;
                 R.has[s] = true;
-                R.aP += fmax(-Fout, 0.0) + Dif;
+                R.aP += fmax(-Fout, T(0)) + Dif;
             } else {
-                R.a[s] = 0.0;
+                R.a[s] = T(0);
                 R.nb[s] = c;
                 R.has[s] = false;
                 if (scal_fixed(g, f, s)) {
-                    double coef = gP * g.SoHD[d] + fmax(-Fout, 0.0);
+                    T coef = gP * (T)g.SoHD[d] + fmax(-Fout, T(0));
                     R.aP += coef;
-                    R.bnd += coef * xin;
+                    R.bnd += coef * (T)xin;
                 }
             }
         }
     }
+}
+
+__device__ inline void scal_row(const Grid& g, const Fields& F, const double* gam, double xin, long long c, int i,
+                                int j, int k, uint16_t f, ScalRow& R) {
+    scal_row_t<double>(g, F.phi, gam, xin, c, i, j, k, f, R);
 }
 
 __global__ void k_scal_asm(Grid g, Params P, Fields F, int eq) {
@@ -175,11 +187,13 @@ __global__ void k_scal_asm(Grid g, Params P, Fields F, int eq) {
         double xold = x[c];
         F.bt[c] = b + P.rlx_t * aP * xold;
         F.diag[c] = aP * P.iurf_t;
+        if (F.mixed) F.diag32[c] = (float)(aP * P.iurf_t);
         double fv;
         if (scal_row_fixed(g, F, eq, c, fv)) {
             // imposed rows start at their imposed values (only neighbours'
             // substituted values are read below, so this write is race-free)
             x[c] = fv;
+            if (F.mixed) F.r32[0][c] = 0.0f;
         } else {
             double Ax = aP * xold, A1 = aP;
             for (int s = 0; s < 2 * g.dims; ++s) {
@@ -193,6 +207,8 @@ __global__ void k_scal_asm(Grid g, Params P, Fields F, int eq) {
             red[0] = fabs(b - Ax);
             red[1] = fabs(Ax - A1 * xbar);
             red[2] = fabs(b - A1 * xbar);
+            // defect of the relaxed system at x_old (relaxation terms cancel)
+            if (F.mixed) F.r32[0][c] = (float)(b - Ax);
         }
     }
     grid_reduce<3, false>(red, F.partials, F.counters + 7, F.scal + (eq == 0 ? SC_RES_W : SC_RES_K));
@@ -221,11 +237,37 @@ __global__ void k_scal_smooth(Grid g, Params P, Fields F, int eq, int colour) {
     x[c] = acc / F.diag[c];
 }
 
+// FP32 red-black sweep on the correction (mixed path): diag d_P + sum a_N d_N
+// = r (FP64 defect rounded); d = 0 on imposed rows
+__global__ void k_scal_smooth32(Grid g, Params P, Fields F, int eq, int colour, int zero_init) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    int i, j, k;
+    cell_ijk(g, c, i, j, k);
+    if (((i + j + k) & 1) != colour) return;
+    double fv;
+    if (scal_row_fixed(g, F, eq, c, fv)) {
+        F.d32[0][c] = 0.0f;
+        return;
+    }
+    const float* gam = eq == 0 ? F.gam32 : F.gamk32;
+    double xin = eq == 0 ? P.w_in : P.k_in;
+    uint16_t f = F.flags[c];
+    ScalRowT<float> R;
+    scal_row_t<float>(g, F.phi32, gam, xin, c, i, j, k, f, R);
+    float acc = F.r32[0][c];
+    if (!zero_init)
+        for (int s = 0; s < 2 * g.dims; ++s)
+            if (R.has[s]) acc -= R.a[s] * F.d32[0][R.nb[s]];
+    F.d32[0][c] = acc / F.diag32[c];
+}
+
 // after the eps/omega solve: bound it, set the k-equation sink and source
 __global__ void k_k_prep(Grid g, Params P, Fields F) {
     long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.N) return;
     double w = F.w[c];
+    if (F.mixed) w += (double)F.d32[0][c];   // apply the FP32 correction
     double wmin = P.model == HFDIB_KEPSILON ? EPS_MIN : OMEGA_MIN;
     w = fmax(w, wmin);
     F.w[c] = w;
@@ -244,20 +286,25 @@ __global__ void k_turb_final(Grid g, Params P, Fields F) {
     long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.N) return;
     uint16_t f = F.flags[c];
-    double k = fmax(F.k[c], K_MIN);
+    double kx = F.k[c];
+    if (F.mixed) kx += (double)F.d32[0][c];  // apply the FP32 correction
+    double k = fmax(kx, K_MIN);
     if (tag_of(f) == TAG_IC) k = k + (0.0 - k);
     else if (f & F_AU) k = k + (F.kib[c] - k);
     F.k[c] = k;
     double w = F.w[c];
+    double nut;
     if (P.model == HFDIB_KEPSILON) {
-        F.nut[c] = C_MU * k * k / w;
+        nut = C_MU * k * k / w;
         F.w2[c] = w / (C_MU * fmax(k, K_MIN));
     } else {
         double y = fmax(F.ywall[c], 1e-3 * g.h);
         double F2 = sst_F2(fmax(k, K_MIN), w, y, g.nu);
-        F.nut[c] = SST_A1 * k / fmax(SST_A1 * w, SST_BB1 * F2 * sqrt(F.S2[c]));
+        nut = SST_A1 * k / fmax(SST_A1 * w, SST_BB1 * F2 * sqrt(F.S2[c]));
         F.w2[c] = C_MU * k * w;
     }
+    F.nut[c] = nut;
+    if (F.mixed) F.nut32[c] = (float)nut;
 }
 
 // ---------------------------------------------------------------- launchers
@@ -274,6 +321,10 @@ void launch_scal_asm(const Grid& g, const Params& P, const Fields& F, int eq, cu
 void launch_scal_smooth(const Grid& g, const Params& P, const Fields& F, int eq, int colour,
                         cudaStream_t s) {
     k_scal_smooth<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F, eq, colour);
+}
+void launch_scal_smooth32(const Grid& g, const Params& P, const Fields& F, int eq, int colour, int zero_init,
+                          cudaStream_t s) {
+    k_scal_smooth32<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F, eq, colour, zero_init);
 }
 void launch_k_prep(const Grid& g, const Params& P, const Fields& F, cudaStream_t s) {
     k_k_prep<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F);

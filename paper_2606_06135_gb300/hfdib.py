@@ -24,7 +24,7 @@ FIELDS = {"ux": 0, "uy": 1, "uz": 2, "p": 3, "k": 4, "eps": 5, "omega": 6, "nut"
 RES_NAMES = ("Ux", "Uy", "Uz", "p", "epsw", "k", "cont", "p_iters", "n_lam", "n_switch")
 NRES = 10
 STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "out of memory",
-          -4: "not converged", -5: "diverged", -6: "state mismatch", -7: "too large"}
+          -4: "not converged", -5: "diverged", -6: "state mismatch", -7: "too large", -8: "timeout"}
 
 ERR_NOT_CONVERGED = -4
 STATUS_TOO_LARGE = -7
@@ -53,7 +53,7 @@ class Options(C.Structure):
                 ("n_u", C.c_int32), ("n_turb", C.c_int32), ("p_reltol", C.c_double),
                 ("p_maxiter", C.c_int32), ("precision", C.c_int32), ("precond", C.c_int32),
                 ("p_check", C.c_int32), ("mg_coarse_sweeps", C.c_int32), ("graph", C.c_int32),
-                ("freeze_switch", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("p_persistent", C.c_int32), ("freeze_switch", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 _LIB = None

@@ -155,3 +155,45 @@ def test_invalid_lambda_rejected():
     case["lam"][0, 3, 3] = 1.5
     with pytest.raises(HfdibError):
         make_solver(case)
+
+
+@pytest.mark.parametrize("name", sorted(CONVERGED))
+def test_converged_state_mixed_precision(name):
+    """FP32 inner sweeps and FP32 multigrid inside FP64 refinement: the steady
+    state solves the FP64 equations, so it must match the FP64 oracle within
+    relative L2 1e-4 per field (it is expected far closer)."""
+    mk, maxit = CONVERGED[name]
+    case = mk()
+    o = O.Oracle(case)
+    _, ores = o.solve(tol=1e-12, max_iter=2000)
+    s = make_solver(case, precision=1)
+    rc, it, res = s.solve(tol=1e-12, max_iter=maxit, check_every=20)
+    assert rc == 0, (rc, it, res)
+    errs = compare_fields(s, o, 1e-4)
+    print("mixed-precision rel-L2 vs FP64 oracle (%s, %d sweeps):" % (name, it),
+          {k: "%.2e" % v for k, v in errs.items()})
+    s.close()
+
+
+def test_mixed_rejects_unsupported_combinations():
+    from paper_2606_06135_gb300.hfdib import HfdibError
+    case = G.case_cylinder(32, 16)
+    with pytest.raises(HfdibError):
+        make_solver(case, precision=1, p_persistent=0)
+    with pytest.raises(HfdibError):
+        make_solver(case, precision=1, precond=0)
+
+
+def test_persistent_and_multikernel_pressure_agree():
+    """The persistent cooperative CG kernel and the one-launch-per-step CG
+    run the same arithmetic: a few sweeps agree to round-off."""
+    case = G.case_cylinder(64, 32)
+    a = make_solver(case)
+    b = make_solver(case, p_persistent=0)
+    a.sweep(10)
+    b.sweep(10)
+    fa, fb = a.fields(), b.fields()
+    for n in fa:
+        assert relL2(fa[n], fb[n]) < 1e-12, n
+    a.close()
+    b.close()
