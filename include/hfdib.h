@@ -82,7 +82,7 @@ typedef struct {
     double urf_turb;             /* k, eps/omega under-relaxation (default 0.85)  */
     int32_t n_u;                 /* red-black Gauss-Seidel sweeps, momentum (2)   */
     int32_t n_turb;              /* red-black Gauss-Seidel sweeps, k and eps/omega (2) */
-    double p_reltol;             /* pressure solve: |r| <= p_reltol |r0| (0.01)   */
+    double p_reltol;             /* pressure solve: |r| <= p_reltol |r0| (0.1)    */
     int32_t p_maxiter;           /* pressure solve iteration cap (50)             */
     int32_t precision;           /* 0: FP64 throughout (default).  1: mixed -- FP64
                                     state, assembly, defects (residuals), CG vectors

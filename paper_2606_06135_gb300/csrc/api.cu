@@ -211,17 +211,14 @@ void enqueue_part_a(Ctx* h, long long* L) {
     // a7 set-up: operator, r0, initial preconditioning, loop state
     const MgLevels& M = h->mg;
     int jac = h->opt.precond == 0;
-    PROF(h, HFDIB_K_P_COEF, launch_p_coef(g, M, F.rAU, h->tail_from, s));
-    *L += 1 + (h->tail_from - 1) + (h->tail_from < M.nl ? 1 : 0);
     if (h->pblocks > 0) {
-        // the whole solve in one cooperative launch
+        // the whole solve, operator hierarchy included, in one cooperative launch
         cudaMemsetAsync(h->pbar, 0, sizeof(unsigned int), s);
         if (F.mixed) {
-            PROF(h, HFDIB_K_P_COEF, launch_p_coef32(g, M, h->mg32, s));
             PROF(h, HFDIB_K_PCG, launch_pressure_persistent32(g, F, M, h->mg32, h->coarse_sweeps,
                                                                h->opt.p_reltol, h->opt.p_maxiter, h->pblocks,
                                                                h->ppart, h->pbar, h->perr, s));
-            *L += 2 + (h->tail_from - 1) + (h->tail_from < M.nl ? 1 : 0);
+            (*L)++;
         } else {
             PROF(h, HFDIB_K_PCG, launch_pressure_persistent(g, F, M, jac, h->coarse_sweeps, h->opt.p_reltol,
                                                              h->opt.p_maxiter, h->pblocks, h->ppart, h->pbar,
@@ -230,6 +227,8 @@ void enqueue_part_a(Ctx* h, long long* L) {
         }
         return;
     }
+    PROF(h, HFDIB_K_P_COEF, launch_p_coef(g, M, F.rAU, h->tail_from, s));
+    *L += 1 + (h->tail_from - 1) + (h->tail_from < M.nl ? 1 : 0);
     PROF(h, HFDIB_K_PCG, launch_pcg_init(g, F, M, jac, s));
     (*L)++;
     if (!jac) {
@@ -436,7 +435,7 @@ void hfdib_default_options(hfdib_options* o) {
     o->urf_turb = 0.85;
     o->n_u = 2;
     o->n_turb = 2;
-    o->p_reltol = 0.01;
+    o->p_reltol = 0.1;
     o->p_maxiter = 50;
     o->precision = 0;
     o->precond = 1;
@@ -865,8 +864,8 @@ int hfdib_get_launch_counts(hfdib_handle hh, int64_t* per_sweep, int64_t* per_pc
     bool turb = h->model != HFDIB_LAMINAR;
     int jac = h->opt.precond == 0;
     int tf = h->tail_from;
-    La = (turb ? 1 : 0) + 4 + 2 * h->opt.n_u + 2 + (1 + (tf - 1) + (tf < h->mg.nl ? 1 : 0)) +
-         (h->pblocks > 0 ? 1 : 1 + (jac ? 0 : 5 * tf + 1) + 1);
+    La = (turb ? 1 : 0) + 4 + 2 * h->opt.n_u + 2 +
+         (h->pblocks > 0 ? 1 : (1 + (tf - 1) + (tf < h->mg.nl ? 1 : 0)) + 1 + (jac ? 0 : 5 * tf + 1) + 1);
     Lb = 1 + (turb ? 4 + 2 * h->opt.n_turb + 2 + 2 * h->opt.n_turb + 1 : 0) + 1;
     Lp = h->pblocks > 0 ? 0 : 3 + (jac ? 0 : 5 * tf + 1);
     if (per_sweep) *per_sweep = La + Lb;

@@ -23,8 +23,9 @@
 
 namespace hf {
 
-constexpr int PT_THREADS = 512;
-constexpr long long PT_TAIL_CELLS = 1024;
+constexpr int PT_THREADS = 1024;
+constexpr long long PT_TAIL_CELLS = 1024;        // block-0 tail read from global memory
+constexpr long long PT_SMEM_TAIL_CELLS = 1024;   // block-0 tail held in shared memory
 constexpr long long PT_SPIN_LIMIT = 1ll << 26;   // ~0.1-1 s of polling
 
 template <typename MT>
@@ -35,35 +36,37 @@ struct PcgpArgs {
     MgLevelsT<MT> M;     // preconditioner hierarchy (level 0 = the grid)
     MT* zp;              // preconditioned residual z (= M.lv[0].x)
     int lf;              // levels 0..lf-1 by the whole grid, lf..nl-1 by block 0
+    int smem_tail;       // 1: block 0 keeps the tail levels in shared memory
     int coarse_sweeps;
     int jacobi;
     double reltol;
     int maxit;
     double* part;        // [8][gridDim.x] block partials
-    unsigned int* bar;   // [2] barrier arrival count, generation
+    unsigned int* bar;   // barrier arrival counter (zeroed before each launch)
     int* err;            // barrier timeout flag
 };
 
 // ---------------------------------------------------------------- barrier
+// monotone arrival counter: barrier number m completes when the counter
+// reaches m * gridDim.x; polled with acquire loads, bounded
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 template <typename AT>
 __device__ inline void grid_sync(const AT& A) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned int* gen = A.bar + 1;
-        unsigned int g0 = *gen;
+        unsigned int nb = gridDim.x;
         __threadfence();
-        unsigned int arrived = atomicAdd(A.bar, 1u);
-        if (arrived == gridDim.x - 1) {
-            A.bar[0] = 0u;
-            __threadfence();
-            atomicAdd(A.bar + 1, 1u);
-        } else {
-            long long spins = 0;
-            while (*gen == g0) {
-                if (++spins > PT_SPIN_LIMIT) { atomicExch(A.err, 1); break; }
-            }
+        unsigned int old = atomicAdd(A.bar, 1u);
+        unsigned int target = (old / nb + 1u) * nb;
+        long long spins = 0;
+        while ((int)(ld_acquire_u32(A.bar) - target) < 0) {
+            if (++spins > PT_SPIN_LIMIT) { atomicExch(A.err, 1); break; }
         }
-        __threadfence();
     }
     __syncthreads();
 }
@@ -248,6 +251,47 @@ __device__ void pl_tail(const MgLevelsT<T>& M, int dims, int l0, int sweeps) {
     }
 }
 
+// block 0's copy of the level table whose tail levels point into dynamic
+// shared memory (set up once per solve by pl_load_tail)
+template <typename MT>
+__device__ inline MgLevelsT<MT>* tail_levels() {
+    __shared__ MgLevelsT<MT> table;
+    return &table;
+}
+
+extern __shared__ __align__(16) unsigned char pt_dyn_smem[];
+
+template <typename MT>
+__device__ void pl_load_tail(const PcgpArgs<MT>& A) {
+    MgLevelsT<MT>* S = tail_levels<MT>();
+    const int dims = A.g.dims;
+    if (threadIdx.x == 0) {
+        *S = A.M;
+        MT* p = (MT*)pt_dyn_smem;
+        for (int l = A.lf; l < A.M.nl; ++l) {
+            LevelT<MT>& L = S->lv[l];
+            L.diag = p; p += L.N;
+            L.idg = p; p += L.N;
+            L.x = p; p += L.N;
+            L.b = p; p += L.N;
+            L.cf[0] = p; p += (long long)(L.nx + 1) * L.ny * L.nz;
+            L.cf[1] = p; p += (long long)L.nx * (L.ny + 1) * L.nz;
+            if (dims == 3) { L.cf[2] = p; p += (long long)L.nx * L.ny * (L.nz + 1); }
+        }
+    }
+    __syncthreads();
+    for (int l = A.lf; l < A.M.nl; ++l) {
+        const LevelT<MT>& G = A.M.lv[l];
+        const LevelT<MT>& L = S->lv[l];
+        for (long long c = threadIdx.x; c < G.N; c += blockDim.x) { L.diag[c] = G.diag[c]; L.idg[c] = G.idg[c]; }
+        long long nf[3] = {(long long)(G.nx + 1) * G.ny * G.nz, (long long)G.nx * (G.ny + 1) * G.nz,
+                           (long long)G.nx * G.ny * (G.nz + 1)};
+        for (int d = 0; d < dims; ++d)
+            for (long long f = threadIdx.x; f < nf[d]; f += blockDim.x) L.cf[d][f] = G.cf[d][f];
+    }
+    __syncthreads();
+}
+
 // z = B r: the level-0 zero-start red half sweep has been done by the caller;
 // the final red half sweep of level 0 accumulates r.z (r in FP64) into slot qdot
 template <typename MT>
@@ -268,7 +312,20 @@ __device__ void pl_vcycle_rest(const PcgpArgs<MT>& A, int qdot) {
     if (lf < M.nl) {
         pl_restrict(M.lv[lf - 1], M.lv[lf], dims, false, t0, TT);
         grid_sync(A);
-        if (blockIdx.x == 0) pl_tail(M, dims, lf, A.coarse_sweeps);
+        if (blockIdx.x == 0) {
+            if (A.smem_tail) {
+                // the tail levels live in shared memory: bring b of level lf in,
+                // cycle, send x of level lf back for the grid's prolongation
+                const MgLevelsT<MT>& S = *tail_levels<MT>();
+                for (long long c = threadIdx.x; c < M.lv[lf].N; c += blockDim.x) S.lv[lf].b[c] = M.lv[lf].b[c];
+                __syncthreads();
+                pl_tail(S, dims, lf, A.coarse_sweeps);
+                for (long long c = threadIdx.x; c < M.lv[lf].N; c += blockDim.x) M.lv[lf].x[c] = S.lv[lf].x[c];
+                __syncthreads();
+            } else {
+                pl_tail(M, dims, lf, A.coarse_sweeps);
+            }
+        }
         grid_sync(A);
     }
     for (int l = lf - 1; l >= 0; --l) {
@@ -295,6 +352,85 @@ __device__ void pl_vcycle_rest(const PcgpArgs<MT>& A, int qdot) {
     grid_sync(A);
 }
 
+// coarse operator: face coefficients half the sum of the covered fine faces
+// (same rule as pressure.cu), diagonal and inverse diagonal
+template <typename T>
+__device__ inline void pl_coarsen(const LevelT<T>& F, const LevelT<T>& Cc, int dims, long long t0, long long TT) {
+    int nf[3] = {F.nx, F.ny, F.nz};
+    int nc[3] = {Cc.nx, Cc.ny, Cc.nz};
+    for (long long C = t0; C < Cc.N; C += TT) {
+        int I, J, K;
+        pl_ijk(Cc, C, I, J, K);
+        int idx[3] = {I, J, K};
+        T diag = T(0);
+        for (int d = 0; d < dims; ++d)
+            for (int side = 0; side < 2; ++side) {
+                int fpos = side == 0 ? 2 * idx[d] : (idx[d] == nc[d] - 1 ? nf[d] : 2 * idx[d] + 2);
+                int a1 = (d + 1) % 3, a2 = (d + 2) % 3;
+                T sum = T(0);
+                for (int o1 = 0; o1 < 2; ++o1)
+                    for (int o2 = 0; o2 < 2; ++o2) {
+                        int fi[3];
+                        fi[d] = fpos;
+                        fi[a1] = 2 * idx[a1] + o1;
+                        fi[a2] = 2 * idx[a2] + o2;
+                        if (fi[a1] >= nf[a1] || fi[a2] >= nf[a2]) continue;
+                        sum += F.cf[d][pl_face(F, d, fi[0], fi[1], fi[2])];
+                    }
+                T v = T(0.5) * sum;
+                diag += v;
+                if (side == 0) Cc.cf[d][pl_face(Cc, d, I, J, K)] = v;
+                else if (idx[d] == nc[d] - 1) Cc.cf[d][pl_face(Cc, d, I, J, K) + pl_fstride(Cc, d)] = v;
+            }
+        Cc.diag[C] = diag;
+        Cc.idg[C] = diag > T(0) ? T(1) / diag : T(0);
+    }
+}
+
+// level-0 operator from rAU (FP64, also used by the flux correction), its
+// copy in the preconditioner precision, then the coarse levels
+template <typename MT>
+__device__ void pl_build_operator(const PcgpArgs<MT>& A) {
+    const Grid& g = A.g;
+    const Level& L = A.L0d;
+    const LevelT<MT>& P0 = A.M.lv[0];
+    const double* rAU = A.F.rAU;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long TT = (long long)gridDim.x * blockDim.x;
+    const bool copy = (void*)P0.diag != (void*)L.diag;
+    for (long long c = t0; c < g.N; c += TT) {
+        int i, j, k;
+        cell_ijk(g, c, i, j, k);
+        int idx[3] = {i, j, k};
+        double diag = 0.0;
+        for (int d = 0; d < g.dims; ++d) {
+            long long fl = pl_face(L, d, i, j, k);
+            long long fs = pl_fstride(L, d);
+            double clo, chi;
+            if (idx[d] > 0) clo = 0.5 * (rAU[c] + rAU[c - g.stride[d]]) * g.SoD[d];
+            else clo = p_fixed(g, 2 * d) ? rAU[c] * g.SoHD[d] : 0.0;
+            if (idx[d] < g.n[d] - 1) chi = 0.5 * (rAU[c] + rAU[c + g.stride[d]]) * g.SoD[d];
+            else chi = p_fixed(g, 2 * d + 1) ? rAU[c] * g.SoHD[d] : 0.0;
+            L.cf[d][fl] = clo;
+            if (copy) P0.cf[d][fl] = (MT)clo;
+            if (idx[d] == g.n[d] - 1) {
+                L.cf[d][fl + fs] = chi;
+                if (copy) P0.cf[d][fl + fs] = (MT)chi;
+            }
+            diag += clo + chi;
+        }
+        double idg = diag > 0.0 ? 1.0 / diag : 0.0;
+        L.diag[c] = diag;
+        L.idg[c] = idg;
+        if (copy) { P0.diag[c] = (MT)diag; P0.idg[c] = (MT)idg; }
+    }
+    grid_sync(A);
+    for (int l = 1; l < A.M.nl; ++l) {
+        pl_coarsen(A.M.lv[l - 1], A.M.lv[l], g.dims, t0, TT);
+        grid_sync(A);
+    }
+}
+
 // ---------------------------------------------------------------- the solver
 enum { Q_RZ = 0, Q_RR = 1, Q_BB = 2, Q_R1 = 3, Q_R2 = 4, Q_R3 = 5, Q_DQ = 6 };
 
@@ -308,6 +444,9 @@ __global__ void __launch_bounds__(PT_THREADS) k_pressure_persistent(PcgpArgs<MT>
     const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long T = (long long)gridDim.x * blockDim.x;
     const bool jac = A.jacobi != 0;
+    // ---- operator hierarchy for this sweep's rAU (tail levels to shared memory)
+    pl_build_operator(A);
+    if (A.smem_tail && A.lf < A.M.nl && blockIdx.x == 0) pl_load_tail(A);
     // ---- r = rhs - A p, residual sums; z0 (Jacobi, or the level-0 red start)
     double s_rz = 0, s_rr = 0, s_bb = 0, s1 = 0, s2 = 0, s3 = 0;
     double pbar = F.scal[SC_SUM_P] * g.iN;
@@ -467,16 +606,46 @@ int pcgp_blocks(int* out) {
     return 0;
 }
 
+// shared-memory bytes of the tail levels l0..nl-1
+template <typename MT>
+static size_t tail_bytes(const MgLevelsT<MT>& M, int dims, int l0) {
+    size_t n = 0;
+    for (int l = l0; l < M.nl; ++l) {
+        const LevelT<MT>& L = M.lv[l];
+        n += 4 * (size_t)L.N + (size_t)(L.nx + 1) * L.ny * L.nz + (size_t)L.nx * (L.ny + 1) * L.nz;
+        if (dims == 3) n += (size_t)L.nx * L.ny * (L.nz + 1);
+    }
+    return n * sizeof(MT);
+}
+
+constexpr size_t PT_SMEM_BUDGET = 160 * 1024;
+
 template <typename MT>
 static cudaError_t launch_pp(PcgpArgs<MT>& A, int nblk, cudaStream_t s) {
+    // tail = the coarsest levels whose operator fits the shared-memory
+    // budget (at most PT_SMEM_TAIL_CELLS cells on its finest level)
     A.lf = A.M.nl;
-    for (int l = 1; l < A.M.nl; ++l)
-        if (A.M.lv[l].N <= PT_TAIL_CELLS) { A.lf = l; break; }
+    A.smem_tail = 0;
+    size_t bytes = 0;
+    for (int l = 1; l < A.M.nl; ++l) {
+        if (A.M.lv[l].N > PT_SMEM_TAIL_CELLS) continue;
+        size_t b = tail_bytes(A.M, A.g.dims, l);
+        if (b <= PT_SMEM_BUDGET) { A.lf = l; A.smem_tail = 1; bytes = b; break; }
+    }
+    if (!A.smem_tail) {
+        for (int l = 1; l < A.M.nl; ++l)
+            if (A.M.lv[l].N <= PT_TAIL_CELLS) { A.lf = l; break; }
+    }
+    if (bytes > 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_pressure_persistent<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bytes);
+        if (e != cudaSuccess) return e;
+    }
     void* args[] = {&A};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nblk);
     cfg.blockDim = dim3(PT_THREADS);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = bytes;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;

@@ -287,5 +287,15 @@ def case_rotated_box(beta_deg=15.0, n=64, model="kepsilon", Re=1e4):
                       I_in=0.02, lt_in=0.2)
 
 
+def case_sphere(nx=32, ny=16, nz=16, model="kepsilon", Re=40.0, D=1.0):
+    """Sphere D = 1 at (4D, 4D, 4D) in a 16D x 8D x 8D box (3D cylinder
+    analogue): inlet x-, outlet x+, slip on the four other sides."""
+    g = make_grid(nx, ny, nz, 0.0, 0.0, 16.0 * D, 8.0 * D, z0=0.0, lz=8.0 * D)
+    X, Y, Z = cell_centres(g)
+    sigma = np.sqrt((X - 4.0 * D) ** 2 + (Y - 4.0 * D) ** 2 + (Z - 4.0 * D) ** 2) - 0.5 * D
+    bc = dict(xmin="inlet", xmax="outlet", ymin="slip", ymax="slip", zmin="slip", zmax="slip")
+    return _base_case("sphere", g, sigma, sigma, model, Re, bc, I_in=0.02, lt_in=0.8 * D, l_ref=D)
+
+
 def nu_of(case):
     return case["u_ref"] * case["l_ref"] / case["Re"]

@@ -197,3 +197,40 @@ def test_persistent_and_multikernel_pressure_agree():
         assert relL2(fa[n], fb[n]) < 1e-12, n
     a.close()
     b.close()
+
+
+# ---------------------------------------------------------------- 3D
+SPHERE = {"laminar": lambda: G.case_sphere(32, 16, 16, model="laminar"),
+          "kepsilon": lambda: G.case_sphere(32, 16, 16, model="kepsilon")}
+
+
+@pytest.mark.parametrize("model", sorted(SPHERE))
+def test_3d_sweeps_match_oracle_with_exact_inner_solves(model):
+    """3D (7-point rows, 26 vertex neighbours, trilinear stencils)."""
+    case = SPHERE[model]()
+    o = O.Oracle(case)
+    s = make_solver(case, **EXACT)
+    for n in range(2):
+        o.sweep()
+        s.sweep()
+    got = s.fields()
+    assert "uz" in got
+    errs = {n: relL2(got[n], ref) for n, ref in (("ux", o.u[0]), ("uy", o.u[1]), ("uz", o.u[2]), ("p", o.p))}
+    assert max(errs.values()) < 1e-9, errs
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_3d_converged_state_matches_oracle(precision):
+    case = SPHERE["kepsilon"]()
+    o = O.Oracle(case)
+    _, ores = o.solve(tol=1e-12, max_iter=1500)
+    assert o.max_residual(ores) <= 1e-12
+    s = make_solver(case, precision=precision)
+    rc, it, res = s.solve(tol=1e-12, max_iter=6000, check_every=20)
+    assert rc == 0, (rc, it, res)
+    got = s.fields()
+    errs = {n: relL2(got[n], ref) for n, ref in (("ux", o.u[0]), ("uy", o.u[1]), ("uz", o.u[2]),
+                                                  ("p", o.p), ("k", o.k), ("eps", o.eps), ("nut", o.nut))}
+    assert max(errs.values()) < 1e-9, errs
+    s.close()
