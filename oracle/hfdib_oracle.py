@@ -684,7 +684,9 @@ class Oracle:
             wf[cells] = wv
             w_ib = wf.reshape(m.shape)
             ef = e_ib.ravel()
-            ef[cells] = C_MU * kP * wv        # eps = C_mu k omega
+            # eps = C_mu k omega with the k this cell takes this sweep: k_ib
+            # where k is imposed (laminar branch), the old k_P where it is solved
+            ef[cells] = C_MU * np.where(lamb, kval, kP) * wv
             e_ib = ef.reshape(m.shape)
         self.alpha_u = alpha_u
         self.u_ib = u_ib

@@ -8,7 +8,8 @@
 // a1 max over bc u fc of omega_old (eps_old) (Eq. imval).
 // a2 u_tau (Eq. frictionvel), y+ (Eq. yplus), alpha_u = alpha_k (Eq.
 //    alphauk), u_ib and k_ib (quadratic interpolation, surface k of Eq. kws),
-//    omega_ib (Eq. omegaws; eps_ib = C_mu k_P omega_ib for k-epsilon).
+//    omega_ib (Eq. omegaws; eps_ib = C_mu k omega_ib for k-epsilon, k = k_ib
+//    in laminar-branch cells, k_P elsewhere).
 //
 // This file is compiled with -fmad=false: the geometry uses IEEE double
 // +,-,*,/ and sqrt in a fixed order, so every integer decision (tags,
@@ -352,10 +353,13 @@ __global__ void k_imposed(Grid g, int model, int freeze, BcList bl, uint16_t* __
         double v1 = interp_cell(g, kf, b1, t1);
         double v2 = interp_cell(g, kf, b2, t2);
         double kv = wS * kS + w1 * v1 + w2 * v2;
-        kib[c] = lamb ? fmax(kv, 0.0) : 0.0;
+        double kimp = fmax(kv, 0.0);
+        kib[c] = lamb ? kimp : 0.0;
         // Eq. omegaws with y+ = y_eff u_tau / nu substituted
         double w = lamb ? 6.0 * g.nu / (BETA1_WF * ye * ye) : ut / (KAPPA * sqrt(C_MU) * ye);
-        wib[c] = (model == HFDIB_KEPSILON) ? C_MU * kP * w : w;
+        // eps = C_mu k omega with the k the cell takes this sweep: k_ib where
+        // k is imposed (laminar branch), the old k_P where k is solved
+        wib[c] = (model == HFDIB_KEPSILON) ? C_MU * (lamb ? kimp : kP) * w : w;
     }
 }
 

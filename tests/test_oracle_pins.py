@@ -341,3 +341,40 @@ def test_transpose_term_linear_velocity():
     Ty = o.transpose_source(Gt, nu, 1)
     np.testing.assert_allclose(Tx[inner], c * a * o.m.V, rtol=1e-10)
     np.testing.assert_allclose(Ty[inner], 0.0, atol=1e-13)
+
+
+def test_keps_wall_eps_uses_the_imposed_k():
+    """k-eps wall value: eps_ib = C_mu k omega_ib (Eq. omegaws) with k the value
+    the cell takes this sweep, so in laminar-branch cells the eddy viscosity
+    C_mu k_ib^2 / eps_ib is k_ib / omega_ib = k_ib beta1 y_eff^2 / (6 nu),
+    whatever the old k_P was (here set to the 1e-14 floor)."""
+    case = G.case_grf(64, 32, seed=1)
+    o = O.Oracle(case)
+    cells = o.geo["cell"]
+    kf = o.k.ravel().copy()
+    kf[cells] = O.K_MIN
+    o.k = kf.reshape(o.m.shape)
+    o.imposed_fields()
+    lam = o.lam_branch
+    assert lam.all()
+    kib = o.k_ib.ravel()[cells]
+    eib = o.eps_ib.ravel()[cells]
+    ye = o.geo["y_eff"]
+    wl = 6.0 * o.nu / (O.BETA1_WF * ye ** 2)
+    np.testing.assert_allclose(eib, O.C_MU * kib * wl, rtol=1e-14)
+    sel = kib > 0
+    assert sel.sum() > 10
+    np.testing.assert_allclose(O.C_MU * kib[sel] ** 2 / eib[sel], kib[sel] / wl[sel], rtol=1e-12)
+
+
+@pytest.mark.slow
+def test_keps_random_obstacle_converges():
+    """k-eps channel with a random smooth obstacle reaches a steady state with
+    vanishing continuity error (it diverged with eps_ib built from a stale
+    k_P)."""
+    case = G.case_grf(64, 32, seed=1)
+    o = O.Oracle(case)
+    it, res = o.solve(tol=1e-6, max_iter=400)
+    assert o.max_residual(res) <= 1e-6, (it, res)
+    assert res["cont"] < 1e-12
+    assert np.isfinite(o.nut).all() and o.nut.max() < 1.0
