@@ -264,6 +264,47 @@ int hfdib_profile_sweeps(hfdib_handle h, int n_sweeps, double* total_us, int64_t
 int hfdib_classify_noalloc(const hfdib_grid* grid, const double* lambda, uint8_t* tags, int32_t* bc_cells,
                            int64_t bc_capacity, int64_t* n_bc, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Batches: B independent problems (design candidates, angles of attack; grid
+ * sizes may differ) advanced together.  Each sweep runs parts A and B of the
+ * extended SIMPLE loop of all problems concurrently and solves all their
+ * pressure equations in ONE persistent cooperative launch (shared grid
+ * barriers, per-problem convergence); the batched sweep is one CUDA graph.
+ * All problems share the options (precond must be 1).  B <= 64.
+ *   grids, bcs, Re : host arrays of B entries.
+ *   lambdas, ywalls: host arrays of B device pointers (ywalls nullable, or
+ *                    entries nullable unless the model is SST).
+ * The handles returned by hfdib_batch_handle give field access to problem i;
+ * do not sweep them individually. */
+typedef struct hfdib_batch_ctx* hfdib_batch;
+
+int hfdib_create_batch(int B, const hfdib_grid* grids, const double* const* lambdas, const double* const* ywalls,
+                       int model, const double* Re, const hfdib_bc* bcs, const hfdib_options* opt, void* stream,
+                       hfdib_batch* out);
+/* residuals: host, B * HFDIB_NRES doubles (nullable). */
+int hfdib_batch_sweep(hfdib_batch b, int n_sweeps, double* residuals);
+/* Sweep until every problem's largest scaled residual is <= tol (or
+ * max_iter); iters_out (host, B ints) receives the sweep at which each
+ * problem first met tol; final_res host B * HFDIB_NRES (both nullable). */
+int hfdib_batch_solve_steady(hfdib_batch b, double tol, int max_iter, int check_every, int* iters_out,
+                             double* final_res);
+int hfdib_batch_handle(hfdib_batch b, int i, hfdib_handle* out);
+
+/* Autotuner of the batched pressure kernel: threads per block {512, 1024},
+ * coarse-tail threshold {256, 1024, 4096 cells} (the tail runs in one block,
+ * in shared memory when it fits) and coarsest-level sweeps {2, 4, 8}.  Every
+ * candidate is timed over trial_sweeps real sweeps (the solution advances),
+ * the fastest is kept for the batch and cached for later batches of the same
+ * shape in this process.  Changing the block size changes the summation
+ * order of the reductions (round-off level). */
+typedef struct {
+    int32_t threads, tail_cells, coarse_sweeps;
+    double us_per_sweep;
+    int32_t candidates;
+} hfdib_tune;
+int hfdib_batch_autotune(hfdib_batch b, int trial_sweeps, hfdib_tune* best);
+void hfdib_destroy_batch(hfdib_batch b);
+
 const char* hfdib_error_string(int code);
 void hfdib_destroy(hfdib_handle h);
 

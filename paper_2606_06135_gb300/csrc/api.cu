@@ -4,7 +4,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -177,8 +180,9 @@ cudaEvent_t prof_event(Prof& p) {
     } while (0)
 
 // ---------------------------------------------------------------- sweep schedule
-// Part A: a1-a6 of Fig. simplehfdibrans and the set-up of the pressure solve.
-void enqueue_part_a(Ctx* h, long long* L) {
+// Part A: a1-a6 of Fig. simplehfdibrans and (with_pressure) the pressure
+// solve or its set-up.
+void enqueue_part_a(Ctx* h, long long* L, bool with_pressure = true) {
     const Grid& g = h->g;
     const Params& P = h->P;
     Fields& F = h->F;
@@ -208,6 +212,7 @@ void enqueue_part_a(Ctx* h, long long* L) {
     PROF(h, HFDIB_K_HBYA, launch_hbya(g, P, F, s));
     PROF(h, HFDIB_K_HBYA, launch_phiH(g, F, s));
     *L += 2;
+    if (!with_pressure) return;
     // a7 set-up: operator, r0, initial preconditioning, loop state
     const MgLevels& M = h->mg;
     int jac = h->opt.precond == 0;
@@ -403,6 +408,173 @@ int run_sweep(Ctx* h) {
     h->sweeps++;
     h->launches += h->graph_launches;
     return HFDIB_OK;
+}
+
+// ---------------------------------------------------------------- batches
+// A batch holds B problems (each a full handle on its own worker stream) and
+// advances them together: parts A of all problems run concurrently on the
+// worker streams, then ONE persistent cooperative launch solves all their
+// pressure equations, then parts B run concurrently.  The whole batched sweep
+// is captured as one CUDA graph (two, alternating the p / pr buffers).
+struct BatchCtx {
+    int B = 0;
+    int mixed = 0;
+    std::vector<Ctx*> d;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<cudaStream_t> ws;
+    std::vector<cudaEvent_t> ej;
+    cudaEvent_t ef = nullptr;
+    void* desc[2] = {nullptr, nullptr};   // device descriptor arrays (parity 0 / 1)
+    std::vector<unsigned char> hdesc[2];
+    std::vector<void*> allocs;
+    std::vector<double*> parts;
+    unsigned int* bar = nullptr;
+    int* err = nullptr;
+    int nblk = 0, threads = 1024, coarse_sweeps = 4, maxlev = 1;
+    long long tail_cells = 1024;
+    size_t smem = 0;
+    int parity = 0;
+    int use_graph = 1;
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    long long sweeps = 0;
+    double* pinned = nullptr;
+    std::string key;
+};
+
+constexpr size_t BATCH_SMEM_BUDGET = 160 * 1024;
+
+void batch_drop_graphs(BatchCtx* b) {
+    for (int q = 0; q < 2; ++q) {
+        if (b->gexec[q]) cudaGraphExecDestroy(b->gexec[q]);
+        if (b->graph[q]) cudaGraphDestroy(b->graph[q]);
+        b->gexec[q] = nullptr;
+        b->graph[q] = nullptr;
+    }
+}
+
+// (re)build both descriptor arrays for the current launch parameters
+int batch_describe(BatchCtx* b) {
+    size_t dsz = pcgb_desc_size(b->mixed);
+    size_t smem = 0;
+    for (int q = 0; q < 2; ++q) {
+        b->hdesc[q].assign(dsz * b->B, 0);
+        for (int i = 0; i < b->B; ++i) {
+            Ctx* h = b->d[i];
+            Fields F = h->F;
+            if (q == 1) std::swap(F.p, F.pr);   // the other parity of the p / pr buffers
+            void* dst = b->hdesc[q].data() + dsz * i;
+            size_t by = b->mixed ? pcgb_describe32(dst, h->g, F, h->mg, h->mg32, b->parts[i], b->tail_cells,
+                                                   BATCH_SMEM_BUDGET)
+                                 : pcgb_describe64(dst, h->g, F, h->mg, b->parts[i], b->tail_cells, BATCH_SMEM_BUDGET);
+            if (by > smem) smem = by;
+        }
+        CK(cudaMemcpyAsync(b->desc[q], b->hdesc[q].data(), dsz * b->B, cudaMemcpyHostToDevice, b->stream));
+    }
+    CK(cudaStreamSynchronize(b->stream));
+    int bps = 0;
+    if (pcgb_fits(b->mixed, b->threads, smem, &bps) != 0 || bps < 1) return HFDIB_ERR_INVALID_ARG;
+    b->smem = smem;
+    return HFDIB_OK;
+}
+
+void batch_enqueue(BatchCtx* b) {
+    cudaStream_t s = b->stream;
+    long long L = 0;
+    cudaEventRecord(b->ef, s);
+    for (int i = 0; i < b->B; ++i) {
+        cudaStreamWaitEvent(b->ws[i], b->ef, 0);
+        enqueue_part_a(b->d[i], &L, false);
+        cudaEventRecord(b->ej[i], b->ws[i]);
+        cudaStreamWaitEvent(s, b->ej[i], 0);
+    }
+    cudaMemsetAsync(b->bar, 0, sizeof(unsigned int), s);
+    const Ctx* h0 = b->d[0];
+    launch_pressure_batched(b->mixed, b->desc[b->parity], b->B, b->maxlev, b->coarse_sweeps, h0->opt.p_reltol,
+                            h0->opt.p_maxiter, b->nblk, b->threads, b->smem, b->bar, b->err, s);
+    cudaEventRecord(b->ef, s);
+    for (int i = 0; i < b->B; ++i) {
+        cudaStreamWaitEvent(b->ws[i], b->ef, 0);
+        enqueue_part_b(b->d[i], &L);
+        cudaEventRecord(b->ej[i], b->ws[i]);
+        cudaStreamWaitEvent(s, b->ej[i], 0);
+    }
+}
+
+void batch_advance(BatchCtx* b) {
+    for (Ctx* h : b->d) {
+        std::swap(h->F.p, h->F.pr);
+        h->parity ^= 1;
+        h->sweeps++;
+    }
+    b->parity ^= 1;
+    b->sweeps++;
+}
+
+int batch_sweep_once(BatchCtx* b) {
+    if (b->use_graph) {
+        if (!b->gexec[b->parity]) {
+            cudaGraph_t g;
+            bool ok = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                batch_enqueue(b);
+                ok = cudaStreamEndCapture(b->stream, &g) == cudaSuccess;
+            }
+            cudaGraphExec_t ex = nullptr;
+            if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+            if (!ok) {
+                cudaGetLastError();
+                b->use_graph = 0;
+            } else {
+                b->graph[b->parity] = g;
+                b->gexec[b->parity] = ex;
+            }
+        }
+        if (b->use_graph) {
+            CK(cudaGraphLaunch(b->gexec[b->parity], b->stream));
+            batch_advance(b);
+            return HFDIB_OK;
+        }
+    }
+    batch_enqueue(b);
+    CK(cudaGetLastError());
+    batch_advance(b);
+    return HFDIB_OK;
+}
+
+int batch_read_residuals(BatchCtx* b, double* out) {
+    for (int i = 0; i < b->B; ++i)
+        CK(cudaMemcpyAsync(b->pinned + (size_t)i * HFDIB_NRES, b->d[i]->res_dev, HFDIB_NRES * sizeof(double),
+                           cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    memcpy(out, b->pinned, sizeof(double) * HFDIB_NRES * b->B);
+    return HFDIB_OK;
+}
+
+void batch_free(BatchCtx* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_drop_graphs(b);
+    for (Ctx* h : b->d)
+        if (h) hfdib_destroy((hfdib_handle)h);
+    for (void* p : b->allocs) cudaFree(p);
+    for (cudaEvent_t e : b->ej) cudaEventDestroy(e);
+    if (b->ef) cudaEventDestroy(b->ef);
+    for (cudaStream_t w : b->ws) cudaStreamDestroy(w);
+    if (b->pinned) cudaFreeHost(b->pinned);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+// autotuner results, keyed by batch shape
+std::map<std::string, hfdib_tune>& tune_cache() {
+    static std::map<std::string, hfdib_tune> m;
+    return m;
+}
+std::mutex& tune_mu() {
+    static std::mutex m;
+    return m;
 }
 
 double* field_ptr(Ctx* h, int field, long long* n) {
@@ -888,5 +1060,202 @@ void hfdib_destroy(hfdib_handle hh) {
     free_all(h);
     delete h;
 }
+
+int hfdib_create_batch(int B, const hfdib_grid* grids, const double* const* lambdas, const double* const* ywalls,
+                       int model, const double* Re, const hfdib_bc* bcs, const hfdib_options* opt, void* stream,
+                       hfdib_batch* out) {
+    if (!out) return HFDIB_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (B < 1 || B > pcgb_max_batch() || !grids || !lambdas || !Re || !bcs) return HFDIB_ERR_INVALID_ARG;
+    hfdib_options o;
+    if (opt) o = *opt; else hfdib_default_options(&o);
+    if (o.precond != 1) return HFDIB_ERR_INVALID_ARG;   // batched solve: multigrid preconditioner
+    o.p_persistent = 1;
+    BatchCtx* b = new (std::nothrow) BatchCtx();
+    if (!b) return HFDIB_ERR_OOM;
+    b->B = B;
+    b->mixed = o.precision == 1 ? 1 : 0;
+    b->stream = (cudaStream_t)stream;
+    if (!b->stream) {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) { delete b; return HFDIB_ERR_CUDA; }
+        b->own_stream = true;
+    }
+    int rc = HFDIB_OK;
+    if (cudaEventCreateWithFlags(&b->ef, cudaEventDisableTiming) != cudaSuccess) rc = HFDIB_ERR_CUDA;
+    for (int i = 0; i < B && !rc; ++i) {
+        cudaStream_t w;
+        cudaEvent_t e;
+        if (cudaStreamCreateWithFlags(&w, cudaStreamNonBlocking) != cudaSuccess) { rc = HFDIB_ERR_CUDA; break; }
+        b->ws.push_back(w);
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) { rc = HFDIB_ERR_CUDA; break; }
+        b->ej.push_back(e);
+        hfdib_handle h = nullptr;
+        rc = hfdib_create(&grids[i], lambdas[i], ywalls ? ywalls[i] : nullptr, model, Re[i], &bcs[i], &o, w, &h);
+        if (rc) break;
+        b->d.push_back((Ctx*)h);
+    }
+    int dev = 0, sms = 0;
+    if (!rc && (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess))
+        rc = HFDIB_ERR_CUDA;
+    b->nblk = sms;
+    for (int i = 0; i < B && !rc; ++i) {
+        double* p = nullptr;
+        if (cudaMalloc(&p, sizeof(double) * 8 * (size_t)sms) != cudaSuccess) { rc = HFDIB_ERR_OOM; break; }
+        b->allocs.push_back(p);
+        b->parts.push_back(p);
+        if (b->d[i]->mg.nl > b->maxlev) b->maxlev = b->d[i]->mg.nl;
+    }
+    size_t dsz = pcgb_desc_size(b->mixed);
+    for (int q = 0; q < 2 && !rc; ++q) {
+        if (cudaMalloc(&b->desc[q], dsz * B) != cudaSuccess) { rc = HFDIB_ERR_OOM; break; }
+        b->allocs.push_back(b->desc[q]);
+    }
+    if (!rc) {
+        if (cudaMalloc(&b->bar, 256) != cudaSuccess || cudaMalloc(&b->err, 256) != cudaSuccess) rc = HFDIB_ERR_OOM;
+        else {
+            b->allocs.push_back(b->bar);
+            b->allocs.push_back(b->err);
+            cudaMemsetAsync(b->bar, 0, 256, b->stream);
+            cudaMemsetAsync(b->err, 0, 256, b->stream);
+        }
+    }
+    if (!rc && cudaMallocHost((void**)&b->pinned, sizeof(double) * HFDIB_NRES * B) != cudaSuccess) rc = HFDIB_ERR_OOM;
+    b->coarse_sweeps = o.mg_coarse_sweeps > 0 ? o.mg_coarse_sweeps : 4;
+    b->use_graph = o.graph != 0;
+    // shape key of the autotuner cache
+    if (!rc) {
+        std::string k = std::to_string(B) + (b->mixed ? "m" : "d") + std::to_string(model);
+        for (int i = 0; i < B; ++i)
+            k += ":" + std::to_string(grids[i].nx) + "x" + std::to_string(grids[i].ny) + "x" + std::to_string(grids[i].nz);
+        b->key = k;
+        std::lock_guard<std::mutex> lock(tune_mu());
+        auto it = tune_cache().find(k);
+        if (it != tune_cache().end()) {
+            b->threads = it->second.threads;
+            b->tail_cells = it->second.tail_cells;
+            b->coarse_sweeps = it->second.coarse_sweeps;
+        }
+    }
+    if (!rc) rc = batch_describe(b);
+    if (rc) { batch_free(b); return rc; }
+    *out = (hfdib_batch)b;
+    return HFDIB_OK;
+}
+
+int hfdib_batch_sweep(hfdib_batch bb, int n_sweeps, double* residuals) {
+    BatchCtx* b = (BatchCtx*)bb;
+    if (!b || n_sweeps < 0) return HFDIB_ERR_INVALID_ARG;
+    for (int n = 0; n < n_sweeps; ++n) {
+        int rc = batch_sweep_once(b);
+        if (rc) return rc;
+    }
+    if (residuals) {
+        int rc = batch_read_residuals(b, residuals);
+        if (rc) return rc;
+        for (int q = 0; q < HFDIB_NRES * b->B; ++q)
+            if (!isfinite(residuals[q])) return HFDIB_ERR_DIVERGED;
+    }
+    return HFDIB_OK;
+}
+
+int hfdib_batch_solve_steady(hfdib_batch bb, double tol, int max_iter, int check_every, int* iters_out,
+                             double* final_res) {
+    BatchCtx* b = (BatchCtx*)bb;
+    if (!b || max_iter < 0 || !(tol >= 0)) return HFDIB_ERR_INVALID_ARG;
+    if (check_every <= 0) check_every = 10;
+    std::vector<double> res((size_t)HFDIB_NRES * b->B, 0.0);
+    std::vector<int> conv_at(b->B, -1);
+    int it = 0, status = HFDIB_ERR_NOT_CONVERGED;
+    while (it < max_iter) {
+        int rc = batch_sweep_once(b);
+        if (rc) return rc;
+        ++it;
+        if (it % check_every == 0 || it == max_iter) {
+            rc = batch_read_residuals(b, res.data());
+            if (rc) return rc;
+            bool all = true, bad = false;
+            for (int i = 0; i < b->B; ++i) {
+                double mx = 0.0;
+                for (int q = 0; q <= HFDIB_RES_K; ++q) {
+                    double v = res[(size_t)i * HFDIB_NRES + q];
+                    if (!isfinite(v)) bad = true;
+                    mx = fmax(mx, v);
+                }
+                if (mx <= tol) { if (conv_at[i] < 0) conv_at[i] = it; }
+                else all = false;
+            }
+            if (bad) { status = HFDIB_ERR_DIVERGED; break; }
+            if (all) { status = HFDIB_OK; break; }
+        }
+    }
+    if (iters_out)
+        for (int i = 0; i < b->B; ++i) iters_out[i] = conv_at[i] >= 0 ? conv_at[i] : it;
+    if (final_res) memcpy(final_res, res.data(), sizeof(double) * res.size());
+    return status;
+}
+
+int hfdib_batch_handle(hfdib_batch bb, int i, hfdib_handle* out) {
+    BatchCtx* b = (BatchCtx*)bb;
+    if (!b || !out || i < 0 || i >= b->B) return HFDIB_ERR_INVALID_ARG;
+    *out = (hfdib_handle)b->d[i];
+    return HFDIB_OK;
+}
+
+int hfdib_batch_autotune(hfdib_batch bb, int trial_sweeps, hfdib_tune* best_out) {
+    BatchCtx* b = (BatchCtx*)bb;
+    if (!b || trial_sweeps < 1) return HFDIB_ERR_INVALID_ARG;
+    const int threads_c[2] = {512, 1024};
+    const long long tail_c[3] = {256, 1024, 4096};
+    const int coarse_c[3] = {2, 4, 8};
+    hfdib_tune best{b->threads, (int)b->tail_cells, b->coarse_sweeps, 1e300, 0};
+    int saved_graph = b->use_graph;
+    b->use_graph = 0;   // trials run host-driven: parameters change between them
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int tried = 0;
+    for (int t : threads_c)
+        for (long long tc : tail_c)
+            for (int cs : coarse_c) {
+                b->threads = t;
+                b->tail_cells = tc;
+                b->coarse_sweeps = cs;
+                if (batch_describe(b) != HFDIB_OK) continue;
+                // warm one sweep, time the rest (the trial sweeps are real sweeps)
+                int rc = batch_sweep_once(b);
+                if (rc) return rc;
+                CK(cudaEventRecord(e0, b->stream));
+                for (int n = 0; n < trial_sweeps; ++n) {
+                    rc = batch_sweep_once(b);
+                    if (rc) return rc;
+                }
+                CK(cudaEventRecord(e1, b->stream));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                double us = 1e3 * ms / trial_sweeps;
+                ++tried;
+                if (us < best.us_per_sweep) best = hfdib_tune{t, (int)tc, cs, us, 0};
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    best.candidates = tried;
+    b->threads = best.threads;
+    b->tail_cells = best.tail_cells;
+    b->coarse_sweeps = best.coarse_sweeps;
+    int rc = batch_describe(b);
+    if (rc) return rc;
+    batch_drop_graphs(b);
+    b->use_graph = saved_graph;
+    {
+        std::lock_guard<std::mutex> lock(tune_mu());
+        tune_cache()[b->key] = best;
+    }
+    if (best_out) *best_out = best;
+    return HFDIB_OK;
+}
+
+void hfdib_destroy_batch(hfdib_batch bb) { batch_free((BatchCtx*)bb); }
 
 }  // extern "C"

@@ -183,6 +183,18 @@ void launch_mom_smooth32(const Grid& g, const Params& P, const Fields& F, int co
 void launch_scal_smooth32(const Grid& g, const Params& P, const Fields& F, int eq, int colour, int zero_init,
                           cudaStream_t s);
 
+// pcgb.cu (batched pressure solve)
+size_t pcgb_describe64(void* dst, const Grid& g, const Fields& F, const MgLevels& M, double* part,
+                       long long tail_cells, size_t smem_budget);
+size_t pcgb_describe32(void* dst, const Grid& g, const Fields& F, const MgLevels& M, const MgLevels32& M32,
+                       double* part, long long tail_cells, size_t smem_budget);
+size_t pcgb_desc_size(int mixed);
+int pcgb_max_batch();
+cudaError_t launch_pressure_batched(int mixed, const void* ddesc, int B, int maxlev, int coarse_sweeps,
+                                    double reltol, int maxit, int nblk, int threads, size_t smem,
+                                    unsigned int* bar, int* err, cudaStream_t s);
+int pcgb_fits(int mixed, int threads, size_t smem, int* blocks_per_sm);
+
 // turb.cu
 void launch_turb_prep(const Grid& g, const Params& P, const Fields& F, cudaStream_t s);
 void launch_bc_prod(const Grid& g, const BcList& bl, const Fields& F, cudaStream_t s);

@@ -20,6 +20,7 @@
 // coarsened in FP32).  The converged pressure solves the FP64 equation.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "pcg_ops.cuh"
 
 namespace hf {
 
@@ -106,149 +107,6 @@ __device__ inline double grid_total(const AT& A, int q) {
     }
     __syncthreads();
     return res;
-}
-
-// ---------------------------------------------------------------- level ops
-template <typename T>
-__device__ inline long long pl_face(const LevelT<T>& L, int d, int i, int j, int k) {
-    if (d == 0) return ((long long)k * L.ny + j) * (L.nx + 1) + i;
-    if (d == 1) return ((long long)k * (L.ny + 1) + j) * L.nx + i;
-    return ((long long)k * L.ny + j) * L.nx + i;
-}
-template <typename T>
-__device__ inline long long pl_fstride(const LevelT<T>& L, int d) {
-    return d == 0 ? 1 : (d == 1 ? L.nx : (long long)L.nx * L.ny);
-}
-template <typename T>
-__device__ inline void pl_ijk(const LevelT<T>& L, long long c, int& i, int& j, int& k) {
-    unsigned int cc = (unsigned int)c, nx = (unsigned int)L.nx;
-    unsigned int r = cc / nx;
-    i = (int)(cc - r * nx);
-    if (L.nz == 1) { j = (int)r; k = 0; return; }
-    unsigned int ny = (unsigned int)L.ny;
-    unsigned int kk = r / ny;
-    j = (int)(r - kk * ny);
-    k = (int)kk;
-}
-template <typename T, typename X>
-__device__ inline T pl_offsum(const LevelT<T>& L, int dims, const X* x, long long c, int i, int j, int k) {
-    T acc = T(0);
-    int idx[3] = {i, j, k};
-    int nn[3] = {L.nx, L.ny, L.nz};
-    for (int d = 0; d < dims; ++d) {
-        long long fl = pl_face(L, d, i, j, k);
-        long long cs = d == 0 ? 1 : (d == 1 ? L.nx : (long long)L.nx * L.ny);
-        if (idx[d] > 0) acc += L.cf[d][fl] * (T)x[c - cs];
-        if (idx[d] < nn[d] - 1) acc += L.cf[d][fl + pl_fstride(L, d)] * (T)x[c + cs];
-    }
-    return acc;
-}
-
-template <typename T>
-__device__ inline void pl_smooth(const LevelT<T>& L, int dims, int colour, long long t0, long long TT) {
-    for (long long c = t0; c < L.N; c += TT) {
-        int i, j, k;
-        pl_ijk(L, c, i, j, k);
-        if (((i + j + k) & 1) != colour) continue;
-        L.x[c] = (L.b[c] + pl_offsum(L, dims, L.x, c, i, j, k)) * L.idg[c];
-    }
-}
-
-// b_C = sum of the children's residuals; fuse_red: also the zero-start red
-// half sweep of the coarse level (x_C = b_C / diag_C on red cells)
-template <typename T>
-__device__ inline void pl_restrict(const LevelT<T>& F, const LevelT<T>& Cc, int dims, bool fuse_red, long long t0,
-                                   long long TT) {
-    for (long long C = t0; C < Cc.N; C += TT) {
-        int I, J, K;
-        pl_ijk(Cc, C, I, J, K);
-        T sum = T(0);
-        for (int oz = 0; oz < (dims == 3 ? 2 : 1); ++oz)
-            for (int oy = 0; oy < 2; ++oy)
-                for (int ox = 0; ox < 2; ++ox) {
-                    int i = 2 * I + ox, j = 2 * J + oy, k = 2 * K + oz;
-                    if (i >= F.nx || j >= F.ny || k >= F.nz) continue;
-                    long long c = ((long long)k * F.ny + j) * F.nx + i;
-                    sum += F.b[c] - (F.diag[c] * F.x[c] - pl_offsum(F, dims, F.x, c, i, j, k));
-                }
-        Cc.b[C] = sum;
-        if (fuse_red && ((I + J + K) & 1) == 0) Cc.x[C] = sum * Cc.idg[C];
-    }
-}
-
-// prolongation fused with the black half sweep (red cells are overwritten by
-// the following red half sweep without being read)
-template <typename T>
-__device__ inline void pl_prolong_black(const LevelT<T>& L, const LevelT<T>& Cc, int dims, long long t0, long long TT) {
-    for (long long c = t0; c < L.N; c += TT) {
-        int i, j, k;
-        pl_ijk(L, c, i, j, k);
-        if (((i + j + k) & 1) != 1) continue;
-        int idx[3] = {i, j, k};
-        int nn[3] = {L.nx, L.ny, L.nz};
-        T acc = L.b[c];
-        for (int d = 0; d < dims; ++d) {
-            long long fl = pl_face(L, d, i, j, k);
-            long long cs = d == 0 ? 1 : (d == 1 ? L.nx : (long long)L.nx * L.ny);
-            for (int side = 0; side < 2; ++side) {
-                if (side == 0 && idx[d] == 0) continue;
-                if (side == 1 && idx[d] == nn[d] - 1) continue;
-                int ni[3] = {i, j, k};
-                ni[d] += side ? 1 : -1;
-                long long nc = side ? c + cs : c - cs;
-                long long C = ((long long)(ni[2] >> 1) * Cc.ny + (ni[1] >> 1)) * Cc.nx + (ni[0] >> 1);
-                acc += L.cf[d][fl + (side ? pl_fstride(L, d) : 0)] * (L.x[nc] + Cc.x[C]);
-            }
-        }
-        L.x[c] = acc * L.idg[c];
-    }
-}
-
-// levels l0..nl-1 inside one block: b of level l0 is set on entry
-template <typename T>
-__device__ void pl_tail(const MgLevelsT<T>& M, int dims, int l0, int sweeps) {
-    const long long t0 = threadIdx.x, TT = blockDim.x;
-    for (int l = l0; l < M.nl - 1; ++l) {
-        const LevelT<T>& L = M.lv[l];
-        for (long long c = t0; c < L.N; c += TT) {
-            int i, j, k;
-            pl_ijk(L, c, i, j, k);
-            if (((i + j + k) & 1) == 0) L.x[c] = L.b[c] * L.idg[c];
-        }
-        __syncthreads();
-        pl_smooth(L, dims, 1, t0, TT);
-        __syncthreads();
-        pl_restrict(L, M.lv[l + 1], dims, false, t0, TT);
-        __syncthreads();
-    }
-    const LevelT<T>& Lc = M.lv[M.nl - 1];
-    for (int s = 0; s < sweeps; ++s) {
-        if (s == 0) {
-            for (long long c = t0; c < Lc.N; c += TT) {
-                int i, j, k;
-                pl_ijk(Lc, c, i, j, k);
-                if (((i + j + k) & 1) == 0) Lc.x[c] = Lc.b[c] * Lc.idg[c];
-            }
-        } else {
-            pl_smooth(Lc, dims, 0, t0, TT);
-        }
-        __syncthreads();
-        pl_smooth(Lc, dims, 1, t0, TT);
-        __syncthreads();
-    }
-    for (int s = 0; s < sweeps; ++s) {
-        pl_smooth(Lc, dims, 1, t0, TT);
-        __syncthreads();
-        pl_smooth(Lc, dims, 0, t0, TT);
-        __syncthreads();
-    }
-    for (int l = M.nl - 2; l >= l0; --l) {
-        const LevelT<T>& L = M.lv[l];
-        pl_prolong_black(L, M.lv[l + 1], dims, t0, TT);
-        __syncthreads();
-        pl_smooth(L, dims, 0, t0, TT);
-        __syncthreads();
-    }
 }
 
 // block 0's copy of the level table whose tail levels point into dynamic
@@ -350,41 +208,6 @@ __device__ void pl_vcycle_rest(const PcgpArgs<MT>& A, int qdot) {
     }
     block_partial(A, qdot, rz);
     grid_sync(A);
-}
-
-// coarse operator: face coefficients half the sum of the covered fine faces
-// (same rule as pressure.cu), diagonal and inverse diagonal
-template <typename T>
-__device__ inline void pl_coarsen(const LevelT<T>& F, const LevelT<T>& Cc, int dims, long long t0, long long TT) {
-    int nf[3] = {F.nx, F.ny, F.nz};
-    int nc[3] = {Cc.nx, Cc.ny, Cc.nz};
-    for (long long C = t0; C < Cc.N; C += TT) {
-        int I, J, K;
-        pl_ijk(Cc, C, I, J, K);
-        int idx[3] = {I, J, K};
-        T diag = T(0);
-        for (int d = 0; d < dims; ++d)
-            for (int side = 0; side < 2; ++side) {
-                int fpos = side == 0 ? 2 * idx[d] : (idx[d] == nc[d] - 1 ? nf[d] : 2 * idx[d] + 2);
-                int a1 = (d + 1) % 3, a2 = (d + 2) % 3;
-                T sum = T(0);
-                for (int o1 = 0; o1 < 2; ++o1)
-                    for (int o2 = 0; o2 < 2; ++o2) {
-                        int fi[3];
-                        fi[d] = fpos;
-                        fi[a1] = 2 * idx[a1] + o1;
-                        fi[a2] = 2 * idx[a2] + o2;
-                        if (fi[a1] >= nf[a1] || fi[a2] >= nf[a2]) continue;
-                        sum += F.cf[d][pl_face(F, d, fi[0], fi[1], fi[2])];
-                    }
-                T v = T(0.5) * sum;
-                diag += v;
-                if (side == 0) Cc.cf[d][pl_face(Cc, d, I, J, K)] = v;
-                else if (idx[d] == nc[d] - 1) Cc.cf[d][pl_face(Cc, d, I, J, K) + pl_fstride(Cc, d)] = v;
-            }
-        Cc.diag[C] = diag;
-        Cc.idg[C] = diag > T(0) ? T(1) / diag : T(0);
-    }
 }
 
 // level-0 operator from rAU (FP64, also used by the flux correction), its

@@ -36,6 +36,11 @@ class HfdibError(RuntimeError):
         self.code = code
 
 
+class Tune(C.Structure):
+    _fields_ = [("threads", C.c_int32), ("tail_cells", C.c_int32), ("coarse_sweeps", C.c_int32),
+                ("us_per_sweep", C.c_double), ("candidates", C.c_int32)]
+
+
 class Grid(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
                 ("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double),
@@ -62,7 +67,8 @@ EXPORTED = ("hfdib_default_options", "hfdib_create", "hfdib_simple_sweep", "hfdi
             "hfdib_get_field", "hfdib_set_field", "hfdib_get_tags", "hfdib_get_bc_list",
             "hfdib_get_history", "hfdib_get_state", "hfdib_set_state", "hfdib_get_counters",
             "hfdib_error_string", "hfdib_destroy", "hfdib_profile_sweeps", "hfdib_get_launch_counts",
-            "hfdib_classify_noalloc")
+            "hfdib_classify_noalloc", "hfdib_create_batch", "hfdib_batch_sweep", "hfdib_batch_solve_steady",
+            "hfdib_batch_handle", "hfdib_batch_autotune", "hfdib_destroy_batch")
 KERNEL_CLASSES = ("imposed", "grad_u", "mom_asm", "mom_smooth", "hbya", "p_coef", "pcg", "vcycle0",
                   "update", "turb_prep", "scal_asm", "scal_smooth", "turb_final", "sweep_end")
 
@@ -96,6 +102,18 @@ def load_library(path=LIBPATH):
     lib.hfdib_get_launch_counts.restype = C.c_int
     lib.hfdib_classify_noalloc.argtypes = [C.POINTER(Grid), vp, vp, vp, i64, C.POINTER(i64), vp]
     lib.hfdib_classify_noalloc.restype = C.c_int
+    lib.hfdib_create_batch.argtypes = [i32, vp, vp, vp, i32, vp, vp, C.POINTER(Options), vp, C.POINTER(vp)]
+    lib.hfdib_create_batch.restype = C.c_int
+    lib.hfdib_batch_sweep.argtypes = [vp, i32, vp]
+    lib.hfdib_batch_sweep.restype = C.c_int
+    lib.hfdib_batch_solve_steady.argtypes = [vp, dbl, i32, i32, vp, vp]
+    lib.hfdib_batch_solve_steady.restype = C.c_int
+    lib.hfdib_batch_handle.argtypes = [vp, i32, C.POINTER(vp)]
+    lib.hfdib_batch_handle.restype = C.c_int
+    lib.hfdib_batch_autotune.argtypes = [vp, i32, C.POINTER(Tune)]
+    lib.hfdib_batch_autotune.restype = C.c_int
+    lib.hfdib_destroy_batch.argtypes = [vp]
+    lib.hfdib_destroy_batch.restype = None
     lib.hfdib_error_string.argtypes = [i32]
     lib.hfdib_error_string.restype = C.c_char_p
     lib.hfdib_destroy.argtypes = [vp]
@@ -281,9 +299,106 @@ class Solver:
         buf = np.ascontiguousarray(buf, dtype=np.uint8)
         _check(self.lib.hfdib_set_state(self.h, buf.ctypes.data, buf.nbytes), "hfdib_set_state")
 
+    @classmethod
+    def view(cls, handle, case, device, stream, lib):
+        """Field access to a problem owned by a batch (does not own the handle)."""
+        self = cls.__new__(cls)
+        import torch
+        self.torch = torch
+        self.lib = lib
+        self.case = case
+        self.device = torch.device(device)
+        g = case["grid"]
+        self.shape = (g["nz"], g["ny"], g["nx"])
+        self.N = g["nx"] * g["ny"] * g["nz"]
+        self.dims = 2 if g["nz"] == 1 else 3
+        self.face_counts = ((g["nx"] + 1) * g["ny"] * g["nz"], g["nx"] * (g["ny"] + 1) * g["nz"],
+                            g["nx"] * g["ny"] * (g["nz"] + 1))
+        self.model = MODELS[case["model"]]
+        self.stream = stream
+        self.h = handle
+        self.owned = False
+        return self
+
+    def close(self):
+        if getattr(self, "h", None) and getattr(self, "owned", True):
+            self.lib.hfdib_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchSolver:
+    """B independent problems advanced together (one batched persistent
+    pressure launch per sweep, the sweep captured as one CUDA graph)."""
+
+    def __init__(self, cases, device="cuda:0", stream=None, **opts):
+        import torch
+        self.torch = torch
+        self.lib = load_library()
+        self.cases = list(cases)
+        self.B = len(self.cases)
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        models = {c["model"] for c in self.cases}
+        if len(models) != 1:
+            raise ValueError("a batch shares one turbulence model")
+        model = MODELS[models.pop()]
+
+        def dev(x):
+            if x is None:
+                return None
+            if isinstance(x, torch.Tensor):
+                return x.to(self.device, torch.float64).contiguous()
+            return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64)).to(self.device)
+        self._lam = [dev(c["lam"]) for c in self.cases]
+        self._yw = [dev(c.get("ywall")) for c in self.cases]
+        torch.cuda.synchronize(self.device)
+        B = self.B
+        grids = (Grid * B)(*[grid_struct(c["grid"]) for c in self.cases])
+        bcs = (Bc * B)(*[bc_struct(c) for c in self.cases])
+        re = (C.c_double * B)(*[float(c["Re"]) for c in self.cases])
+        lam = (C.c_void_p * B)(*[t.data_ptr() for t in self._lam])
+        yw = (C.c_void_p * B)(*[(t.data_ptr() if t is not None else None) for t in self._yw])
+        self._opts = default_options(**opts)
+        h = C.c_void_p()
+        rc = self.lib.hfdib_create_batch(B, grids, lam, yw, model, re, bcs, C.byref(self._opts),
+                                         C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        _check(rc, "hfdib_create_batch")
+        self.h = h
+
+    def sweep(self, n=1, read=True):
+        res = np.zeros((self.B, NRES)) if read else None
+        _check(self.lib.hfdib_batch_sweep(self.h, int(n), res.ctypes.data if read else None), "hfdib_batch_sweep")
+        return res
+
+    def solve(self, tol=1e-6, max_iter=1000, check_every=10):
+        it = np.zeros(self.B, dtype=np.int32)
+        res = np.zeros((self.B, NRES))
+        rc = self.lib.hfdib_batch_solve_steady(self.h, float(tol), int(max_iter), int(check_every),
+                                               it.ctypes.data, res.ctypes.data)
+        if rc not in (0, ERR_NOT_CONVERGED):
+            _check(rc, "hfdib_batch_solve_steady")
+        return rc, it, res
+
+    def problem(self, i):
+        hh = C.c_void_p()
+        _check(self.lib.hfdib_batch_handle(self.h, int(i), C.byref(hh)), "hfdib_batch_handle")
+        return Solver.view(hh, self.cases[i], self.device, self.stream, self.lib)
+
+    def autotune(self, trial_sweeps=2):
+        t = Tune()
+        _check(self.lib.hfdib_batch_autotune(self.h, int(trial_sweeps), C.byref(t)), "hfdib_batch_autotune")
+        return dict(threads=t.threads, tail_cells=t.tail_cells, coarse_sweeps=t.coarse_sweeps,
+                    us_per_sweep=t.us_per_sweep, candidates=t.candidates)
+
     def close(self):
         if getattr(self, "h", None):
-            self.lib.hfdib_destroy(self.h)
+            self.lib.hfdib_destroy_batch(self.h)
             self.h = None
 
     def __del__(self):
