@@ -71,6 +71,14 @@ TAG_FC, TAG_BC, TAG_IC = 0, 1, 2
 DEFAULT_OPTS = dict(urf_u=0.7, urf_p=0.3, urf_turb=0.85, freeze_switch=0)
 
 
+def _zeros(shape, *like):
+    """Zeros in float64, or complex128 when any of `like` is complex (the
+    adjoint checks differentiate these blocks by the complex step; real
+    inputs take exactly the float64 path)."""
+    dt = np.result_type(np.float64, *[np.asarray(a).dtype for a in like])
+    return np.zeros(shape, dtype=dt)
+
+
 def _sl(ax, a, b):
     s = [slice(None)] * 3
     s[ax] = slice(a, b)
@@ -420,7 +428,7 @@ def face_values(m: Mesh, f, spec):
         n = m.n[d]
         shp = list(f.shape)
         shp[ax] = n + 1
-        F = np.zeros(shp)
+        F = _zeros(shp, f)
         F[_sl(ax, 1, n)] = 0.5 * (f[_sl(ax, 0, n - 1)] + f[_sl(ax, 1, n)])
         for hi in (0, 1):
             fm, val = spec[(d, hi)]
@@ -450,10 +458,11 @@ def assemble_transport(m: Mesh, phi, gamma, spec):
     Returns aP, aM[d], aPl[d], b with aP f_P + sum aM f_minus + aPl f_plus = b.
     phi[d] holds the volumetric flux through each d-face in the +d direction.
     """
-    aP = np.zeros(m.shape)
-    b = np.zeros(m.shape)
-    aM = [np.zeros(m.shape) for _ in range(3)]
-    aPl = [np.zeros(m.shape) for _ in range(3)]
+    like = [phi[d] for d in range(m.dims)] + [gamma]
+    aP = _zeros(m.shape, *like)
+    b = _zeros(m.shape, *like)
+    aM = [_zeros(m.shape, *like) for _ in range(3)]
+    aPl = [_zeros(m.shape, *like) for _ in range(3)]
     for d in range(m.dims):
         ax = 2 - d
         n = m.n[d]
@@ -503,7 +512,7 @@ def to_sparse(m: Mesh, aP, aM, aPl):
 
 def apply_offdiag(m: Mesh, aM, aPl, f):
     """sum over neighbours a_N f_N."""
-    out = np.zeros(m.shape)
+    out = _zeros(m.shape, f, *aM[:m.dims], *aPl[:m.dims])
     for d in range(m.dims):
         ax = 2 - d
         n = m.n[d]
@@ -695,8 +704,11 @@ class Oracle:
         self.eps_ib = e_ib
 
     # ---------------------------------------------------------------- sweep
-    def sweep(self):
-        """One extended SIMPLE iteration (Fig. simplehfdibrans)."""
+    def sweep(self, frozen_turbulence=False):
+        """One extended SIMPLE iteration (Fig. simplehfdibrans).  With
+        frozen_turbulence the turbulence steps a9-a12 are skipped: nu_t, k and
+        eps/omega keep their values (the frozen-turbulence flow problem whose
+        adjoint the gradient checks differentiate)."""
         m = self.m
         o = self.opts
         au, ap = o["urf_u"], o["urf_p"]
@@ -751,7 +763,9 @@ class Oracle:
         divphi = self.divergence(self.phi)
         res["cont"] = float(np.abs(np.where(self.mask_m, divphi, 0.0)).sum())
         # ---- a9-a12: turbulence
-        if self.model == "kepsilon":
+        if frozen_turbulence:
+            pass
+        elif self.model == "kepsilon":
             self.kepsilon(res)
         elif self.model == "komegasst":
             self.komegasst(res)
@@ -763,13 +777,13 @@ class Oracle:
         """Explicit div(nu_eff (grad u)^T) for component c: face flux
         nu_f (d u_a / d x_c)_f S_a through the a-faces."""
         m = self.m
-        T = np.zeros(m.shape)
+        T = _zeros(m.shape, nu_eff, *[G[c][a] for a in range(m.dims)])
         for a in range(m.dims):
             ax = 2 - a
             n = m.n[a]
             val = G[c][a]                 # d u_a / d x_c
-            Fv = np.zeros([n + 1 if q == ax else s for q, s in enumerate(m.shape)])
-            Fn = np.zeros_like(Fv)
+            Fv = _zeros([n + 1 if q == ax else s for q, s in enumerate(m.shape)], val)
+            Fn = _zeros(Fv.shape, nu_eff)
             Fv[_sl(ax, 1, n)] = 0.5 * (val[_sl(ax, 0, n - 1)] + val[_sl(ax, 1, n)])
             Fn[_sl(ax, 1, n)] = 0.5 * (nu_eff[_sl(ax, 0, n - 1)] + nu_eff[_sl(ax, 1, n)])
             Fv[_sl(ax, 0, 1)] = m.slab(val, a, 0)
@@ -786,16 +800,16 @@ class Oracle:
         matrix of -laplacian plus the outlet right-hand side."""
         m = self.m
         coef = []
-        aP = np.zeros(m.shape)
-        aM = [np.zeros(m.shape) for _ in range(3)]
-        aPl = [np.zeros(m.shape) for _ in range(3)]
-        rhs = np.zeros(m.shape)
+        aP = _zeros(m.shape, rAU)
+        aM = [_zeros(m.shape, rAU) for _ in range(3)]
+        aPl = [_zeros(m.shape, rAU) for _ in range(3)]
+        rhs = _zeros(m.shape, rAU)
         for d in range(m.dims):
             ax = 2 - d
             n = m.n[d]
             shp = list(m.shape)
             shp[ax] = n + 1
-            C = np.zeros(shp)
+            C = _zeros(shp, rAU)
             C[_sl(ax, 1, n)] = 0.5 * (rAU[_sl(ax, 0, n - 1)] + rAU[_sl(ax, 1, n)]) * m.S[d] / m.D[d]
             for hi in (0, 1):
                 if self.bnd.kind[(d, hi)] == "outlet":
@@ -819,7 +833,7 @@ class Oracle:
 
     def divergence(self, phi):
         m = self.m
-        div = np.zeros(m.shape)
+        div = _zeros(m.shape, *phi[:m.dims])
         for d in range(m.dims):
             ax = 2 - d
             n = m.n[d]
