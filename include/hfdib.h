@@ -107,7 +107,11 @@ typedef struct {
                                     laminar branch but not re-enter it, which ends
                                     limit cycles of the discrete switch (not part
                                     of the paper)                                  */
-    int32_t reserved[2];
+    int32_t frozen_turbulence;   /* 1: sweeps skip the turbulence steps (a9-a12):
+                                    nu_t, k and eps/omega keep their values; the
+                                    flow problem whose adjoint hfdib_adjoint_grad
+                                    differentiates (0)                             */
+    int32_t reserved;
 } hfdib_options;
 
 typedef struct hfdib_ctx* hfdib_handle;
@@ -175,6 +179,39 @@ int hfdib_simple_sweep(hfdib_handle h, int n_sweeps, double* residuals);
  * (HFDIB_NRES doubles) are host pointers and nullable. */
 int hfdib_solve_steady(hfdib_handle h, double tol, int max_iter, int check_every,
                        int* iters_out, double* final_res);
+
+/* Objectives of hfdib_adjoint_grad. */
+enum { HFDIB_OBJ_PRESSURE_DROP = 0 };
+
+/* hfdib_adjoint_grad -- frozen-turbulence discrete adjoint of the converged
+ * state: the gradient of an objective J with respect to the indicator lambda.
+ * The paper has no adjoint; this entry point differentiates its discrete
+ * method.  Hold fixed nu_t, k, eps/omega, the cell groups (Sec. 2.3), the
+ * wall-function branch of each bc cell (Eq. alphauk), the closed faces and
+ * the continuity mask.  Then the converged state is a fixed point of the
+ * sweep's momentum-pressure part (steps a2-a8 of Fig. simplehfdibrans), and
+ * lambda moves it only through the imposed velocity u_ib of the
+ * laminar-branch bc cells: the normal n = -grad(lambda)/|grad(lambda)|
+ * (Eq. yorthoaux), y_perp (Eq. yortho) and the interpolation of Sec. 2.5.
+ * The adjoint psi of that fixed point is found by iterating the transposed
+ * sweep (reverse accumulation through the same red-black momentum passes,
+ * with exact pressure solves).  Then dJ/dlambda = psi^T dG/dlambda.
+ *   objective  : HFDIB_OBJ_PRESSURE_DROP, J = mean p over the cells of the open
+ *                inlet faces minus mean p over the cells of the outlet faces
+ *   tol        : stop when max|psi_new - psi| <= tol max|psi| (checked every
+ *                10 iterations); max_iter caps the iterations; max_iter = 0
+ *                only evaluates J (dJ_dlambda may then be NULL)
+ *   dJ_dlambda : DEVICE pointer, N doubles (cell order of lambda), caller-owned
+ *   J_out, iters_out, change_out : host pointers, nullable
+ * Call it on a converged state (hfdib_solve_steady to a tight tolerance): the
+ * gradient is that of the fixed point, and its error follows the residual.
+ * 2D grids only (INVALID_ARG otherwise).  The state is left unchanged.
+ * Returns HFDIB_OK, HFDIB_ERR_NOT_CONVERGED (gradient of the last iterate
+ * still written), HFDIB_ERR_DIVERGED, HFDIB_ERR_INVALID_ARG, or CUDA/OOM errors.
+ * The first call allocates about 90 doubles per cell of work arrays, which
+ * live until hfdib_destroy. */
+int hfdib_adjoint_grad(hfdib_handle h, int objective, double tol, int max_iter, double* dJ_dlambda,
+                       double* J_out, int* iters_out, double* change_out);
 
 /* Copy a field (HFDIB_FIELD_*) device-to-device into dst (caller-owned, sized
  * like the field: cells, or faces (nx+1)*ny*nz / nx*(ny+1)*nz / nx*ny*(nz+1)). */

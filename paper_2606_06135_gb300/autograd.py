@@ -1,0 +1,57 @@
+"""torch.autograd.Function around the steady solve and its adjoint.
+
+forward: build the HFDIB problem on the given lambda, converge it with
+hfdib_solve_steady and return the objective J (pressure drop) as a 0-d
+tensor.  backward: hfdib_adjoint_grad, the frozen-turbulence discrete
+adjoint of that converged state, gives dJ/dlambda; it is multiplied by the
+incoming gradient.  Both steps run in the library's CUDA kernels; this module
+only passes pointers.
+
+Typical use (topology optimisation over many designs):
+
+    lam = torch.tensor(case["lam"], device="cuda", requires_grad=True)
+    J = pressure_drop(lam, case)
+    J.backward()          # lam.grad = dJ/dlambda
+"""
+from __future__ import annotations
+
+import torch
+
+from .hfdib import Solver
+
+
+class SteadyRANS(torch.autograd.Function):
+    """J(lambda) = pressure drop of the converged steady state."""
+
+    @staticmethod
+    def forward(ctx, lam, case, solve_tol, max_sweeps, adj_tol, adj_max_iter, opts):
+        c = dict(case)
+        c["lam"] = lam.detach().to(torch.float64)
+        s = Solver(c, device=lam.device, **opts)
+        rc, it, res = s.solve(tol=solve_tol, max_iter=max_sweeps, check_every=20)
+        if rc != 0:
+            s.close()
+            raise RuntimeError("steady solve did not reach %g in %d sweeps (status %d)" % (solve_tol, it, rc))
+        ctx.solver = s
+        ctx.adj = (adj_tol, adj_max_iter)
+        ctx.lam_shape = lam.shape
+        return torch.tensor(s.objective(), dtype=torch.float64, device=lam.device)
+
+    @staticmethod
+    def backward(ctx, gout):
+        s = ctx.solver
+        tol, max_iter = ctx.adj
+        try:
+            J, g, it, ch, rc = s.adjoint_grad(tol=tol, max_iter=max_iter)
+        finally:
+            s.close()
+            ctx.solver = None
+        if rc != 0:
+            raise RuntimeError("adjoint did not converge to %g in %d iterations (change %.2e)" % (tol, it, ch))
+        return gout * g.reshape(ctx.lam_shape), None, None, None, None, None, None
+
+
+def pressure_drop(lam, case, solve_tol=1e-11, max_sweeps=20000, adj_tol=1e-11, adj_max_iter=50000, **opts):
+    """Differentiable pressure drop of the case with indicator `lam` (a CUDA
+    float64 tensor shaped (nz, ny, nx)); `opts` are hfdib options."""
+    return SteadyRANS.apply(lam, case, solve_tol, max_sweeps, adj_tol, adj_max_iter, opts)

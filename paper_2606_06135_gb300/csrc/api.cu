@@ -1,6 +1,7 @@
 // api.cu -- C ABI of the HFDIB SIMPLE solver: handle set-up, the sweep
 // schedule (Fig. simplehfdibrans), steady solve, field access, checkpoints.
 #include <math.h>
+#include <cmath>
 #include <stdio.h>
 #include <string.h>
 
@@ -62,6 +63,9 @@ struct Ctx {
     long long launches = 0;
     int last_piters = 0;
     double* pinned = nullptr;    // host pinned scratch (64 doubles)
+    Adj adj;                     // adjoint work arrays (allocated by the first adjoint call)
+    bool adj_ready = false;
+    long long adj_tcap = 0;      // capacity of adj.tent
 };
 
 #define CK(x)                                         \
@@ -260,7 +264,7 @@ void enqueue_part_b(Ctx* h, long long* L) {
     const Params& P = h->P;
     Fields& F = h->F;
     cudaStream_t s = h->stream;
-    bool turb = h->model != HFDIB_LAMINAR;
+    bool turb = h->model != HFDIB_LAMINAR && !h->opt.frozen_turbulence;
     // a8: flux, pressure relaxation, velocity update (writes the relaxed p to pr)
     PROF(h, HFDIB_K_UPDATE, launch_update(g, P, F, h->mg.lv[0], s));
     (*L)++;
@@ -300,7 +304,9 @@ void enqueue_part_b(Ctx* h, long long* L) {
         PROF(h, HFDIB_K_TURB_FINAL, launch_turb_final(g, P, G, s));
         (*L)++;
     }
-    PROF(h, HFDIB_K_SWEEP_END, launch_sweep_end(P, F, g.dims, h->res_dev, h->hist, HIST, s));
+    Params Pe = P;
+    if (!turb) Pe.model = HFDIB_LAMINAR;  // frozen turbulence: no k / eps|omega residuals
+    PROF(h, HFDIB_K_SWEEP_END, launch_sweep_end(Pe, F, g.dims, h->res_dev, h->hist, HIST, s));
     (*L)++;
 }
 
@@ -595,6 +601,197 @@ double* field_ptr(Ctx* h, int field, long long* n) {
     }
 }
 
+// ---------------------------------------------------------------- adjoint
+#define RC(x)                                  \
+    do {                                       \
+        int r_ = (x);                          \
+        if (r_ != HFDIB_OK) return r_;         \
+    } while (0)
+
+int adj_alloc(Ctx* h) {
+    if (h->adj_ready) return HFDIB_OK;
+    const Grid& g = h->g;
+    const long long N = g.N;
+    Adj& A = h->adj;
+    memset(&A, 0, sizeof(A));
+    A.nu = h->opt.n_u;
+    int rc = HFDIB_OK;
+#define AL(p, n) \
+    if (!rc) rc = dalloc_n(h, &(p), (long long)(n))
+    AL(A.snap, (2LL * A.nu + 1) * 3 * N);
+    AL(A.As, 6 * N); AL(A.AP, 3 * N); AL(A.aavg, N); AL(A.jw, N);
+    for (int q = 0; q < 3; ++q) {
+        AL(A.psu[q], N); AL(A.xbu[q], N); AL(A.Hb[q], N); AL(A.b0b[q], N); AL(A.bmb[q], N);
+        AL(A.aPb[q], N); AL(A.usb[0][q], N); AL(A.usb[1][q], N); AL(A.fixb[q], N);
+        AL(A.psf[q], g.nface[q]); AL(A.xbf[q], g.nface[q]);
+    }
+    AL(A.psp, N); AL(A.xbp, N); AL(A.pnb, N); AL(A.ps, N); AL(A.rAUb, N);
+    AL(A.asb, 6 * N); AL(A.Gb, 9 * N); AL(A.tptr, N + 1); AL(A.dlam, N);
+#undef AL
+    if (rc) return rc;
+    // objective weights from the closed-face flags (fixed for the handle's lambda)
+    cudaStream_t s = h->stream;
+    std::vector<uint16_t> flags(N);
+    CK(cudaMemcpyAsync(flags.data(), h->F.flags, N * sizeof(uint16_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    // objective: mean p over the cells of each open inlet side minus the mean over each outlet side
+    std::vector<double> jw(N, 0.0);
+    for (int sd = 0; sd < 2 * g.dims; ++sd) {
+        int kind = g.kind[sd];
+        if (kind != HFDIB_BC_INLET && kind != HFDIB_BC_OUTLET) continue;
+        int d = sd >> 1, hi = sd & 1;
+        std::vector<long long> cells;
+        for (long long c = 0; c < N; ++c) {
+            long long i = c % g.nx, j = (c / g.nx) % g.ny, k = c / ((long long)g.nx * g.ny);
+            long long pos = d == 0 ? i : (d == 1 ? j : k);
+            if (pos != (hi ? g.n[d] - 1 : 0)) continue;
+            if (kind == HFDIB_BC_INLET && closed_side(flags[c], sd)) continue;
+            cells.push_back(c);
+        }
+        if (cells.empty()) continue;
+        double w = (kind == HFDIB_BC_INLET ? 1.0 : -1.0) / (double)cells.size();
+        for (long long c : cells) jw[c] += w;
+    }
+    CK(cudaMemcpyAsync(A.jw, jw.data(), N * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    h->adj_ready = true;
+    return HFDIB_OK;
+}
+
+// CG to a relative tolerance on the redirected Fields (the loop kernels are
+// no-ops once the device flag says done; the host looks every 8 iterations)
+int adj_pcg_run(Ctx* h, const Fields& Fa, double reltol, int maxit) {
+    int jac = h->opt.precond == 0;
+    launch_pcg_start(Fa, jac, reltol, maxit, 0, 0, h->stream);
+    for (int it = 0; it < maxit; it += 8) {
+        for (int r = 0; r < 8; ++r)
+            launch_pcg_body(h->g, Fa, h->mg, h->tail_from, jac, h->coarse_sweeps, maxit, 0, 0, h->stream);
+        double done = 0.0;
+        RC(sync_read(h, Fa.scal + SC_PCG_DONE, &done, 1));
+        if (done != 0.0) return HFDIB_OK;
+    }
+    return HFDIB_OK;
+}
+
+// The frozen-turbulence sweep at the converged state, kept for the reverse
+// pass: imposed rows and u_ib, the predictor iterates, HbyA, rAU, phiHbyA,
+// the exact pressure solution and the momentum-row coefficients.  The state
+// (u, p, phi, turbulence) is not modified.  Host work: index bookkeeping only
+// (objective cells, the per-cell entry list of the transposed interpolation).
+int adj_setup(Ctx* h) {
+    const Grid& g = h->g;
+    Fields F = h->F;
+    F.mixed = 0;  // the differentiated sweep is FP64
+    const Params& P = h->P;
+    cudaStream_t s = h->stream;
+    Adj& A = h->adj;
+    const long long N = g.N;
+    int jac = h->opt.precond == 0;
+    launch_imposed(g, h->model, h->opt.freeze_switch, h->bl, F.flags, F.scal, F.u[0], F.u[1], F.u[2], F.k,
+                   F.uib[0], F.uib[1], F.uib[2], F.kib, F.wib, s);
+    CK(cudaMemsetAsync(F.scal + SC_NLAM, 0, 2 * sizeof(double), s));
+    launch_grad_u(g, F, s);
+    launch_mom_asm(g, P, F, s);
+    for (int n = 0; n < A.nu; ++n)
+        for (int col = 0; col < 2; ++col) {
+            for (int q = 0; q < g.dims; ++q)
+                CK(cudaMemcpyAsync(A.snap + ((long long)(2 * n + col) * 3 + q) * N, F.us[q], N * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, s));
+            launch_mom_smooth(g, P, F, col, s);
+        }
+    for (int q = 0; q < g.dims; ++q)
+        CK(cudaMemcpyAsync(A.snap + ((long long)(2 * A.nu) * 3 + q) * N, F.us[q], N * sizeof(double),
+                           cudaMemcpyDeviceToDevice, s));
+    launch_hbya(g, P, F, s);
+    launch_phiH(g, F, s);
+    launch_p_coef(g, h->mg, F.rAU, h->tail_from, s);
+    launch_pcg_init(g, F, h->mg, jac, s);
+    if (!jac) launch_vcycle(g, h->mg, h->tail_from, F, F.scal + SC_PCG_RZN, h->coarse_sweeps, s);
+    RC(adj_pcg_run(h, F, 1e-14, 4000));
+    launch_adj_coef(g, P, F, A, s);
+    CK(cudaGetLastError());
+    // index bookkeeping on the host
+    int nbc = h->bl.nbc;
+    std::vector<uint16_t> flags(N);
+    std::vector<int> cell(nbc > 0 ? nbc : 1), lamb(nbc > 0 ? nbc : 1), b1(3 * (nbc > 0 ? nbc : 1)),
+        b2(3 * (nbc > 0 ? nbc : 1));
+    CK(cudaMemcpyAsync(flags.data(), F.flags, N * sizeof(uint16_t), cudaMemcpyDeviceToHost, s));
+    if (nbc > 0) {
+        CK(cudaMemcpyAsync(cell.data(), h->bl.cell, nbc * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(lamb.data(), h->bl.lamb, nbc * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(b1.data(), h->bl.b1, 3 * nbc * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(b2.data(), h->bl.b2, 3 * nbc * sizeof(int), cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    // transposed interpolation: for every cell, the (bc entry, stencil, corner) that read it
+    std::vector<int> cnt(N + 1, 0);
+    std::vector<std::pair<long long, int>> ent;
+    for (int q = 0; q < nbc; ++q) {
+        if (!lamb[q] || !(flags[cell[q]] & F_AU)) continue;
+        for (int st = 0; st < 2; ++st) {
+            const int* b = (st ? b2.data() : b1.data()) + 3 * q;
+            for (int corner = 0; corner < 8; ++corner) {
+                int id[3];
+                bool skip = false;
+                for (int d = 0; d < 3; ++d) {
+                    int cc = (corner >> d) & 1;
+                    if (g.n[d] == 1 && cc) skip = true;
+                    id[d] = b[d] + (g.n[d] == 1 ? 0 : cc);
+                }
+                if (skip) continue;
+                long long t = ((long long)id[2] * g.ny + id[1]) * g.nx + id[0];
+                ent.push_back({t, q * 16 + st * 8 + corner});
+            }
+        }
+    }
+    for (auto& e : ent) cnt[e.first + 1]++;
+    for (long long c = 0; c < N; ++c) cnt[c + 1] += cnt[c];
+    std::vector<int> tent(ent.size() > 0 ? ent.size() : 1);
+    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+    for (auto& e : ent) tent[fill[e.first]++] = e.second;
+    if ((long long)tent.size() > h->adj_tcap) {
+        RC(dalloc_n(h, &A.tent, (long long)tent.size()));
+        h->adj_tcap = (long long)tent.size();
+    }
+    CK(cudaMemcpyAsync(A.tptr, cnt.data(), (N + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(A.tent, tent.data(), tent.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return HFDIB_OK;
+}
+
+// x-bar = G_x^T psi, and u_ib-bar (A.fixb) = the part of G_lambda^T psi
+int adj_pass(Ctx* h, double ptol) {
+    const Grid& g = h->g;
+    Fields F = h->F;
+    F.mixed = 0;
+    const Params& P = h->P;
+    cudaStream_t s = h->stream;
+    Adj& A = h->adj;
+    const Level& L0 = h->mg.lv[0];
+    int jac = h->opt.precond == 0;
+    launch_adj_update(g, P, F, L0, A, s);
+    Fields Fa = F;
+    Fa.pn = A.ps;
+    launch_adj_pcg_init(g, Fa, L0, A.pnb, jac, s);
+    if (!jac) launch_vcycle(g, h->mg, h->tail_from, Fa, Fa.scal + SC_PCG_RZN, h->coarse_sweeps, s);
+    RC(adj_pcg_run(h, Fa, ptol, 4000));
+    launch_adj_pressure(g, F, L0, A, s);
+    launch_adj_hbya(g, P, F, A, s);
+    int buf = 0;
+    for (int hs = 2 * A.nu; hs >= 1; --hs) {
+        const double* Sin = A.snap + (long long)(hs - 1) * 3 * g.N;
+        const double* Sout = A.snap + (long long)hs * 3 * g.N;
+        launch_adj_gs(g, P, F, A, (hs - 1) & 1, Sin, Sout, buf, s);
+        buf = 1 - buf;
+    }
+    launch_adj_b0(g, P, F, A, buf, s);
+    launch_adj_transpose(g, F, A, s);
+    launch_adj_gradu(g, F, h->bl, A, s);
+    launch_adj_phi(g, F, A, s);
+    CK(cudaGetLastError());
+    return HFDIB_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -660,6 +857,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
     // the mixed path runs its FP32 V-cycle inside the persistent CG kernel
     if (o.precision == 1 && (o.p_persistent == 0 || o.precond != 1)) return HFDIB_ERR_INVALID_ARG;
     if (o.p_maxiter > 100000 || o.freeze_switch < 0) return HFDIB_ERR_INVALID_ARG;
+    if (o.frozen_turbulence < 0 || o.frozen_turbulence > 1) return HFDIB_ERR_INVALID_ARG;
 
     Ctx* h = new (std::nothrow) Ctx();
     if (!h) return HFDIB_ERR_OOM;
@@ -1038,7 +1236,8 @@ int hfdib_get_launch_counts(hfdib_handle hh, int64_t* per_sweep, int64_t* per_pc
     int tf = h->tail_from;
     La = (turb ? 1 : 0) + 4 + 2 * h->opt.n_u + 2 +
          (h->pblocks > 0 ? 1 : (1 + (tf - 1) + (tf < h->mg.nl ? 1 : 0)) + 1 + (jac ? 0 : 5 * tf + 1) + 1);
-    Lb = 1 + (turb ? 4 + 2 * h->opt.n_turb + 2 + 2 * h->opt.n_turb + 1 : 0) + 1;
+    bool turb_b = turb && !h->opt.frozen_turbulence;
+    Lb = 1 + (turb_b ? 4 + 2 * h->opt.n_turb + 2 + 2 * h->opt.n_turb + 1 : 0) + 1;
     Lp = h->pblocks > 0 ? 0 : 3 + (jac ? 0 : 5 * tf + 1);
     if (per_sweep) *per_sweep = La + Lb;
     if (per_pcg_iteration) *per_pcg_iteration = Lp;
@@ -1051,6 +1250,62 @@ int hfdib_get_counters(hfdib_handle hh, int64_t* sweeps, int64_t* launches) {
     if (sweeps) *sweeps = h->sweeps;
     if (launches) *launches = h->launches;
     return HFDIB_OK;
+}
+
+int hfdib_adjoint_grad(hfdib_handle hh, int objective, double tol, int max_iter, double* dJ_dlambda, double* J_out,
+                       int* iters_out, double* change_out) {
+    Ctx* h = (Ctx*)hh;
+    if (iters_out) *iters_out = 0;
+    if (change_out) *change_out = 0.0;
+    if (!h) return HFDIB_ERR_INVALID_ARG;
+    if (objective != HFDIB_OBJ_PRESSURE_DROP) return HFDIB_ERR_INVALID_ARG;
+    if (h->g.dims != 2) return HFDIB_ERR_INVALID_ARG;
+    if (!(tol > 0.0) || max_iter < 0 || (max_iter > 0 && !dJ_dlambda)) return HFDIB_ERR_INVALID_ARG;
+    const Grid& g = h->g;
+    cudaStream_t s = h->stream;
+    RC(adj_alloc(h));
+    Adj& A = h->adj;
+    if (max_iter == 0) {
+        // the objective alone
+        Fields F0 = h->F;
+        launch_adj_objective(g, F0, A, s);
+        CK(cudaGetLastError());
+        double J = 0.0;
+        RC(sync_read(h, F0.scal + SC_ADJ_J, &J, 1));
+        if (J_out) *J_out = J;
+        return HFDIB_OK;
+    }
+    RC(adj_setup(h));
+    for (int q = 0; q < 3; ++q) {
+        CK(cudaMemsetAsync(A.psu[q], 0, g.N * sizeof(double), s));
+        CK(cudaMemsetAsync(A.psf[q], 0, g.nface[q] * sizeof(double), s));
+    }
+    CK(cudaMemsetAsync(A.psp, 0, g.N * sizeof(double), s));
+    CK(cudaMemsetAsync(A.ps, 0, g.N * sizeof(double), s));
+    Fields F = h->F;
+    F.mixed = 0;
+    int it = 0, converged = 0;
+    double ch[2] = {0.0, 0.0};
+    for (it = 0; it < max_iter; ++it) {
+        RC(adj_pass(h, 1e-12));
+        launch_adj_next(g, F, A, it == 0, s);
+        if ((it + 1) % 10 == 0 || it + 1 == max_iter) {
+            RC(sync_read(h, F.scal + SC_ADJ_DIFF, ch, 2));
+            if (!std::isfinite(ch[0]) || !std::isfinite(ch[1])) return HFDIB_ERR_DIVERGED;
+            if (ch[0] <= tol * ch[1]) { converged = 1; ++it; break; }
+        }
+    }
+    if (iters_out) *iters_out = it;
+    if (change_out) *change_out = ch[1] > 0.0 ? ch[0] / ch[1] : ch[0];
+    CK(cudaMemsetAsync(A.dlam, 0, g.N * sizeof(double), s));
+    launch_adj_dlambda(g, F, h->bl, h->lam, A, s);
+    CK(cudaMemcpyAsync(dJ_dlambda, A.dlam, g.N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    launch_adj_objective(g, F, A, s);
+    CK(cudaGetLastError());
+    double J = 0.0;
+    RC(sync_read(h, F.scal + SC_ADJ_J, &J, 1));
+    if (J_out) *J_out = J;
+    return converged ? HFDIB_OK : HFDIB_ERR_NOT_CONVERGED;
 }
 
 void hfdib_destroy(hfdib_handle hh) {

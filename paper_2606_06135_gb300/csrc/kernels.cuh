@@ -195,6 +195,55 @@ cudaError_t launch_pressure_batched(int mixed, const void* ddesc, int B, int max
                                     unsigned int* bar, int* err, cudaStream_t s);
 int pcgb_fits(int mixed, int threads, size_t smem, int* blocks_per_sm);
 
+// adjoint.cu: reverse pass of the frozen-turbulence sweep (reverse fixed
+// point of Christianson type for d(pressure drop)/d(lambda))
+struct Adj {
+    int nu;              // red-black momentum sweep pairs of the differentiated sweep
+    double* snap;        // [2 nu][3][N] predictor iterates S_0 .. S_{2nu-1} (S_{2nu} = F.us)
+    double* As;          // [6][N] neighbour coefficients of the momentum rows (0: no neighbour)
+    double* AP;          // [3][N] unrelaxed diagonal per component
+    double* aavg;        // [N] component-averaged relaxed diagonal
+    double* jw;          // [N] objective weights on p
+    double* psu[3];      // adjoint state: velocity, pressure, face flux (input of a pass)
+    double* psp;
+    double* psf[3];
+    double* xbu[3];      // output of a pass
+    double* xbp;
+    double* xbf[3];
+    double* pnb;         // right-hand side of the adjoint pressure solve
+    double* ps;          // its solution (kept as the next warm start)
+    double* Hb[3];       // adjoints of HbyA, rAU, b0, bm, aP, a_s
+    double* rAUb;
+    double* b0b[3];
+    double* bmb[3];
+    double* aPb[3];
+    double* asb;         // [6][N]
+    double* usb[2][3];   // ping-pong adjoint of the predictor iterates
+    double* fixb[3];     // adjoint of the imposed velocity u_ib
+    double* Gb;          // [9][N] adjoint of the velocity gradient, layout of F.G
+    int* tptr;           // [N+1] interpolation transpose: entries per cell
+    int* tent;           // entries: bc index * 16 + stencil * 8 + corner
+    double* dlam;        // output dJ/dlambda [N]
+};
+void launch_adj_coef(const Grid& g, const Params& P, const Fields& F, const Adj& A, cudaStream_t s);
+void launch_adj_update(const Grid& g, const Params& P, const Fields& F, const Level& L0, const Adj& A,
+                       cudaStream_t s);
+void launch_adj_pcg_init(const Grid& g, const Fields& Fa, const Level& L0, const double* rhs, int jacobi,
+                         cudaStream_t s);
+void launch_adj_pressure(const Grid& g, const Fields& F, const Level& L0, const Adj& A, cudaStream_t s);
+void launch_adj_hbya(const Grid& g, const Params& P, const Fields& F, const Adj& A, cudaStream_t s);
+void launch_adj_gs(const Grid& g, const Params& P, const Fields& F, const Adj& A, int colour, const double* Sin,
+                   const double* Sout, int in_buf, cudaStream_t s);
+void launch_adj_b0(const Grid& g, const Params& P, const Fields& F, const Adj& A, int buf, cudaStream_t s);
+void launch_adj_transpose(const Grid& g, const Fields& F, const Adj& A, cudaStream_t s);
+void launch_adj_gradu(const Grid& g, const Fields& F, const BcList& bl, const Adj& A, cudaStream_t s);
+void launch_adj_phi(const Grid& g, const Fields& F, const Adj& A, cudaStream_t s);
+void launch_adj_next(const Grid& g, const Fields& F, const Adj& A, int first, cudaStream_t s);
+void launch_adj_objective(const Grid& g, const Fields& F, const Adj& A, cudaStream_t s);
+void launch_adj_dlambda(const Grid& g, const Fields& F, const BcList& bl, const double* lam, const Adj& A,
+                        cudaStream_t s);
+enum { SC_ADJ_DIFF = 48, SC_ADJ_NORM = 49, SC_ADJ_J = 50 };
+
 // turb.cu
 void launch_turb_prep(const Grid& g, const Params& P, const Fields& F, cudaStream_t s);
 void launch_bc_prod(const Grid& g, const BcList& bl, const Fields& F, cudaStream_t s);

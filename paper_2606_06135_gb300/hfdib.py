@@ -58,7 +58,8 @@ class Options(C.Structure):
                 ("n_u", C.c_int32), ("n_turb", C.c_int32), ("p_reltol", C.c_double),
                 ("p_maxiter", C.c_int32), ("precision", C.c_int32), ("precond", C.c_int32),
                 ("p_check", C.c_int32), ("mg_coarse_sweeps", C.c_int32), ("graph", C.c_int32),
-                ("p_persistent", C.c_int32), ("freeze_switch", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("p_persistent", C.c_int32), ("freeze_switch", C.c_int32), ("frozen_turbulence", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 _LIB = None
@@ -68,7 +69,7 @@ EXPORTED = ("hfdib_default_options", "hfdib_create", "hfdib_simple_sweep", "hfdi
             "hfdib_get_history", "hfdib_get_state", "hfdib_set_state", "hfdib_get_counters",
             "hfdib_error_string", "hfdib_destroy", "hfdib_profile_sweeps", "hfdib_get_launch_counts",
             "hfdib_classify_noalloc", "hfdib_create_batch", "hfdib_batch_sweep", "hfdib_batch_solve_steady",
-            "hfdib_batch_handle", "hfdib_batch_autotune", "hfdib_destroy_batch")
+            "hfdib_batch_handle", "hfdib_batch_autotune", "hfdib_destroy_batch", "hfdib_adjoint_grad")
 KERNEL_CLASSES = ("imposed", "grad_u", "mom_asm", "mom_smooth", "hbya", "p_coef", "pcg", "vcycle0",
                   "update", "turb_prep", "scal_asm", "scal_smooth", "turb_final", "sweep_end")
 
@@ -114,6 +115,8 @@ def load_library(path=LIBPATH):
     lib.hfdib_batch_autotune.restype = C.c_int
     lib.hfdib_destroy_batch.argtypes = [vp]
     lib.hfdib_destroy_batch.restype = None
+    lib.hfdib_adjoint_grad.argtypes = [vp, i32, dbl, i32, vp, C.POINTER(dbl), C.POINTER(i32), C.POINTER(dbl)]
+    lib.hfdib_adjoint_grad.restype = i32
     lib.hfdib_error_string.argtypes = [i32]
     lib.hfdib_error_string.restype = C.c_char_p
     lib.hfdib_destroy.argtypes = [vp]
@@ -287,6 +290,31 @@ class Solver:
         a, b = C.c_int64(0), C.c_int64(0)
         _check(self.lib.hfdib_get_launch_counts(self.h, C.byref(a), C.byref(b)), "hfdib_get_launch_counts")
         return a.value, b.value
+
+    def adjoint_grad(self, tol=1e-10, max_iter=20000, objective=0):
+        """Frozen-turbulence adjoint of the converged state: returns (J,
+        dJ/dlambda as a device tensor shaped like lambda, iterations, relative
+        change at the stop, status).  Status 0, or -4 when max_iter ran out."""
+        torch = self.torch
+        out = torch.zeros(self.N, dtype=torch.float64, device=self.device)
+        J = C.c_double(0.0)
+        it = C.c_int(0)
+        ch = C.c_double(0.0)
+        self.stream.synchronize()
+        rc = self.lib.hfdib_adjoint_grad(self.h, int(objective), float(tol), int(max_iter),
+                                         C.c_void_p(out.data_ptr()), C.byref(J), C.byref(it), C.byref(ch))
+        if rc not in (0, ERR_NOT_CONVERGED):
+            _check(rc, "hfdib_adjoint_grad")
+        self.stream.synchronize()
+        return J.value, out.reshape(self.shape), it.value, ch.value, rc
+
+    def objective(self, objective=0):
+        """J of the current state (hfdib_adjoint_grad with max_iter = 0)."""
+        J = C.c_double(0.0)
+        self.stream.synchronize()
+        rc = self.lib.hfdib_adjoint_grad(self.h, int(objective), 1.0, 0, None, C.byref(J), None, None)
+        _check(rc, "hfdib_adjoint_grad")
+        return J.value
 
     def get_state(self):
         n = C.c_size_t(0)
