@@ -180,8 +180,9 @@ int hfdib_simple_sweep(hfdib_handle h, int n_sweeps, double* residuals);
 int hfdib_solve_steady(hfdib_handle h, double tol, int max_iter, int check_every,
                        int* iters_out, double* final_res);
 
-/* Objectives of hfdib_adjoint_grad. */
+/* Objectives of hfdib_adjoint_grad, and the largest GMRES restart length. */
 enum { HFDIB_OBJ_PRESSURE_DROP = 0 };
+enum { HFDIB_GMRES_MAX_RESTART = 200 };
 
 /* hfdib_adjoint_grad -- frozen-turbulence discrete adjoint of the converged
  * state: the gradient of an objective J with respect to the indicator lambda.
@@ -193,25 +194,34 @@ enum { HFDIB_OBJ_PRESSURE_DROP = 0 };
  * lambda moves it only through the imposed velocity u_ib of the
  * laminar-branch bc cells: the normal n = -grad(lambda)/|grad(lambda)|
  * (Eq. yorthoaux), y_perp (Eq. yortho) and the interpolation of Sec. 2.5.
- * The adjoint psi of that fixed point is found by iterating the transposed
- * sweep (reverse accumulation through the same red-black momentum passes,
- * with exact pressure solves).  Then dJ/dlambda = psi^T dG/dlambda.
+ * The adjoint psi of that fixed point solves (I - G_x^T) psi = J_x^T.  G_x^T
+ * is one transposed sweep: reverse accumulation through the same red-black
+ * momentum passes, with exact pressure solves, run as one CUDA graph.
+ * Then dJ/dlambda = psi^T dG/dlambda.
  *   objective  : HFDIB_OBJ_PRESSURE_DROP, J = mean p over the cells of the open
  *                inlet faces minus mean p over the cells of the outlet faces
- *   tol        : stop when max|psi_new - psi| <= tol max|psi| (checked every
- *                10 iterations); max_iter caps the iterations; max_iter = 0
- *                only evaluates J (dJ_dlambda may then be NULL)
+ *   gmres_restart : 0 (recommended): the reverse fixed point
+ *                psi <- G_x^T psi + J_x^T; stop when max|psi_new - psi| <=
+ *                tol max|psi| (checked every 10 iterations).  m > 0:
+ *                GMRES(m) on (I - G_x^T) psi = J_x^T; stop when the residual
+ *                2-norm is <= tol |J_x^T| (restarted GMRES can stagnate on
+ *                these operators).  At most HFDIB_GMRES_MAX_RESTART.  Either
+ *                way each adjoint pressure solve is warm-started from the
+ *                previous one and accurate to 1e-12 of its right-hand side.
+ *   tol, max_iter : tolerance as above; max_iter caps the transposed sweeps;
+ *                max_iter = 0 only evaluates J (dJ_dlambda may then be NULL)
  *   dJ_dlambda : DEVICE pointer, N doubles (cell order of lambda), caller-owned
- *   J_out, iters_out, change_out : host pointers, nullable
+ *   J_out, iters_out (transposed sweeps run), change_out (final relative
+ *                residual or change) : host pointers, nullable
  * Call it on a converged state (hfdib_solve_steady to a tight tolerance): the
  * gradient is that of the fixed point, and its error follows the residual.
  * 2D grids only (INVALID_ARG otherwise).  The state is left unchanged.
  * Returns HFDIB_OK, HFDIB_ERR_NOT_CONVERGED (gradient of the last iterate
  * still written), HFDIB_ERR_DIVERGED, HFDIB_ERR_INVALID_ARG, or CUDA/OOM errors.
- * The first call allocates about 90 doubles per cell of work arrays, which
- * live until hfdib_destroy. */
-int hfdib_adjoint_grad(hfdib_handle h, int objective, double tol, int max_iter, double* dJ_dlambda,
-                       double* J_out, int* iters_out, double* change_out);
+ * The first call allocates about 90 doubles per cell of work arrays (plus
+ * (m + 2) flat state vectors for GMRES), which live until hfdib_destroy. */
+int hfdib_adjoint_grad(hfdib_handle h, int objective, double tol, int max_iter, int gmres_restart,
+                       double* dJ_dlambda, double* J_out, int* iters_out, double* change_out);
 
 /* Copy a field (HFDIB_FIELD_*) device-to-device into dst (caller-owned, sized
  * like the field: cells, or faces (nx+1)*ny*nz / nx*(ny+1)*nz / nx*ny*(nz+1)). */

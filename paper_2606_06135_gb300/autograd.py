@@ -51,7 +51,7 @@ class SteadyRANS(torch.autograd.Function):
         return gout * g.reshape(ctx.lam_shape), None, None, None, None, None, None
 
 
-def pressure_drop(lam, case, solve_tol=1e-11, max_sweeps=20000, adj_tol=1e-11, adj_max_iter=50000, **opts):
+def pressure_drop(lam, case, solve_tol=1e-11, max_sweeps=40000, adj_tol=1e-10, adj_max_iter=20000, **opts):
     """Differentiable pressure drop of the case with indicator `lam` (a CUDA
     float64 tensor shaped (nz, ny, nx)); `opts` are hfdib options."""
     return SteadyRANS.apply(lam, case, solve_tol, max_sweeps, adj_tol, adj_max_iter, opts)

@@ -160,6 +160,9 @@ __global__ void k_adj_update(Grid g, Params P, Fields F, Level L0, Adj A) {
 // ---------------------------------------------------------------- a7 reversed: solve set-up
 // r = rhs - L x0 with x0 = the previous adjoint solution (warm start); the
 // loop kernels of pressure.cu then run unchanged on the redirected Fields.
+// The slot the loop takes as |r0|^2 receives |rhs|^2 + |r0|^2, so the
+// relative tolerance is measured against the right-hand side, not against the
+// (small) warm-started residual: every solve is accurate to tol |rhs|.
 __global__ void k_adj_pcg_init(Grid g, Fields F, Level L0, const double* __restrict__ rhs, int jacobi) {
     long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double red[6] = {0, 0, 0, 0, 0, 0};
@@ -181,7 +184,7 @@ __global__ void k_adj_pcg_init(Grid g, Fields F, Level L0, const double* __restr
         double z = 0.0;
         if (jacobi) { z = dg > 0.0 ? r / dg : 0.0; F.z[c] = z; }
         red[0] = r * z;
-        red[1] = r * r;
+        red[1] = r * r + rhs[c] * rhs[c];
         red[2] = rhs[c] * rhs[c];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) F.scal[SC_PCG_DONE] = 0.0;

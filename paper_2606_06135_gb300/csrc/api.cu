@@ -30,6 +30,15 @@ struct Prof {
     size_t used = 0;
 };
 
+// GMRES(m) workspace of the adjoint solve (device arrays)
+struct AdjGmres {
+    int m = 0;
+    double *V = nullptr, *W = nullptr, *x = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr;
+    double *gv = nullptr, *y = nullptr, *h1 = nullptr, *h2 = nullptr, *nrm2 = nullptr, *st = nullptr;
+    double* part = nullptr;
+    unsigned int* cnt = nullptr;
+};
+
 struct Ctx {
     Grid g;
     Params P;
@@ -64,6 +73,9 @@ struct Ctx {
     int last_piters = 0;
     double* pinned = nullptr;    // host pinned scratch (64 doubles)
     Adj adj;                     // adjoint work arrays (allocated by the first adjoint call)
+    AdjGmres gm;                 // GMRES workspace of the adjoint
+    cudaGraph_t adj_graph = nullptr;
+    cudaGraphExec_t adj_gexec = nullptr;
     bool adj_ready = false;
     long long adj_tcap = 0;      // capacity of adj.tent
 };
@@ -101,6 +113,10 @@ void free_all(Ctx* h) {
         h->gexec[q] = nullptr;
         h->graph[q] = nullptr;
     }
+    if (h->adj_gexec) cudaGraphExecDestroy(h->adj_gexec);
+    if (h->adj_graph) cudaGraphDestroy(h->adj_graph);
+    h->adj_gexec = nullptr;
+    h->adj_graph = nullptr;
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
     if (h->pinned) cudaFreeHost(h->pinned);
@@ -621,14 +637,33 @@ int adj_alloc(Ctx* h) {
     AL(A.snap, (2LL * A.nu + 1) * 3 * N);
     AL(A.As, 6 * N); AL(A.AP, 3 * N); AL(A.aavg, N); AL(A.jw, N);
     for (int q = 0; q < 3; ++q) {
-        AL(A.psu[q], N); AL(A.xbu[q], N); AL(A.Hb[q], N); AL(A.b0b[q], N); AL(A.bmb[q], N);
+        AL(A.Hb[q], N); AL(A.b0b[q], N); AL(A.bmb[q], N);
         AL(A.aPb[q], N); AL(A.usb[0][q], N); AL(A.usb[1][q], N); AL(A.fixb[q], N);
-        AL(A.psf[q], g.nface[q]); AL(A.xbf[q], g.nface[q]);
     }
-    AL(A.psp, N); AL(A.xbp, N); AL(A.pnb, N); AL(A.ps, N); AL(A.rAUb, N);
+    // flat adjoint state: u components, p, face fluxes of the active directions
+    long long nv = (long long)(g.dims + 1) * N;
+    for (int d = 0; d < g.dims; ++d) nv += g.nface[d];
+    A.nvec = nv;
+    AL(A.vpsi, nv); AL(A.vxb, nv); AL(A.vb, nv);
+    AL(A.pnb, N); AL(A.ps, N); AL(A.rAUb, N);
     AL(A.asb, 6 * N); AL(A.Gb, 9 * N); AL(A.tptr, N + 1); AL(A.dlam, N);
 #undef AL
     if (rc) return rc;
+    {
+        long long off = 0;
+        for (int q = 0; q < g.dims; ++q, off += N) { A.psu[q] = A.vpsi + off; A.xbu[q] = A.vxb + off; }
+        A.psp = A.vpsi + off;
+        A.xbp = A.vxb + off;
+        off += N;
+        for (int d = 0; d < g.dims; ++d) {
+            A.psf[d] = A.vpsi + off;
+            A.xbf[d] = A.vxb + off;
+            off += g.nface[d];
+        }
+        for (int q = g.dims; q < 3; ++q) {  // not read in 2D; point at valid memory
+            A.psu[q] = A.psu[0]; A.xbu[q] = A.xbu[0]; A.psf[q] = A.psf[0]; A.xbf[q] = A.xbf[0];
+        }
+    }
     // objective weights from the closed-face flags (fixed for the handle's lambda)
     cudaStream_t s = h->stream;
     std::vector<uint16_t> flags(N);
@@ -653,6 +688,8 @@ int adj_alloc(Ctx* h) {
         for (long long c : cells) jw[c] += w;
     }
     CK(cudaMemcpyAsync(A.jw, jw.data(), N * sizeof(double), cudaMemcpyHostToDevice, s));
+    // J_x^T as a flat vector: jw in the pressure block
+    CK(cudaMemcpyAsync(A.vb + (long long)g.dims * N, jw.data(), N * sizeof(double), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
     h->adj_ready = true;
     return HFDIB_OK;
@@ -759,23 +796,35 @@ int adj_setup(Ctx* h) {
     return HFDIB_OK;
 }
 
-// x-bar = G_x^T psi, and u_ib-bar (A.fixb) = the part of G_lambda^T psi
-int adj_pass(Ctx* h, double ptol) {
+// One reverse pass: x-bar = G_x^T psi (A.vxb from A.vpsi) and u_ib-bar (A.fixb),
+// the part of G_lambda^T psi.  Part A ends with the set-up of the adjoint
+// pressure solve (zero start, relative tolerance), part B follows it.
+void adj_enqueue_a(Ctx* h, bool warm) {
+    const Grid& g = h->g;
+    Fields F = h->F;
+    F.mixed = 0;
+    cudaStream_t s = h->stream;
+    Adj& A = h->adj;
+    const Level& L0 = h->mg.lv[0];
+    int jac = h->opt.precond == 0;
+    launch_adj_update(g, h->P, F, L0, A, s);
+    // the adjoint pressure solve starts from the previous pass's solution
+    // (warm) and stops at tol |rhs| (see k_adj_pcg_init), or from zero
+    if (!warm) cudaMemsetAsync(A.ps, 0, g.N * sizeof(double), s);
+    Fields Fa = F;
+    Fa.pn = A.ps;
+    launch_adj_pcg_init(g, Fa, L0, A.pnb, jac, s);
+    if (!jac) launch_vcycle(g, h->mg, h->tail_from, Fa, Fa.scal + SC_PCG_RZN, h->coarse_sweeps, s);
+}
+
+void adj_enqueue_b(Ctx* h) {
     const Grid& g = h->g;
     Fields F = h->F;
     F.mixed = 0;
     const Params& P = h->P;
     cudaStream_t s = h->stream;
     Adj& A = h->adj;
-    const Level& L0 = h->mg.lv[0];
-    int jac = h->opt.precond == 0;
-    launch_adj_update(g, P, F, L0, A, s);
-    Fields Fa = F;
-    Fa.pn = A.ps;
-    launch_adj_pcg_init(g, Fa, L0, A.pnb, jac, s);
-    if (!jac) launch_vcycle(g, h->mg, h->tail_from, Fa, Fa.scal + SC_PCG_RZN, h->coarse_sweeps, s);
-    RC(adj_pcg_run(h, Fa, ptol, 4000));
-    launch_adj_pressure(g, F, L0, A, s);
+    launch_adj_pressure(g, F, h->mg.lv[0], A, s);
     launch_adj_hbya(g, P, F, A, s);
     int buf = 0;
     for (int hs = 2 * A.nu; hs >= 1; --hs) {
@@ -788,8 +837,163 @@ int adj_pass(Ctx* h, double ptol) {
     launch_adj_transpose(g, F, A, s);
     launch_adj_gradu(g, F, h->bl, A, s);
     launch_adj_phi(g, F, A, s);
+}
+
+Fields adj_pfields(Ctx* h) {
+    Fields Fa = h->F;
+    Fa.mixed = 0;
+    Fa.pn = h->adj.ps;
+    return Fa;
+}
+
+// the pass as one CUDA graph, the adjoint CG in a device-controlled while node
+int adj_build_graph(Ctx* h, double ptol, bool warm) {
+    cudaStream_t s = h->stream;
+    int jac = h->opt.precond == 0;
+    Fields Fa = adj_pfields(h);
+    cudaGraph_t graph;
+    CK(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle hc;
+    CK(cudaGraphConditionalHandleCreate(&hc, graph, 1, cudaGraphCondAssignDefault));
+    CK(cudaStreamBeginCaptureToGraph(s, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    adj_enqueue_a(h, warm);
+    launch_pcg_start(Fa, jac, ptol, 4000, hc, 1, s);
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    CK(cudaStreamGetCaptureInfo(s, &st, nullptr, nullptr, &deps, nullptr, &ndeps));
+    std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
+    CK(cudaStreamEndCapture(s, &graph));
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = hc;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    CK(cudaGraphAddNode(&cnode, graph, dv.data(), nullptr, dv.size(), &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    launch_pcg_body(h->g, Fa, h->mg, h->tail_from, jac, h->coarse_sweeps, 4000, hc, 1, s);
+    CK(cudaStreamEndCapture(s, &body));
+    CK(cudaStreamBeginCaptureToGraph(s, graph, &cnode, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+    adj_enqueue_b(h);
+    CK(cudaStreamEndCapture(s, &graph));
+    cudaGraphExec_t exec;
+    CK(cudaGraphInstantiate(&exec, graph, 0));
+    h->adj_graph = graph;
+    h->adj_gexec = exec;
+    return HFDIB_OK;
+}
+
+void adj_drop_graph(Ctx* h) {
+    if (h->adj_gexec) cudaGraphExecDestroy(h->adj_gexec);
+    if (h->adj_graph) cudaGraphDestroy(h->adj_graph);
+    h->adj_gexec = nullptr;
+    h->adj_graph = nullptr;
+}
+
+int adj_pass(Ctx* h, double ptol, bool warm) {
+    if (h->adj_gexec) {
+        CK(cudaGraphLaunch(h->adj_gexec, h->stream));
+        return HFDIB_OK;
+    }
+    adj_enqueue_a(h, warm);
+    RC(adj_pcg_run(h, adj_pfields(h), ptol, 4000));
+    adj_enqueue_b(h);
     CK(cudaGetLastError());
     return HFDIB_OK;
+}
+
+// GMRES(m) on (I - G_x^T) psi = J_x^T; psi ends in A.vpsi and the last pass
+// (with that psi) leaves u_ib-bar in A.fixb.  mv counts reverse passes.
+int adj_gmres_alloc(Ctx* h, int m) {
+    AdjGmres& G = h->gm;
+    if (G.m >= m && G.V) return HFDIB_OK;
+    const long long n = h->adj.nvec;
+    int rc = HFDIB_OK;
+    G.m = m;
+    int pg = mdot_grid(n);
+#define AL(p, k) \
+    if (!rc) rc = dalloc_n(h, &(p), (long long)(k))
+    AL(G.V, (long long)(m + 1) * n); AL(G.W, n); AL(G.x, n);
+    AL(G.H, (long long)(m + 1) * m); AL(G.cs, m + 1); AL(G.sn, m + 1); AL(G.gv, m + 1); AL(G.y, m + 1);
+    AL(G.h1, m + 1); AL(G.h2, m + 1); AL(G.nrm2, 2); AL(G.st, 4);
+    AL(G.part, (long long)(m + 1) * pg); AL(G.cnt, 1);
+#undef AL
+    return rc;
+}
+
+int adj_gmres(Ctx* h, int m, double tol, int max_mv, int* mv_out, double* rel_out) {
+    Adj& A = h->adj;
+    AdjGmres& G = h->gm;
+    cudaStream_t s = h->stream;
+    const long long n = A.nvec;
+    const double ptol = 1e-12;
+    RC(adj_gmres_alloc(h, m));
+    launch_mdot(n, A.vb, A.vb, n, 1, G.part, G.cnt, G.nrm2 + 1, s);
+    double bn2 = 0.0;
+    RC(sync_read(h, G.nrm2 + 1, &bn2, 1));
+    double bnorm = sqrt(bn2);
+    CK(cudaMemsetAsync(G.x, 0, n * sizeof(double), s));
+    int mv = 0;
+    double relres = 1.0;
+    bool first = true, done = bnorm == 0.0;
+    while (!done && mv < max_mv) {
+        // r0 = b - (x - M x)
+        if (first) {
+            CK(cudaMemcpyAsync(G.W, A.vb, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        } else {
+            CK(cudaMemcpyAsync(A.vpsi, G.x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            RC(adj_pass(h, ptol, true));
+            ++mv;
+            launch_vsub_add(n, A.vb, G.x, A.vxb, G.W, s);
+        }
+        first = false;
+        launch_mdot(n, G.W, G.W, n, 1, G.part, G.cnt, G.nrm2, s);
+        launch_vnormalize(n, G.W, G.V, G.nrm2, s);
+        launch_gmres_start(m, G.nrm2, G.gv, G.st, s);
+        double beta = 0.0;
+        RC(sync_read(h, G.st, &beta, 1));
+        relres = beta / bnorm;
+        if (!(beta > tol * bnorm)) break;
+        int k = 0;
+        for (int j = 0; j < m && mv < max_mv; ++j) {
+            double* Vj = G.V + (long long)j * n;
+            CK(cudaMemcpyAsync(A.vpsi, Vj, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            RC(adj_pass(h, ptol, true));
+            ++mv;
+            launch_vsub(n, Vj, A.vxb, G.W, s);  // w = (I - M) V_j
+            launch_mdot(n, G.W, G.V, n, j + 1, G.part, G.cnt, G.h1, s);
+            launch_maxpy(n, G.W, G.V, n, j + 1, G.h1, -1.0, s);
+            launch_mdot(n, G.W, G.V, n, j + 1, G.part, G.cnt, G.h2, s);
+            launch_maxpy(n, G.W, G.V, n, j + 1, G.h2, -1.0, s);
+            launch_mdot(n, G.W, G.W, n, 1, G.part, G.cnt, G.nrm2, s);
+            launch_gmres_column(j, m, G.H, G.h1, G.h2, G.nrm2, G.cs, G.sn, G.gv, G.st, s);
+            launch_vnormalize(n, G.W, G.V + (long long)(j + 1) * n, G.nrm2, s);
+            k = j + 1;
+            double est = 0.0;
+            RC(sync_read(h, G.st + 1, &est, 1));
+            if (!std::isfinite(est)) return HFDIB_ERR_DIVERGED;
+            relres = est / bnorm;
+            if (est <= tol * bnorm) { done = true; break; }
+        }
+        if (k > 0) {
+            launch_gmres_y(k, m, G.H, G.gv, G.y, s);
+            launch_maxpy(n, G.x, G.V, n, k, G.y, 1.0, s);
+        }
+    }
+    // the pass with the final psi: u_ib-bar for the gradient, and the true residual
+    CK(cudaMemcpyAsync(A.vpsi, G.x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    RC(adj_pass(h, ptol, true));
+    ++mv;
+    launch_vsub_add(n, A.vb, G.x, A.vxb, G.W, s);
+    launch_mdot(n, G.W, G.W, n, 1, G.part, G.cnt, G.nrm2, s);
+    double r2 = 0.0;
+    RC(sync_read(h, G.nrm2, &r2, 1));
+    if (!std::isfinite(r2)) return HFDIB_ERR_DIVERGED;
+    relres = bnorm > 0.0 ? sqrt(r2) / bnorm : 0.0;
+    if (mv_out) *mv_out = mv;
+    if (rel_out) *rel_out = relres;
+    return relres <= tol ? HFDIB_OK : HFDIB_ERR_NOT_CONVERGED;
 }
 
 }  // namespace
@@ -1252,8 +1456,8 @@ int hfdib_get_counters(hfdib_handle hh, int64_t* sweeps, int64_t* launches) {
     return HFDIB_OK;
 }
 
-int hfdib_adjoint_grad(hfdib_handle hh, int objective, double tol, int max_iter, double* dJ_dlambda, double* J_out,
-                       int* iters_out, double* change_out) {
+int hfdib_adjoint_grad(hfdib_handle hh, int objective, double tol, int max_iter, int gmres_restart,
+                       double* dJ_dlambda, double* J_out, int* iters_out, double* change_out) {
     Ctx* h = (Ctx*)hh;
     if (iters_out) *iters_out = 0;
     if (change_out) *change_out = 0.0;
@@ -1261,42 +1465,65 @@ int hfdib_adjoint_grad(hfdib_handle hh, int objective, double tol, int max_iter,
     if (objective != HFDIB_OBJ_PRESSURE_DROP) return HFDIB_ERR_INVALID_ARG;
     if (h->g.dims != 2) return HFDIB_ERR_INVALID_ARG;
     if (!(tol > 0.0) || max_iter < 0 || (max_iter > 0 && !dJ_dlambda)) return HFDIB_ERR_INVALID_ARG;
+    if (gmres_restart < 0 || gmres_restart > HFDIB_GMRES_MAX_RESTART) return HFDIB_ERR_INVALID_ARG;
     const Grid& g = h->g;
     cudaStream_t s = h->stream;
     RC(adj_alloc(h));
     Adj& A = h->adj;
+    Fields F = h->F;
+    F.mixed = 0;
     if (max_iter == 0) {
         // the objective alone
-        Fields F0 = h->F;
-        launch_adj_objective(g, F0, A, s);
+        launch_adj_objective(g, F, A, s);
         CK(cudaGetLastError());
         double J = 0.0;
-        RC(sync_read(h, F0.scal + SC_ADJ_J, &J, 1));
+        RC(sync_read(h, F.scal + SC_ADJ_J, &J, 1));
         if (J_out) *J_out = J;
         return HFDIB_OK;
     }
     RC(adj_setup(h));
-    for (int q = 0; q < 3; ++q) {
-        CK(cudaMemsetAsync(A.psu[q], 0, g.N * sizeof(double), s));
-        CK(cudaMemsetAsync(A.psf[q], 0, g.nface[q] * sizeof(double), s));
-    }
-    CK(cudaMemsetAsync(A.psp, 0, g.N * sizeof(double), s));
+    const bool warm = true;
+    const double ptol = 1e-12;
     CK(cudaMemsetAsync(A.ps, 0, g.N * sizeof(double), s));
-    Fields F = h->F;
-    F.mixed = 0;
-    int it = 0, converged = 0;
-    double ch[2] = {0.0, 0.0};
-    for (it = 0; it < max_iter; ++it) {
-        RC(adj_pass(h, 1e-12));
-        launch_adj_next(g, F, A, it == 0, s);
-        if ((it + 1) % 10 == 0 || it + 1 == max_iter) {
-            RC(sync_read(h, F.scal + SC_ADJ_DIFF, ch, 2));
-            if (!std::isfinite(ch[0]) || !std::isfinite(ch[1])) return HFDIB_ERR_DIVERGED;
-            if (ch[0] <= tol * ch[1]) { converged = 1; ++it; break; }
+    adj_drop_graph(h);
+    if (adj_build_graph(h, ptol, warm) != HFDIB_OK) {
+        // capture not possible here: abandon it and run the pass host-driven
+        cudaStreamCaptureStatus st;
+        if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+            cudaGraph_t gg = nullptr;
+            cudaStreamEndCapture(s, &gg);
+            if (gg) cudaGraphDestroy(gg);
         }
+        cudaGetLastError();
+        adj_drop_graph(h);
     }
+    int rc = HFDIB_OK, it = 0;
+    double change = 0.0;
+    if (gmres_restart > 0) {
+        rc = adj_gmres(h, gmres_restart, tol, max_iter, &it, &change);
+        if (rc != HFDIB_OK && rc != HFDIB_ERR_NOT_CONVERGED) { adj_drop_graph(h); return rc; }
+    } else {
+        // plain reverse fixed point psi <- G_x^T psi + J_x^T
+        CK(cudaMemsetAsync(A.vpsi, 0, A.nvec * sizeof(double), s));
+        double ch[2] = {0.0, 0.0};
+        rc = HFDIB_ERR_NOT_CONVERGED;
+        for (it = 0; it < max_iter;) {
+            int r = adj_pass(h, ptol, warm);
+            if (r) { adj_drop_graph(h); return r; }
+            launch_adj_next(g, F, A, it == 0, s);
+            ++it;
+            if (it % 10 == 0 || it == max_iter) {
+                r = sync_read(h, F.scal + SC_ADJ_DIFF, ch, 2);
+                if (r) { adj_drop_graph(h); return r; }
+                if (!std::isfinite(ch[0]) || !std::isfinite(ch[1])) { adj_drop_graph(h); return HFDIB_ERR_DIVERGED; }
+                if (ch[0] <= tol * ch[1]) { rc = HFDIB_OK; break; }
+            }
+        }
+        change = ch[1] > 0.0 ? ch[0] / ch[1] : ch[0];
+    }
+    adj_drop_graph(h);
     if (iters_out) *iters_out = it;
-    if (change_out) *change_out = ch[1] > 0.0 ? ch[0] / ch[1] : ch[0];
+    if (change_out) *change_out = change;
     CK(cudaMemsetAsync(A.dlam, 0, g.N * sizeof(double), s));
     launch_adj_dlambda(g, F, h->bl, h->lam, A, s);
     CK(cudaMemcpyAsync(dJ_dlambda, A.dlam, g.N * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1305,7 +1532,7 @@ int hfdib_adjoint_grad(hfdib_handle hh, int objective, double tol, int max_iter,
     double J = 0.0;
     RC(sync_read(h, F.scal + SC_ADJ_J, &J, 1));
     if (J_out) *J_out = J;
-    return converged ? HFDIB_OK : HFDIB_ERR_NOT_CONVERGED;
+    return rc;
 }
 
 void hfdib_destroy(hfdib_handle hh) {

@@ -199,6 +199,10 @@ int pcgb_fits(int mixed, int threads, size_t smem, int* blocks_per_sm);
 // point of Christianson type for d(pressure drop)/d(lambda))
 struct Adj {
     int nu;              // red-black momentum sweep pairs of the differentiated sweep
+    long long nvec;      // length of the flat adjoint state (u components, p, face fluxes)
+    double* vpsi;        // flat psi; psu / psp / psf point into it
+    double* vxb;         // flat x-bar; xbu / xbp / xbf point into it
+    double* vb;          // flat J_x^T
     double* snap;        // [2 nu][3][N] predictor iterates S_0 .. S_{2nu-1} (S_{2nu} = F.us)
     double* As;          // [6][N] neighbour coefficients of the momentum rows (0: no neighbour)
     double* AP;          // [3][N] unrelaxed diagonal per component
@@ -243,6 +247,20 @@ void launch_adj_objective(const Grid& g, const Fields& F, const Adj& A, cudaStre
 void launch_adj_dlambda(const Grid& g, const Fields& F, const BcList& bl, const double* lam, const Adj& A,
                         cudaStream_t s);
 enum { SC_ADJ_DIFF = 48, SC_ADJ_NORM = 49, SC_ADJ_J = 50 };
+
+// krylov.cu: GMRES(m) vector kernels and the Hessenberg bookkeeping
+void launch_vsub(long long n, const double* a, const double* b, double* out, cudaStream_t s);
+void launch_vsub_add(long long n, const double* a, const double* b, const double* c, double* out, cudaStream_t s);
+int mdot_grid(long long n);
+void launch_mdot(long long n, const double* w, const double* V, long long ldv, int k, double* partials,
+                 unsigned int* counter, double* out, cudaStream_t s);
+void launch_maxpy(long long n, double* w, const double* V, long long ldv, int k, const double* c, double sgn,
+                  cudaStream_t s);
+void launch_vnormalize(long long n, const double* src, double* dst, const double* nrm2, cudaStream_t s);
+void launch_gmres_start(int m, const double* nrm2, double* gv, double* st, cudaStream_t s);
+void launch_gmres_column(int j, int m, double* H, const double* h1, const double* h2, const double* nrm2, double* cs,
+                         double* sn, double* gv, double* st, cudaStream_t s);
+void launch_gmres_y(int k, int m, const double* H, const double* gv, double* y, cudaStream_t s);
 
 // turb.cu
 void launch_turb_prep(const Grid& g, const Params& P, const Fields& F, cudaStream_t s);

@@ -115,7 +115,7 @@ def load_library(path=LIBPATH):
     lib.hfdib_batch_autotune.restype = C.c_int
     lib.hfdib_destroy_batch.argtypes = [vp]
     lib.hfdib_destroy_batch.restype = None
-    lib.hfdib_adjoint_grad.argtypes = [vp, i32, dbl, i32, vp, C.POINTER(dbl), C.POINTER(i32), C.POINTER(dbl)]
+    lib.hfdib_adjoint_grad.argtypes = [vp, i32, dbl, i32, i32, vp, C.POINTER(dbl), C.POINTER(i32), C.POINTER(dbl)]
     lib.hfdib_adjoint_grad.restype = i32
     lib.hfdib_error_string.argtypes = [i32]
     lib.hfdib_error_string.restype = C.c_char_p
@@ -291,17 +291,18 @@ class Solver:
         _check(self.lib.hfdib_get_launch_counts(self.h, C.byref(a), C.byref(b)), "hfdib_get_launch_counts")
         return a.value, b.value
 
-    def adjoint_grad(self, tol=1e-10, max_iter=20000, objective=0):
+    def adjoint_grad(self, tol=1e-10, max_iter=20000, objective=0, gmres_restart=0):
         """Frozen-turbulence adjoint of the converged state: returns (J,
-        dJ/dlambda as a device tensor shaped like lambda, iterations, relative
-        change at the stop, status).  Status 0, or -4 when max_iter ran out."""
+        dJ/dlambda as a device tensor shaped like lambda, transposed sweeps,
+        final relative residual (GMRES) or change (gmres_restart=0: plain
+        reverse fixed point), status).  Status 0, or -4 when max_iter ran out."""
         torch = self.torch
         out = torch.zeros(self.N, dtype=torch.float64, device=self.device)
         J = C.c_double(0.0)
         it = C.c_int(0)
         ch = C.c_double(0.0)
         self.stream.synchronize()
-        rc = self.lib.hfdib_adjoint_grad(self.h, int(objective), float(tol), int(max_iter),
+        rc = self.lib.hfdib_adjoint_grad(self.h, int(objective), float(tol), int(max_iter), int(gmres_restart),
                                          C.c_void_p(out.data_ptr()), C.byref(J), C.byref(it), C.byref(ch))
         if rc not in (0, ERR_NOT_CONVERGED):
             _check(rc, "hfdib_adjoint_grad")
@@ -312,7 +313,7 @@ class Solver:
         """J of the current state (hfdib_adjoint_grad with max_iter = 0)."""
         J = C.c_double(0.0)
         self.stream.synchronize()
-        rc = self.lib.hfdib_adjoint_grad(self.h, int(objective), 1.0, 0, None, C.byref(J), None, None)
+        rc = self.lib.hfdib_adjoint_grad(self.h, int(objective), 1.0, 0, 0, None, C.byref(J), None, None)
         _check(rc, "hfdib_adjoint_grad")
         return J.value
 
