@@ -15,7 +15,15 @@ in L2.  Also reported: converged solves/s to max scaled residual 1e-6, the
 end-to-end rate through the public API from host arrays, the roofline of the
 dominant kernel class, and the CPU oracle on the host cores.
 
+Two more legs (rank 0): `batch` -- 16 NACA 0012 lambda fields (angles of
+attack 0-15 deg, 2048 x 1024 each, k-omega SST, mixed precision) advanced
+together by the batched persistent pressure launch, against the same designs
+one at a time; `adjoint` -- channel designs with random smooth obstacles
+(k-epsilon, 256 x 128 and 264 x 132) solved together to 1e-10, then the
+frozen-turbulence adjoint gradient of the pressure drop per design.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--no-solve] [--no-cpu] [--no-batch] [--no-adjoint]
 """
 import argparse
 import json
@@ -44,6 +52,12 @@ def PCG_ITERS_FACTOR(piters):
     return max(float(piters.mean()), 1.0)
 
 
+# DRAM bytes of one launch of the dominant kernel, from an ncu capture of this
+# workload (dram__bytes_read.sum + dram__bytes_write.sum; mixed: the FP32
+# V-cycle variant).  At 262k cells the pressure hierarchy stays in L2, so
+# this is far below the algorithmic count.
+TRAFFIC = {("pcg", "mixed"): 10.798592e6 + 3.507456e6, ("pcg", "fp64"): 12.204544e6 + 2.468352e6}
+
 BYTES_PER_CELL = {
     # u, v, p, nut, phi_x, phi_y, 4 gradient comps read; bm x2, u* x2 written
     "mom_asm": 8 * (10 + 4) + 2,
@@ -51,10 +65,6 @@ BYTES_PER_CELL = {
     "mom_smooth": 8 * (1 + 2 + 2 + 1 + 1) + 2,
     # u*, bm x2, p, phi x2, nut read; HbyA x2, rAU, phiH x2 written
     "hbya": 8 * (7 + 5) + 2,
-    # per CG iteration (x iterations per launch): A-product (z, d, cf x2,
-    # diag; d, q) + update (pn, d, r, q; pn, r) + fine-level V-cycle (~26
-    # words) x 4/3 for the coarser levels
-    "pcg": 8 * (7 + 6) + int(8 * 26 * 4 / 3),
     "vcycle0": int(8 * 26 * 4 / 3),
     # phiH x2, pn, p, HbyA x2, rAU, cf x2 read; phi x2, u x2, p written
     "update": 8 * (9 + 5) + 2,
@@ -196,6 +206,91 @@ print(json.dumps({"seconds": time.perf_counter() - t0}))
     return 0
 
 
+# ---------------------------------------------------------------- extra legs
+NACA_NX, NACA_NY, NACA_AOAS = 2048, 1024, 16   # batched multi-lambda workload (16 angles of attack)
+ADJ_DESIGNS = 2                                # random-obstacle designs for the adjoint leg
+
+
+def _naca_case(aoa):
+    """Geometry of one angle of attack (runs in a spawned worker)."""
+    sys.path.insert(0, ROOT)
+    from paper_2606_06135_gb300 import geometry as G
+    return G.case_naca(NACA_NX, NACA_NY, aoa_deg=float(aoa))
+
+
+def _grf_case(b):
+    sys.path.insert(0, ROOT)
+    from paper_2606_06135_gb300 import geometry as G
+    nx, ny = G.grf_design_size(b)
+    return G.case_grf(nx, ny, seed=b)
+
+
+def batch_leg(hfdib, torch, cases, dev, steps, warmup):
+    """B lambda fields advanced together (one batched persistent pressure
+    launch per sweep) against the same designs solved one at a time."""
+    N = sum(c["grid"]["nx"] * c["grid"]["ny"] for c in cases)
+    bs = hfdib.BatchSolver(cases, device=str(dev), precision=1)
+    bs.sweep(warmup, read=False)
+    tune = bs.autotune(2)
+    bs.sweep(2, read=False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    bs.stream.synchronize()
+    e0.record(bs.stream)
+    bs.sweep(steps, read=False)
+    e1.record(bs.stream)
+    bs.stream.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    res = bs.sweep(1)
+    bs.close()
+    one = 0.0
+    n1 = 0
+    for c in cases[:2]:
+        s = hfdib.Solver(c, device=str(dev), precision=1)
+        s.sweep(warmup, read=False)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.stream.synchronize()
+        a.record(s.stream)
+        s.sweep(steps, read=False)
+        b.record(s.stream)
+        s.stream.synchronize()
+        one += a.elapsed_time(b) / 1e3
+        n1 += c["grid"]["nx"] * c["grid"]["ny"]
+        s.close()
+    return {"workload": "naca0012_%daoa_%dx%d_sst" % (len(cases), NACA_NX, NACA_NY), "designs": len(cases),
+            "cells": N, "sweeps": steps, "value": N * steps / t, "unit": "cell-updates/s",
+            "ms_per_batched_sweep": 1e3 * t / steps, "precision": "mixed",
+            "one_by_one": {"designs": 2, "value": n1 * steps / one, "unit": "cell-updates/s"},
+            "autotune": tune, "max_residual_after": float(max(res[:, :6].max(), 0.0)),
+            "l2": "working set %.0f MB per field set > L2" % (N * 8 / 1e6)}
+
+
+def adjoint_leg(hfdib, torch, cases, dev):
+    """Designs solved together to 1e-10 (FP64), then one frozen-turbulence
+    adjoint gradient dJ/dlambda (pressure drop) per design."""
+    import time as _t
+    N = sum(c["grid"]["nx"] * c["grid"]["ny"] for c in cases)
+    bs = hfdib.BatchSolver(cases, device=str(dev), precision=0)
+    t0 = _t.perf_counter()
+    rc, its, res = bs.solve(tol=1e-10, max_iter=40000, check_every=100)
+    torch.cuda.synchronize(dev)
+    t_solve = _t.perf_counter() - t0
+    per = []
+    t_adj = 0.0
+    for i in range(len(cases)):
+        p = bs.problem(i)
+        t0 = _t.perf_counter()
+        J, g, passes, ch, arc = p.adjoint_grad(tol=1e-9, max_iter=40000)
+        dt = _t.perf_counter() - t0
+        t_adj += dt
+        per.append({"grid": [cases[i]["grid"]["nx"], cases[i]["grid"]["ny"]], "J": J, "status": arc,
+                    "transposed_sweeps": passes, "seconds": dt, "ms_per_transposed_sweep": 1e3 * dt / max(passes, 1),
+                    "forward_sweeps": int(its[i])})
+    bs.close()
+    return {"workload": "grf_channel_keps_designs_%d" % len(cases), "cells": N, "solve_status": rc,
+            "solve_tol": 1e-10, "adjoint_tol": 1e-9, "solve_seconds": t_solve, "adjoint_seconds": t_adj,
+            "gradients_per_s": len(cases) / (t_solve + t_adj), "designs": per}
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -205,6 +300,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true", help="skip the converged-solve and e2e legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched multi-lambda leg")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -213,6 +310,18 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank)
+
+    # geometry of the extra legs, generated by spawned workers while the
+    # GPU legs run (the pool starts before the first CUDA call)
+    pool, fut_naca, fut_grf = None, [], []
+    if rank == 0 and (not args.no_batch or not args.no_adjoint):
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        pool = ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1), mp_context=mp.get_context("spawn"))
+        if not args.no_batch:
+            fut_naca = [pool.submit(_naca_case, a) for a in range(NACA_AOAS)]
+        if not args.no_adjoint:
+            fut_grf = [pool.submit(_grf_case, b) for b in range(ADJ_DESIGNS)]
 
     import numpy as np
     import torch
@@ -275,11 +384,20 @@ def main():
         prof = s.profile(3)
         dname, (dus, dcalls) = max(prof.items(), key=lambda kv: kv[1][0])
         avg_us = dus / max(dcalls, 1)
-        bpc = BYTES_PER_CELL.get(dname, 0) * (PCG_ITERS_FACTOR(piters) if dname == "pcg" else 1)
+        if dname == "pcg":
+            # per CG iteration: FP64 CG vectors (13 words) + the V-cycle (26
+            # words x 4/3 for the coarse levels) in the preconditioner's type
+            wv = 4 if precision == "mixed" else 8
+            bpc = (8 * (7 + 6) + int(wv * 26 * 4 / 3)) * PCG_ITERS_FACTOR(piters)
+        else:
+            bpc = BYTES_PER_CELL.get(dname, 0)
         achieved = bpc * N / (avg_us * 1e-6) / 1e9
         total = sum(x[0] for x in prof.values())
+        traffic = TRAFFIC.get((dname, precision))
         roof = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
+                "traffic_note": "ncu DRAM bytes of one launch; the pressure hierarchy is L2-resident at this size"
+                if traffic else None,
                 "algorithmic_bytes_per_launch": bpc * N, "avg_launch_us": avg_us,
                 "class_share": {k: round(v[0] / total, 4) for k, v in prof.items()}}
         s.close()
@@ -345,6 +463,12 @@ def main():
         out["solve"] = lm
         out["fp64"]["solve"] = lf
         out["fp64"]["solves_per_s"] = lf["solves_per_s"]
+    if rank == 0 and fut_naca:
+        out["batch"] = batch_leg(hfdib, torch, [f.result() for f in fut_naca], dev, args.steps, args.warmup)
+    if rank == 0 and fut_grf:
+        out["adjoint"] = adjoint_leg(hfdib, torch, [f.result() for f in fut_grf], dev)
+    if pool is not None:
+        pool.shutdown()
     if rank == 0 and not args.no_cpu:
         r = oracle_rate(seconds=15.0)
         out["cpu_baseline"] = {"value": r["cells"] * r["sweeps"] / r["seconds"], "unit": "cell-updates/s",
