@@ -86,7 +86,8 @@ __global__ void k_adj_coef(Grid g, Params P, Fields F, Adj A) {
     const double nu = g.nu;
     double nuP = nu + F.nut[c];
     double aP[3] = {0.0, 0.0, 0.0};
-    for (int d = 0; d < g.dims; ++d) {
+    #pragma unroll
+    for (int d = 0; d < 3 && d < g.dims; ++d) {
         long long fl = face_lo(g, d, i, j, k);
         long long fs = face_stride(g, d);
         for (int side = 0; side < 2; ++side) {
@@ -98,10 +99,12 @@ __global__ void k_adj_coef(Grid g, Params P, Fields F, Adj A) {
                 double Dif = 0.5 * (nuP + (nu + F.nut[nc])) * g.SoD[d];
                 A.As[(long long)s * g.N + c] = fmin(Fout, 0.0) - Dif;
                 double add = fmax(-Fout, 0.0) + Dif;
-                for (int q = 0; q < g.dims; ++q) aP[q] += add;
+                #pragma unroll
+                for (int q = 0; q < 3 && q < g.dims; ++q) aP[q] += add;
             } else {
                 A.As[(long long)s * g.N + c] = 0.0;
-                for (int q = 0; q < g.dims; ++q) {
+                #pragma unroll
+                for (int q = 0; q < 3 && q < g.dims; ++q) {
                     double val;
                     if (vel_fixed(g, f, s, q, val)) aP[q] += nuP * g.SoHD[d] + fmax(-Fout, 0.0);
                 }
@@ -109,7 +112,8 @@ __global__ void k_adj_coef(Grid g, Params P, Fields F, Adj A) {
         }
     }
     double avg = 0.0;
-    for (int q = 0; q < g.dims; ++q) {
+    #pragma unroll
+    for (int q = 0; q < 3 && q < g.dims; ++q) {
         A.AP[(long long)q * g.N + c] = aP[q];
         avg += aP[q] * P.iurf_u;
     }
@@ -127,7 +131,8 @@ __global__ void k_adj_update(Grid g, Params P, Fields F, Level L0, Adj A) {
     const double a = P.urf_p;
     double rAUb = 0.0;
     double prb = A.psp[c];
-    for (int d = 0; d < g.dims; ++d) {
+    #pragma unroll
+    for (int d = 0; d < 3 && d < g.dims; ++d) {
         const double* psu = A.psu[d];
         double gp = grad_pr(g, F.p, F.pn, a, c, d, i, j, k);
         A.Hb[d][c] = psu[c];
@@ -146,7 +151,8 @@ __global__ void k_adj_update(Grid g, Params P, Fields F, Level L0, Adj A) {
     }
     A.xbp[c] = (1.0 - a) * prb;
     double pnb = a * prb;
-    for (int d = 0; d < g.dims; ++d) {
+    #pragma unroll
+    for (int d = 0; d < 3 && d < g.dims; ++d) {
         long long fl = face_lo(g, d, i, j, k);
         long long fh = fl + face_stride(g, d);
         // phi'_lo = phiH - cf (pn_c - pn_lo | p_out); phi'_hi = phiH - cf (pn_hi | p_out - pn_c)
@@ -172,7 +178,8 @@ __global__ void k_adj_pcg_init(Grid g, Fields F, Level L0, const double* __restr
         int idx[3] = {i, j, k};
         double dg = L0.diag[c];
         double Ax = dg * F.pn[c];
-        for (int d = 0; d < g.dims; ++d) {
+        #pragma unroll
+        for (int d = 0; d < 3 && d < g.dims; ++d) {
             long long fl = face_lo(g, d, i, j, k);
             if (idx[d] > 0) Ax -= L0.cf[d][fl] * F.pn[c - g.stride[d]];
             if (idx[d] < g.n[d] - 1) Ax -= L0.cf[d][fl + face_stride(g, d)] * F.pn[c + g.stride[d]];
@@ -205,7 +212,8 @@ __global__ void k_adj_pressure(Grid g, Fields F, Level L0, Adj A) {
     const double* pn = F.pn;
     double mc = (f & F_M) ? 1.0 : 0.0;
     double rAUb = A.rAUb[c];
-    for (int d = 0; d < g.dims; ++d) {
+    #pragma unroll
+    for (int d = 0; d < 3 && d < g.dims; ++d) {
         long long fl = face_lo(g, d, i, j, k);
         long long fh = fl + face_stride(g, d);
         double Hb = A.Hb[d][c];
@@ -259,7 +267,8 @@ __global__ void k_adj_hbya(Grid g, Params P, Fields F, Adj A) {
     double iab = g.V * A.rAUb[c];
     double avb = 0.0;
     double Hb[3] = {0.0, 0.0, 0.0};
-    for (int q = 0; q < g.dims; ++q) {
+    #pragma unroll
+    for (int q = 0; q < 3 && q < g.dims; ++q) {
         Hb[q] = A.Hb[q][c];
         double us = F.us[q][c];
         double aPq = A.AP[q * N + c];
@@ -268,7 +277,8 @@ __global__ void k_adj_hbya(Grid g, Params P, Fields F, Adj A) {
         iab += F.HbyA[q][c] * aavg * Hb[q];
         avb += us * ia * Hb[q];
         double usb = -(aPq * P.iurf_u - aavg) * ia * Hb[q];
-        for (int d = 0; d < g.dims; ++d)
+        #pragma unroll
+        for (int d = 0; d < 3 && d < g.dims; ++d)
             for (int side = 0; side < 2; ++side) {
                 if (!has_nb(g, d, side, i, j, k)) continue;
                 long long r = side ? c + g.stride[d] : c - g.stride[d];
@@ -280,15 +290,18 @@ __global__ void k_adj_hbya(Grid g, Params P, Fields F, Adj A) {
         A.fixb[q][c] = 0.0;
     }
     avb += -ia * ia * iab;
-    for (int q = 0; q < g.dims; ++q)
+    #pragma unroll
+    for (int q = 0; q < 3 && q < g.dims; ++q)
         A.aPb[q][c] = ia * Hb[q] * (rlx * F.u[q][c] - F.us[q][c] / urf) + avb / (urf * g.dims);
-    for (int d = 0; d < g.dims; ++d)
+    #pragma unroll
+    for (int d = 0; d < 3 && d < g.dims; ++d)
         for (int side = 0; side < 2; ++side) {
             int s = 2 * d + side;
             double v = 0.0;
             if (has_nb(g, d, side, i, j, k)) {
                 long long r = side ? c + g.stride[d] : c - g.stride[d];
-                for (int q = 0; q < g.dims; ++q) v -= F.us[q][r] * ia * Hb[q];
+                #pragma unroll
+                for (int q = 0; q < 3 && q < g.dims; ++q) v -= F.us[q][r] * ia * Hb[q];
             }
             A.asb[s * N + c] = v;
         }
@@ -312,18 +325,21 @@ __global__ void k_adj_gs(Grid g, Params P, Fields F, Adj A, int colour, const do
     double* const* bout = A.usb[1 - in_buf];
     if (colour_of(i, j, k) == colour) {
         if (tag_of(f) == TAG_IC) {
-            for (int q = 0; q < g.dims; ++q) bout[q][c] = 0.0;
+            #pragma unroll
+            for (int q = 0; q < 3 && q < g.dims; ++q) bout[q][c] = 0.0;
             return;
         }
         if (f & F_AU) {
-            for (int q = 0; q < g.dims; ++q) {
+            #pragma unroll
+            for (int q = 0; q < 3 && q < g.dims; ++q) {
                 A.fixb[q][c] += bin[q][c];
                 bout[q][c] = 0.0;
             }
             return;
         }
         double gq[3] = {0.0, 0.0, 0.0};
-        for (int q = 0; q < g.dims; ++q) {
+        #pragma unroll
+        for (int q = 0; q < 3 && q < g.dims; ++q) {
             double ub = bin[q][c];
             double aPq = A.AP[q * N + c];
             gq[q] = ub * urf / aPq;
@@ -331,19 +347,23 @@ __global__ void k_adj_gs(Grid g, Params P, Fields F, Adj A, int colour, const do
             A.aPb[q][c] += -Sout[q * N + c] / aPq * ub;
             bout[q][c] = 0.0;
         }
-        for (int d = 0; d < g.dims; ++d)
+        #pragma unroll
+        for (int d = 0; d < 3 && d < g.dims; ++d)
             for (int side = 0; side < 2; ++side) {
                 if (!has_nb(g, d, side, i, j, k)) continue;
                 long long r = side ? c + g.stride[d] : c - g.stride[d];
                 double v = 0.0;
-                for (int q = 0; q < g.dims; ++q) v -= Sin[q * N + r] * gq[q];
+                #pragma unroll
+                for (int q = 0; q < 3 && q < g.dims; ++q) v -= Sin[q * N + r] * gq[q];
                 A.asb[(2 * d + side) * N + c] += v;
             }
         return;
     }
-    for (int q = 0; q < g.dims; ++q) {
+    #pragma unroll
+    for (int q = 0; q < 3 && q < g.dims; ++q) {
         double v = bin[q][c];
-        for (int d = 0; d < g.dims; ++d)
+        #pragma unroll
+        for (int d = 0; d < 3 && d < g.dims; ++d)
             for (int side = 0; side < 2; ++side) {
                 if (!has_nb(g, d, side, i, j, k)) continue;
                 long long r = side ? c + g.stride[d] : c - g.stride[d];
@@ -363,7 +383,8 @@ __global__ void k_adj_b0(Grid g, Params P, Fields F, Adj A, int buf) {
     if (c >= g.N) return;
     uint16_t f = F.flags[c];
     const long long N = g.N;
-    for (int q = 0; q < g.dims; ++q) {
+    #pragma unroll
+    for (int q = 0; q < 3 && q < g.dims; ++q) {
         double us0 = A.usb[buf][q][c];
         double bmb = A.bmb[q][c];
         double xu = A.xbu[q][c];
@@ -389,7 +410,8 @@ __global__ void k_adj_transpose(Grid g, Fields F, Adj A) {
     cell_ijk(g, c, i, j, k);
     const long long N = g.N;
     double pb = 0.0;
-    for (int d = 0; d < g.dims; ++d) {
+    #pragma unroll
+    for (int d = 0; d < 3 && d < g.dims; ++d) {
         bool lo = has_nb(g, d, 0, i, j, k), hi = has_nb(g, d, 1, i, j, k);
         pb += -g.V * A.bmb[d][c] * own_grad_coef(lo, hi, p_fixed(g, 2 * d), p_fixed(g, 2 * d + 1), g.iD[d]);
         if (lo) pb += -g.V * A.bmb[d][c - g.stride[d]] * 0.5 * g.iD[d];
@@ -397,10 +419,12 @@ __global__ void k_adj_transpose(Grid g, Fields F, Adj A) {
     }
     A.xbp[c] += pb;
     double nuc = g.nu + F.nut[c];
-    for (int q = 0; q < g.dims; ++q) {
+    #pragma unroll
+    for (int q = 0; q < 3 && q < g.dims; ++q) {
         const double* Tb = A.b0b[q];
         double Tc = Tb[c];
-        for (int a = 0; a < g.dims; ++a) {
+        #pragma unroll
+        for (int a = 0; a < 3 && a < g.dims; ++a) {
             double v;
             if (has_nb(g, a, 1, i, j, k)) {
                 long long n = c + g.stride[a];
@@ -441,9 +465,11 @@ __global__ void k_adj_gradu(Grid g, Fields F, BcList bl, Adj A) {
     const long long N = g.N;
     uint16_t f = F.flags[c];
     int e0 = A.tptr[c], e1 = A.tptr[c + 1];
-    for (int b = 0; b < g.dims; ++b) {
+    #pragma unroll
+    for (int b = 0; b < 3 && b < g.dims; ++b) {
         double ub = 0.0;
-        for (int a = 0; a < g.dims; ++a) {
+        #pragma unroll
+        for (int a = 0; a < 3 && a < g.dims; ++a) {
             const double* Gb = A.Gb + (3 * a + b) * N;
             double val;
             bool lo = has_nb(g, a, 0, i, j, k), hi = has_nb(g, a, 1, i, j, k);
@@ -471,7 +497,8 @@ __global__ void k_adj_phi(Grid g, Fields F, Adj A) {
     int i, j, k;
     cell_ijk(g, c, i, j, k);
     const long long N = g.N;
-    for (int d = 0; d < g.dims; ++d) {
+    #pragma unroll
+    for (int d = 0; d < 3 && d < g.dims; ++d) {
         long long fl = face_lo(g, d, i, j, k);
         double v = 0.0;
         if (has_nb(g, d, 0, i, j, k)) {
@@ -479,10 +506,12 @@ __global__ void k_adj_phi(Grid g, Fields F, Adj A) {
             double Fv = F.phi[d][fl];
             if (Fv < 0.0) {  // inflow into n through its high side
                 v += A.asb[(2 * d + 1) * N + n];
-                for (int q = 0; q < g.dims; ++q) v -= A.aPb[q][n];
+                #pragma unroll
+                for (int q = 0; q < 3 && q < g.dims; ++q) v -= A.aPb[q][n];
             } else if (Fv > 0.0) {  // inflow into c through its low side
                 v -= A.asb[(2 * d) * N + c];
-                for (int q = 0; q < g.dims; ++q) v += A.aPb[q][c];
+                #pragma unroll
+                for (int q = 0; q < 3 && q < g.dims; ++q) v += A.aPb[q][c];
             }
         }
         A.xbf[d][fl] = v;
@@ -497,7 +526,8 @@ __global__ void k_adj_next(Grid g, Fields F, Adj A, int first) {
     if (c < g.N) {
         int i, j, k;
         cell_ijk(g, c, i, j, k);
-        for (int q = 0; q < g.dims; ++q) {
+        #pragma unroll
+        for (int q = 0; q < 3 && q < g.dims; ++q) {
             double nw = A.xbu[q][c];
             double old = first ? 0.0 : A.psu[q][c];
             v[0] = fmax(v[0], fabs(nw - old));
@@ -511,7 +541,8 @@ __global__ void k_adj_next(Grid g, Fields F, Adj A, int first) {
             v[1] = fmax(v[1], fabs(nw));
             A.psp[c] = nw;
         }
-        for (int d = 0; d < g.dims; ++d) {
+        #pragma unroll
+        for (int d = 0; d < 3 && d < g.dims; ++d) {
             long long fl = face_lo(g, d, i, j, k);
             for (int e = 0; e < 2; ++e) {
                 if (e == 1 && has_nb(g, d, 1, i, j, k)) break;
@@ -653,7 +684,8 @@ __global__ void k_adj_dlambda(Grid g, Fields F, BcList bl, const double* __restr
         unc2[d] = (r2 >= 0.0 && r2 <= 1.0) ? 2.0 * h / g.D[d] : 0.0;
     }
     double dUdy = 0.0, dUdn[3] = {0.0, 0.0, 0.0};
-    for (int qq = 0; qq < g.dims; ++qq) {
+    #pragma unroll
+    for (int qq = 0; qq < 3 && qq < g.dims; ++qq) {
         double fb = A.fixb[qq][c];
         if (fb == 0.0) continue;
         double v1, v2, dv1[3], dv2[3];

@@ -48,7 +48,8 @@ __device__ void mom_row_t(const Grid& g, T* const* phi, const T* nut, long long 
     const T nu = (T)g.nu;
     T nuP = nu + nut[c];
     for (int q = 0; q < 3; ++q) { R.aP[q] = T(0); R.bnd[q] = T(0); }
-    for (int d = 0; d < g.dims; ++d) {
+    #pragma unroll
+    for (int d = 0; d < 3 && d < g.dims; ++d) {
         long long fl = face_lo(g, d, i, j, k);
         long long fs = face_stride(g, d);
         for (int side = 0; side < 2; ++side) {
@@ -63,12 +64,14 @@ __device__ void mom_row_t(const Grid& g, T* const* phi, const T* nut, long long 
                 R.nb[s] = nc;
                 R.has[s] = true;
                 T add = fmax(-Fout, T(0)) + Dif;
-                for (int q = 0; q < g.dims; ++q) R.aP[q] += add;
+                #pragma unroll
+                for (int q = 0; q < 3 && q < g.dims; ++q) R.aP[q] += add;
             } else {
                 R.a[s] = T(0);
                 R.nb[s] = c;
                 R.has[s] = false;
-                for (int q = 0; q < g.dims; ++q) {
+                #pragma unroll
+                for (int q = 0; q < 3 && q < g.dims; ++q) {
                     double val;
                     if (vel_fixed(g, f, s, q, val)) {
                         T coef = nuP * (T)g.SoHD[d] + fmax(-Fout, T(0));
@@ -130,7 +133,8 @@ __global__ void k_face_flux(Grid g, const uint16_t* __restrict__ flags, const do
     uint16_t f = flags[c];
     const double* v[3] = {vx, vy, vz};
     double* out[3] = {fx, fy, fz};
-    for (int d = 0; d < g.dims; ++d) {
+    #pragma unroll
+    for (int d = 0; d < 3 && d < g.dims; ++d) {
         long long fl = face_lo(g, d, i, j, k);
         if (interior(g, d, 0, i, j, k))
             out[d][fl] = 0.5 * (v[d][c - g.stride[d]] + v[d][c]) * g.S[d];
@@ -150,7 +154,8 @@ __global__ void k_means(Grid g, Params P, Fields F) {
     if (c < g.N) {
         uint16_t f = F.flags[c];
         int tag = tag_of(f);
-        for (int q = 0; q < g.dims; ++q) {
+        #pragma unroll
+        for (int q = 0; q < 3 && q < g.dims; ++q) {
             double x;
             if (!vel_row_fixed(g, F, c, q, x)) x = F.u[q][c];
             v[q] = x;
@@ -171,10 +176,12 @@ __global__ void k_grad_u(Grid g, Fields F) {
     int i, j, k;
     cell_ijk(g, c, i, j, k);
     uint16_t f = F.flags[c];
-    for (int b = 0; b < g.dims; ++b) {
+    #pragma unroll
+    for (int b = 0; b < 3 && b < g.dims; ++b) {
         const double* u = F.u[b];
         double uP = u[c];
-        for (int a = 0; a < g.dims; ++a) {
+        #pragma unroll
+        for (int a = 0; a < 3 && a < g.dims; ++a) {
             double lo, hi, val;
             if (interior(g, a, 0, i, j, k)) lo = 0.5 * (u[c - g.stride[a]] + uP);
             else lo = vel_fixed(g, f, 2 * a, b, val) ? val : uP;
@@ -197,10 +204,12 @@ __global__ void k_mom_asm(Grid g, Params P, Fields F) {
         mom_row(g, F, c, i, j, k, f, R);
         double nuP = g.nu + F.nut[c];
         bool fixed_row = (tag_of(f) == TAG_IC) || (f & F_AU);
-        for (int q = 0; q < g.dims; ++q) {
+        #pragma unroll
+        for (int q = 0; q < 3 && q < g.dims; ++q) {
             // explicit div(nu_eff (grad u)^T), component q: face flux nu_f (d u_a/d x_q)_f S_a
             double T = 0.0;
-            for (int a = 0; a < g.dims; ++a) {
+            #pragma unroll
+            for (int a = 0; a < 3 && a < g.dims; ++a) {
                 const double* Gq = F.G + (long long)(3 * q + a) * g.N;
                 double GP = Gq[c];
                 double flo, fhi;
@@ -231,7 +240,8 @@ __global__ void k_mom_asm(Grid g, Params P, Fields F) {
             if (!fixed_row) {
                 double xP = uold;
                 double Ax = R.aP[q] * xP, A1 = R.aP[q];
-                for (int s = 0; s < 2 * g.dims; ++s) {
+                #pragma unroll
+                for (int s = 0; s < 6 && s < 2 * g.dims; ++s) {
                     if (!R.has[s]) continue;
                     double xN;
                     long long nc = R.nb[s];
@@ -265,18 +275,22 @@ __global__ void k_mom_smooth(Grid g, Params P, Fields F, int colour) {
     if (((i + j + k) & 1) != colour) return;
     uint16_t f = F.flags[c];
     if (tag_of(f) == TAG_IC) {
-        for (int q = 0; q < g.dims; ++q) F.us[q][c] = g.u_s[q];
+        #pragma unroll
+        for (int q = 0; q < 3 && q < g.dims; ++q) F.us[q][c] = g.u_s[q];
         return;
     }
     if (f & F_AU) {
-        for (int q = 0; q < g.dims; ++q) F.us[q][c] = F.uib[q][c];
+        #pragma unroll
+        for (int q = 0; q < 3 && q < g.dims; ++q) F.us[q][c] = F.uib[q][c];
         return;
     }
     MomRow R;
     mom_row(g, F, c, i, j, k, f, R);
-    for (int q = 0; q < g.dims; ++q) {
+    #pragma unroll
+    for (int q = 0; q < 3 && q < g.dims; ++q) {
         double acc = F.bm[q][c];
-        for (int s = 0; s < 2 * g.dims; ++s)
+        #pragma unroll
+        for (int s = 0; s < 6 && s < 2 * g.dims; ++s)
             if (R.has[s]) acc -= R.a[s] * F.us[q][R.nb[s]];
         F.us[q][c] = acc * P.urf_u / R.aP[q];
     }
@@ -293,16 +307,19 @@ __global__ void k_mom_smooth32(Grid g, Params P, Fields F, int colour, int zero_
     if (((i + j + k) & 1) != colour) return;
     uint16_t f = F.flags[c];
     if (tag_of(f) == TAG_IC || (f & F_AU)) {
-        for (int q = 0; q < g.dims; ++q) F.d32[q][c] = 0.0f;
+        #pragma unroll
+        for (int q = 0; q < 3 && q < g.dims; ++q) F.d32[q][c] = 0.0f;
         return;
     }
     MomRowT<float> R;
     mom_row_t<float>(g, F.phi32, F.nut32, c, i, j, k, f, R);
     const float urf = (float)P.urf_u;
-    for (int q = 0; q < g.dims; ++q) {
+    #pragma unroll
+    for (int q = 0; q < 3 && q < g.dims; ++q) {
         float acc = F.r32[q][c];
         if (!zero_init)
-            for (int s = 0; s < 2 * g.dims; ++s)
+            #pragma unroll
+            for (int s = 0; s < 6 && s < 2 * g.dims; ++s)
                 if (R.has[s]) acc -= R.a[s] * F.d32[q][R.nb[s]];
         F.d32[q][c] = acc * urf / R.aP[q];
     }
@@ -319,13 +336,16 @@ __global__ void k_hbya(Grid g, Params P, Fields F) {
     mom_row(g, F, c, i, j, k, f, R);
     double aavg = 0.0;
     double aPr[3];
-    for (int q = 0; q < g.dims; ++q) { aPr[q] = R.aP[q] * P.iurf_u; aavg += aPr[q]; }
+    #pragma unroll
+    for (int q = 0; q < 3 && q < g.dims; ++q) { aPr[q] = R.aP[q] * P.iurf_u; aavg += aPr[q]; }
     aavg = aavg * (g.dims == 2 ? 0.5 : (1.0 / 3.0));
     double ia = 1.0 / aavg;
-    for (int q = 0; q < g.dims; ++q) {
+    #pragma unroll
+    for (int q = 0; q < 3 && q < g.dims; ++q) {
         double br = F.bm[q][c] + grad_p(g, F.p, c, q, i, j, k) * g.V;
         double off = 0.0;
-        for (int s = 0; s < 2 * g.dims; ++s)
+        #pragma unroll
+        for (int s = 0; s < 6 && s < 2 * g.dims; ++s)
             if (R.has[s]) off += R.a[s] * ustar(F, q, R.nb[s]);
         double H = br - off - (aPr[q] - aavg) * ustar(F, q, c);
         F.HbyA[q][c] = H * ia;
@@ -340,7 +360,8 @@ __global__ void k_phiH(Grid g, Fields F) {
     int i, j, k;
     cell_ijk(g, c, i, j, k);
     uint16_t f = F.flags[c];
-    for (int d = 0; d < g.dims; ++d) {
+    #pragma unroll
+    for (int d = 0; d < 3 && d < g.dims; ++d) {
         long long fl = face_lo(g, d, i, j, k);
         const double* H = F.HbyA[d];
         if (interior(g, d, 0, i, j, k))
@@ -364,7 +385,8 @@ __global__ void k_update(Grid g, Params P, Fields F, Level L0) {
         uint16_t f = F.flags[c];
         double pnP = F.pn[c];
         double div = 0.0;
-        for (int d = 0; d < g.dims; ++d) {
+        #pragma unroll
+        for (int d = 0; d < 3 && d < g.dims; ++d) {
             long long fl = face_lo(g, d, i, j, k);
             long long fs = face_stride(g, d);
             double flo, fhi;
@@ -397,7 +419,8 @@ __global__ void k_update(Grid g, Params P, Fields F, Level L0) {
         // relaxed pressure and the velocity update
         double a = P.urf_p;
         double prP = prelax(F.p, F.pn, c, a);
-        for (int d = 0; d < g.dims; ++d) {
+        #pragma unroll
+        for (int d = 0; d < 3 && d < g.dims; ++d) {
             double lo, hi;
             if (interior(g, d, 0, i, j, k)) lo = 0.5 * (prelax(F.p, F.pn, c - g.stride[d], a) + prP);
             else lo = p_fixed(g, 2 * d) ? g.p_out : prP;

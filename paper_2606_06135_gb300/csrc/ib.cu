@@ -51,7 +51,8 @@ __global__ void k_classify(Grid g, const double* __restrict__ lam, uint16_t* __r
     if (tag == TAG_IC) f |= F_AU;
     // closed boundary faces: wall/slip sides where lambda > 0, inlet sides
     // where lambda >= 0.5 (walls inside the solid phase, Sec. 3.1)
-    for (int s = 0; s < 2 * g.dims; ++s) {
+    #pragma unroll
+    for (int s = 0; s < 6 && s < 2 * g.dims; ++s) {
         int d = s >> 1;
         int pos = coord(d, i, j, k);
         bool on = (s & 1) ? (pos == g.n[d] - 1) : (pos == 0);
@@ -340,7 +341,8 @@ __global__ void k_imposed(Grid g, int model, int freeze, BcList bl, uint16_t* __
     flags[c] = f;
     const double* us[3] = {ux, uy, uz};
     double* ub[3] = {uibx, uiby, uibz};
-    for (int cpt = 0; cpt < g.dims; ++cpt) {
+    #pragma unroll
+    for (int cpt = 0; cpt < 3 && cpt < g.dims; ++cpt) {
         double v1 = interp_cell(g, us[cpt], b1, t1);
         double v2 = interp_cell(g, us[cpt], b2, t2);
         ub[cpt][c] = lamb ? (wS * g.u_s[cpt] + w1 * v1 + w2 * v2) : 0.0;

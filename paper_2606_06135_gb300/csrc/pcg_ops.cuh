@@ -31,12 +31,56 @@ __device__ inline void pl_ijk(const LevelT<T>& L, long long c, int& i, int& j, i
     j = (int)(r - kk * ny);
     k = (int)kk;
 }
+// Red-black passes visit the cells as x-pairs: pair p of row (j, k) holds
+// cells 2p and 2p + 1, one of each colour (the last pair of an odd row has
+// one cell).  A colour pass then runs half the iterations of a full pass with
+// no lane of a warp skipping its cell.
+template <typename T>
+__device__ inline long long pl_npairs(const LevelT<T>& L) {
+    return (long long)((L.nx + 1) >> 1) * L.ny * L.nz;
+}
+// first cell of pair p: i0 = 2 * (pair column), j, k, its linear index
+template <typename T>
+__device__ inline void pl_pair(const LevelT<T>& L, long long p, int& i0, int& j, int& k, long long& c0) {
+    unsigned int npx = (unsigned int)((L.nx + 1) >> 1);
+    unsigned int pp = (unsigned int)p;
+    unsigned int r = pp / npx;
+    unsigned int pi = pp - r * npx;
+    if (L.nz == 1) {
+        j = (int)r;
+        k = 0;
+    } else {
+        unsigned int ny = (unsigned int)L.ny;
+        unsigned int kk = r / ny;
+        j = (int)(r - kk * ny);
+        k = (int)kk;
+    }
+    i0 = 2 * (int)pi;
+    c0 = ((long long)k * L.ny + j) * L.nx + i0;
+}
+// the cell of colour `colour` in pair p; false if the pair has none (odd rows)
+template <typename T>
+__device__ inline bool pl_pair_cell(const LevelT<T>& L, long long p, int colour, int& i, int& j, int& k,
+                                    long long& c) {
+    int i0;
+    long long c0;
+    pl_pair(L, p, i0, j, k, c0);
+    int o = (i0 + j + k + colour) & 1;
+    i = i0 + o;
+    c = c0 + o;
+    return i < L.nx;
+}
+
+// the loops over directions run to a fixed bound of 3 with a dims guard, so
+// they unroll and the per-direction index arrays stay in registers
 template <typename T, typename X>
 __device__ inline T pl_offsum(const LevelT<T>& L, int dims, const X* x, long long c, int i, int j, int k) {
     T acc = T(0);
-    int idx[3] = {i, j, k};
-    int nn[3] = {L.nx, L.ny, L.nz};
-    for (int d = 0; d < dims; ++d) {
+    const int idx[3] = {i, j, k};
+    const int nn[3] = {L.nx, L.ny, L.nz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d >= dims) break;
         long long fl = pl_face(L, d, i, j, k);
         long long cs = d == 0 ? 1 : (d == 1 ? L.nx : (long long)L.nx * L.ny);
         if (idx[d] > 0) acc += L.cf[d][fl] * (T)x[c - cs];
@@ -47,11 +91,24 @@ __device__ inline T pl_offsum(const LevelT<T>& L, int dims, const X* x, long lon
 
 template <typename T>
 __device__ inline void pl_smooth(const LevelT<T>& L, int dims, int colour, long long t0, long long TT) {
-    for (long long c = t0; c < L.N; c += TT) {
+    const long long NP = pl_npairs(L);
+    for (long long p = t0; p < NP; p += TT) {
         int i, j, k;
-        pl_ijk(L, c, i, j, k);
-        if (((i + j + k) & 1) != colour) continue;
+        long long c;
+        if (!pl_pair_cell(L, p, colour, i, j, k, c)) continue;
         L.x[c] = (L.b[c] + pl_offsum(L, dims, L.x, c, i, j, k)) * L.idg[c];
+    }
+}
+
+// zero-start red half sweep: x = b / diag on red cells
+template <typename T>
+__device__ inline void pl_red_start(const LevelT<T>& L, long long t0, long long TT) {
+    const long long NP = pl_npairs(L);
+    for (long long p = t0; p < NP; p += TT) {
+        int i, j, k;
+        long long c;
+        if (!pl_pair_cell(L, p, 0, i, j, k, c)) continue;
+        L.x[c] = L.b[c] * L.idg[c];
     }
 }
 
@@ -64,14 +121,19 @@ __device__ inline void pl_restrict(const LevelT<T>& F, const LevelT<T>& Cc, int 
         int I, J, K;
         pl_ijk(Cc, C, I, J, K);
         T sum = T(0);
-        for (int oz = 0; oz < (dims == 3 ? 2 : 1); ++oz)
+#pragma unroll
+        for (int oz = 0; oz < 2; ++oz) {
+            if (oz == 1 && dims != 3) break;
+#pragma unroll
             for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
                 for (int ox = 0; ox < 2; ++ox) {
                     int i = 2 * I + ox, j = 2 * J + oy, k = 2 * K + oz;
                     if (i >= F.nx || j >= F.ny || k >= F.nz) continue;
                     long long c = ((long long)k * F.ny + j) * F.nx + i;
                     sum += F.b[c] - (F.diag[c] * F.x[c] - pl_offsum(F, dims, F.x, c, i, j, k));
                 }
+        }
         Cc.b[C] = sum;
         if (fuse_red && ((I + J + K) & 1) == 0) Cc.x[C] = sum * Cc.idg[C];
     }
@@ -81,16 +143,20 @@ __device__ inline void pl_restrict(const LevelT<T>& F, const LevelT<T>& Cc, int 
 // the following red half sweep without being read)
 template <typename T>
 __device__ inline void pl_prolong_black(const LevelT<T>& L, const LevelT<T>& Cc, int dims, long long t0, long long TT) {
-    for (long long c = t0; c < L.N; c += TT) {
+    const long long NP = pl_npairs(L);
+    for (long long p = t0; p < NP; p += TT) {
         int i, j, k;
-        pl_ijk(L, c, i, j, k);
-        if (((i + j + k) & 1) != 1) continue;
-        int idx[3] = {i, j, k};
-        int nn[3] = {L.nx, L.ny, L.nz};
+        long long c;
+        if (!pl_pair_cell(L, p, 1, i, j, k, c)) continue;
+        const int idx[3] = {i, j, k};
+        const int nn[3] = {L.nx, L.ny, L.nz};
         T acc = L.b[c];
-        for (int d = 0; d < dims; ++d) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (d >= dims) break;
             long long fl = pl_face(L, d, i, j, k);
             long long cs = d == 0 ? 1 : (d == 1 ? L.nx : (long long)L.nx * L.ny);
+#pragma unroll
             for (int side = 0; side < 2; ++side) {
                 if (side == 0 && idx[d] == 0) continue;
                 if (side == 1 && idx[d] == nn[d] - 1) continue;
@@ -111,11 +177,7 @@ __device__ void pl_tail(const MgLevelsT<T>& M, int dims, int l0, int sweeps) {
     const long long t0 = threadIdx.x, TT = blockDim.x;
     for (int l = l0; l < M.nl - 1; ++l) {
         const LevelT<T>& L = M.lv[l];
-        for (long long c = t0; c < L.N; c += TT) {
-            int i, j, k;
-            pl_ijk(L, c, i, j, k);
-            if (((i + j + k) & 1) == 0) L.x[c] = L.b[c] * L.idg[c];
-        }
+        pl_red_start(L, t0, TT);
         __syncthreads();
         pl_smooth(L, dims, 1, t0, TT);
         __syncthreads();
@@ -125,11 +187,7 @@ __device__ void pl_tail(const MgLevelsT<T>& M, int dims, int l0, int sweeps) {
     const LevelT<T>& Lc = M.lv[M.nl - 1];
     for (int s = 0; s < sweeps; ++s) {
         if (s == 0) {
-            for (long long c = t0; c < Lc.N; c += TT) {
-                int i, j, k;
-                pl_ijk(Lc, c, i, j, k);
-                if (((i + j + k) & 1) == 0) Lc.x[c] = Lc.b[c] * Lc.idg[c];
-            }
+            pl_red_start(Lc, t0, TT);
         } else {
             pl_smooth(Lc, dims, 0, t0, TT);
         }
@@ -156,19 +214,24 @@ __device__ void pl_tail(const MgLevelsT<T>& M, int dims, int l0, int sweeps) {
 // (same rule as pressure.cu), diagonal and inverse diagonal
 template <typename T>
 __device__ inline void pl_coarsen(const LevelT<T>& F, const LevelT<T>& Cc, int dims, long long t0, long long TT) {
-    int nf[3] = {F.nx, F.ny, F.nz};
-    int nc[3] = {Cc.nx, Cc.ny, Cc.nz};
+    const int nf[3] = {F.nx, F.ny, F.nz};
+    const int nc[3] = {Cc.nx, Cc.ny, Cc.nz};
     for (long long C = t0; C < Cc.N; C += TT) {
         int I, J, K;
         pl_ijk(Cc, C, I, J, K);
-        int idx[3] = {I, J, K};
+        const int idx[3] = {I, J, K};
         T diag = T(0);
-        for (int d = 0; d < dims; ++d)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (d >= dims) break;
+#pragma unroll
             for (int side = 0; side < 2; ++side) {
                 int fpos = side == 0 ? 2 * idx[d] : (idx[d] == nc[d] - 1 ? nf[d] : 2 * idx[d] + 2);
-                int a1 = (d + 1) % 3, a2 = (d + 2) % 3;
+                const int a1 = (d + 1) % 3, a2 = (d + 2) % 3;
                 T sum = T(0);
+#pragma unroll
                 for (int o1 = 0; o1 < 2; ++o1)
+#pragma unroll
                     for (int o2 = 0; o2 < 2; ++o2) {
                         int fi[3];
                         fi[d] = fpos;
@@ -182,6 +245,7 @@ __device__ inline void pl_coarsen(const LevelT<T>& F, const LevelT<T>& Cc, int d
                 if (side == 0) Cc.cf[d][pl_face(Cc, d, I, J, K)] = v;
                 else if (idx[d] == nc[d] - 1) Cc.cf[d][pl_face(Cc, d, I, J, K) + pl_fstride(Cc, d)] = v;
             }
+        }
         Cc.diag[C] = diag;
         Cc.idg[C] = diag > T(0) ? T(1) / diag : T(0);
     }

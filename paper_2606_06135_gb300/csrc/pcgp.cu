@@ -144,8 +144,11 @@ __device__ void pl_load_tail(const PcgpArgs<MT>& A) {
         for (long long c = threadIdx.x; c < G.N; c += blockDim.x) { L.diag[c] = G.diag[c]; L.idg[c] = G.idg[c]; }
         long long nf[3] = {(long long)(G.nx + 1) * G.ny * G.nz, (long long)G.nx * (G.ny + 1) * G.nz,
                            (long long)G.nx * G.ny * (G.nz + 1)};
-        for (int d = 0; d < dims; ++d)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (d >= dims) break;
             for (long long f = threadIdx.x; f < nf[d]; f += blockDim.x) L.cf[d][f] = G.cf[d][f];
+        }
     }
     __syncthreads();
 }
@@ -200,11 +203,19 @@ __device__ void pl_vcycle_rest(const PcgpArgs<MT>& A, int qdot) {
     const LevelT<MT>& L0 = M.lv[0];
     const double* r = A.F.r;
     double rz = 0.0;
-    for (long long c = t0; c < L0.N; c += TT) {
-        int i, j, k;
-        pl_ijk(L0, c, i, j, k);
-        if (((i + j + k) & 1) == 0) L0.x[c] = (L0.b[c] + pl_offsum(L0, dims, L0.x, c, i, j, k)) * L0.idg[c];
-        rz += r[c] * (double)L0.x[c];
+    const long long NP = pl_npairs(L0);
+    for (long long p = t0; p < NP; p += TT) {
+        int i0, j, k;
+        long long c0;
+        pl_pair(L0, p, i0, j, k, c0);
+#pragma unroll
+        for (int o = 0; o < 2; ++o) {
+            if (i0 + o >= L0.nx) break;
+            long long c = c0 + o;
+            if (((i0 + o + j + k) & 1) == 0)
+                L0.x[c] = (L0.b[c] + pl_offsum(L0, dims, L0.x, c, i0 + o, j, k)) * L0.idg[c];
+            rz += r[c] * (double)L0.x[c];
+        }
     }
     block_partial(A, qdot, rz);
     grid_sync(A);
@@ -224,9 +235,11 @@ __device__ void pl_build_operator(const PcgpArgs<MT>& A) {
     for (long long c = t0; c < g.N; c += TT) {
         int i, j, k;
         cell_ijk(g, c, i, j, k);
-        int idx[3] = {i, j, k};
+        const int idx[3] = {i, j, k};
         double diag = 0.0;
-        for (int d = 0; d < g.dims; ++d) {
+        #pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (d >= g.dims) break;
             long long fl = pl_face(L, d, i, j, k);
             long long fs = pl_fstride(L, d);
             double clo, chi;
@@ -277,9 +290,11 @@ __global__ void __launch_bounds__(PT_THREADS) k_pressure_persistent(PcgpArgs<MT>
         int i, j, k;
         cell_ijk(g, c, i, j, k);
         uint16_t f = F.flags[c];
-        int idx[3] = {i, j, k};
+        const int idx[3] = {i, j, k};
         double div = 0.0, bout = 0.0, A1 = 0.0;
-        for (int d = 0; d < g.dims; ++d) {
+        #pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (d >= g.dims) break;
             long long fl = face_lo(g, d, i, j, k);
             long long fs = face_stride(g, d);
             div += F.phiH[d][fl + fs] - F.phiH[d][fl];
@@ -349,10 +364,12 @@ __global__ void __launch_bounds__(PT_THREADS) k_pressure_persistent(PcgpArgs<MT>
             for (long long c = t0; c < g.N; c += T) {
                 int i, j, k;
                 cell_ijk(g, c, i, j, k);
-                int idx[3] = {i, j, k};
+                const int idx[3] = {i, j, k};
                 double dP = (double)z[c] + beta * dold[c];
                 double acc = L0.diag[c] * dP;
-                for (int d = 0; d < g.dims; ++d) {
+                #pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    if (d >= g.dims) break;
                     long long fl = face_lo(g, d, i, j, k);
                     if (idx[d] > 0) {
                         long long nc = c - g.stride[d];

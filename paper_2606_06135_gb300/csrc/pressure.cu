@@ -51,9 +51,11 @@ __device__ inline void lv_ijk(const LevelT<T>& L, long long c, int& i, int& j, i
 // (A x)_P = diag x_P - sum over interior faces cf x_N
 __device__ inline double lv_offsum(const Level& L, int dims, const double* x, long long c, int i, int j, int k) {
     double acc = 0.0;
-    int idx[3] = {i, j, k};
-    int nn[3] = {L.nx, L.ny, L.nz};
-    for (int d = 0; d < dims; ++d) {
+    const int idx[3] = {i, j, k};
+    const int nn[3] = {L.nx, L.ny, L.nz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d >= dims) break;
         long long fl = lv_face(L, d, i, j, k);
         long long cs = lv_cstride(L, d);
         if (idx[d] > 0) acc += L.cf[d][fl] * x[c - cs];
@@ -68,9 +70,11 @@ __global__ void k_p_coef(Grid g, Level L, const double* __restrict__ rAU) {
     if (c >= g.N) return;
     int i, j, k;
     cell_ijk(g, c, i, j, k);
-    int idx[3] = {i, j, k};
+    const int idx[3] = {i, j, k};
     double diag = 0.0;
-    for (int d = 0; d < g.dims; ++d) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d >= g.dims) break;
         long long fl = lv_face(L, d, i, j, k);
         long long fs = lv_fstride(L, d);
         double clo, chi;
@@ -91,11 +95,13 @@ template <typename T>
 __device__ void coarsen_cell(const LevelT<T>& F, const LevelT<T>& Cc, int dims, long long C) {
     int I, J, K;
     lv_ijk(Cc, C, I, J, K);
-    int idx[3] = {I, J, K};
-    int nc[3] = {Cc.nx, Cc.ny, Cc.nz};
-    int nf[3] = {F.nx, F.ny, F.nz};
+    const int idx[3] = {I, J, K};
+    const int nc[3] = {Cc.nx, Cc.ny, Cc.nz};
+    const int nf[3] = {F.nx, F.ny, F.nz};
     T diag = T(0);
-    for (int d = 0; d < dims; ++d) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d >= dims) break;
         for (int side = 0; side < 2; ++side) {
             if (side == 1 && idx[d] != nc[d] - 1) continue;  // high faces: boundary only (owner writes low faces)
             int fpos = side == 0 ? 2 * idx[d] : nf[d];
@@ -118,7 +124,10 @@ __device__ void coarsen_cell(const LevelT<T>& F, const LevelT<T>& Cc, int dims, 
     // diagonal: all faces of the coarse cell (low faces of this cell and the
     // low faces of the +d neighbours are written by their owners, so compute
     // the sums directly from the fine level again)
-    for (int d = 0; d < dims; ++d)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d >= dims) break;
+#pragma unroll
         for (int side = 0; side < 2; ++side) {
             int fpos = side == 0 ? 2 * idx[d] : (idx[d] == nc[d] - 1 ? nf[d] : 2 * idx[d] + 2);
             int a1 = (d + 1) % 3, a2 = (d + 2) % 3;
@@ -134,6 +143,7 @@ __device__ void coarsen_cell(const LevelT<T>& F, const LevelT<T>& Cc, int dims, 
                 }
             diag += T(0.5) * sum;
         }
+    }
     Cc.diag[C] = diag;
     Cc.idg[C] = diag > T(0) ? T(1) / diag : T(0);
 }
@@ -163,10 +173,12 @@ __device__ inline void prolong_smooth_black(const Level& L, const Level& Cc, int
     int i, j, k;
     lv_ijk(L, c, i, j, k);
     if (((i + j + k) & 1) != 1) return;
-    int idx[3] = {i, j, k};
-    int nn[3] = {L.nx, L.ny, L.nz};
+    const int idx[3] = {i, j, k};
+    const int nn[3] = {L.nx, L.ny, L.nz};
     double acc = L.b[c];
-    for (int d = 0; d < dims; ++d) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d >= dims) break;
         long long fl = lv_face(L, d, i, j, k);
         long long cs = lv_cstride(L, d);
         for (int side = 0; side < 2; ++side) {
@@ -188,8 +200,12 @@ __device__ inline void restrict_cell(const Level& F, const Level& Cc, int dims, 
     int I, J, K;
     lv_ijk(Cc, C, I, J, K);
     double sum = 0.0;
-    for (int oz = 0; oz < (dims == 3 ? 2 : 1); ++oz)
+#pragma unroll
+    for (int oz = 0; oz < 2; ++oz) {
+        if (oz == 1 && dims != 3) break;
+#pragma unroll
         for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
             for (int ox = 0; ox < 2; ++ox) {
                 int i = 2 * I + ox, j = 2 * J + oy, k = 2 * K + oz;
                 if (i >= F.nx || j >= F.ny || k >= F.nz) continue;
@@ -197,6 +213,7 @@ __device__ inline void restrict_cell(const Level& F, const Level& Cc, int dims, 
                 double Ax = F.diag[c] * F.x[c] - lv_offsum(F, dims, F.x, c, i, j, k);
                 sum += F.b[c] - Ax;
             }
+    }
     Cc.b[C] = sum;
 }
 
@@ -316,9 +333,11 @@ __global__ void k_pcg_init(Grid g, Fields F, Level L0, int jacobi) {
         int i, j, k;
         cell_ijk(g, c, i, j, k);
         uint16_t f = F.flags[c];
-        int idx[3] = {i, j, k};
+        const int idx[3] = {i, j, k};
         double div = 0.0, bout = 0.0, A1 = 0.0;
-        for (int d = 0; d < g.dims; ++d) {
+    #pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (d >= g.dims) break;
             long long fl = face_lo(g, d, i, j, k);
             long long fs = face_stride(g, d);
             div += F.phiH[d][fl + fs] - F.phiH[d][fl];
@@ -378,10 +397,12 @@ __global__ void k_pcg_A(Grid g, Fields F, Level L0) {
     if (c < g.N) {
         int i, j, k;
         cell_ijk(g, c, i, j, k);
-        int idx[3] = {i, j, k};
+        const int idx[3] = {i, j, k};
         double dP = F.z[c] + beta * dold[c];
         double acc = L0.diag[c] * dP;
-        for (int d = 0; d < g.dims; ++d) {
+    #pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (d >= g.dims) break;
             long long fl = face_lo(g, d, i, j, k);
             if (idx[d] > 0) {
                 long long nc = c - g.stride[d];
@@ -463,8 +484,10 @@ __global__ void k_p_coef32(Grid g, Level L, Level32 P) {
     if (c >= g.N) return;
     int i, j, k;
     cell_ijk(g, c, i, j, k);
-    int idx[3] = {i, j, k};
-    for (int d = 0; d < g.dims; ++d) {
+    const int idx[3] = {i, j, k};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d >= g.dims) break;
         long long fl = lv_face(L, d, i, j, k);
         P.cf[d][fl] = (float)L.cf[d][fl];
         if (idx[d] == g.n[d] - 1) {

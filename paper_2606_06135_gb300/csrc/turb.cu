@@ -43,8 +43,10 @@ __global__ void k_turb_prep(Grid g, Params P, Fields F) {
     cell_ijk(g, c, i, j, k);
     uint16_t f = F.flags[c];
     double S2 = 0.0;
-    for (int a = 0; a < g.dims; ++a)
-        for (int b = 0; b < g.dims; ++b) {
+    #pragma unroll
+    for (int a = 0; a < 3 && a < g.dims; ++a)
+        #pragma unroll
+        for (int b = 0; b < 3 && b < g.dims; ++b) {
             double s = 0.5 * (F.G[(long long)(3 * a + b) * g.N + c] + F.G[(long long)(3 * b + a) * g.N + c]);
             S2 += s * s;
         }
@@ -64,7 +66,8 @@ __global__ void k_turb_prep(Grid g, Params P, Fields F) {
         if (F.mixed) { F.gam32[c] = (float)F.gam[c]; F.gamk32[c] = (float)F.gamk[c]; }
     } else {
         double gk = 0.0;
-        for (int d = 0; d < g.dims; ++d)
+        #pragma unroll
+        for (int d = 0; d < 3 && d < g.dims; ++d)
             gk += grad_s(g, F.k, f, P.k_in, c, d, i, j, k) * grad_s(g, F.w, f, P.w_in, c, d, i, j, k);
         double y = fmax(F.ywall[c], 1e-3 * g.h);
         double kk = fmax(kold, K_MIN), ww = wold;
@@ -94,9 +97,11 @@ __global__ void k_bc_prod(Grid g, BcList bl, Fields F) {
     if (bl.lamb[q]) return;
     long long c = bl.cell[q];
     double dudn2 = 0.0;
-    for (int b = 0; b < g.dims; ++b) {
+    #pragma unroll
+    for (int b = 0; b < 3 && b < g.dims; ++b) {
         double comp = 0.0;
-        for (int a = 0; a < g.dims; ++a) comp += bl.n[3 * q + a] * F.G[(long long)(3 * a + b) * g.N + c];
+        #pragma unroll
+        for (int a = 0; a < 3 && a < g.dims; ++a) comp += bl.n[3 * q + a] * F.G[(long long)(3 * a + b) * g.N + c];
         dudn2 += comp * comp;
     }
     // y+ > y+_lam in the log branch; the max only matters for cells kept
@@ -137,7 +142,8 @@ __device__ void scal_row_t(const Grid& g, T* const* phi, const T* gam, double xi
     T gP = gam[c];
     R.aP = T(0);
     R.bnd = T(0);
-    for (int d = 0; d < g.dims; ++d) {
+    #pragma unroll
+    for (int d = 0; d < 3 && d < g.dims; ++d) {
         long long fl = face_lo(g, d, i, j, k);
         long long fs = face_stride(g, d);
         for (int side = 0; side < 2; ++side) {
@@ -196,7 +202,8 @@ __global__ void k_scal_asm(Grid g, Params P, Fields F, int eq) {
             if (F.mixed) F.r32[0][c] = 0.0f;
         } else {
             double Ax = aP * xold, A1 = aP;
-            for (int s = 0; s < 2 * g.dims; ++s) {
+            #pragma unroll
+            for (int s = 0; s < 6 && s < 2 * g.dims; ++s) {
                 if (!R.has[s]) continue;
                 double xN;
                 if (!scal_row_fixed(g, F, eq, R.nb[s], xN)) xN = x[R.nb[s]];
@@ -232,7 +239,8 @@ __global__ void k_scal_smooth(Grid g, Params P, Fields F, int eq, int colour) {
     ScalRow R;
     scal_row(g, F, gam, xin, c, i, j, k, f, R);
     double acc = F.bt[c];
-    for (int s = 0; s < 2 * g.dims; ++s)
+    #pragma unroll
+    for (int s = 0; s < 6 && s < 2 * g.dims; ++s)
         if (R.has[s]) acc -= R.a[s] * x[R.nb[s]];
     x[c] = acc / F.diag[c];
 }
@@ -257,7 +265,8 @@ __global__ void k_scal_smooth32(Grid g, Params P, Fields F, int eq, int colour, 
     scal_row_t<float>(g, F.phi32, gam, xin, c, i, j, k, f, R);
     float acc = F.r32[0][c];
     if (!zero_init)
-        for (int s = 0; s < 2 * g.dims; ++s)
+        #pragma unroll
+        for (int s = 0; s < 6 && s < 2 * g.dims; ++s)
             if (R.has[s]) acc -= R.a[s] * F.d32[0][R.nb[s]];
     F.d32[0][c] = acc / F.diag32[c];
 }
