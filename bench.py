@@ -42,6 +42,8 @@ WORKLOAD = "bfs_1024x256_sst"
 NX, NY = 1024, 256
 TOL = 1e-6
 FREEZE = 300           # one-way y+ switch from sweep 300 (limit cycles otherwise)
+P_RELTOL = 0.2         # per-sweep pressure tolerance on this workload (time to 1e-6:
+                       # 0.1 -> 19.7 s, 0.2 -> 17.2 s mixed; 0.3 diverged); both legs use it
 MAX_SOLVE_SWEEPS = 20000
 
 # Algorithmic bytes per cell for one launch group of each kernel class
@@ -56,7 +58,7 @@ def PCG_ITERS_FACTOR(piters):
 # workload (dram__bytes_read.sum + dram__bytes_write.sum; mixed: the FP32
 # V-cycle variant).  At 262k cells the pressure hierarchy stays in L2, so
 # this is far below the algorithmic count.
-TRAFFIC = {("pcg", "mixed"): 10.798592e6 + 3.507456e6, ("pcg", "fp64"): 12.204544e6 + 2.468352e6}
+TRAFFIC = {}
 
 BYTES_PER_CELL = {
     # u, v, p, nut, phi_x, phi_y, 4 gradient comps read; bm x2, u* x2 written
@@ -350,7 +352,7 @@ def main():
 
     def timed_sweeps(precision):
         """W warm-up + K timed sweeps; L2 flushed between timed sweeps."""
-        opts = dict(freeze_switch=FREEZE, precision=1 if precision == "mixed" else 0)
+        opts = dict(freeze_switch=FREEZE, p_reltol=P_RELTOL, precision=1 if precision == "mixed" else 0)
         s = hfdib.Solver(case, device=str(dev), stream=stream, **opts)
         for _ in range(args.warmup):
             s.sweep(1, read=False)
@@ -414,7 +416,7 @@ def main():
                       "Re_h": 36000, "precision": "mixed (FP32 inner sweeps + FP32 multigrid, FP64 defects)",
                       "l2": "flushed (512 MB write) between timed steps",
                       "parallelism": "replicas" if world > 1 else "single",
-                      "freeze_switch": FREEZE, "pcg_iters_mean": head["piters"]},
+                      "freeze_switch": FREEZE, "p_reltol": P_RELTOL, "pcg_iters_mean": head["piters"]},
            "gpu_launches": head["launches"], "clocks": head["clocks"], "roofline": head["roofline"],
            "fp64": {"value": res["fp64"]["value"], "ms_per_step": res["fp64"]["ms"],
                     "roofline": res["fp64"]["roofline"], "clocks": res["fp64"]["clocks"],
@@ -424,7 +426,7 @@ def main():
     # converged solves (both precisions) and the end-to-end leg (mixed, public
     # API from host arrays)
     def solve_leg(precision, e2e):
-        o = dict(freeze_switch=FREEZE, precision=1 if precision == "mixed" else 0)
+        o = dict(freeze_switch=FREEZE, p_reltol=P_RELTOL, precision=1 if precision == "mixed" else 0)
         lam_h = torch.from_numpy(np.ascontiguousarray(case["lam"])).pin_memory()
         yw_h = torch.from_numpy(np.ascontiguousarray(case["ywall"])).pin_memory()
         barrier()

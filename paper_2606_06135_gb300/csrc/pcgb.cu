@@ -372,7 +372,8 @@ __global__ void __launch_bounds__(1024) k_pressure_batched(PcgbArgs<MT> A) {
         bool all = true;
         for (int b = 0; b < B; ++b) all = all && S.done[b];
         if (all || *A.err) break;
-        // d = z + beta d_old; q = A d; d.q
+        // d = z + beta d_old; q = A d = A z + beta q_old (linearity: the
+        // neighbours' d need not be rebuilt); d.q
         for (int b = 0; b < B; ++b) {
             if (S.done[b]) continue;
             const PcgbDesign<MT>& D = A.D[b];
@@ -389,24 +390,20 @@ __global__ void __launch_bounds__(1024) k_pressure_batched(PcgbArgs<MT> A) {
                 int i, j, k;
                 cell_ijk(g, c, i, j, k);
                 const int idx[3] = {i, j, k};
-                double dP = (double)z[c] + beta * dold[c];
-                double acc = L0.diag[c] * dP;
+                double zc = (double)z[c];
+                double acc = L0.diag[c] * zc;
                 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
                     if (d >= g.dims) break;
                     long long fl = face_lo(g, d, i, j, k);
-                    if (idx[d] > 0) {
-                        long long nc = c - g.stride[d];
-                        acc -= L0.cf[d][fl] * ((double)z[nc] + beta * dold[nc]);
-                    }
-                    if (idx[d] < g.n[d] - 1) {
-                        long long nc = c + g.stride[d];
-                        acc -= L0.cf[d][fl + face_stride(g, d)] * ((double)z[nc] + beta * dold[nc]);
-                    }
+                    if (idx[d] > 0) acc -= L0.cf[d][fl] * (double)z[c - g.stride[d]];
+                    if (idx[d] < g.n[d] - 1) acc -= L0.cf[d][fl + face_stride(g, d)] * (double)z[c + g.stride[d]];
                 }
+                double dP = zc + beta * dold[c];
+                double qv = it == 0 ? acc : acc + beta * F.q[c];
                 dnew[c] = dP;
-                F.q[c] = acc;
-                s_dq += dP * acc;
+                F.q[c] = qv;
+                s_dq += dP * qv;
             }
             pb_partial(D.part, QB_DQ, s_dq);
         }
@@ -460,7 +457,8 @@ __global__ void __launch_bounds__(1024) k_pressure_batched(PcgbArgs<MT> A) {
             }
         }
         __syncthreads();
-        pb_sync(A.bar, A.err);   // partial slots are rewritten next iteration
+        // no grid barrier here: every partial slot read above is written again
+        // only after the next iteration's product and update barriers
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         for (int b = 0; b < B; ++b) {

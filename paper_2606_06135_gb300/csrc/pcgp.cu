@@ -359,30 +359,27 @@ __global__ void __launch_bounds__(PT_THREADS) k_pressure_persistent(PcgpArgs<MT>
             double beta = it == 0 ? 0.0 : rz / rz_prev;
             const double* dold = F.d[it & 1];
             double* dnew = F.d[(it + 1) & 1];
-            // d = z + beta d_old; q = A d; d.q
+            // d = z + beta d_old; q = A d = A z + beta q_old (linearity: the
+            // neighbours' d need not be rebuilt); d.q
             double s_dq = 0.0;
             for (long long c = t0; c < g.N; c += T) {
                 int i, j, k;
                 cell_ijk(g, c, i, j, k);
                 const int idx[3] = {i, j, k};
-                double dP = (double)z[c] + beta * dold[c];
-                double acc = L0.diag[c] * dP;
+                double zc = (double)z[c];
+                double acc = L0.diag[c] * zc;
                 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
                     if (d >= g.dims) break;
                     long long fl = face_lo(g, d, i, j, k);
-                    if (idx[d] > 0) {
-                        long long nc = c - g.stride[d];
-                        acc -= L0.cf[d][fl] * ((double)z[nc] + beta * dold[nc]);
-                    }
-                    if (idx[d] < g.n[d] - 1) {
-                        long long nc = c + g.stride[d];
-                        acc -= L0.cf[d][fl + face_stride(g, d)] * ((double)z[nc] + beta * dold[nc]);
-                    }
+                    if (idx[d] > 0) acc -= L0.cf[d][fl] * (double)z[c - g.stride[d]];
+                    if (idx[d] < g.n[d] - 1) acc -= L0.cf[d][fl + face_stride(g, d)] * (double)z[c + g.stride[d]];
                 }
+                double dP = zc + beta * dold[c];
+                double qv = it == 0 ? acc : acc + beta * F.q[c];
                 dnew[c] = dP;
-                F.q[c] = acc;
-                s_dq += dP * acc;
+                F.q[c] = qv;
+                s_dq += dP * qv;
             }
             block_partial(A, Q_DQ, s_dq);
             grid_sync(A);
@@ -420,7 +417,8 @@ __global__ void __launch_bounds__(PT_THREADS) k_pressure_persistent(PcgpArgs<MT>
             }
             ++it;
             if (!(rr > tol2)) break;
-            grid_sync(A);   // partial slots are rewritten next iteration
+            // no barrier here: every partial slot read above is written again
+            // only after the next iteration's product and update barriers
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
