@@ -160,4 +160,20 @@ __device__ void grid_reduce(double (&v)[NV], double* partials, unsigned int* cou
 
 inline unsigned int nblocks(long long n) { return (unsigned int)((n + BLOCK - 1) / BLOCK); }
 
+// Grid of the per-cell kernels that end in a grid-wide FP64 reduction: at most
+// two blocks per SM, each thread looping over several cells, so the
+// block-level shuffle tree (five FP64 adds per reduced value and thread, on a
+// GPU with little FP64 throughput) is paid once per several cells.
+inline unsigned int rblocks(long long n) {
+    static int sms = 0;
+    if (sms <= 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 1;
+    }
+    long long cap = 2LL * sms, b = nblocks(n);
+    return (unsigned int)(b < cap ? b : cap);
+}
+
 }  // namespace hf

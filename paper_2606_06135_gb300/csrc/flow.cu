@@ -149,21 +149,21 @@ __global__ void k_face_flux(Grid g, const uint16_t* __restrict__ flags, const do
 // Sums of the fields the residual normalisation needs, with imposed rows
 // replaced by their imposed values.
 __global__ void k_means(Grid g, Params P, Fields F) {
-    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double v[6] = {0, 0, 0, 0, 0, 0};
-    if (c < g.N) {
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < g.N;
+         c += (long long)gridDim.x * blockDim.x) {
         uint16_t f = F.flags[c];
         int tag = tag_of(f);
         #pragma unroll
         for (int q = 0; q < 3 && q < g.dims; ++q) {
             double x;
             if (!vel_row_fixed(g, F, c, q, x)) x = F.u[q][c];
-            v[q] = x;
+            v[q] += x;
         }
-        v[3] = F.p[c];
+        v[3] += F.p[c];
         if (P.model != HFDIB_LAMINAR) {
-            v[4] = tag == TAG_IC ? 0.0 : ((f & F_AU) ? F.kib[c] : F.k[c]);
-            v[5] = tag == TAG_IC ? F.scal[SC_WMAX] : (tag == TAG_BC ? F.wib[c] : F.w[c]);
+            v[4] += tag == TAG_IC ? 0.0 : ((f & F_AU) ? F.kib[c] : F.k[c]);
+            v[5] += tag == TAG_IC ? F.scal[SC_WMAX] : (tag == TAG_BC ? F.wib[c] : F.w[c]);
         }
     }
     grid_reduce<6, false>(v, F.partials, F.counters + 1, F.scal + SC_SUM_U);
@@ -194,9 +194,9 @@ __global__ void k_grad_u(Grid g, Fields F) {
 
 // ---------------------------------------------------------------- a3 assembly
 __global__ void k_mom_asm(Grid g, Params P, Fields F) {
-    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double red[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    if (c < g.N) {
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < g.N;
+         c += (long long)gridDim.x * blockDim.x) {
         int i, j, k;
         cell_ijk(g, c, i, j, k);
         uint16_t f = F.flags[c];
@@ -250,9 +250,9 @@ __global__ void k_mom_asm(Grid g, Params P, Fields F) {
                     A1 += R.a[s];
                 }
                 double xbar = F.scal[SC_SUM_U + q] * g.iN;
-                red[3 * q + 0] = fabs(bfull - Ax);
-                red[3 * q + 1] = fabs(Ax - A1 * xbar);
-                red[3 * q + 2] = fabs(bfull - A1 * xbar);
+                red[3 * q + 0] += fabs(bfull - Ax);
+                red[3 * q + 1] += fabs(Ax - A1 * xbar);
+                red[3 * q + 2] += fabs(bfull - A1 * xbar);
                 // defect of the relaxed system at the initial guess: with
                 // x_P = u_old the relaxation terms cancel, leaving b - A x
                 if (F.mixed) F.r32[q][c] = (float)(bfull - Ax);
@@ -377,9 +377,9 @@ __global__ void k_phiH(Grid g, Fields F) {
 // phi = phiHbyA - rAU_f (p_N - p_P)/Delta S with the new (unrelaxed) pressure;
 // p <- p + urf_p (p_new - p); u = HbyA - rAU grad(p_relaxed); continuity error.
 __global__ void k_update(Grid g, Params P, Fields F, Level L0) {
-    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double red[1] = {0.0};
-    if (c < g.N) {
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < g.N;
+         c += (long long)gridDim.x * blockDim.x) {
         int i, j, k;
         cell_ijk(g, c, i, j, k);
         uint16_t f = F.flags[c];
@@ -415,7 +415,7 @@ __global__ void k_update(Grid g, Params P, Fields F, Level L0) {
             }
             div += fhi - flo;
         }
-        red[0] = (f & F_M) ? fabs(div) : 0.0;
+        red[0] += (f & F_M) ? fabs(div) : 0.0;
         // relaxed pressure and the velocity update
         double a = P.urf_p;
         double prP = prelax(F.p, F.pn, c, a);
@@ -470,13 +470,13 @@ void launch_init_flux(const Grid& g, const Fields& F, cudaStream_t s) {
                                                 F.phi[2]);
 }
 void launch_means(const Grid& g, const Params& P, const Fields& F, cudaStream_t s) {
-    k_means<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F);
+    k_means<<<rblocks(g.N), BLOCK, 0, s>>>(g, P, F);
 }
 void launch_grad_u(const Grid& g, const Fields& F, cudaStream_t s) {
     k_grad_u<<<nblocks(g.N), BLOCK, 0, s>>>(g, F);
 }
 void launch_mom_asm(const Grid& g, const Params& P, const Fields& F, cudaStream_t s) {
-    k_mom_asm<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F);
+    k_mom_asm<<<rblocks(g.N), BLOCK, 0, s>>>(g, P, F);
 }
 void launch_mom_smooth(const Grid& g, const Params& P, const Fields& F, int colour, cudaStream_t s) {
     k_mom_smooth<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F, colour);
@@ -491,7 +491,7 @@ void launch_phiH(const Grid& g, const Fields& F, cudaStream_t s) {
     k_phiH<<<nblocks(g.N), BLOCK, 0, s>>>(g, F);
 }
 void launch_update(const Grid& g, const Params& P, const Fields& F, const Level& L0, cudaStream_t s) {
-    k_update<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F, L0);
+    k_update<<<rblocks(g.N), BLOCK, 0, s>>>(g, P, F, L0);
 }
 void launch_sweep_end(const Params& P, const Fields& F, int dims, double* res_out, double* hist, int nhist,
                       cudaStream_t s) {

@@ -177,12 +177,12 @@ __device__ inline void scal_row(const Grid& g, const Fields& F, const double* ga
 }
 
 __global__ void k_scal_asm(Grid g, Params P, Fields F, int eq) {
-    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double red[3] = {0.0, 0.0, 0.0};
     double* x = eq == 0 ? F.w : F.k;
     const double* gam = eq == 0 ? F.gam : F.gamk;
     double xin = eq == 0 ? P.w_in : P.k_in;
-    if (c < g.N) {
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < g.N;
+         c += (long long)gridDim.x * blockDim.x) {
         int i, j, k;
         cell_ijk(g, c, i, j, k);
         uint16_t f = F.flags[c];
@@ -211,9 +211,9 @@ __global__ void k_scal_asm(Grid g, Params P, Fields F, int eq) {
                 A1 += R.a[s];
             }
             double xbar = F.scal[eq == 0 ? SC_SUM_W : SC_SUM_K] * g.iN;
-            red[0] = fabs(b - Ax);
-            red[1] = fabs(Ax - A1 * xbar);
-            red[2] = fabs(b - A1 * xbar);
+            red[0] += fabs(b - Ax);
+            red[1] += fabs(Ax - A1 * xbar);
+            red[2] += fabs(b - A1 * xbar);
             // defect of the relaxed system at x_old (relaxation terms cancel)
             if (F.mixed) F.r32[0][c] = (float)(b - Ax);
         }
@@ -325,7 +325,7 @@ void launch_bc_prod(const Grid& g, const BcList& bl, const Fields& F, cudaStream
     k_bc_prod<<<nblocks(bl.nbc), BLOCK, 0, s>>>(g, bl, F);
 }
 void launch_scal_asm(const Grid& g, const Params& P, const Fields& F, int eq, cudaStream_t s) {
-    k_scal_asm<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F, eq);
+    k_scal_asm<<<rblocks(g.N), BLOCK, 0, s>>>(g, P, F, eq);
 }
 void launch_scal_smooth(const Grid& g, const Params& P, const Fields& F, int eq, int colour,
                         cudaStream_t s) {
