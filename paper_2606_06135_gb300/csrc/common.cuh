@@ -75,6 +75,30 @@ __device__ inline void cell_ijk(const Grid& g, long long c, int& i, int& j, int&
     k = (int)kk;
 }
 
+// Red-black passes launch one thread per x-pair of cells (cells 2p and 2p+1
+// of a row, one of each colour; an odd row's last pair has one cell): the
+// thread takes the cell of `colour`, so no lane of a warp is idle.
+__host__ __device__ inline long long npairs(const Grid& g) { return (long long)((g.nx + 1) >> 1) * g.ny * g.nz; }
+__device__ inline bool pair_cell(const Grid& g, long long p, int colour, long long& c, int& i, int& j, int& k) {
+    unsigned int npx = (unsigned int)((g.nx + 1) >> 1);
+    unsigned int pp = (unsigned int)p;
+    unsigned int r = pp / npx;
+    unsigned int pi = pp - r * npx;
+    if (g.nz == 1) {
+        j = (int)r;
+        k = 0;
+    } else {
+        unsigned int ny = (unsigned int)g.ny;
+        unsigned int kk = r / ny;
+        j = (int)(r - kk * ny);
+        k = (int)kk;
+    }
+    int i0 = 2 * (int)pi;
+    i = i0 + ((i0 + j + k + colour) & 1);
+    c = ((long long)k * g.ny + j) * g.nx + i;
+    return i < g.nx;
+}
+
 // index of the low face of cell (i,j,k) in direction d; the high face is +fstride
 __device__ inline long long face_lo(const Grid& g, int d, int i, int j, int k) {
     if (d == 0) return ((long long)k * g.ny + j) * (g.nx + 1) + i;

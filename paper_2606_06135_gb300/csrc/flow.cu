@@ -268,11 +268,11 @@ __global__ void k_mom_asm(Grid g, Params P, Fields F) {
 // Red-black Gauss-Seidel on the relaxed momentum rows; rows with alpha_u = 1
 // hold u = u_ib (ic: u_s), which realises the correction of Eq. (corru).
 __global__ void k_mom_smooth(Grid g, Params P, Fields F, int colour) {
-    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.N) return;
+    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npairs(g)) return;
+    long long c;
     int i, j, k;
-    cell_ijk(g, c, i, j, k);
-    if (((i + j + k) & 1) != colour) return;
+    if (!pair_cell(g, p, colour, c, i, j, k)) return;
     uint16_t f = F.flags[c];
     if (tag_of(f) == TAG_IC) {
         #pragma unroll
@@ -300,11 +300,11 @@ __global__ void k_mom_smooth(Grid g, Params P, Fields F, int colour) {
 // (aP/urf) d_P + sum a_N d_N = r (FP64 defect rounded), d = 0 on imposed rows.
 // zero_init: the other colour is taken as 0 (first half sweep).
 __global__ void k_mom_smooth32(Grid g, Params P, Fields F, int colour, int zero_init) {
-    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.N) return;
+    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npairs(g)) return;
+    long long c;
     int i, j, k;
-    cell_ijk(g, c, i, j, k);
-    if (((i + j + k) & 1) != colour) return;
+    if (!pair_cell(g, p, colour, c, i, j, k)) return;
     uint16_t f = F.flags[c];
     if (tag_of(f) == TAG_IC || (f & F_AU)) {
         #pragma unroll
@@ -479,10 +479,10 @@ void launch_mom_asm(const Grid& g, const Params& P, const Fields& F, cudaStream_
     k_mom_asm<<<rblocks(g.N), BLOCK, 0, s>>>(g, P, F);
 }
 void launch_mom_smooth(const Grid& g, const Params& P, const Fields& F, int colour, cudaStream_t s) {
-    k_mom_smooth<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F, colour);
+    k_mom_smooth<<<nblocks(npairs(g)), BLOCK, 0, s>>>(g, P, F, colour);
 }
 void launch_mom_smooth32(const Grid& g, const Params& P, const Fields& F, int colour, int zero_init, cudaStream_t s) {
-    k_mom_smooth32<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F, colour, zero_init);
+    k_mom_smooth32<<<nblocks(npairs(g)), BLOCK, 0, s>>>(g, P, F, colour, zero_init);
 }
 void launch_hbya(const Grid& g, const Params& P, const Fields& F, cudaStream_t s) {
     k_hbya<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F);

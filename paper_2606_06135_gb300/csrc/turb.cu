@@ -222,11 +222,11 @@ __global__ void k_scal_asm(Grid g, Params P, Fields F, int eq) {
 }
 
 __global__ void k_scal_smooth(Grid g, Params P, Fields F, int eq, int colour) {
-    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.N) return;
+    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npairs(g)) return;
+    long long c;
     int i, j, k;
-    cell_ijk(g, c, i, j, k);
-    if (((i + j + k) & 1) != colour) return;
+    if (!pair_cell(g, p, colour, c, i, j, k)) return;
     double* x = eq == 0 ? F.w : F.k;
     double fv;
     if (scal_row_fixed(g, F, eq, c, fv)) {
@@ -248,11 +248,11 @@ __global__ void k_scal_smooth(Grid g, Params P, Fields F, int eq, int colour) {
 // FP32 red-black sweep on the correction (mixed path): diag d_P + sum a_N d_N
 // = r (FP64 defect rounded); d = 0 on imposed rows
 __global__ void k_scal_smooth32(Grid g, Params P, Fields F, int eq, int colour, int zero_init) {
-    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.N) return;
+    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npairs(g)) return;
+    long long c;
     int i, j, k;
-    cell_ijk(g, c, i, j, k);
-    if (((i + j + k) & 1) != colour) return;
+    if (!pair_cell(g, p, colour, c, i, j, k)) return;
     double fv;
     if (scal_row_fixed(g, F, eq, c, fv)) {
         F.d32[0][c] = 0.0f;
@@ -329,11 +329,11 @@ void launch_scal_asm(const Grid& g, const Params& P, const Fields& F, int eq, cu
 }
 void launch_scal_smooth(const Grid& g, const Params& P, const Fields& F, int eq, int colour,
                         cudaStream_t s) {
-    k_scal_smooth<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F, eq, colour);
+    k_scal_smooth<<<nblocks(npairs(g)), BLOCK, 0, s>>>(g, P, F, eq, colour);
 }
 void launch_scal_smooth32(const Grid& g, const Params& P, const Fields& F, int eq, int colour, int zero_init,
                           cudaStream_t s) {
-    k_scal_smooth32<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F, eq, colour, zero_init);
+    k_scal_smooth32<<<nblocks(npairs(g)), BLOCK, 0, s>>>(g, P, F, eq, colour, zero_init);
 }
 void launch_k_prep(const Grid& g, const Params& P, const Fields& F, cudaStream_t s) {
     k_k_prep<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F);
