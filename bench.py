@@ -58,7 +58,7 @@ def PCG_ITERS_FACTOR(piters):
 # workload (dram__bytes_read.sum + dram__bytes_write.sum; mixed: the FP32
 # V-cycle variant).  At 262k cells the pressure hierarchy stays in L2, so
 # this is far below the algorithmic count.
-TRAFFIC = {}
+TRAFFIC = {("pcg", "mixed"): 10.661632e6 + 0.983808e6, ("pcg", "fp64"): 12.071168e6 + 0.745728e6}
 
 BYTES_PER_CELL = {
     # u, v, p, nut, phi_x, phi_y, 4 gradient comps read; bm x2, u* x2 written
