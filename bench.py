@@ -60,6 +60,13 @@ def PCG_ITERS_FACTOR(piters):
 # this is far below the algorithmic count.
 TRAFFIC = {("pcg", "mixed"): 10.661632e6 + 0.983808e6, ("pcg", "fp64"): 12.071168e6 + 0.745728e6}
 
+# FP64 flops of one launch of the FP64 assembly kernels on this workload
+# (ncu: 2 x DFMA + DADD + DMUL thread instructions).  These kernels are bound
+# by FP64 arithmetic, so their roofline is the FP64 rate.  Only the profiling
+# classes that time exactly one kernel are listed.
+FP64_FLOPS = {"mom_asm": 4.7356e7, "turb_final": 3.1783e7, "scal_asm": 1.5748e7}
+FP64_PEAK_GFLOPS = 1250.0   # nominal GB300 FP64 rate (no measured FP64 peak is available)
+
 BYTES_PER_CELL = {
     # u, v, p, nut, phi_x, phi_y, 4 gradient comps read; bm x2, u* x2 written
     "mom_asm": 8 * (10 + 4) + 2,
@@ -402,9 +409,22 @@ def main():
                 if traffic else None,
                 "algorithmic_bytes_per_launch": bpc * N, "avg_launch_us": avg_us,
                 "class_share": {k: round(v[0] / total, 4) for k, v in prof.items()}}
+        # FP64-ALU roofline of the assembly classes (live event timing)
+        alu = {}
+        for cls, fl in FP64_FLOPS.items():
+            if cls in prof and prof[cls][1] > 0:
+                us = prof[cls][0] / prof[cls][1]
+                gf = fl / (us * 1e-6) / 1e9
+                alu[cls] = {"achieved": gf, "avg_launch_us": us, "flops_per_launch": fl}
+        top = max(alu, key=lambda c: prof[c][0]) if alu else None
+        roof_alu = None
+        if top:
+            roof_alu = {"bound": "alu", "kernel": top, "achieved": alu[top]["achieved"], "peak": FP64_PEAK_GFLOPS,
+                        "unit": "GFLOP/s (FP64)", "frac": alu[top]["achieved"] / FP64_PEAK_GFLOPS,
+                        "peak_source": "nominal", "per_class": alu}
         s.close()
         return dict(value=world * N * args.steps / t_dev, ms=1e3 * t_dev / args.steps, clocks=clk,
-                    launches=launches, piters=float(piters.mean()), roofline=roof)
+                    launches=launches, piters=float(piters.mean()), roofline=roof, roofline_alu=roof_alu)
 
     res = {p: timed_sweeps(p) for p in ("mixed", "fp64")}
     head = res["mixed"]
@@ -418,8 +438,10 @@ def main():
                       "parallelism": "replicas" if world > 1 else "single",
                       "freeze_switch": FREEZE, "p_reltol": P_RELTOL, "pcg_iters_mean": head["piters"]},
            "gpu_launches": head["launches"], "clocks": head["clocks"], "roofline": head["roofline"],
+           "roofline_alu": head["roofline_alu"],
            "fp64": {"value": res["fp64"]["value"], "ms_per_step": res["fp64"]["ms"],
-                    "roofline": res["fp64"]["roofline"], "clocks": res["fp64"]["clocks"],
+                    "roofline": res["fp64"]["roofline"], "roofline_alu": res["fp64"]["roofline_alu"],
+                    "clocks": res["fp64"]["clocks"],
                     "pcg_iters_mean": res["fp64"]["piters"]}}
 
 
