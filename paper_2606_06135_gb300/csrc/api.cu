@@ -1129,7 +1129,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
     }
     A(F.p, N); A(F.pn, N); A(F.pr, N); A(F.rAU, N);
     A(F.k, N); A(F.w, N); A(F.w2, N); A(F.nut, N); A(F.kib, N); A(F.wib, N);
-    A(F.G, 9 * N); A(F.Pk, N); A(F.S2, N); A(F.gam, N); A(F.gamk, N); A(F.sp, N); A(F.src, N);
+    A(F.G, 9 * N); A(F.mrow, 9 * N); A(F.Pk, N); A(F.S2, N); A(F.gam, N); A(F.gamk, N); A(F.sp, N); A(F.src, N);
     A(F.bt, N); A(F.diag, N); A(F.ywall, N); A(F.flags, N);
     A(F.prhs, N); A(F.pdiag, N); A(F.r, N); A(F.z, N); A(F.d[0], N); A(F.d[1], N); A(F.q, N);
     A(F.scal, SC_NSCAL); A(F.partials, 16 * (long long)nb + 64); A(F.counters, 64);

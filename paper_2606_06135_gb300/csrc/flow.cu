@@ -193,7 +193,7 @@ __global__ void k_grad_u(Grid g, Fields F) {
 }
 
 // ---------------------------------------------------------------- a3 assembly
-__global__ void k_mom_asm(Grid g, Params P, Fields F) {
+__global__ void __launch_bounds__(BLOCK, 2) k_mom_asm(Grid g, Params P, Fields F) {
     double red[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < g.N;
          c += (long long)gridDim.x * blockDim.x) {
@@ -202,6 +202,11 @@ __global__ void k_mom_asm(Grid g, Params P, Fields F) {
         uint16_t f = F.flags[c];
         MomRow R;
         mom_row(g, F, c, i, j, k, f, R);
+        // keep the row for HbyA (same phi and nu_t later in the sweep)
+        #pragma unroll
+        for (int q = 0; q < 3 && q < g.dims; ++q) F.mrow[(long long)q * g.N + c] = R.aP[q];
+        #pragma unroll
+        for (int s = 0; s < 6 && s < 2 * g.dims; ++s) F.mrow[(long long)(3 + s) * g.N + c] = R.a[s];
         double nuP = g.nu + F.nut[c];
         bool fixed_row = (tag_of(f) == TAG_IC) || (f & F_AU);
         #pragma unroll
@@ -331,13 +336,12 @@ __global__ void k_hbya(Grid g, Params P, Fields F) {
     if (c >= g.N) return;
     int i, j, k;
     cell_ijk(g, c, i, j, k);
-    uint16_t f = F.flags[c];
-    MomRow R;
-    mom_row(g, F, c, i, j, k, f, R);
+    const long long N = g.N;
+    // the row of this sweep, kept by the assembly (k_mom_asm)
     double aavg = 0.0;
     double aPr[3];
     #pragma unroll
-    for (int q = 0; q < 3 && q < g.dims; ++q) { aPr[q] = R.aP[q] * P.iurf_u; aavg += aPr[q]; }
+    for (int q = 0; q < 3 && q < g.dims; ++q) { aPr[q] = F.mrow[(long long)q * N + c] * P.iurf_u; aavg += aPr[q]; }
     aavg = aavg * (g.dims == 2 ? 0.5 : (1.0 / 3.0));
     double ia = 1.0 / aavg;
     #pragma unroll
@@ -345,8 +349,12 @@ __global__ void k_hbya(Grid g, Params P, Fields F) {
         double br = F.bm[q][c] + grad_p(g, F.p, c, q, i, j, k) * g.V;
         double off = 0.0;
         #pragma unroll
-        for (int s = 0; s < 6 && s < 2 * g.dims; ++s)
-            if (R.has[s]) off += R.a[s] * ustar(F, q, R.nb[s]);
+        for (int s = 0; s < 6 && s < 2 * g.dims; ++s) {
+            int d = s >> 1, side = s & 1;
+            if (!interior(g, d, side, i, j, k)) continue;
+            long long nb = side ? c + g.stride[d] : c - g.stride[d];
+            off += F.mrow[(long long)(3 + s) * N + c] * ustar(F, q, nb);
+        }
         double H = br - off - (aPr[q] - aavg) * ustar(F, q, c);
         F.HbyA[q][c] = H * ia;
     }

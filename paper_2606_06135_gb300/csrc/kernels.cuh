@@ -60,6 +60,8 @@ struct Fields {
     double* HbyA[3];
     double* rAU;
     double* bm[3];
+    double* mrow;      // [9][N] momentum rows of the sweep, written by the
+                       // assembly for HbyA: aP per component (3), a per side (6)
     double* k;
     double* w;         // eps (k-epsilon) or omega (SST)
     double* w2;        // the other one (omega for k-eps, eps for SST), diagnostic

@@ -71,17 +71,21 @@ __global__ void k_turb_prep(Grid g, Params P, Fields F) {
             gk += grad_s(g, F.k, f, P.k_in, c, d, i, j, k) * grad_s(g, F.w, f, P.w_in, c, d, i, j, k);
         double y = fmax(F.ywall[c], 1e-3 * g.h);
         double kk = fmax(kold, K_MIN), ww = wold;
-        double CDkw = 2.0 * SST_AW2 * gk / ww;
+        // reciprocals once: FP64 division is many FP64 operations on this GPU
+        double iw = 1.0 / ww, iy = 1.0 / y;
+        double CDkw = 2.0 * SST_AW2 * gk * iw;
         double CDp = fmax(CDkw, 1e-10);
         double sk = sqrt(kk);
-        double arg1 = fmin(fmax(sk / (SST_BSTAR * ww * y), 500.0 * g.nu / (y * y * ww)),
-                           4.0 * SST_AW2 * kk / (CDp * y * y));
+        double t_k = sk * iw * iy * (1.0 / SST_BSTAR);     // sqrt(k) / (beta* omega y)
+        double t_nu = 500.0 * g.nu * iy * iy * iw;          // 500 nu / (y^2 omega)
+        double arg1 = fmin(fmax(t_k, t_nu), 4.0 * SST_AW2 * kk * iy * iy / CDp);
         double F1 = tanh(arg1 * arg1 * arg1 * arg1);
-        double F2 = sst_F2(kk, ww, y, g.nu);
+        double arg2 = fmin(fmax(2.0 * t_k, t_nu), 100.0);   // F2 of the same k, omega, y
+        double F2 = tanh(arg2 * arg2);
         double gamma = F1 * SST_G1 + (1.0 - F1) * SST_G2;
         double beta = F1 * SST_B1 + (1.0 - F1) * SST_B2;
         double GbyNu = fmin(S2, (SST_C1 / SST_A1) * SST_BSTAR * wold * fmax(SST_A1 * wold, SST_BB1 * F2 * sqrt(S2)));
-        double cdc = (F1 - 1.0) * CDkw / wold;
+        double cdc = (F1 - 1.0) * CDkw * iw;
         F.gam[c] = g.nu + (F1 * SST_AW1 + (1.0 - F1) * SST_AW2) * nut;
         F.sp[c] = beta * wold * V + (cdc > 0.0 ? cdc : 0.0) * V;
         F.src[c] = gamma * GbyNu * V - (cdc > 0.0 ? 0.0 : cdc) * wold * V;
