@@ -30,9 +30,15 @@ lambda enters R only through u_ib: the normal n = -grad(lambda)/|grad(lambda)|
 (Eq. yorthoaux), y_perp (Eq. yortho with sigma = h atanh(1 - 2 lambda)) and
 through them the interpolation fractions and the quadratic weights.
 
-Objective (pressure drop): J = mean p over the cells on open inlet faces minus
-mean p over the cells on outlet faces.  The adjoint psi solves
-R_z^T psi = J_z^T and dJ/dlambda = -psi^T R_lambda.  R_z and R_lambda are
+Objectives.  Pressure drop: J = mean p over the cells on open inlet faces
+minus mean p over the cells on outlet faces.  Drag: J = minus the sum over
+the imposed rows of the x-momentum row residual aP ut + sum a_N ut_N - b0
++ V dp/dx, the forcing the immersed boundary applies to the fluid there (the
+divergence-form terms telescope to fluxes through the boundary of the imposed
+region, so this is the force of the fluid on the body).  The adjoint psi
+solves R_z^T psi = J_z^T and dJ/dlambda = J_lambda - psi^T R_lambda (J_lambda
+is zero for the pressure drop; for the drag it is the explicit dependence
+through u_ib).  R_z and R_lambda are
 exact sparse Jacobians from complex-step derivatives (imaginary step 1e-20),
 one evaluation of R per colour of a distance colouring of the grid.
 
@@ -126,7 +132,10 @@ class FrozenSteady:
     """The steady equations R(z; lambda) around a converged oracle state `o`
     (an hfdib_oracle.Oracle whose sweeps have converged)."""
 
-    def __init__(self, o):
+    def __init__(self, o, objective="pressure_drop"):
+        if objective not in ("pressure_drop", "drag"):
+            raise ValueError("objective: pressure_drop or drag")
+        self.kind = objective
         m = o.m
         if m.dims != 2:
             raise ValueError("the oracle adjoint covers 2D grids")
@@ -138,6 +147,10 @@ class FrozenSteady:
         self.geo = o.geo
         self.sel = o.lam_branch.copy() if o.model != "laminar" else np.ones(len(o.geo["cell"]), bool)
         self.nu_eff = o.nu + o.nut
+        # imposed rows: ic cells and the laminar-branch bc cells
+        fixed = o.ic.copy()
+        fixed.reshape(-1)[o.geo["cell"][self.sel]] = True
+        self.fixed = fixed
         shapes = [m.shape] * m.dims + [m.shape]
         for d in range(m.dims):
             shp = list(m.shape)
@@ -184,11 +197,11 @@ class FrozenSteady:
         return self.pack(o.u[:self.m.dims], o.p, o.phi[:self.m.dims])
 
     # ---------------------------------------------------------------- equations
-    def residual(self, z, lam=None):
+    def _momentum_pieces(self, z, lam):
+        """ut (u with the imposed values in imposed rows), the momentum rows
+        aP, aM, aPl, the explicit right-hand sides b0 and grad p."""
         m, o = self.m, self.o
         lam = self.lam0 if lam is None else lam
-        au = o.opts["urf_u"]
-        rlx = (1.0 - au) / au
         u, p, phi = self.unpack(z)
         geo = dict(self.geo)
         geo.update(bc_weights(m, lam, self.geo))
@@ -209,6 +222,14 @@ class FrozenSteady:
             aPc, aM, aPl, bc = O.assemble_transport(m, phi, self.nu_eff, o.bnd.velocity_spec(c))
             aP.append(aPc)
             b0.append(bc + o.transpose_source(G, self.nu_eff, c))
+        return u, p, phi, ut, aP, aM, aPl, b0, gradp
+
+    def residual(self, z, lam=None):
+        m, o = self.m, self.o
+        lam = self.lam0 if lam is None else lam
+        au = o.opts["urf_u"]
+        rlx = (1.0 - au) / au
+        u, p, phi, ut, aP, aM, aPl, b0, gradp = self._momentum_pieces(z, lam)
         aavg = sum(a / au for a in aP) / m.dims
         Rm, H = [], []
         for c in range(m.dims):
@@ -224,15 +245,41 @@ class FrozenSteady:
         Rf = [phi[d] - phin[d] for d in range(m.dims)]
         return self.pack(Rm, Rp, Rf)
 
-    def objective(self, z):
+    def drag_rows(self, z, lam=None):
+        """The x-momentum row residual aP ut + sum a_N ut_N - b0 + V dp/dx of
+        the imposed rows (ic and laminar-branch bc cells), zero elsewhere,
+        laid out like R.  In an imposed row this is the force the immersed
+        boundary applies to the fluid (the f_ib of Eq. hfdibrans_1)."""
+        m = self.m
+        lam = self.lam0 if lam is None else lam
+        u, p, phi, ut, aP, aM, aPl, b0, gradp = self._momentum_pieces(z, lam)
+        r = aP[0] * ut[0] + O.apply_offdiag(m, aM, aPl, ut[0]) - b0[0] + m.V * gradp[0]
+        r = np.where(self.fixed, r, 0.0)
+        zero = np.zeros(m.shape, dtype=r.dtype)
+        faces = [np.zeros(self.shapes[m.dims + 1 + d], dtype=r.dtype) for d in range(m.dims)]
+        return self.pack([r] + [zero] * (m.dims - 1), zero, faces)
+
+    def objective(self, z, lam=None):
+        if self.kind == "drag":
+            # the force of the fluid on the body: minus the forcing applied to the fluid
+            return float(-np.sum(self.drag_rows(z, lam).real))
         _, p, _ = self.unpack(z)
         return float(np.sum(self.jw * p.real))
 
-    def objective_grad(self):
+    def objective_grad(self, z=None):
+        """(J_z, J_lambda) as dense vectors."""
+        if self.kind == "drag":
+            z = self.state() if z is None else z
+            Fz = self._colour_jacobian(lambda x: self.drag_rows(x), z.astype(complex), self.shapes, self.offs)
+            zc = z.astype(complex)
+            shp = self.m.shape
+            Fl = self._colour_jacobian(lambda l: self.drag_rows(zc, l.reshape(shp)),
+                                       self.lam0.ravel().astype(complex), [shp], np.array([0, self.m.N]))
+            return -np.asarray(Fz.sum(axis=0)).ravel().real, -np.asarray(Fl.sum(axis=0)).ravel().real
         g = np.zeros(self.offs[-1])
         b = self.m.dims
         g[self.offs[b]:self.offs[b + 1]] = self.jw.ravel()
-        return g
+        return g, np.zeros(self.m.N)
 
     # ---------------------------------------------------------------- Jacobians
     def _colour_jacobian(self, f, x0, shapes, offs):
@@ -300,9 +347,10 @@ class FrozenSteady:
         z = self.state()
         Rz = self.jacobian_z(z)
         Rl = self.jacobian_lambda(z)
-        psi = spla.spsolve(Rz.T.tocsc(), self.objective_grad())
-        g = -(Rl.T @ psi)
-        return self.objective(z), g.real.reshape(self.m.shape), psi
+        Jz, Jl = self.objective_grad(z)
+        psi = spla.spsolve(Rz.T.tocsc(), Jz)
+        g = Jl - (Rl.T @ psi).real
+        return self.objective(z), g.reshape(self.m.shape), psi
 
 
 # ---------------------------------------------------------------- finite differences
@@ -341,10 +389,10 @@ def with_lambda(o, lam_new):
     return q
 
 
-def fd_gradient(o, cells, delta=1e-6, tol=1e-13):
+def fd_gradient(o, cells, delta=1e-6, tol=1e-13, objective="pressure_drop"):
     """Central differences of J over frozen-turbulence solves started from
     the converged state, for the flat cell indices `cells`."""
-    fs = FrozenSteady(o)
+    fs = FrozenSteady(o, objective)
     out = []
     for c in cells:
         vals = []
@@ -356,6 +404,10 @@ def fd_gradient(o, cells, delta=1e-6, tol=1e-13):
             if not np.array_equal(q.lam_branch, fs.o.lam_branch if o.model != "laminar" else q.lam_branch):
                 raise ValueError("perturbation flips a wall-function branch")
             frozen_solve(q, tol=tol)
-            vals.append(float(np.sum(fs.jw * q.p)))
+            if objective == "drag":
+                fq = FrozenSteady(q, objective)
+                vals.append(fq.objective(fq.state()))
+            else:
+                vals.append(float(np.sum(fs.jw * q.p)))
         out.append((vals[0] - vals[1]) / (2.0 * delta))
     return np.array(out)

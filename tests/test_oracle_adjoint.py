@@ -106,3 +106,25 @@ def test_laminar_gradient_matches_finite_differences():
     pick = cut[np.argsort(-np.abs(gf[cut]))[:3]]
     fd = A.fd_gradient(o, pick, delta=1e-6)
     np.testing.assert_allclose(gf[pick], fd, rtol=1e-5)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("which", ["grf", "box15"])
+def test_drag_gradient_matches_finite_differences(which, grf_state):
+    """Drag (the x force of the fluid on the body, minus the immersed-boundary
+    forcing of the imposed rows): J_lambda - psi^T R_lambda against central
+    differences of frozen-turbulence solves, and positive for flow in +x."""
+    if which == "grf":
+        o = grf_state
+    else:
+        o = O.Oracle(G.case_rotated_box(15.0, 16, model="laminar", Re=20.0))
+        o.solve(tol=1e-13, max_iter=4000)
+    fs = A.FrozenSteady(o, "drag")
+    J, g, _ = fs.gradient()
+    assert J > 0.0
+    gf = g.ravel()
+    lam = o.lam.ravel()
+    cut = np.flatnonzero((lam > 0.05) & (lam < 0.95))
+    pick = cut[np.argsort(-np.abs(gf[cut]))[:3]]
+    fd = A.fd_gradient(o, pick, delta=1e-6, objective="drag")
+    np.testing.assert_allclose(gf[pick], fd, rtol=1e-5)
