@@ -181,7 +181,7 @@ int hfdib_solve_steady(hfdib_handle h, double tol, int max_iter, int check_every
                        int* iters_out, double* final_res);
 
 /* Objectives of hfdib_adjoint_grad, and the largest GMRES restart length. */
-enum { HFDIB_OBJ_PRESSURE_DROP = 0 };
+enum { HFDIB_OBJ_PRESSURE_DROP = 0, HFDIB_OBJ_DRAG = 1 };
 enum { HFDIB_GMRES_MAX_RESTART = 200 };
 
 /* hfdib_adjoint_grad -- frozen-turbulence discrete adjoint of the converged
@@ -199,7 +199,14 @@ enum { HFDIB_GMRES_MAX_RESTART = 200 };
  * momentum passes, with exact pressure solves, run as one CUDA graph.
  * Then dJ/dlambda = psi^T dG/dlambda.
  *   objective  : HFDIB_OBJ_PRESSURE_DROP, J = mean p over the cells of the open
- *                inlet faces minus mean p over the cells of the outlet faces
+ *                inlet faces minus mean p over the cells of the outlet faces;
+ *                HFDIB_OBJ_DRAG, J = the x force of the fluid on the body:
+ *                minus the sum over the imposed rows (in-solid cells and
+ *                laminar-branch bc cells) of the x-momentum row residual
+ *                aP u~ + sum a_N u~_N - b0 + V dp/dx, the forcing of Eq.
+ *                hfdibrans_1 applied there (u~: u_s, u_ib or u).  The drag
+ *                also depends on lambda directly through u_ib, which the
+ *                gradient includes.
  *   gmres_restart : 0 (recommended): the reverse fixed point
  *                psi <- G_x^T psi + J_x^T; stop when max|psi_new - psi| <=
  *                tol max|psi| (checked every 10 iterations).  m > 0:

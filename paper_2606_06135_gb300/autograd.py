@@ -1,8 +1,8 @@
 """torch.autograd.Function around the steady solve and its adjoint.
 
 forward: build the HFDIB problem on the given lambda, converge it with
-hfdib_solve_steady and return the objective J (pressure drop) as a 0-d
-tensor.  backward: hfdib_adjoint_grad, the frozen-turbulence discrete
+hfdib_solve_steady and return the objective J (pressure drop or drag) as a
+0-d tensor.  backward: hfdib_adjoint_grad, the frozen-turbulence discrete
 adjoint of that converged state, gives dJ/dlambda; it is multiplied by the
 incoming gradient.  Both steps run in the library's CUDA kernels; this module
 only passes pointers.
@@ -24,7 +24,7 @@ class SteadyRANS(torch.autograd.Function):
     """J(lambda) = pressure drop of the converged steady state."""
 
     @staticmethod
-    def forward(ctx, lam, case, solve_tol, max_sweeps, adj_tol, adj_max_iter, opts):
+    def forward(ctx, lam, case, solve_tol, max_sweeps, adj_tol, adj_max_iter, opts, objective="pressure_drop"):
         c = dict(case)
         c["lam"] = lam.detach().to(torch.float64)
         s = Solver(c, device=lam.device, **opts)
@@ -33,25 +33,31 @@ class SteadyRANS(torch.autograd.Function):
             s.close()
             raise RuntimeError("steady solve did not reach %g in %d sweeps (status %d)" % (solve_tol, it, rc))
         ctx.solver = s
-        ctx.adj = (adj_tol, adj_max_iter)
+        ctx.adj = (adj_tol, adj_max_iter, objective)
         ctx.lam_shape = lam.shape
-        return torch.tensor(s.objective(), dtype=torch.float64, device=lam.device)
+        return torch.tensor(s.objective(objective), dtype=torch.float64, device=lam.device)
 
     @staticmethod
     def backward(ctx, gout):
         s = ctx.solver
-        tol, max_iter = ctx.adj
+        tol, max_iter, objective = ctx.adj
         try:
-            J, g, it, ch, rc = s.adjoint_grad(tol=tol, max_iter=max_iter)
+            J, g, it, ch, rc = s.adjoint_grad(tol=tol, max_iter=max_iter, objective=objective)
         finally:
             s.close()
             ctx.solver = None
         if rc != 0:
             raise RuntimeError("adjoint did not converge to %g in %d iterations (change %.2e)" % (tol, it, ch))
-        return gout * g.reshape(ctx.lam_shape), None, None, None, None, None, None
+        return gout * g.reshape(ctx.lam_shape), None, None, None, None, None, None, None
 
 
 def pressure_drop(lam, case, solve_tol=1e-11, max_sweeps=40000, adj_tol=1e-10, adj_max_iter=20000, **opts):
     """Differentiable pressure drop of the case with indicator `lam` (a CUDA
     float64 tensor shaped (nz, ny, nx)); `opts` are hfdib options."""
     return SteadyRANS.apply(lam, case, solve_tol, max_sweeps, adj_tol, adj_max_iter, opts)
+
+
+def drag(lam, case, solve_tol=1e-11, max_sweeps=40000, adj_tol=1e-10, adj_max_iter=20000, **opts):
+    """Differentiable drag (x force of the fluid on the body) of the case with
+    indicator `lam`; see pressure_drop."""
+    return SteadyRANS.apply(lam, case, solve_tol, max_sweeps, adj_tol, adj_max_iter, opts, "drag")

@@ -519,7 +519,7 @@ __global__ void k_adj_phi(Grid g, Fields F, Adj A) {
     }
 }
 
-// psi <- x-bar + J_x^T; max |change| and max |psi| for the stop test
+// psi <- x-bar + J_x^T (A.vb); max |change| and max |psi| for the stop test
 __global__ void k_adj_next(Grid g, Fields F, Adj A, int first) {
     long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double v[2] = {0.0, 0.0};
@@ -528,14 +528,14 @@ __global__ void k_adj_next(Grid g, Fields F, Adj A, int first) {
         cell_ijk(g, c, i, j, k);
         #pragma unroll
         for (int q = 0; q < 3 && q < g.dims; ++q) {
-            double nw = A.xbu[q][c];
+            double nw = A.xbu[q][c] + A.vbu[q][c];
             double old = first ? 0.0 : A.psu[q][c];
             v[0] = fmax(v[0], fabs(nw - old));
             v[1] = fmax(v[1], fabs(nw));
             A.psu[q][c] = nw;
         }
         {
-            double nw = A.xbp[c] + A.jw[c];
+            double nw = A.xbp[c] + A.vbp[c];
             double old = first ? 0.0 : A.psp[c];
             v[0] = fmax(v[0], fabs(nw - old));
             v[1] = fmax(v[1], fabs(nw));
@@ -547,7 +547,7 @@ __global__ void k_adj_next(Grid g, Fields F, Adj A, int first) {
             for (int e = 0; e < 2; ++e) {
                 if (e == 1 && has_nb(g, d, 1, i, j, k)) break;
                 long long fi = fl + e * face_stride(g, d);
-                double nw = A.xbf[d][fi];
+                double nw = A.xbf[d][fi] + A.vbf[d][fi];
                 double old = first ? 0.0 : A.psf[d][fi];
                 v[0] = fmax(v[0], fabs(nw - old));
                 v[1] = fmax(v[1], fabs(nw));
@@ -564,6 +564,135 @@ __global__ void k_adj_objective(Grid g, Fields F, Adj A) {
     double v[1] = {0.0};
     if (c < g.N) v[0] = A.jw[c] * F.p[c];
     grid_reduce<1, false>(v, F.partials, F.counters + 11, F.scal + SC_ADJ_J);
+}
+
+// ---------------------------------------------------------------- drag objective
+// Drag: the x force of the fluid on the body, minus the x-momentum row
+// residual of the imposed rows (ic and laminar-branch bc cells):
+//   r = aP ut + sum_s a_s ut_N - (bnd + T) + V dp/dx,
+// the forcing the immersed boundary applies to the fluid there (Eq.
+// hfdibrans_1).  ut = u_s in ic cells, u_ib in laminar-branch bc cells, u
+// elsewhere; the row is that of the sweep at the converged state (k_adj_coef).
+namespace {
+
+__device__ inline double drag_ut(const Grid& g, const Fields& F, long long c, uint16_t f) {
+    if (tag_of(f) == TAG_IC) return g.u_s[0];
+    if (f & F_AU) return F.uib[0][c];
+    return F.u[0][c];
+}
+
+// boundary part and explicit transpose term of the x row, as the assembly forms them
+__device__ double drag_b0(const Grid& g, const Fields& F, long long c, int i, int j, int k, uint16_t f) {
+    const long long N = g.N;
+    double nuP = g.nu + F.nut[c];
+    double bnd = 0.0, T = 0.0;
+    #pragma unroll
+    for (int d = 0; d < 3 && d < g.dims; ++d) {
+        long long fl = face_lo(g, d, i, j, k);
+        long long fs = face_stride(g, d);
+        for (int side = 0; side < 2; ++side) {
+            if (has_nb(g, d, side, i, j, k)) continue;
+            double val;
+            if (vel_fixed(g, f, 2 * d + side, 0, val)) {
+                double Fb = F.phi[d][fl + side * fs];
+                double Fout = side ? Fb : -Fb;
+                bnd += (nuP * g.SoHD[d] + fmax(-Fout, 0.0)) * val;
+            }
+        }
+    }
+    #pragma unroll
+    for (int a = 0; a < 3 && a < g.dims; ++a) {
+        const double* Gq = F.G + (long long)a * N;   // d u_a / d x (component q = 0)
+        double GP = Gq[c];
+        double flo, fhi;
+        if (has_nb(g, a, 0, i, j, k)) {
+            long long nc = c - g.stride[a];
+            flo = (0.5 * (nuP + g.nu + F.nut[nc])) * (0.5 * (GP + Gq[nc])) * g.S[a];
+        } else {
+            flo = nuP * GP * g.S[a];
+        }
+        if (has_nb(g, a, 1, i, j, k)) {
+            long long nc = c + g.stride[a];
+            fhi = (0.5 * (nuP + g.nu + F.nut[nc])) * (0.5 * (GP + Gq[nc])) * g.S[a];
+        } else {
+            fhi = nuP * GP * g.S[a];
+        }
+        T += fhi - flo;
+    }
+    return bnd + T;
+}
+
+}  // namespace
+
+// J = -sum over imposed rows of r
+__global__ void k_adj_drag_value(Grid g, Fields F, Adj A) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double v[1] = {0.0};
+    if (c < g.N) {
+        uint16_t f = F.flags[c];
+        if (fixed_row(f)) {
+            int i, j, k;
+            cell_ijk(g, c, i, j, k);
+            const long long N = g.N;
+            double r = A.AP[c] * drag_ut(g, F, c, f);
+            #pragma unroll
+            for (int s = 0; s < 6 && s < 2 * g.dims; ++s) {
+                int d = s >> 1, side = s & 1;
+                if (!has_nb(g, d, side, i, j, k)) continue;
+                long long n = side ? c + g.stride[d] : c - g.stride[d];
+                r += A.As[(long long)s * N + c] * drag_ut(g, F, n, F.flags[n]);
+            }
+            r -= drag_b0(g, F, c, i, j, k, f);
+            r += g.V * grad_pr(g, F.p, F.p, 0.0, c, 0, i, j, k);
+            v[0] = -r;
+        }
+    }
+    grid_reduce<1, false>(v, F.partials, F.counters + 11, F.scal + SC_ADJ_J);
+}
+
+// Seed of the drag's derivative, laid out for the reverse-pass kernels that
+// follow (k_adj_transpose, k_adj_gradu, k_adj_phi): with w = dJ/dr = -1 in
+// imposed rows, b0-bar = -w (r holds -b0), bm-bar = -w (their p-bar is the
+// transposed gradient of -V bm-bar, and r holds +V dp/dx), aP-bar and
+// a_s-bar of the x row, and ut-bar gathered from the rows that read ut: into
+// u-bar in free cells, into u_ib-bar in laminar-branch bc cells.
+__global__ void k_adj_drag_seed(Grid g, Fields F, Adj A) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    int i, j, k;
+    cell_ijk(g, c, i, j, k);
+    const long long N = g.N;
+    uint16_t f = F.flags[c];
+    double w = fixed_row(f) ? -1.0 : 0.0;
+    #pragma unroll
+    for (int q = 0; q < 3 && q < g.dims; ++q) {
+        A.b0b[q][c] = 0.0;
+        A.bmb[q][c] = 0.0;
+        A.aPb[q][c] = 0.0;
+        A.fixb[q][c] = 0.0;
+        A.xbu[q][c] = 0.0;
+    }
+    A.xbp[c] = 0.0;
+    A.b0b[0][c] = -w;
+    A.bmb[0][c] = -w;
+    A.aPb[0][c] = w * drag_ut(g, F, c, f);
+    double utb = w * A.AP[c];
+    #pragma unroll
+    for (int s = 0; s < 6 && s < 2 * g.dims; ++s) {
+        int d = s >> 1, side = s & 1;
+        double as = 0.0;
+        if (has_nb(g, d, side, i, j, k)) {
+            long long n = side ? c + g.stride[d] : c - g.stride[d];
+            uint16_t fn = F.flags[n];
+            as = w * drag_ut(g, F, n, fn);
+            if (fixed_row(fn)) utb -= A.As[(long long)(s ^ 1) * N + n];
+        }
+        A.asb[(long long)s * N + c] = as;
+    }
+    if (tag_of(f) != TAG_IC) {
+        if (f & F_AU) A.fixb[0][c] = utb;
+        else A.xbu[0][c] = utb;
+    }
 }
 
 // ---------------------------------------------------------------- lambda chain
@@ -760,6 +889,12 @@ void launch_adj_phi(const Grid& g, const Fields& F, const Adj& A, cudaStream_t s
 }
 void launch_adj_next(const Grid& g, const Fields& F, const Adj& A, int first, cudaStream_t s) {
     k_adj_next<<<nblocks(g.N), BLOCK, 0, s>>>(g, F, A, first);
+}
+void launch_adj_drag_value(const Grid& g, const Fields& F, const Adj& A, cudaStream_t s) {
+    k_adj_drag_value<<<nblocks(g.N), BLOCK, 0, s>>>(g, F, A);
+}
+void launch_adj_drag_seed(const Grid& g, const Fields& F, const Adj& A, cudaStream_t s) {
+    k_adj_drag_seed<<<nblocks(g.N), BLOCK, 0, s>>>(g, F, A);
 }
 void launch_adj_objective(const Grid& g, const Fields& F, const Adj& A, cudaStream_t s) {
     k_adj_objective<<<nblocks(g.N), BLOCK, 0, s>>>(g, F, A);

@@ -638,7 +638,7 @@ int adj_alloc(Ctx* h) {
     AL(A.As, 6 * N); AL(A.AP, 3 * N); AL(A.aavg, N); AL(A.jw, N);
     for (int q = 0; q < 3; ++q) {
         AL(A.Hb[q], N); AL(A.b0b[q], N); AL(A.bmb[q], N);
-        AL(A.aPb[q], N); AL(A.usb[0][q], N); AL(A.usb[1][q], N); AL(A.fixb[q], N);
+        AL(A.aPb[q], N); AL(A.usb[0][q], N); AL(A.usb[1][q], N); AL(A.fixb[q], N); AL(A.fixs[q], N);
     }
     // flat adjoint state: u components, p, face fluxes of the active directions
     long long nv = (long long)(g.dims + 1) * N;
@@ -651,17 +651,22 @@ int adj_alloc(Ctx* h) {
     if (rc) return rc;
     {
         long long off = 0;
-        for (int q = 0; q < g.dims; ++q, off += N) { A.psu[q] = A.vpsi + off; A.xbu[q] = A.vxb + off; }
+        for (int q = 0; q < g.dims; ++q, off += N) {
+            A.psu[q] = A.vpsi + off; A.xbu[q] = A.vxb + off; A.vbu[q] = A.vb + off;
+        }
         A.psp = A.vpsi + off;
         A.xbp = A.vxb + off;
+        A.vbp = A.vb + off;
         off += N;
         for (int d = 0; d < g.dims; ++d) {
             A.psf[d] = A.vpsi + off;
             A.xbf[d] = A.vxb + off;
+            A.vbf[d] = A.vb + off;
             off += g.nface[d];
         }
         for (int q = g.dims; q < 3; ++q) {  // not read in 2D; point at valid memory
             A.psu[q] = A.psu[0]; A.xbu[q] = A.xbu[0]; A.psf[q] = A.psf[0]; A.xbf[q] = A.xbf[0];
+            A.vbu[q] = A.vbu[0]; A.vbf[q] = A.vbf[0];
         }
     }
     // objective weights from the closed-face flags (fixed for the handle's lambda)
@@ -688,8 +693,6 @@ int adj_alloc(Ctx* h) {
         for (long long c : cells) jw[c] += w;
     }
     CK(cudaMemcpyAsync(A.jw, jw.data(), N * sizeof(double), cudaMemcpyHostToDevice, s));
-    // J_x^T as a flat vector: jw in the pressure block
-    CK(cudaMemcpyAsync(A.vb + (long long)g.dims * N, jw.data(), N * sizeof(double), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
     h->adj_ready = true;
     return HFDIB_OK;
@@ -1462,7 +1465,8 @@ int hfdib_adjoint_grad(hfdib_handle hh, int objective, double tol, int max_iter,
     if (iters_out) *iters_out = 0;
     if (change_out) *change_out = 0.0;
     if (!h) return HFDIB_ERR_INVALID_ARG;
-    if (objective != HFDIB_OBJ_PRESSURE_DROP) return HFDIB_ERR_INVALID_ARG;
+    if (objective != HFDIB_OBJ_PRESSURE_DROP && objective != HFDIB_OBJ_DRAG) return HFDIB_ERR_INVALID_ARG;
+    const bool drag = objective == HFDIB_OBJ_DRAG;
     if (h->g.dims != 2) return HFDIB_ERR_INVALID_ARG;
     if (!(tol > 0.0) || max_iter < 0 || (max_iter > 0 && !dJ_dlambda)) return HFDIB_ERR_INVALID_ARG;
     if (gmres_restart < 0 || gmres_restart > HFDIB_GMRES_MAX_RESTART) return HFDIB_ERR_INVALID_ARG;
@@ -1472,7 +1476,7 @@ int hfdib_adjoint_grad(hfdib_handle hh, int objective, double tol, int max_iter,
     Adj& A = h->adj;
     Fields F = h->F;
     F.mixed = 0;
-    if (max_iter == 0) {
+    if (max_iter == 0 && !drag) {
         // the objective alone
         launch_adj_objective(g, F, A, s);
         CK(cudaGetLastError());
@@ -1482,6 +1486,30 @@ int hfdib_adjoint_grad(hfdib_handle hh, int objective, double tol, int max_iter,
         return HFDIB_OK;
     }
     RC(adj_setup(h));
+    if (max_iter == 0) {
+        // the drag alone (it needs the rows and u_ib of the set-up)
+        launch_adj_drag_value(g, F, A, s);
+        CK(cudaGetLastError());
+        double J = 0.0;
+        RC(sync_read(h, F.scal + SC_ADJ_J, &J, 1));
+        if (J_out) *J_out = J;
+        return HFDIB_OK;
+    }
+    // right-hand side J_x^T of the adjoint
+    CK(cudaMemsetAsync(A.vb, 0, A.nvec * sizeof(double), s));
+    if (drag) {
+        // the objective's own derivative through the reverse-pass tail; its
+        // u_ib-bar (the explicit lambda dependence) is kept in fixs
+        launch_adj_drag_seed(g, F, A, s);
+        launch_adj_transpose(g, F, A, s);
+        launch_adj_gradu(g, F, h->bl, A, s);
+        launch_adj_phi(g, F, A, s);
+        CK(cudaMemcpyAsync(A.vb, A.vxb, A.nvec * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        for (int q = 0; q < g.dims; ++q)
+            CK(cudaMemcpyAsync(A.fixs[q], A.fixb[q], g.N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else {
+        CK(cudaMemcpyAsync(A.vbp, A.jw, g.N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
     const bool warm = true;
     const double ptol = 1e-12;
     CK(cudaMemsetAsync(A.ps, 0, g.N * sizeof(double), s));
@@ -1526,8 +1554,15 @@ int hfdib_adjoint_grad(hfdib_handle hh, int objective, double tol, int max_iter,
     if (change_out) *change_out = change;
     CK(cudaMemsetAsync(A.dlam, 0, g.N * sizeof(double), s));
     launch_adj_dlambda(g, F, h->bl, h->lam, A, s);
+    if (drag) {
+        // plus the explicit dependence of the drag on lambda through u_ib
+        Adj Ae = A;
+        for (int q = 0; q < 3; ++q) Ae.fixb[q] = A.fixs[q];
+        launch_adj_dlambda(g, F, h->bl, h->lam, Ae, s);
+    }
     CK(cudaMemcpyAsync(dJ_dlambda, A.dlam, g.N * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    launch_adj_objective(g, F, A, s);
+    if (drag) launch_adj_drag_value(g, F, A, s);
+    else launch_adj_objective(g, F, A, s);
     CK(cudaGetLastError());
     double J = 0.0;
     RC(sync_read(h, F.scal + SC_ADJ_J, &J, 1));

@@ -204,7 +204,11 @@ struct Adj {
     long long nvec;      // length of the flat adjoint state (u components, p, face fluxes)
     double* vpsi;        // flat psi; psu / psp / psf point into it
     double* vxb;         // flat x-bar; xbu / xbp / xbf point into it
-    double* vb;          // flat J_x^T
+    double* vb;          // flat J_x^T (right-hand side of the adjoint)
+    double* vbu[3];      // its velocity, pressure and face-flux blocks
+    double* vbp;
+    double* vbf[3];
+    double* fixs[3];     // drag: adjoint of u_ib from the objective itself (explicit J_lambda)
     double* snap;        // [2 nu][3][N] predictor iterates S_0 .. S_{2nu-1} (S_{2nu} = F.us)
     double* As;          // [6][N] neighbour coefficients of the momentum rows (0: no neighbour)
     double* AP;          // [3][N] unrelaxed diagonal per component
@@ -246,6 +250,8 @@ void launch_adj_gradu(const Grid& g, const Fields& F, const BcList& bl, const Ad
 void launch_adj_phi(const Grid& g, const Fields& F, const Adj& A, cudaStream_t s);
 void launch_adj_next(const Grid& g, const Fields& F, const Adj& A, int first, cudaStream_t s);
 void launch_adj_objective(const Grid& g, const Fields& F, const Adj& A, cudaStream_t s);
+void launch_adj_drag_value(const Grid& g, const Fields& F, const Adj& A, cudaStream_t s);
+void launch_adj_drag_seed(const Grid& g, const Fields& F, const Adj& A, cudaStream_t s);
 void launch_adj_dlambda(const Grid& g, const Fields& F, const BcList& bl, const double* lam, const Adj& A,
                         cudaStream_t s);
 enum { SC_ADJ_DIFF = 48, SC_ADJ_NORM = 49, SC_ADJ_J = 50 };

@@ -26,6 +26,8 @@ NRES = 10
 STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "out of memory",
           -4: "not converged", -5: "diverged", -6: "state mismatch", -7: "too large", -8: "timeout"}
 
+OBJECTIVES = {"pressure_drop": 0, "drag": 1}
+
 ERR_NOT_CONVERGED = -4
 STATUS_TOO_LARGE = -7
 
@@ -291,7 +293,7 @@ class Solver:
         _check(self.lib.hfdib_get_launch_counts(self.h, C.byref(a), C.byref(b)), "hfdib_get_launch_counts")
         return a.value, b.value
 
-    def adjoint_grad(self, tol=1e-10, max_iter=20000, objective=0, gmres_restart=0):
+    def adjoint_grad(self, tol=1e-10, max_iter=20000, objective="pressure_drop", gmres_restart=0):
         """Frozen-turbulence adjoint of the converged state: returns (J,
         dJ/dlambda as a device tensor shaped like lambda, transposed sweeps,
         final relative residual (GMRES) or change (gmres_restart=0: plain
@@ -302,6 +304,7 @@ class Solver:
         it = C.c_int(0)
         ch = C.c_double(0.0)
         self.stream.synchronize()
+        objective = OBJECTIVES.get(objective, objective)
         rc = self.lib.hfdib_adjoint_grad(self.h, int(objective), float(tol), int(max_iter), int(gmres_restart),
                                          C.c_void_p(out.data_ptr()), C.byref(J), C.byref(it), C.byref(ch))
         if rc not in (0, ERR_NOT_CONVERGED):
@@ -309,8 +312,9 @@ class Solver:
         self.stream.synchronize()
         return J.value, out.reshape(self.shape), it.value, ch.value, rc
 
-    def objective(self, objective=0):
+    def objective(self, objective="pressure_drop"):
         """J of the current state (hfdib_adjoint_grad with max_iter = 0)."""
+        objective = OBJECTIVES.get(objective, objective)
         J = C.c_double(0.0)
         self.stream.synchronize()
         rc = self.lib.hfdib_adjoint_grad(self.h, int(objective), 1.0, 0, 0, None, C.byref(J), None, None)

@@ -175,3 +175,41 @@ def test_adjoint_rejects_3d_and_unknown_objective():
     with pytest.raises(HfdibError):
         s.adjoint_grad(max_iter=10, objective=7)
     s.close()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_drag_gradient_matches_oracle(name):
+    """Drag (minus the immersed-boundary forcing of the imposed rows): value
+    and dJ/dlambda = J_lambda - psi^T R_lambda against the oracle."""
+    case = CASES[name]()
+    o = O.Oracle(case)
+    it, res = o.solve(tol=1e-13, max_iter=6000)
+    assert o.max_residual(res) <= 1e-13
+    fs = A.FrozenSteady(o, "drag")
+    Jo, go, _ = fs.gradient()
+    go = go.ravel()
+    s = gpu_converged(case)
+    J, g, it, ch, rc = s.adjoint_grad(tol=1e-12, max_iter=40000, objective="drag")
+    assert rc == 0, (it, ch)
+    g = g.cpu().numpy().ravel()
+    e = rel(g, go)
+    print("%s drag: J gpu %.15f oracle %.15f, grad rel-L2 %.2e, %d iterations" % (name, J, Jo, e, it))
+    assert abs(J - Jo) <= 1e-9 * abs(Jo)
+    assert abs(s.objective("drag") - J) <= 1e-14 * abs(J)
+    assert e <= 1e-10
+    s.close()
+
+
+def test_autograd_drag_delivers_the_gradient():
+    import torch
+    from paper_2606_06135_gb300.autograd import drag
+    case = G.case_grf(32, 16, seed=1)
+    lam = torch.tensor(case["lam"], dtype=torch.float64, device="cuda", requires_grad=True)
+    J = drag(lam, case, solve_tol=1e-12, adj_tol=1e-12)
+    J.backward()
+    s = gpu_converged(case)
+    Jd, g, _, _, rc = s.adjoint_grad(tol=1e-12, max_iter=40000, objective="drag")
+    assert rc == 0
+    assert abs(J.item() - Jd) <= 1e-12 * abs(Jd)
+    assert rel(lam.grad.cpu().numpy(), g.cpu().numpy()) <= 1e-9
+    s.close()
