@@ -230,6 +230,41 @@ enum { HFDIB_GMRES_MAX_RESTART = 200 };
 int hfdib_adjoint_grad(hfdib_handle h, int objective, double tol, int max_iter, int gmres_restart,
                        double* dJ_dlambda, double* J_out, int* iters_out, double* change_out);
 
+/* hfdib_ib_force -- force of the fluid on the immersed body at the current
+ * state (Eq. dragcoeff, Eq. dlcoeffs: the integrand f_tot = f_n + f_t).  The
+ * surface integral over the fluid-solid interface is taken through the
+ * momentum balance of the imposed rows (in-solid cells and laminar-branch bc
+ * cells): the force is minus the sum over those rows of the momentum row
+ * residual aP u~ + sum a_N u~_N - b0 + V grad p, the forcing of Eq.
+ * hfdibrans_1 applied there, with the imposed values u~ and grad u of the
+ * current state (the rows of the next sweep).
+ *   force : HOST pointer, 6 doubles: [0..2] the pressure part -sum V grad p
+ *           (f_n), [3..5] the rest, viscous and convective (f_t); components
+ *           beyond the grid's dimensions are 0.  Kinematic units (pressure /
+ *           rho times area).  C_d = 2 F.v_d / (A_ref |u_in|^2) with
+ *           F = force[0..2] + force[3..5].
+ * Waits for the handle's stream.  Leaves the state unchanged (it refreshes
+ * the imposed fields and grad u, which the next sweep recomputes from the
+ * same state).  Errors: INVALID_ARG (NULL), CUDA. */
+int hfdib_ib_force(hfdib_handle h, double* force);
+
+/* hfdib_wall_shear -- wall shear stress along one no-slip domain side
+ * (Sec. 3.3, tau_w = nu du/dn at the wall): the shear of the discrete wall
+ * flux, (nu + nu_t,P) u_P / (Delta/2) per tangential component, u_P the
+ * velocity of the wall cell as its row sees it.  Zero on closed faces (a
+ * wall inside the solid) and for the normal component.  C_f = 2 tau_w /
+ * |u_in|^2.
+ *   side  : 0..5 = x-, x+, y-, y+, z-, z+; must be an HFDIB_BC_WALL side of
+ *           the grid's dimensions (INVALID_ARG otherwise)
+ *   tau   : DEVICE pointer, 3 * n_faces doubles, caller-owned: component q of
+ *           face f at tau[q * n_faces + f]; faces in the order of the wall's
+ *           cells (the two tangential indices, the lower direction fastest).
+ *           n_faces = the product of the other two cell counts.  NULL with
+ *           n_faces_out set only reports the size.
+ *   n_faces_out : host pointer, nullable
+ * Asynchronous on the handle's stream. */
+int hfdib_wall_shear(hfdib_handle h, int side, double* tau, int64_t* n_faces_out);
+
 /* Copy a field (HFDIB_FIELD_*) device-to-device into dst (caller-owned, sized
  * like the field: cells, or faces (nx+1)*ny*nz / nx*(ny+1)*nz / nx*ny*(nz+1)). */
 int hfdib_get_field(hfdib_handle h, int field, double* dst);

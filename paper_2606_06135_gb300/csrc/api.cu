@@ -1459,6 +1459,40 @@ int hfdib_get_counters(hfdib_handle hh, int64_t* sweeps, int64_t* launches) {
     return HFDIB_OK;
 }
 
+int hfdib_ib_force(hfdib_handle hh, double* force) {
+    Ctx* h = (Ctx*)hh;
+    if (!h || !force) return HFDIB_ERR_INVALID_ARG;
+    const Grid& g = h->g;
+    Fields F = h->F;
+    cudaStream_t s = h->stream;
+    // the imposed fields and grad u of the current state, as the next sweep sets them
+    launch_imposed(g, h->model, h->opt.freeze_switch, h->bl, F.flags, F.scal, F.u[0], F.u[1], F.u[2], F.k,
+                   F.uib[0], F.uib[1], F.uib[2], F.kib, F.wib, s);
+    CK(cudaMemsetAsync(F.scal + SC_NLAM, 0, 2 * sizeof(double), s));
+    launch_grad_u(g, F, s);
+    launch_ib_force(g, F, s);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(force, F.scal + SC_FORCE, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return HFDIB_OK;
+}
+
+int hfdib_wall_shear(hfdib_handle hh, int side, double* tau, int64_t* n_faces_out) {
+    Ctx* h = (Ctx*)hh;
+    if (!h || side < 0 || side > 5) return HFDIB_ERR_INVALID_ARG;
+    const Grid& g = h->g;
+    int d = side >> 1;
+    if (d >= g.dims || g.kind[side] != HFDIB_BC_WALL) return HFDIB_ERR_INVALID_ARG;
+    long long nf = 1;
+    for (int a = 0; a < 3; ++a)
+        if (a != d) nf *= g.n[a];
+    if (n_faces_out) *n_faces_out = nf;
+    if (!tau) return HFDIB_OK;
+    launch_wall_shear(g, h->F, side, nf, tau, h->stream);
+    CK(cudaGetLastError());
+    return HFDIB_OK;
+}
+
 int hfdib_adjoint_grad(hfdib_handle hh, int objective, double tol, int max_iter, int gmres_restart,
                        double* dJ_dlambda, double* J_out, int* iters_out, double* change_out) {
     Ctx* h = (Ctx*)hh;

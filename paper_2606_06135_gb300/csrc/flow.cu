@@ -192,6 +192,33 @@ __global__ void k_grad_u(Grid g, Fields F) {
     }
 }
 
+// explicit div(nu_eff (grad u)^T) of cell c, component q: face flux
+// nu_f (d u_a/d x_q)_f S_a through the a-faces (cell values on boundary faces)
+__device__ __forceinline__ double transpose_src(const Grid& g, const Fields& F, long long c, int i, int j, int k,
+                                                int q, double nuP) {
+    double T = 0.0;
+    #pragma unroll
+    for (int a = 0; a < 3 && a < g.dims; ++a) {
+        const double* Gq = F.G + (long long)(3 * q + a) * g.N;
+        double GP = Gq[c];
+        double flo, fhi;
+        if (interior(g, a, 0, i, j, k)) {
+            long long nc = c - g.stride[a];
+            flo = (0.5 * (nuP + g.nu + F.nut[nc])) * (0.5 * (GP + Gq[nc])) * g.S[a];
+        } else {
+            flo = nuP * GP * g.S[a];
+        }
+        if (interior(g, a, 1, i, j, k)) {
+            long long nc = c + g.stride[a];
+            fhi = (0.5 * (nuP + g.nu + F.nut[nc])) * (0.5 * (GP + Gq[nc])) * g.S[a];
+        } else {
+            fhi = nuP * GP * g.S[a];
+        }
+        T += fhi - flo;
+    }
+    return T;
+}
+
 // ---------------------------------------------------------------- a3 assembly
 __global__ void __launch_bounds__(BLOCK, 2) k_mom_asm(Grid g, Params P, Fields F) {
     double red[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -211,28 +238,7 @@ __global__ void __launch_bounds__(BLOCK, 2) k_mom_asm(Grid g, Params P, Fields F
         bool fixed_row = (tag_of(f) == TAG_IC) || (f & F_AU);
         #pragma unroll
         for (int q = 0; q < 3 && q < g.dims; ++q) {
-            // explicit div(nu_eff (grad u)^T), component q: face flux nu_f (d u_a/d x_q)_f S_a
-            double T = 0.0;
-            #pragma unroll
-            for (int a = 0; a < 3 && a < g.dims; ++a) {
-                const double* Gq = F.G + (long long)(3 * q + a) * g.N;
-                double GP = Gq[c];
-                double flo, fhi;
-                if (interior(g, a, 0, i, j, k)) {
-                    long long nc = c - g.stride[a];
-                    flo = (0.5 * (nuP + g.nu + F.nut[nc])) * (0.5 * (GP + Gq[nc])) * g.S[a];
-                } else {
-                    flo = nuP * GP * g.S[a];
-                }
-                if (interior(g, a, 1, i, j, k)) {
-                    long long nc = c + g.stride[a];
-                    fhi = (0.5 * (nuP + g.nu + F.nut[nc])) * (0.5 * (GP + Gq[nc])) * g.S[a];
-                } else {
-                    fhi = nuP * GP * g.S[a];
-                }
-                T += fhi - flo;
-            }
-            double b0 = R.bnd[q] + T;
+            double b0 = R.bnd[q] + transpose_src(g, F, c, i, j, k, q, nuP);
             double gp = grad_p(g, F.p, c, q, i, j, k);
             double uold = F.u[q][c];
             double bfull = b0 - gp * g.V;
@@ -442,6 +448,80 @@ __global__ void k_update(Grid g, Params P, Fields F, Level L0) {
     grid_reduce<1, false>(red, F.partials, F.counters + 6, F.scal + SC_CONT);
 }
 
+// ---------------------------------------------------------------- force on the body
+// Eq. dragcoeff read through the momentum balance of the imposed rows (ic and
+// laminar-branch bc cells): there the row residual at the imposed values ut,
+//   r_q = aP ut_P + sum_s a_s ut_N - b0_q + V dp/dx_q,
+// is the forcing f_ib V of Eq. hfdibrans_1, and the force of the fluid on the
+// body is -sum r.  Out: scal[SC_FORCE + q] = -sum V dp/dx_q (pressure part,
+// f_n), scal[SC_FORCE + 3 + q] = the rest (viscous and convective, f_t).
+// Needs the imposed fields and grad u of the current state.
+__global__ void k_ib_force(Grid g, Fields F) {
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < g.N;
+         c += (long long)gridDim.x * blockDim.x) {
+        uint16_t f = F.flags[c];
+        if (!((tag_of(f) == TAG_IC) || (f & F_AU))) continue;
+        int i, j, k;
+        cell_ijk(g, c, i, j, k);
+        MomRow R;
+        mom_row(g, F, c, i, j, k, f, R);
+        double nuP = g.nu + F.nut[c];
+        #pragma unroll
+        for (int q = 0; q < 3 && q < g.dims; ++q) {
+            double uP;
+            vel_row_fixed(g, F, c, q, uP);
+            double r = R.aP[q] * uP;
+            #pragma unroll
+            for (int s = 0; s < 6 && s < 2 * g.dims; ++s) {
+                if (!R.has[s]) continue;
+                long long nc = R.nb[s];
+                double uN;
+                if (!vel_row_fixed(g, F, nc, q, uN)) uN = F.u[q][nc];
+                r += R.a[s] * uN;
+            }
+            r -= R.bnd[q] + transpose_src(g, F, c, i, j, k, q, nuP);
+            v[q] -= g.V * grad_p(g, F.p, c, q, i, j, k);
+            v[3 + q] -= r;
+        }
+    }
+    grid_reduce<6, false>(v, F.partials, F.counters + 12, F.scal + SC_FORCE);
+}
+
+// ---------------------------------------------------------------- wall shear
+// tau_w along one no-slip domain side (Sec. 3.3): the shear of the discrete
+// wall flux, nu_eff,P (u_P - 0)/(Delta/2) per tangential component, with
+// u_P the velocity the row sees (the imposed value in an imposed row); zero
+// on closed faces (a wall inside the solid carries no flux) and for the
+// normal component.  tau[q * n_faces + f], faces in cell order along the wall.
+__global__ void k_wall_shear(Grid g, Fields F, int side, long long nf, double* tau) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nf) return;
+    const int d = side >> 1, hi = side & 1;
+    // the wall's cells: coordinate d fixed, the other two in x, y, z order
+    const int n0 = (d == 0) ? g.n[1] : g.n[0];
+    const int t0 = (int)(e % n0), t1 = (int)(e / n0);
+    const int w = hi ? (d == 0 ? g.n[0] : (d == 1 ? g.n[1] : g.n[2])) - 1 : 0;
+    int i, j, k;
+    if (d == 0) { i = w; j = t0; k = t1; }
+    else if (d == 1) { i = t0; j = w; k = t1; }
+    else { i = t0; j = t1; k = w; }
+    long long c = ((long long)k * g.n[1] + j) * g.n[0] + i;
+    uint16_t f = F.flags[c];
+    bool open = !closed_side(f, side);
+    double nuP = g.nu + F.nut[c];
+    #pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        double val = 0.0;
+        if (open && q != d && q < g.dims) {
+            double uP;
+            if (!vel_row_fixed(g, F, c, q, uP)) uP = F.u[q][c];
+            val = nuP * uP * g.iD[d] * 2.0;
+        }
+        tau[(long long)q * nf + e] = val;
+    }
+}
+
 // ---------------------------------------------------------------- sweep end
 __global__ void k_sweep_end(Fields F, int dims, int model, double* res_out, double* hist, int nhist) {
     double* s = F.scal;
@@ -500,6 +580,12 @@ void launch_phiH(const Grid& g, const Fields& F, cudaStream_t s) {
 }
 void launch_update(const Grid& g, const Params& P, const Fields& F, const Level& L0, cudaStream_t s) {
     k_update<<<rblocks(g.N), BLOCK, 0, s>>>(g, P, F, L0);
+}
+void launch_ib_force(const Grid& g, const Fields& F, cudaStream_t s) {
+    k_ib_force<<<rblocks(g.N), BLOCK, 0, s>>>(g, F);
+}
+void launch_wall_shear(const Grid& g, const Fields& F, int side, long long nf, double* tau, cudaStream_t s) {
+    if (nf > 0) k_wall_shear<<<nblocks(nf), BLOCK, 0, s>>>(g, F, side, nf, tau);
 }
 void launch_sweep_end(const Params& P, const Fields& F, int dims, double* res_out, double* hist, int nhist,
                       cudaStream_t s) {

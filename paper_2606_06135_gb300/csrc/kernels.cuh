@@ -46,6 +46,7 @@ enum {
     SC_NSWITCH = 39,             // bc cells whose branch changed
     SC_TIMEOUT = 46,             // 1 once a persistent kernel's grid barrier gave up
     SC_PCG_INIT = 40,            // r0.z0, r0.r0, b.b, then the 3 scaled-residual sums of p
+    SC_FORCE = 52,               // 6: force on the body, pressure part xyz then the rest xyz
     SC_NSCAL = 64
 };
 
@@ -155,6 +156,8 @@ void launch_init_flux(const Grid& g, const Fields& F, cudaStream_t s);
 void launch_means(const Grid& g, const Params& P, const Fields& F, cudaStream_t s);
 void launch_grad_u(const Grid& g, const Fields& F, cudaStream_t s);
 void launch_mom_asm(const Grid& g, const Params& P, const Fields& F, cudaStream_t s);
+void launch_ib_force(const Grid& g, const Fields& F, cudaStream_t s);
+void launch_wall_shear(const Grid& g, const Fields& F, int side, long long nf, double* tau, cudaStream_t s);
 void launch_mom_smooth(const Grid& g, const Params& P, const Fields& F, int colour, cudaStream_t s);
 void launch_hbya(const Grid& g, const Params& P, const Fields& F, cudaStream_t s);
 void launch_phiH(const Grid& g, const Fields& F, cudaStream_t s);

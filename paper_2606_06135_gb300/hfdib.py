@@ -8,6 +8,7 @@ fallback -- load_library() raises when it is missing.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 
 import numpy as np
@@ -27,6 +28,7 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "out of memory"
           -4: "not converged", -5: "diverged", -6: "state mismatch", -7: "too large", -8: "timeout"}
 
 OBJECTIVES = {"pressure_drop": 0, "drag": 1}
+WALL_SIDES = ("xmin", "xmax", "ymin", "ymax", "zmin", "zmax")
 
 ERR_NOT_CONVERGED = -4
 STATUS_TOO_LARGE = -7
@@ -119,6 +121,10 @@ def load_library(path=LIBPATH):
     lib.hfdib_destroy_batch.restype = None
     lib.hfdib_adjoint_grad.argtypes = [vp, i32, dbl, i32, i32, vp, C.POINTER(dbl), C.POINTER(i32), C.POINTER(dbl)]
     lib.hfdib_adjoint_grad.restype = i32
+    lib.hfdib_ib_force.argtypes = [vp, vp]
+    lib.hfdib_ib_force.restype = i32
+    lib.hfdib_wall_shear.argtypes = [vp, i32, vp, C.POINTER(i64)]
+    lib.hfdib_wall_shear.restype = i32
     lib.hfdib_error_string.argtypes = [i32]
     lib.hfdib_error_string.restype = C.c_char_p
     lib.hfdib_destroy.argtypes = [vp]
@@ -320,6 +326,42 @@ class Solver:
         rc = self.lib.hfdib_adjoint_grad(self.h, int(objective), 1.0, 0, 0, None, C.byref(J), None, None)
         _check(rc, "hfdib_adjoint_grad")
         return J.value
+
+    # ------------------------------------------------------------------ forces
+    def force(self):
+        """Force of the fluid on the body (hfdib_ib_force): (pressure part,
+        viscous and convective part), each a length-3 numpy array."""
+        out = np.zeros(6)
+        self.stream.synchronize()
+        _check(self.lib.hfdib_ib_force(self.h, out.ctypes.data), "hfdib_ib_force")
+        return out[:3].copy(), out[3:].copy()
+
+    def force_coefficients(self, A_ref=None, gamma=0.0):
+        """(C_d, C_l) of Eqs. dragcoeff and dlcoeffs.  A_ref defaults, on a 2D
+        grid, to l_ref times the cell depth dz."""
+        if A_ref is None:
+            if self.dims != 2:
+                raise ValueError("A_ref is required on a 3D grid")
+            A_ref = self.case["l_ref"] * self.case["grid"]["dz"]
+        Fn, Ft = self.force()
+        F = Fn + Ft
+        u_in = np.asarray(self.case["u_in"], dtype=np.float64)
+        q = 0.5 * A_ref * float(u_in @ u_in)
+        vl = np.array([-math.sin(gamma), math.cos(gamma), 0.0])
+        return float(F[0]) / q, float(F @ vl) / q
+
+    def wall_shear(self, side):
+        """tau_w along a no-slip domain side ('ymin', ...): device tensor
+        [3, n_faces] (hfdib_wall_shear)."""
+        torch = self.torch
+        sid = WALL_SIDES.index(side) if isinstance(side, str) else int(side)
+        nf = C.c_int64(0)
+        _check(self.lib.hfdib_wall_shear(self.h, sid, None, C.byref(nf)), "hfdib_wall_shear")
+        out = torch.empty((3, nf.value), dtype=torch.float64, device=self.device)
+        self.stream.synchronize()
+        _check(self.lib.hfdib_wall_shear(self.h, sid, C.c_void_p(out.data_ptr()), None), "hfdib_wall_shear")
+        self.stream.synchronize()
+        return out
 
     def get_state(self):
         n = C.c_size_t(0)

@@ -60,3 +60,15 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(libpath):
     assert rc == -1                                   # bad model
     rc = lib.hfdib_create(C.byref(g), C.c_void_p(8), None, 2, 100.0, C.byref(bc), None, None, C.byref(h))
     assert rc == -1                                   # SST without wall distance
+
+
+def test_force_and_wall_shear_reject_null_handles_without_touching_the_gpu(libpath):
+    import ctypes as C
+    import numpy as np
+    from paper_2606_06135_gb300 import hfdib
+    lib = hfdib.load_library(libpath)
+    out = np.zeros(6)
+    assert lib.hfdib_ib_force(None, out.ctypes.data) == -1
+    n = C.c_int64(-5)
+    assert lib.hfdib_wall_shear(None, 2, None, C.byref(n)) == -1
+    assert n.value == -5
