@@ -34,9 +34,15 @@ scipy's sparse LU.  Floating point is FP64 throughout; the geometry step a0
 uses plain IEEE double operations in a fixed order so that its integer
 decisions (tags, chosen neighbour, interpolation cells) are reproducible.
 
+Turbulence models (Sec. 2.1 names four): standard k-epsilon, k-omega SST,
+the k-omega model written out in Eq. hfdibkomega, and realizable
+k-epsilon.  All four share the HFDIB treatment: imposed eps/omega rows in ic
+and bc cells, imposed k rows where alpha_k = 1, P_ib in bc cells.
+
 Readings where the paper is silent are stated at each function; the wall
 function and turbulence-model constants are the standard published values
-(Wilcox; Launder-Spalding; Menter), which the paper names but does not print.
+(Wilcox; Launder-Spalding; Menter; Shih et al.), which the paper names but
+does not print.
 """
 from __future__ import annotations
 
@@ -61,6 +67,19 @@ KE_C1, KE_C2, KE_SIGK, KE_SIGE = 1.44, 1.92, 1.0, 1.3
 # k-omega SST (Menter), standard coefficients
 SST = dict(ak1=0.85, ak2=1.0, aw1=0.5, aw2=0.856, g1=5.0 / 9.0, g2=0.44,
            b1=0.075, b2=0.0828, bstar=0.09, a1=0.31, bb1=1.0, c1=10.0)
+
+# k-omega (Wilcox), Eq. hfdibkomega: sink beta* k omega in the k equation,
+# source C_alpha1 (omega/k) P_k and sink C_beta1 omega^2 in the omega
+# equation, diffusivities nu + nu_t/sigma; nu_t = k/omega.  The printed form
+# has no cross-diffusion and no stress limiter.  Coefficients: the standard
+# high-Reynolds set (beta* 0.09, beta 0.072, alpha 0.52, 1/sigma_k =
+# 1/sigma_omega = 0.5).
+KW = dict(bstar=0.09, beta=0.072, gamma=0.52, ak=0.5, aw=0.5)
+
+# realizable k-epsilon (Shih, Liou, Shabbir, Yang, Zhu 1995): variable C_mu =
+# 1/(A0 + A_s U* k/eps), eps source C1 S eps with C1 = max(0.43, eta/(eta+5)),
+# eta = S k/eps, sink C2 eps^2/(k + sqrt(nu eps))
+RKE = dict(A0=4.0, C2=1.9, sigk=1.0, sige=1.2)
 
 K_MIN = 1e-14
 EPS_MIN = 1e-14
@@ -769,6 +788,10 @@ class Oracle:
             self.kepsilon(res)
         elif self.model == "komegasst":
             self.komegasst(res)
+        elif self.model == "komega":
+            self.komega(res)
+        elif self.model == "realizableke":
+            self.realizable_ke(res)
         self.iteration += 1
         self.history.append(res)
         return res
@@ -991,6 +1014,98 @@ class Oracle:
         # nu_t = a1 k / max(a1 omega, b1 F2 sqrt(S2)) with the new k, omega
         _, _, F2n = self._sst_blend(np.maximum(k, K_MIN), w, S2, gradk, gradw)
         self.nut = c["a1"] * k / np.maximum(c["a1"] * w, c["bb1"] * F2n * np.sqrt(S2))
+
+    def komega(self, res):
+        """k-omega (Wilcox) of Eq. hfdibkomega with the HFDIB treatment (the
+        same imposed rows and P_ib as SST)."""
+        m = self.m
+        V = m.V
+        c = KW
+        urf = self.opts["urf_turb"]
+        G, S2, Gk, Gmod = self._production()
+        alpha_w = self.ic | self.bcm
+        k_old = self.k
+        w_old = self.omega
+        sspec = self.bnd.scalar_spec
+        # omega: C_alpha1 (omega/k) P_k - C_beta1 omega^2, nu + nu_t/sigma_omega1
+        gam = self.nu + c["aw"] * self.nut
+        aP, aM, aPl, b = assemble_transport(m, self.phi, gam, sspec(self.omega_in))
+        aP = aP + c["beta"] * w_old * V
+        b = b + c["gamma"] * w_old / np.maximum(k_old, K_MIN) * Gk * V
+        w = self._turb_solve(aP, aM, aPl, b, w_old, alpha_w, self.omega_ib, urf, "omega", res)
+        w = np.maximum(w, OMEGA_MIN)
+        # k: P_k (P_ib in bc cells) - beta* k omega, nu + nu_t/sigma_k1
+        gam = self.nu + c["ak"] * self.nut
+        aP, aM, aPl, b = assemble_transport(m, self.phi, gam, sspec(self.k_in))
+        aP = aP + c["bstar"] * w * V
+        b = b + Gmod * V
+        fixed_k = self.alpha_u > 0.5
+        k = self._turb_solve(aP, aM, aPl, b, k_old, fixed_k, self.k_ib, urf, "k", res)
+        k = np.maximum(k, K_MIN)
+        k = k + self.alpha_u * (self.k_ib - k)
+        self.k = k
+        self.omega = w
+        self.eps = C_MU * k * w
+        self.nut = k / w
+
+    def rke_coefficients(self, G):
+        """Realizable k-eps: (A_s U*, S) per cell from the velocity gradient
+        G[a][b] = d u_b / d x_a.  S_ij = sym(grad u), Omega_ij = skew(grad
+        u), S~ = sqrt(S_ij S_ij), W = S_ij S_jk S_ki / S~^3 (0 where S~ = 0),
+        phi = arccos(sqrt(6) W)/3 (argument clipped to [-1, 1]), A_s =
+        sqrt(6) cos(phi), U* = sqrt(S_ij S_ij + Omega_ij Omega_ij), S =
+        sqrt(2 S_ij S_ij)."""
+        m = self.m
+        d = m.dims
+        Sm = [[0.5 * (G[a][b] + G[b][a]) for b in range(d)] for a in range(d)]
+        Om = [[0.5 * (G[a][b] - G[b][a]) for b in range(d)] for a in range(d)]
+        SS = sum(Sm[a][b] * Sm[a][b] for a in range(d) for b in range(d))
+        OO = sum(Om[a][b] * Om[a][b] for a in range(d) for b in range(d))
+        SSS = sum(Sm[a][b] * Sm[b][c] * Sm[c][a] for a in range(d) for b in range(d) for c in range(d))
+        St = np.sqrt(SS)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            W = np.where(St > 0.0, SSS / (St * St * St), 0.0)
+        phi = np.arccos(np.clip(math.sqrt(6.0) * W, -1.0, 1.0)) / 3.0
+        As = math.sqrt(6.0) * np.cos(phi)
+        Us = np.sqrt(SS + OO)
+        return As * Us, np.sqrt(2.0 * SS)
+
+    def realizable_ke(self, res):
+        """Realizable k-epsilon with the HFDIB treatment (the imposed rows and
+        P_ib of standard k-epsilon)."""
+        m = self.m
+        V = m.V
+        c = RKE
+        urf = self.opts["urf_turb"]
+        G, S2, Gk, Gmod = self._production()
+        AsUs, S = self.rke_coefficients(G)
+        alpha_w = self.ic | self.bcm
+        k_old = self.k
+        e_old = self.eps
+        # eps: C1 S eps - C2 eps^2 / (k + sqrt(nu eps)), nu + nu_t/sigma_eps
+        kk = np.maximum(k_old, K_MIN)
+        eta = S * kk / e_old
+        C1 = np.maximum(0.43, eta / (eta + 5.0))
+        gam = self.nu + self.nut / c["sige"]
+        aP, aM, aPl, b = assemble_transport(m, self.phi, gam, self.bnd.scalar_spec(self.eps_in))
+        aP = aP + c["C2"] * e_old / (kk + np.sqrt(self.nu * e_old)) * V
+        b = b + C1 * S * e_old * V
+        eps = self._turb_solve(aP, aM, aPl, b, e_old, alpha_w, self.eps_ib, urf, "eps", res)
+        eps = np.maximum(eps, EPS_MIN)
+        # k: P_k (P_ib in bc cells) - eps, nu + nu_t/sigma_k
+        gam = self.nu + self.nut / c["sigk"]
+        aP, aM, aPl, b = assemble_transport(m, self.phi, gam, self.bnd.scalar_spec(self.k_in))
+        aP = aP + eps / kk * V
+        b = b + Gmod * V
+        fixed_k = self.alpha_u > 0.5
+        k = self._turb_solve(aP, aM, aPl, b, k_old, fixed_k, self.k_ib, urf, "k", res)
+        k = np.maximum(k, K_MIN)
+        k = k + self.alpha_u * (self.k_ib - k)
+        self.k = k
+        self.eps = eps
+        self.omega = eps / (C_MU * np.maximum(k, K_MIN))
+        # nu_t = C_mu k^2/eps = k^2 / (A0 eps + A_s U* k)
+        self.nut = k * k / (c["A0"] * eps + AsUs * k)
 
     # ---------------------------------------------------------------- driver
     def max_residual(self, res):

@@ -14,7 +14,7 @@ A case is a dict with keys
              one cell thick, dz := sqrt(dx*dy) so that V^(1/3) = sqrt(dx*dy))
     lam    : float64 [nz, ny, nx]  lambda in [0, 1]
     ywall  : float64 [nz, ny, nx]  distance to the nearest no-slip wall
-    model  : 'laminar' | 'kepsilon' | 'komegasst'
+    model  : 'laminar' | 'kepsilon' | 'komegasst' | 'komega' | 'realizableke'
     Re, u_ref, l_ref           nu = u_ref * l_ref / Re
     bc     : dict side -> 'inlet' | 'outlet' | 'slip' | 'wall' | 'empty'
              for sides xmin, xmax, ymin, ymax, zmin, zmax
