@@ -44,7 +44,19 @@ typedef enum {
     HFDIB_ERR_TIMEOUT = -8        /* a device-wide barrier gave up (should not occur) */
 } hfdib_status;
 
-typedef enum { HFDIB_LAMINAR = 0, HFDIB_KEPSILON = 1, HFDIB_KOMEGA_SST = 2 } hfdib_model;
+/* Turbulence closures (Sec. 2.1 names four, each with the same HFDIB
+ * treatment: imposed eps/omega rows in ic and bc cells, imposed k rows where
+ * alpha_k = 1, P_ib in bc cells):
+ *   KEPSILON     : standard k-epsilon (Launder-Spalding coefficients)
+ *   KOMEGA_SST   : Menter's SST (needs ywall)
+ *   KOMEGA       : the k-omega model of Eq. hfdibkomega as printed (no
+ *                  cross-diffusion, no stress limiter), nu_t = k/omega,
+ *                  beta* 0.09, C_beta1 0.072, C_alpha1 0.52, 1/sigma 0.5
+ *   REALIZABLE_KE: Shih et al.'s realizable k-epsilon: C_mu = 1/(A0 + A_s U*
+ *                  k/eps) (A0 = 4), eps source C1 S eps, sink C2 eps^2/(k +
+ *                  sqrt(nu eps)), C2 1.9, sigma_k 1.0, sigma_eps 1.2 */
+typedef enum { HFDIB_LAMINAR = 0, HFDIB_KEPSILON = 1, HFDIB_KOMEGA_SST = 2, HFDIB_KOMEGA = 3,
+               HFDIB_REALIZABLE_KE = 4 } hfdib_model;
 
 /* Domain boundary kinds (Sec. 3.1 "Boundary conditions"):
  *  INLET  : Dirichlet u = u_in, k, eps/omega from Eq. (bcspkoein); zero-gradient p

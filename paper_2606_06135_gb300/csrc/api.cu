@@ -153,9 +153,9 @@ __global__ void k_init_state(Grid g, Params P, Fields F, int model) {
         F.k[c] = k;
         F.w[c] = P.w_in;
         // nu_t = C_mu k^2/eps = k/omega for the inlet pair
-        double eps = model == HFDIB_KEPSILON ? P.w_in : C_MU * P.k_in * P.w_in;
+        double eps = eps_model(model) ? P.w_in : C_MU * P.k_in * P.w_in;
         F.nut[c] = ic ? 0.0 : C_MU * k * k / eps;
-        F.w2[c] = model == HFDIB_KEPSILON ? P.w_in / (C_MU * fmax(k, K_MIN)) : C_MU * k * P.w_in;
+        F.w2[c] = eps_model(model) ? P.w_in / (C_MU * fmax(k, K_MIN)) : C_MU * k * P.w_in;
     }
 }
 
@@ -607,8 +607,8 @@ double* field_ptr(Ctx* h, int field, long long* n) {
         case HFDIB_FIELD_UZ: return h->g.dims == 3 ? h->F.u[2] : nullptr;
         case HFDIB_FIELD_P: return h->F.p;
         case HFDIB_FIELD_K: return h->model ? h->F.k : nullptr;
-        case HFDIB_FIELD_EPS: return h->model == HFDIB_KEPSILON ? h->F.w : (h->model ? h->F.w2 : nullptr);
-        case HFDIB_FIELD_OMEGA: return h->model == HFDIB_KOMEGA_SST ? h->F.w : (h->model ? h->F.w2 : nullptr);
+        case HFDIB_FIELD_EPS: return !h->model ? nullptr : (eps_model(h->model) ? h->F.w : h->F.w2);
+        case HFDIB_FIELD_OMEGA: return !h->model ? nullptr : (eps_model(h->model) ? h->F.w2 : h->F.w);
         case HFDIB_FIELD_NUT: return h->F.nut;
         case HFDIB_FIELD_PHIX: *n = h->g.nface[0]; return h->F.phi[0];
         case HFDIB_FIELD_PHIY: *n = h->g.nface[1]; return h->F.phi[1];
@@ -1044,7 +1044,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
     if (!grid || !lambda || !bc) return HFDIB_ERR_INVALID_ARG;
     if (grid->nx < 2 || grid->ny < 2 || grid->nz < 1) return HFDIB_ERR_INVALID_ARG;
     if (!(grid->dx > 0 && grid->dy > 0 && grid->dz > 0)) return HFDIB_ERR_INVALID_ARG;
-    if (model < HFDIB_LAMINAR || model > HFDIB_KOMEGA_SST) return HFDIB_ERR_INVALID_ARG;
+    if (model < HFDIB_LAMINAR || model > HFDIB_REALIZABLE_KE) return HFDIB_ERR_INVALID_ARG;
     if (model == HFDIB_KOMEGA_SST && !ywall) return HFDIB_ERR_INVALID_ARG;
     if (!(Re > 0) || !(bc->u_ref > 0) || !(bc->l_ref > 0)) return HFDIB_ERR_INVALID_ARG;
     long long N = (long long)grid->nx * grid->ny * grid->nz;
@@ -1115,7 +1115,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
     double ein = C_MU * pow(kin, 1.5) / bc->lt_in;
     double win = ein / (C_MU * kin);
     P.k_in = kin;
-    P.w_in = model == HFDIB_KOMEGA_SST ? win : ein;
+    P.w_in = eps_model(model) ? ein : win;
     if (model != HFDIB_LAMINAR && !(kin > 0 && bc->lt_in > 0)) { delete h; return HFDIB_ERR_INVALID_ARG; }
 
     int rc = HFDIB_OK;
@@ -1132,7 +1132,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
     }
     A(F.p, N); A(F.pn, N); A(F.pr, N); A(F.rAU, N);
     A(F.k, N); A(F.w, N); A(F.w2, N); A(F.nut, N); A(F.kib, N); A(F.wib, N);
-    A(F.G, 9 * N); A(F.mrow, 9 * N); A(F.Pk, N); A(F.S2, N); A(F.gam, N); A(F.gamk, N); A(F.sp, N); A(F.src, N);
+    A(F.G, 9 * N); A(F.mrow, 9 * N); A(F.Pk, N); A(F.S2, N); A(F.gam, N); A(F.gamk, N); A(F.sp, N); A(F.src, N); A(F.asus, N);
     A(F.bt, N); A(F.diag, N); A(F.ywall, N); A(F.flags, N);
     A(F.prhs, N); A(F.pdiag, N); A(F.r, N); A(F.z, N); A(F.d[0], N); A(F.d[1], N); A(F.q, N);
     A(F.scal, SC_NSCAL); A(F.partials, 16 * (long long)nb + 64); A(F.counters, 64);

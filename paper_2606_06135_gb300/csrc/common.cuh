@@ -29,7 +29,17 @@ constexpr double SST_AK1 = 0.85, SST_AK2 = 1.0, SST_AW1 = 0.5, SST_AW2 = 0.856;
 constexpr double SST_G1 = 5.0 / 9.0, SST_G2 = 0.44, SST_B1 = 0.075, SST_B2 = 0.0828;
 constexpr double SST_BSTAR = 0.09, SST_A1 = 0.31, SST_BB1 = 1.0, SST_C1 = 10.0;
 
+// k-omega of Eq. (hfdibkomega): beta*, C_beta1, C_alpha1, 1/sigma_k1, 1/sigma_omega1
+constexpr double KW_BSTAR = 0.09, KW_BETA = 0.072, KW_GAMMA = 0.52, KW_AK = 0.5, KW_AW = 0.5;
+// realizable k-epsilon (Shih et al.)
+constexpr double RKE_A0 = 4.0, RKE_C2 = 1.9, RKE_SIGK = 1.0, RKE_SIGE = 1.2;
+
 constexpr double K_MIN = 1e-14, EPS_MIN = 1e-14, OMEGA_MIN = 1e-14;
+
+// the second transported variable is eps (k-eps models) or omega (k-omega models)
+__host__ __device__ inline bool eps_model(int model) {
+    return model == HFDIB_KEPSILON || model == HFDIB_REALIZABLE_KE;
+}
 
 enum { TAG_FC = 0, TAG_BC = 1, TAG_IC = 2 };
 

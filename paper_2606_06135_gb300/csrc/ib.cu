@@ -361,7 +361,7 @@ __global__ void k_imposed(Grid g, int model, int freeze, BcList bl, uint16_t* __
         double w = lamb ? 6.0 * g.nu / (BETA1_WF * ye * ye) : ut / (KAPPA * sqrt(C_MU) * ye);
         // eps = C_mu k omega with the k the cell takes this sweep: k_ib where
         // k is imposed (laminar branch), the old k_P where k is solved
-        wib[c] = (model == HFDIB_KEPSILON) ? C_MU * (lamb ? kimp : kP) * w : w;
+        wib[c] = eps_model(model) ? C_MU * (lamb ? kimp : kP) * w : w;
     }
 }
 

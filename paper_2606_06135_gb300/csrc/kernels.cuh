@@ -77,6 +77,7 @@ struct Fields {
     double* gamk;
     double* sp;        // extra implicit diagonal (integrated)
     double* src;       // explicit source (integrated)
+    double* asus;      // realizable k-eps: A_s U* of the velocity gradient (for nu_t)
     double* bt;        // relaxed right-hand side
     double* diag;      // relaxed diagonal
     double* ywall;

@@ -4,9 +4,10 @@
 // alphaomega, "matrix manipulation"), the k equation with its rows fixed to
 // k_ib where alpha_k = 1 followed by the k correction, and nu_t.
 //
-// Models: standard k-epsilon (Launder-Spalding) and k-omega SST (Menter),
-// both with their published coefficients; the paper cites them without
-// printing the equations.  eq = 0 is eps (k-epsilon) or omega (SST), eq = 1 is k.
+// Models (Sec. 2.1): standard k-epsilon (Launder-Spalding), k-omega SST
+// (Menter), the k-omega model of Eq. hfdibkomega, and realizable k-epsilon
+// (Shih et al.), with their published coefficients.  eq = 0 is eps (k-eps
+// models) or omega (k-omega models), eq = 1 is k.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -63,6 +64,51 @@ __global__ void k_turb_prep(Grid g, Params P, Fields F) {
         F.sp[c] = KE_C2 * ratio * V;
         F.src[c] = KE_C1 * (nut * S2) * ratio * V;
         F.gamk[c] = g.nu + nut / KE_SIGK;
+        if (F.mixed) { F.gam32[c] = (float)F.gam[c]; F.gamk32[c] = (float)F.gamk[c]; }
+    } else if (P.model == HFDIB_KOMEGA) {
+        // Eq. hfdibkomega: omega source C_alpha1 (omega/k) P_k, sink C_beta1 omega^2
+        F.gam[c] = g.nu + KW_AW * nut;
+        F.sp[c] = KW_BETA * wold * V;
+        F.src[c] = KW_GAMMA * wold / fmax(kold, K_MIN) * (nut * S2) * V;
+        F.gamk[c] = g.nu + KW_AK * nut;
+        if (F.mixed) { F.gam32[c] = (float)F.gam[c]; F.gamk32[c] = (float)F.gamk[c]; }
+    } else if (P.model == HFDIB_REALIZABLE_KE) {
+        // S_ij, Omega_ij of grad u; W = S_ij S_jk S_ki / S~^3 (0 where S~ = 0),
+        // A_s = sqrt(6) cos(acos(sqrt(6) W)/3), U* = sqrt(S:S + Omega:Omega)
+        double Sm[3][3], SS = 0.0, OO = 0.0;
+        #pragma unroll
+        for (int a = 0; a < 3; ++a)
+            #pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                double gab = (a < g.dims && b < g.dims) ? F.G[(long long)(3 * a + b) * g.N + c] : 0.0;
+                double gba = (a < g.dims && b < g.dims) ? F.G[(long long)(3 * b + a) * g.N + c] : 0.0;
+                Sm[a][b] = 0.5 * (gab + gba);
+                double o = 0.5 * (gab - gba);
+                SS += Sm[a][b] * Sm[a][b];
+                OO += o * o;
+            }
+        double SSS = 0.0;
+        #pragma unroll
+        for (int a = 0; a < 3; ++a)
+            #pragma unroll
+            for (int b = 0; b < 3; ++b)
+                #pragma unroll
+                for (int d = 0; d < 3; ++d) SSS += Sm[a][b] * Sm[b][d] * Sm[d][a];
+        double St = sqrt(SS);
+        double W = St > 0.0 ? SSS / (St * St * St) : 0.0;
+        double arg = fmin(fmax(sqrt(6.0) * W, -1.0), 1.0);
+        // cos(acos(arg)/3) through cospi: its argument is in [0, 1/3], and
+        // cospi needs no large-argument reduction (no local-memory path)
+        double As = sqrt(6.0) * cospi(acos(arg) * (1.0 / (3.0 * 3.14159265358979323846)));
+        F.asus[c] = As * sqrt(SS + OO);
+        double S = sqrt(S2);
+        double kk = fmax(kold, K_MIN);
+        double eta = S * kk / wold;
+        double C1 = fmax(0.43, eta / (eta + 5.0));
+        F.gam[c] = g.nu + nut / RKE_SIGE;
+        F.sp[c] = RKE_C2 * wold / (kk + sqrt(g.nu * wold)) * V;
+        F.src[c] = C1 * S * wold * V;
+        F.gamk[c] = g.nu + nut / RKE_SIGK;
         if (F.mixed) { F.gam32[c] = (float)F.gam[c]; F.gamk32[c] = (float)F.gamk[c]; }
     } else {
         double gk = 0.0;
@@ -281,12 +327,15 @@ __global__ void k_k_prep(Grid g, Params P, Fields F) {
     if (c >= g.N) return;
     double w = F.w[c];
     if (F.mixed) w += (double)F.d32[0][c];   // apply the FP32 correction
-    double wmin = P.model == HFDIB_KEPSILON ? EPS_MIN : OMEGA_MIN;
+    double wmin = eps_model(P.model) ? EPS_MIN : OMEGA_MIN;
     w = fmax(w, wmin);
     F.w[c] = w;
     double kold = F.k[c];
-    if (P.model == HFDIB_KEPSILON) {
+    if (eps_model(P.model)) {
         F.sp[c] = w / fmax(kold, K_MIN) * g.V;
+        F.src[c] = F.Pk[c] * g.V;
+    } else if (P.model == HFDIB_KOMEGA) {
+        F.sp[c] = KW_BSTAR * w * g.V;
         F.src[c] = F.Pk[c] * g.V;
     } else {
         F.sp[c] = SST_BSTAR * w * g.V;
@@ -310,6 +359,13 @@ __global__ void k_turb_final(Grid g, Params P, Fields F) {
     if (P.model == HFDIB_KEPSILON) {
         nut = C_MU * k * k / w;
         F.w2[c] = w / (C_MU * fmax(k, K_MIN));
+    } else if (P.model == HFDIB_REALIZABLE_KE) {
+        // C_mu k^2/eps = k^2 / (A0 eps + A_s U* k)
+        nut = k * k / (RKE_A0 * w + F.asus[c] * k);
+        F.w2[c] = w / (C_MU * fmax(k, K_MIN));
+    } else if (P.model == HFDIB_KOMEGA) {
+        nut = k / w;
+        F.w2[c] = C_MU * k * w;
     } else {
         double y = fmax(F.ywall[c], 1e-3 * g.h);
         double F2 = sst_F2(fmax(k, K_MIN), w, y, g.nu);

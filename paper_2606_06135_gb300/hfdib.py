@@ -16,8 +16,9 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(HERE, "lib", "libhfdib.so")
 
-LAMINAR, KEPSILON, KOMEGA_SST = 0, 1, 2
-MODELS = {"laminar": LAMINAR, "kepsilon": KEPSILON, "komegasst": KOMEGA_SST}
+LAMINAR, KEPSILON, KOMEGA_SST, KOMEGA, REALIZABLE_KE = 0, 1, 2, 3, 4
+MODELS = {"laminar": LAMINAR, "kepsilon": KEPSILON, "komegasst": KOMEGA_SST, "komega": KOMEGA,
+          "realizableke": REALIZABLE_KE}
 BC_KIND = {"inlet": 0, "outlet": 1, "slip": 2, "wall": 3, "empty": 4}
 SIDES = ("xmin", "xmax", "ymin", "ymax", "zmin", "zmax")
 FIELDS = {"ux": 0, "uy": 1, "uz": 2, "p": 3, "k": 4, "eps": 5, "omega": 6, "nut": 7,

@@ -86,9 +86,20 @@ SWEEP_CASES = {
     "cylinder_keps": lambda: G.case_cylinder(48, 24),
     "bfs_sst": lambda: G.case_bfs(64, 16),
     "bfs_keps": lambda: G.case_bfs(64, 16, model="kepsilon"),
+    "bfs_komega": lambda: G.case_bfs(64, 16, model="komega"),
+    "bfs_rke": lambda: G.case_bfs(64, 16, model="realizableke"),
+    "cylinder_komega": lambda: G.case_cylinder(48, 24, model="komega"),
+    "cylinder_rke": lambda: G.case_cylinder(48, 24, model="realizableke"),
 }
 
 EXACT = dict(n_u=600, n_turb=600, p_reltol=1e-15, p_maxiter=4000)
+
+# The realizable k-eps step after three sweeps has a small pressure (|p| ~ 1.1
+# against ~28 for standard k-eps) that moves ~400x the relative change of
+# nu_t (oracle alone: a 1e-15 relative perturbation of nu_t per sweep moves p
+# by 4e-13).  Rounding-level nu_t differences of ~1e-12 therefore reach p at
+# ~2e-9; every other field agrees to ~1e-11, as does p once converged.
+SWEEP_TOL = {"bfs_rke": 1e-8}
 
 
 @pytest.mark.parametrize("name", sorted(SWEEP_CASES))
@@ -99,7 +110,7 @@ def test_sweeps_match_oracle_with_exact_inner_solves(name):
     for n in range(3):
         o.sweep()
         s.sweep()
-    compare_fields(s, o, 1e-9)
+    compare_fields(s, o, SWEEP_TOL.get(name, 1e-9))
     s.close()
 
 
@@ -107,6 +118,8 @@ CONVERGED = {
     "channel_laminar": (lambda: G.case_channel(8, 24, Re=10.0), 3000),
     "cylinder_keps": (lambda: G.case_cylinder(64, 32), 6000),
     "bfs_sst": (lambda: G.case_bfs(128, 32), 8000),
+    "cylinder_komega": (lambda: G.case_cylinder(64, 32, model="komega"), 6000),
+    "bfs_rke": (lambda: G.case_bfs(128, 32, model="realizableke"), 8000),
 }
 
 
