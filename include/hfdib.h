@@ -123,7 +123,9 @@ typedef struct {
                                     nu_t, k and eps/omega keep their values; the
                                     flow problem whose adjoint hfdib_adjoint_grad
                                     differentiates (0)                             */
-    int32_t reserved;
+    int32_t wall_distance;       /* distance in y+ (Eq. yplus) and omega_ib (Eq.
+                                    omegaws): 0 y_eff = (y_perp + h/2)/2 (default),
+                                    1 y_perp (the comparison of App. A)           */
 } hfdib_options;
 
 typedef struct hfdib_ctx* hfdib_handle;
@@ -276,6 +278,16 @@ int hfdib_ib_force(hfdib_handle h, double* force);
  *   n_faces_out : host pointer, nullable
  * Asynchronous on the handle's stream. */
 int hfdib_wall_shear(hfdib_handle h, int side, double* tau, int64_t* n_faces_out);
+
+/* hfdib_recirculation -- size of the recirculation region behind a body
+ * (Sec. 3.6): the cells outside the solid (not in-solid cells) whose centre
+ * lies downstream of x_rear (x_c > x_rear) and whose u_x is negative.
+ *   x_rear : x of the body's rear end (finite)
+ *   out    : HOST pointer, 3 doubles: [0] length = the largest x_c - x_rear
+ *            over those cells (0 when there is none), [1] volume = their
+ *            number times the cell volume, [2] their number.
+ * Waits for the handle's stream.  Errors: INVALID_ARG (NULL, NaN), CUDA. */
+int hfdib_recirculation(hfdib_handle h, double x_rear, double* out);
 
 /* Copy a field (HFDIB_FIELD_*) device-to-device into dst (caller-owned, sized
  * like the field: cells, or faces (nx+1)*ny*nz / nx*(ny+1)*nz / nx*ny*(nz+1)). */

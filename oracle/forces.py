@@ -32,6 +32,11 @@ for each tangential component, with nu_eff,P = nu + nu_t,P as on the face.
 C_f = 2 tau_w / |u_in|^2.  The reattachment point is the downstream end of
 the main recirculation: the last sign change of tau_x from negative to
 positive, located by linear interpolation between cell centres.
+
+Recirculation region (Sec. 3.6): the cells with negative u_x behind the body.
+Read as cells outside the solid (not ic) whose centre lies downstream of the
+body's rear end x_rear; its length is the largest distance from x_rear to
+such a cell centre, its volume the sum of their volumes.
 """
 from __future__ import annotations
 
@@ -118,3 +123,14 @@ def reattachment(x, tau_x):
         return None
     i = int(idx[-1])
     return float(x[i] - t[i] * (x[i + 1] - x[i]) / (t[i + 1] - t[i]))
+
+
+def recirculation(o, x_rear):
+    """(length, volume, cells) of the recirculation region behind x_rear."""
+    m = o.m
+    X = m.x0 + (np.arange(m.nx) + 0.5) * m.dx
+    X = np.broadcast_to(X[None, None, :], m.shape)
+    sel = (~o.ic) & (X > x_rear) & (o.u[0] < 0.0)
+    n = int(sel.sum())
+    length = float((X[sel] - x_rear).max()) if n else 0.0
+    return length, n * m.V, n

@@ -87,7 +87,9 @@ OMEGA_MIN = 1e-14
 
 TAG_FC, TAG_BC, TAG_IC = 0, 1, 2
 
-DEFAULT_OPTS = dict(urf_u=0.7, urf_p=0.3, urf_turb=0.85, freeze_switch=0)
+# wall_distance: "y_eff" (Eq. yplus, default) or "y_perp", the distance the
+# wall functions use in y+ and omega_ib (the comparison of App. A)
+DEFAULT_OPTS = dict(urf_u=0.7, urf_p=0.3, urf_turb=0.85, freeze_switch=0, wall_distance="y_eff")
 
 
 def _zeros(shape, *like):
@@ -665,7 +667,9 @@ class Oracle:
         kP = kf[cells]
         # Eq. frictionvel, Eq. yplus
         ut = C_MU ** 0.25 * np.sqrt(kP)
-        yplus = geo["y_eff"] * ut / self.nu
+        # Eq. yplus uses y_eff; App. A compares it with y_perp
+        ywf = geo["y_perp"] if self.opts.get("wall_distance", "y_eff") == "y_perp" else geo["y_eff"]
+        yplus = ywf * ut / self.nu
         lamb = (yplus <= YPLUS_LAM) if turb else np.ones(len(cells), bool)
         # reading (opt-in, not in the paper): from sweep `freeze_switch` on, a
         # bc cell may leave the laminar branch but never re-enter it.  The
@@ -704,7 +708,7 @@ class Oracle:
             # Eq. omegaws, written with y+ = y_eff u_tau / nu substituted:
             # lam: (u_tau^2/nu) 6/(beta1 y+^2) = 6 nu/(beta1 y_eff^2)
             # log: (u_tau^2/nu) /(kappa sqrt(C_nu) y+) = u_tau/(kappa sqrt(C_nu) y_eff)
-            ye = geo["y_eff"]
+            ye = ywf
             wl = 6.0 * self.nu / (BETA1_WF * ye ** 2)
             wg = ut / (KAPPA * math.sqrt(C_MU) * ye)
             wv = np.where(lamb, wl, wg)

@@ -1061,6 +1061,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
     if (o.n_u < 1 || o.n_turb < 1 || o.p_maxiter < 0 || !(o.p_reltol >= 0)) return HFDIB_ERR_INVALID_ARG;
     if (o.precond < 0 || o.precond > 1 || o.p_check < 0 || o.mg_coarse_sweeps < 0) return HFDIB_ERR_INVALID_ARG;
     if (o.precision < 0 || o.precision > 1) return HFDIB_ERR_INVALID_ARG;
+    if (o.wall_distance < 0 || o.wall_distance > 1) return HFDIB_ERR_INVALID_ARG;
     // the mixed path runs its FP32 V-cycle inside the persistent CG kernel
     if (o.precision == 1 && (o.p_persistent == 0 || o.precond != 1)) return HFDIB_ERR_INVALID_ARG;
     if (o.p_maxiter > 100000 || o.freeze_switch < 0) return HFDIB_ERR_INVALID_ARG;
@@ -1225,6 +1226,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
     A(bl.b2, 3 * (long long)nbc); A(bl.lamb, nbc); A(bl.n, 3 * (long long)nbc); A(bl.yp, nbc);
     A(bl.ye, nbc); A(bl.wS, nbc); A(bl.w1, nbc); A(bl.w2, nbc); A(bl.t1, 3 * (long long)nbc);
     A(bl.t2, 3 * (long long)nbc); A(bl.yplus, nbc);
+    bl.ywf = o.wall_distance ? bl.yp : bl.ye;
 #undef A
     if (rc) { free_all(h); delete h; return rc; }
     if (nbc > 0 && cudaMemcpyAsync(bl.cell, F.bt, nbc * sizeof(int), cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
@@ -1490,6 +1492,27 @@ int hfdib_wall_shear(hfdib_handle hh, int side, double* tau, int64_t* n_faces_ou
     if (!tau) return HFDIB_OK;
     launch_wall_shear(g, h->F, side, nf, tau, h->stream);
     CK(cudaGetLastError());
+    return HFDIB_OK;
+}
+
+int hfdib_recirculation(hfdib_handle hh, double x_rear, double* out) {
+    Ctx* h = (Ctx*)hh;
+    if (!h || !out || !(x_rear == x_rear)) return HFDIB_ERR_INVALID_ARG;
+    const Grid& g = h->g;
+    const Fields& F = h->F;
+    cudaStream_t s = h->stream;
+    unsigned int* count = F.counters + 13;
+    CK(cudaMemsetAsync(count, 0, sizeof(unsigned int), s));
+    launch_recirc(g, F, x_rear, count, s);
+    CK(cudaGetLastError());
+    double len = 0.0;
+    unsigned int n = 0;
+    CK(cudaMemcpyAsync(&len, F.scal + SC_RECIRC, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&n, count, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    out[0] = n ? len : 0.0;
+    out[1] = (double)n * g.V;
+    out[2] = (double)n;
     return HFDIB_OK;
 }
 

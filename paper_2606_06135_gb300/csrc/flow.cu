@@ -522,6 +522,31 @@ __global__ void k_wall_shear(Grid g, Fields F, int side, long long nf, double* t
     }
 }
 
+// ---------------------------------------------------------------- recirculation
+// The recirculation region behind a body (Sec. 3.6): cells outside the solid
+// (not ic) with centre x > x_rear and u_x < 0.  Out: scal[SC_RECIRC] = the
+// largest x_c - x_rear over them (-1e308 when there is none); *count = their
+// number (integer atomics: exact), so the volume is count V.
+__global__ void k_recirc(Grid g, Fields F, double x_rear, unsigned int* count) {
+    double v[1] = {-1.0e308};
+    unsigned int n = 0;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < g.N;
+         c += (long long)gridDim.x * blockDim.x) {
+        if (tag_of(F.flags[c]) == TAG_IC || !(F.u[0][c] < 0.0)) continue;
+        int i, j, k;
+        cell_ijk(g, c, i, j, k);
+        // centre x without contraction into an FMA (the same rounding as a
+        // plain multiply-add on the host)
+        double dx = __dsub_rn(__dadd_rn(g.o[0], __dmul_rn(i + 0.5, g.D[0])), x_rear);
+        if (dx > 0.0) {
+            v[0] = fmax(v[0], dx);
+            ++n;
+        }
+    }
+    if (n) atomicAdd(count, n);
+    grid_reduce<1, true>(v, F.partials, F.counters + 14, F.scal + SC_RECIRC);
+}
+
 // ---------------------------------------------------------------- sweep end
 __global__ void k_sweep_end(Fields F, int dims, int model, double* res_out, double* hist, int nhist) {
     double* s = F.scal;
@@ -586,6 +611,9 @@ void launch_ib_force(const Grid& g, const Fields& F, cudaStream_t s) {
 }
 void launch_wall_shear(const Grid& g, const Fields& F, int side, long long nf, double* tau, cudaStream_t s) {
     if (nf > 0) k_wall_shear<<<nblocks(nf), BLOCK, 0, s>>>(g, F, side, nf, tau);
+}
+void launch_recirc(const Grid& g, const Fields& F, double x_rear, unsigned int* count, cudaStream_t s) {
+    k_recirc<<<rblocks(g.N), BLOCK, 0, s>>>(g, F, x_rear, count);
 }
 void launch_sweep_end(const Params& P, const Fields& F, int dims, double* res_out, double* hist, int nhist,
                       cudaStream_t s) {

@@ -320,7 +320,7 @@ __global__ void k_imposed(Grid g, int model, int freeze, BcList bl, uint16_t* __
     const int* b2 = bl.b2 + 3 * q;
     const double* t1 = bl.t1 + 3 * q;
     const double* t2 = bl.t2 + 3 * q;
-    double wS = bl.wS[q], w1 = bl.w1[q], w2 = bl.w2[q], ye = bl.ye[q];
+    double wS = bl.wS[q], w1 = bl.w1[q], w2 = bl.w2[q], ye = bl.ywf[q];
     bool turb = model != HFDIB_LAMINAR;
     double kP = turb ? kf[c] : 0.0;
     double ut = pow(C_MU, 0.25) * sqrt(kP);

@@ -17,6 +17,7 @@ struct BcList {
     double* n;      // [3*nbc] outer unit normal
     double* yp;     // y_perp
     double* ye;     // y_eff
+    const double* ywf;  // the distance the wall functions use: ye (Eq. yplus) or yp (App. A)
     double *wS, *w1, *w2;  // quadratic weights
     double* t1;     // [3*nbc]
     double* t2;     // [3*nbc]
@@ -47,6 +48,7 @@ enum {
     SC_TIMEOUT = 46,             // 1 once a persistent kernel's grid barrier gave up
     SC_PCG_INIT = 40,            // r0.z0, r0.r0, b.b, then the 3 scaled-residual sums of p
     SC_FORCE = 52,               // 6: force on the body, pressure part xyz then the rest xyz
+    SC_RECIRC = 58,              // largest x - x_rear of a recirculating cell
     SC_NSCAL = 64
 };
 
@@ -158,6 +160,7 @@ void launch_means(const Grid& g, const Params& P, const Fields& F, cudaStream_t 
 void launch_grad_u(const Grid& g, const Fields& F, cudaStream_t s);
 void launch_mom_asm(const Grid& g, const Params& P, const Fields& F, cudaStream_t s);
 void launch_ib_force(const Grid& g, const Fields& F, cudaStream_t s);
+void launch_recirc(const Grid& g, const Fields& F, double x_rear, unsigned int* count, cudaStream_t s);
 void launch_wall_shear(const Grid& g, const Fields& F, int side, long long nf, double* tau, cudaStream_t s);
 void launch_mom_smooth(const Grid& g, const Params& P, const Fields& F, int colour, cudaStream_t s);
 void launch_hbya(const Grid& g, const Params& P, const Fields& F, cudaStream_t s);

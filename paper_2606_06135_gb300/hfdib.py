@@ -64,7 +64,7 @@ class Options(C.Structure):
                 ("p_maxiter", C.c_int32), ("precision", C.c_int32), ("precond", C.c_int32),
                 ("p_check", C.c_int32), ("mg_coarse_sweeps", C.c_int32), ("graph", C.c_int32),
                 ("p_persistent", C.c_int32), ("freeze_switch", C.c_int32), ("frozen_turbulence", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("wall_distance", C.c_int32)]
 
 
 _LIB = None
@@ -74,7 +74,8 @@ EXPORTED = ("hfdib_default_options", "hfdib_create", "hfdib_simple_sweep", "hfdi
             "hfdib_get_history", "hfdib_get_state", "hfdib_set_state", "hfdib_get_counters",
             "hfdib_error_string", "hfdib_destroy", "hfdib_profile_sweeps", "hfdib_get_launch_counts",
             "hfdib_classify_noalloc", "hfdib_create_batch", "hfdib_batch_sweep", "hfdib_batch_solve_steady",
-            "hfdib_batch_handle", "hfdib_batch_autotune", "hfdib_destroy_batch", "hfdib_adjoint_grad")
+            "hfdib_batch_handle", "hfdib_batch_autotune", "hfdib_destroy_batch", "hfdib_adjoint_grad",
+            "hfdib_ib_force", "hfdib_wall_shear", "hfdib_recirculation")
 KERNEL_CLASSES = ("imposed", "grad_u", "mom_asm", "mom_smooth", "hbya", "p_coef", "pcg", "vcycle0",
                   "update", "turb_prep", "scal_asm", "scal_smooth", "turb_final", "sweep_end")
 
@@ -126,6 +127,8 @@ def load_library(path=LIBPATH):
     lib.hfdib_ib_force.restype = i32
     lib.hfdib_wall_shear.argtypes = [vp, i32, vp, C.POINTER(i64)]
     lib.hfdib_wall_shear.restype = i32
+    lib.hfdib_recirculation.argtypes = [vp, dbl, vp]
+    lib.hfdib_recirculation.restype = i32
     lib.hfdib_error_string.argtypes = [i32]
     lib.hfdib_error_string.restype = C.c_char_p
     lib.hfdib_destroy.argtypes = [vp]
@@ -363,6 +366,14 @@ class Solver:
         _check(self.lib.hfdib_wall_shear(self.h, sid, C.c_void_p(out.data_ptr()), None), "hfdib_wall_shear")
         self.stream.synchronize()
         return out
+
+    def recirculation(self, x_rear):
+        """(length, volume, cells) of the region behind x_rear with u_x < 0
+        (hfdib_recirculation)."""
+        out = np.zeros(3)
+        self.stream.synchronize()
+        _check(self.lib.hfdib_recirculation(self.h, float(x_rear), out.ctypes.data), "hfdib_recirculation")
+        return float(out[0]), float(out[1]), int(out[2])
 
     def get_state(self):
         n = C.c_size_t(0)

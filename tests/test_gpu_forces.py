@@ -9,6 +9,9 @@ oracle and the closed form of developed duct flow.
   within 1e-9 (relative to max |tau|), on a k-omega SST and a k-epsilon
   backward-facing step, including the closed faces under the step.
 * Developed laminar duct flow on the GPU: tau_w = 6 nu U H / (H^2 + 2 Delta^2).
+* Recirculation (hfdib_recirculation, Sec. 3.6) on identical inputs: the
+  same cells as the oracle's definition, bit for bit, on the 64 x 16 and the
+  1024 x 256 step.
 """
 import math
 
@@ -151,4 +154,47 @@ def test_wall_shear_rejects_non_wall_sides():
         s.wall_shear("ymin")          # slip, not a wall
     with pytest.raises(HfdibError):
         s.wall_shear("zmin")          # beyond a 2D grid
+    s.close()
+
+
+def test_recirculation_matches_oracle_on_the_same_state():
+    """Integer decisions (u_x < 0, x_c > x_rear) on identical inputs: the
+    oracle's converged step loaded into the GPU solver gives the same cells,
+    hence the same count, volume and length, bit for bit."""
+    from paper_2606_06135_gb300.hfdib import Solver
+    case = G.case_bfs(64, 16, model="komegasst")
+    o = oracle_converged(case, tol=1e-8)
+    s = Solver(case)
+    for name, val in (("ux", o.u[0]), ("uy", o.u[1]), ("p", o.p), ("k", o.k), ("omega", o.omega)):
+        s.set_field(name, val)
+    for x_rear in (0.0, 1.0, 1e9):
+        got = s.recirculation(x_rear)
+        ref = Fo.recirculation(o, x_rear)
+        assert got[2] == ref[2] and got[0] == ref[0] and got[1] == ref[1], (x_rear, got, ref)
+    assert s.recirculation(0.0)[2] > 0
+    s.close()
+
+
+class _State:
+    """The oracle's view (mesh, in-solid mask, velocity) of a GPU state."""
+    def __init__(self, case, s):
+        self.m = O.Mesh(case["grid"])
+        tags, _ = s.tags()
+        self.ic = tags == O.TAG_IC
+        f = s.fields()
+        self.u = [f["ux"], f["uy"]]
+
+
+def test_recirculation_on_the_full_step():
+    """1024 x 256 step after 2000 sweeps: the GPU metric equals the oracle's
+    definition applied to the GPU's own fields."""
+    from paper_2606_06135_gb300.hfdib import Solver
+    case = G.case_bfs(1024, 256)
+    s = Solver(case, precision=1, freeze_switch=300)
+    s.sweep(2000, read=False)
+    st = _State(case, s)
+    got = s.recirculation(0.0)
+    ref = Fo.recirculation(st, 0.0)
+    assert got[2] == ref[2] and got[0] == ref[0] and got[1] == ref[1], (got, ref)
+    assert got[2] > 100
     s.close()

@@ -90,6 +90,7 @@ SWEEP_CASES = {
     "bfs_rke": lambda: G.case_bfs(64, 16, model="realizableke"),
     "cylinder_komega": lambda: G.case_cylinder(48, 24, model="komega"),
     "cylinder_rke": lambda: G.case_cylinder(48, 24, model="realizableke"),
+    "bfs_keps_yperp": lambda: G.case_bfs(64, 16, model="kepsilon"),
 }
 
 EXACT = dict(n_u=600, n_turb=600, p_reltol=1e-15, p_maxiter=4000)
@@ -101,12 +102,16 @@ EXACT = dict(n_u=600, n_turb=600, p_reltol=1e-15, p_maxiter=4000)
 # ~2e-9; every other field agrees to ~1e-11, as does p once converged.
 SWEEP_TOL = {"bfs_rke": 1e-8}
 
+# (GPU options, oracle options) of cases that change an option
+SWEEP_OPTS = {"bfs_keps_yperp": (dict(wall_distance=1), dict(wall_distance="y_perp"))}
+
 
 @pytest.mark.parametrize("name", sorted(SWEEP_CASES))
 def test_sweeps_match_oracle_with_exact_inner_solves(name):
     case = SWEEP_CASES[name]()
-    o = O.Oracle(case)
-    s = make_solver(case, **EXACT)
+    gopt, oopt = SWEEP_OPTS.get(name, ({}, None))
+    o = O.Oracle(case, oopt)
+    s = make_solver(case, **EXACT, **gopt)
     for n in range(3):
         o.sweep()
         s.sweep()

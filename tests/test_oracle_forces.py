@@ -182,3 +182,20 @@ def test_reattachment_interpolates_the_last_upward_zero():
     t = np.array([0.5, 0.2, -0.1, -0.4, -0.3, -0.2, 0.2, 0.4, 0.5, 0.6])
     assert abs(Fo.reattachment(x, t) - 5.5) <= 1e-15
     assert Fo.reattachment(x, np.abs(t) + 0.1) is None
+
+
+@pytest.mark.parametrize("model", ["komegasst", "kepsilon"])
+def test_recirculation_ends_at_the_reattachment_point(model):
+    """Behind the step the furthest recirculating cell sits on the bottom
+    wall, where tau_x has the sign of u_x: its centre L and the zero of tau_x
+    satisfy L <= x_reat < L + dx (two definitions of Sec. 3.3 and 3.6)."""
+    o = converged(G.case_bfs(64, 16, model=model), tol=1e-8, max_iter=3000)
+    m = o.m
+    xs = m.x0 + (np.arange(m.nx) + 0.5) * m.dx
+    x_reat = Fo.reattachment(xs, Fo.wall_shear(o, "ymin")[0])
+    L, V, n = Fo.recirculation(o, 0.0)
+    assert n > 0 and abs(V - n * m.V) <= 1e-15 * V
+    assert L <= x_reat < L + m.dx, (L, x_reat)
+    # nothing recirculates upstream of the step's rear end inside the solid
+    L0, V0, n0 = Fo.recirculation(o, 1e9)
+    assert (L0, V0, n0) == (0.0, 0.0, 0)

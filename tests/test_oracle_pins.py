@@ -378,3 +378,35 @@ def test_keps_random_obstacle_converges():
     assert o.max_residual(res) <= 1e-6, (it, res)
     assert res["cont"] < 1e-12
     assert np.isfinite(o.nut).all() and o.nut.max() < 1.0
+
+
+@pytest.mark.parametrize("wall_distance", ["y_eff", "y_perp"])
+def test_wall_distance_option_on_the_flat_wall(wall_distance):
+    """y+ (Eq. yplus) and the laminar-branch omega_ib (Eq. omegaws) use y_eff =
+    (y_perp + h/2)/2 by default and y_perp under the App. A option; on the
+    flat wall y_perp = 0.2 (golden) and h = 1, so y_eff = 0.35."""
+    gold = read_golden_tags()
+    case = flat_wall_case(2.3)
+    case["model"] = "komegasst"
+    o = O.Oracle(case, dict(wall_distance=wall_distance))
+    o.k = np.full(o.m.shape, 0.01)
+    o.imposed_fields()
+    y = gold["yperp_row2"] if wall_distance == "y_perp" else 0.5 * (gold["yperp_row2"] + 0.5)
+    ut = O.C_MU ** 0.25 * math.sqrt(0.01)
+    np.testing.assert_allclose(o.yplus_bc, y * ut / o.nu, rtol=1e-13)
+    cells = o.geo["cell"]
+    lam = o.lam_branch
+    assert lam.all()                         # y+ < 11 at nu = 0.01: laminar branch
+    np.testing.assert_allclose(o.omega_ib.ravel()[cells], 6.0 * o.nu / (O.BETA1_WF * y * y), rtol=1e-13)
+
+
+def test_wall_distance_option_changes_the_step():
+    """On the k-eps step the two distances give different sweeps (the option
+    reaches omega_ib / eps_ib and the branch of Eq. alphauk)."""
+    case = G.case_bfs(64, 16, model="kepsilon")
+    a = O.Oracle(case)
+    b = O.Oracle(case, dict(wall_distance="y_perp"))
+    for _ in range(3):
+        a.sweep()
+        b.sweep()
+    assert np.linalg.norm(a.eps - b.eps) > 1e-3 * np.linalg.norm(a.eps)
