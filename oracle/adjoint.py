@@ -8,8 +8,9 @@ What is differentiated.  A converged state is a fixed point of the extended
 SIMPLE sweep (Fig. simplehfdibrans).  Hold fixed the turbulence fields (nu_t,
 k, eps/omega), the cell groups (Sec. 2.3), the wall-function branch of each bc
 cell (alpha_u, Eq. alphauk), the closed boundary faces, the continuity mask m
-and the integer choices of the bc-cell geometry (in-solid neighbour, y_perp
-case, interpolation cells, clamps).  The fixed point z = (u, p, phi) then
+(under reading A, m = [lambda < 1]; under reading B, m = 1 - lambda is smooth
+and differentiated) and the integer choices of the bc-cell geometry
+(in-solid neighbour, y_perp case, interpolation cells, clamps).  The fixed point z = (u, p, phi) then
 solves the steady equations R(z; lambda) = 0:
 
   momentum, every cell and component:
@@ -26,9 +27,10 @@ In free rows ut = u and the first line is the steady momentum equation; in
 imposed rows it is the velocity update u = HbyA - rAU grad p of a8 at the
 fixed point.  Each line is assembled from the oracle's own blocks.
 
-lambda enters R only through u_ib: the normal n = -grad(lambda)/|grad(lambda)|
+lambda enters R through u_ib: the normal n = -grad(lambda)/|grad(lambda)|
 (Eq. yorthoaux), y_perp (Eq. yortho with sigma = h atanh(1 - 2 lambda)) and
-through them the interpolation fractions and the quadratic weights.
+through them the interpolation fractions and the quadratic weights; under
+reading B also through m in the pressure line.
 
 Objectives.  Pressure drop: J = mean p over the cells on open inlet faces
 minus mean p over the cells on outlet faces.  Drag: J = minus the sum over
@@ -240,7 +242,11 @@ class FrozenSteady:
         rAU = m.V / aavg
         phiH = o._flux_of(H)
         coef, pA_P, pA_M, pA_Pl, prhs = o.pressure_operator(rAU)
-        Rp = pA_P * p + O.apply_offdiag(m, pA_M, pA_Pl, p) + np.where(o.mask_m, o.divergence(phiH), 0.0) - prhs
+        if o.opts.get("continuity_mask", "A") == "B":
+            cm = 1.0 - lam
+        else:
+            cm = np.where(o.mask_m, 1.0, 0.0)
+        Rp = pA_P * p + O.apply_offdiag(m, pA_M, pA_Pl, p) + cm * o.divergence(phiH) - prhs
         phin = o.correct_flux(phiH, coef, p)
         Rf = [phi[d] - phin[d] for d in range(m.dims)]
         return self.pack(Rm, Rp, Rf)
@@ -373,7 +379,7 @@ def with_lambda(o, lam_new):
     tag = O.classify(m, lam_new)
     if not np.array_equal(tag, o.tag):
         raise ValueError("perturbation changes the cell groups")
-    if not np.array_equal(lam_new < 1.0, o.mask_m):
+    if o.opts.get("continuity_mask", "A") != "B" and not np.array_equal(lam_new < 1.0, o.mask_m):
         raise ValueError("perturbation changes the continuity mask")
     bnd = O.Boundaries(m, o.case, lam_new)
     for key in o.bnd.closed:

@@ -21,7 +21,8 @@ It follows the paper step by step (Sec. 2, Fig. "simplehfdibrans"):
   a5  correction u = u + alpha_u (u_ib - u) (Eq. corru)
   a6  rAU, HbyA, face flux phiHbyA (standard SIMPLE, Sec. 2.5.1)
   a7  pressure equation laplacian(rAU_f, p) = m div(phiHbyA) with m = 1
-      where lambda < 1 (lambda-masked continuity, Eq. hfdibrans_2)
+      where lambda < 1 (lambda-masked continuity, Eq. hfdibrans_2; reading
+      B, an option: m = 1 - lambda)
   a8  flux / pressure relaxation / velocity update
   a9  production, P_ib assignment (Eq. omegaws)
   a10 eps/omega equation with rows eps = eps_ib (omega = omega_ib) where
@@ -89,7 +90,9 @@ TAG_FC, TAG_BC, TAG_IC = 0, 1, 2
 
 # wall_distance: "y_eff" (Eq. yplus, default) or "y_perp", the distance the
 # wall functions use in y+ and omega_ib (the comparison of App. A)
-DEFAULT_OPTS = dict(urf_u=0.7, urf_p=0.3, urf_turb=0.85, freeze_switch=0, wall_distance="y_eff")
+# continuity_mask: "A" (default) m = 1 where lambda < 1, else 0; "B" m = 1 - lambda
+DEFAULT_OPTS = dict(urf_u=0.7, urf_p=0.3, urf_turb=0.85, freeze_switch=0, wall_distance="y_eff",
+                    continuity_mask="A")
 
 
 def _zeros(shape, *like):
@@ -593,7 +596,7 @@ class Oracle:
         self.geo = ib_geometry(m, self.lam, self.tag)
         self.ic = self.tag == TAG_IC
         self.bcm = self.tag == TAG_BC
-        self.mask_m = self.lam < 1.0     # continuity enforced where lambda < 1
+        self.mask_m = self.lam < 1.0     # continuity enforced where lambda < 1 (reading A)
         # inlet turbulence (Eq. bcspkoein), literal C_nu k^1.5 / l_t
         U = float(np.linalg.norm(case["u_in"]))
         self.k_in = 1.5 * (U * case["I_in"]) ** 2
@@ -602,6 +605,17 @@ class Oracle:
         self.init_state()
         self.iteration = 0
         self.history = []
+
+    def continuity_mask(self, lam=None):
+        """m of the pressure source m div(phiHbyA), the discrete form of the
+        (1 - lambda) factor of Eq. hfdibrans_2.  Reading A (default): m = 1
+        where lambda < 1, else 0 -- continuity everywhere but in the fully
+        solid cells, whose rows stay nonsingular.  Reading B: m = 1 - lambda,
+        the factor itself, smooth in lambda."""
+        lam = self.lam if lam is None else lam
+        if self.opts.get("continuity_mask", "A") == "B":
+            return 1.0 - lam
+        return np.where(lam < 1.0, 1.0, 0.0)
 
     # ---------------------------------------------------------------- state
     def init_state(self):
@@ -775,7 +789,8 @@ class Oracle:
         # ---- a7: pressure equation
         coef, pA_P, pA_M, pA_Pl, prhs_b = self.pressure_operator(rAU)
         div = self.divergence(phiH)
-        rhs = -np.where(self.mask_m, div, 0.0) + prhs_b
+        cm = self.continuity_mask()
+        rhs = -(cm * div) + prhs_b
         res["p"] = scaled_residual(m, pA_P, pA_M, pA_Pl, rhs, self.p, np.ones(m.shape, bool))
         pnew = solve_with_rows(m, pA_P, pA_M, pA_Pl, rhs, np.zeros(m.shape, bool), 0.0)
         # ---- a8: flux, pressure relaxation, velocity update
@@ -784,7 +799,7 @@ class Oracle:
         gradp = gauss_grad(m, self.p, self.bnd.pressure_spec())
         self.u = [HbyA[c] - rAU * gradp[c] for c in range(m.dims)]
         divphi = self.divergence(self.phi)
-        res["cont"] = float(np.abs(np.where(self.mask_m, divphi, 0.0)).sum())
+        res["cont"] = float(np.abs(cm * divphi).sum())
         # ---- a9-a12: turbulence
         if frozen_turbulence:
             pass

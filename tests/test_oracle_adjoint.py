@@ -128,3 +128,74 @@ def test_drag_gradient_matches_finite_differences(which, grf_state):
     pick = cut[np.argsort(-np.abs(gf[cut]))[:3]]
     fd = A.fd_gradient(o, pick, delta=1e-6, objective="drag")
     np.testing.assert_allclose(gf[pick], fd, rtol=1e-5)
+
+
+# ---------------------------------------------------------------- reading B
+def box15_reading_b():
+    case = G.case_rotated_box(15.0, 16, model="laminar", Re=20.0)
+    o = O.Oracle(case, dict(continuity_mask="B"))
+    it, res = o.solve(tol=1e-13, max_iter=4000)
+    assert o.max_residual(res) <= 1e-13
+    return o
+
+
+def test_readings_agree_without_cut_cells():
+    """With lambda in {0, 1} only, m = [lambda < 1] = 1 - lambda: both readings
+    run the same arithmetic, bit for bit."""
+    case = G.case_rotated_box(15.0, 16, model="laminar", Re=20.0)
+    case["lam"] = np.where(case["lam"] >= 0.5, 1.0, 0.0)
+    a = O.Oracle(case)
+    b = O.Oracle(case, dict(continuity_mask="B"))
+    for _ in range(5):
+        a.sweep()
+        b.sweep()
+    for x, y in ((a.u[0], b.u[0]), (a.u[1], b.u[1]), (a.p, b.p)):
+        assert np.array_equal(x, y)
+
+
+def test_reading_b_scales_the_continuity_of_cut_cells():
+    """At a reading-B fixed point the corrected flux keeps lambda times the
+    divergence of phiHbyA in every cell: div phi = div phiH - (1 - lambda)
+    div phiH (the pressure equation, Eq. hfdibrans_2 with m = 1 - lambda)."""
+    o = box15_reading_b()
+    fs = A.FrozenSteady(o)
+    z = fs.state()
+    assert np.abs(fs.residual(z)).max() <= 1e-9 * np.abs(fs.residual(z * 1.01)).max()
+    # the fluid cells (lambda = 0) are divergence-free, the cut cells not
+    div = o.divergence(o.phi)
+    fluid = o.lam == 0.0
+    cut = (o.lam > 0.05) & (o.lam < 0.95)
+    scale = float(np.abs(o.phi[0]).max())
+    assert np.abs(div[fluid]).max() <= 1e-10 * scale
+    assert np.abs(div[cut]).max() > 1e-6 * scale
+
+
+@pytest.mark.slow
+def test_reading_b_gradient_matches_finite_differences():
+    """Reading B differentiates m = 1 - lambda: the gradient in the cut cells,
+    in-solid (0.5 <= lambda < 1) and bc, matches central differences, and it
+    reaches fluid cells far from the body, where reading A has none (there
+    lambda moves no imposed velocity)."""
+    o = box15_reading_b()
+    fs = A.FrozenSteady(o)
+    assert fs.n_kinks == 0
+    J, g, _ = fs.gradient()
+    gf = g.ravel()
+    lam = o.lam.ravel()
+    ic_cut = np.flatnonzero((lam >= 0.5) & (lam < 0.95))
+    bc_cut = np.flatnonzero((lam > 0.05) & (lam < 0.5))
+    assert np.abs(gf[ic_cut]).max() > 1e-3 * np.abs(gf).max()
+    pick = np.concatenate([ic_cut[np.argsort(-np.abs(gf[ic_cut]))[:2]],
+                           bc_cut[np.argsort(-np.abs(gf[bc_cut]))[:2]]])
+    fd = A.fd_gradient(o, pick, delta=1e-6)
+    np.testing.assert_allclose(gf[pick], fd, rtol=1e-5)
+    # fluid cells more than 3 cells from any lambda > 0
+    from scipy.ndimage import binary_dilation
+    near = binary_dilation(o.lam[0] > 0.0, iterations=3)
+    far = np.flatnonzero(~near.ravel())
+    assert far.size > 100
+    assert np.count_nonzero(gf[far]) > 0.9 * far.size
+    a = O.Oracle(o.case)
+    a.solve(tol=1e-13, max_iter=4000)
+    _, ga, _ = A.FrozenSteady(a).gradient()
+    assert np.all(ga.ravel()[far] == 0.0)
