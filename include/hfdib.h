@@ -126,6 +126,12 @@ typedef struct {
     int32_t wall_distance;       /* distance in y+ (Eq. yplus) and omega_ib (Eq.
                                     omegaws): 0 y_eff = (y_perp + h/2)/2 (default),
                                     1 y_perp (the comparison of App. A)           */
+    int32_t continuity_mask;     /* the (1 - lambda) factor of Eq. hfdibrans_2 as the
+                                    pressure source m div(phiHbyA): 0 reading A,
+                                    m = 1 where lambda < 1, else 0 (default);
+                                    1 reading B, m = 1 - lambda (smooth in lambda:
+                                    hfdib_adjoint_grad then differentiates it)     */
+    int32_t reserved;
 } hfdib_options;
 
 typedef struct hfdib_ctx* hfdib_handle;
@@ -202,12 +208,14 @@ enum { HFDIB_GMRES_MAX_RESTART = 200 };
  * state: the gradient of an objective J with respect to the indicator lambda.
  * The paper has no adjoint; this entry point differentiates its discrete
  * method.  Hold fixed nu_t, k, eps/omega, the cell groups (Sec. 2.3), the
- * wall-function branch of each bc cell (Eq. alphauk), the closed faces and
- * the continuity mask.  Then the converged state is a fixed point of the
- * sweep's momentum-pressure part (steps a2-a8 of Fig. simplehfdibrans), and
- * lambda moves it only through the imposed velocity u_ib of the
- * laminar-branch bc cells: the normal n = -grad(lambda)/|grad(lambda)|
- * (Eq. yorthoaux), y_perp (Eq. yortho) and the interpolation of Sec. 2.5.
+ * wall-function branch of each bc cell (Eq. alphauk), the closed faces and,
+ * under reading A, the continuity mask.  Then the converged state is a fixed
+ * point of the sweep's momentum-pressure part (steps a2-a8 of Fig.
+ * simplehfdibrans), and lambda moves it through the imposed velocity u_ib of
+ * the laminar-branch bc cells: the normal n = -grad(lambda)/|grad(lambda)|
+ * (Eq. yorthoaux), y_perp (Eq. yortho) and the interpolation of Sec. 2.5;
+ * under reading B (options.continuity_mask = 1) also through the pressure
+ * source (1 - lambda) div(phiHbyA), which reaches every cell.
  * The adjoint psi of that fixed point solves (I - G_x^T) psi = J_x^T.  G_x^T
  * is one transposed sweep: reverse accumulation through the same red-black
  * momentum passes, with exact pressure solves, run as one CUDA graph.

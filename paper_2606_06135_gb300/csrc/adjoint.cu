@@ -210,7 +210,7 @@ __global__ void k_adj_pressure(Grid g, Fields F, Level L0, Adj A) {
     uint16_t f = F.flags[c];
     const double* ps = A.ps;
     const double* pn = F.pn;
-    double mc = (f & F_M) ? 1.0 : 0.0;
+    double mc = cont_mask(g, F.lam, f, c);
     double rAUb = A.rAUb[c];
     #pragma unroll
     for (int d = 0; d < 3 && d < g.dims; ++d) {
@@ -221,7 +221,7 @@ __global__ void k_adj_pressure(Grid g, Fields F, Level L0, Adj A) {
         // low face
         if (has_nb(g, d, 0, i, j, k)) {
             long long n = c - g.stride[d];
-            double mn = (F.flags[n] & F_M) ? 1.0 : 0.0;
+            double mn = cont_mask(g, F.lam, F.flags[n], n);
             double psi_f = A.psf[d][fl];
             double cfb = (pn[c] - pn[n]) * (-psi_f + ps[n] - ps[c]);
             rAUb += half * cfb;
@@ -234,7 +234,7 @@ __global__ void k_adj_pressure(Grid g, Fields F, Level L0, Adj A) {
         // high face
         if (has_nb(g, d, 1, i, j, k)) {
             long long n = c + g.stride[d];
-            double mn = (F.flags[n] & F_M) ? 1.0 : 0.0;
+            double mn = cont_mask(g, F.lam, F.flags[n], n);
             double psi_f = A.psf[d][fh];
             double cfb = (pn[n] - pn[c]) * (-psi_f + ps[c] - ps[n]);
             rAUb += half * cfb;
@@ -695,6 +695,24 @@ __global__ void k_adj_drag_seed(Grid g, Fields F, Adj A) {
     }
 }
 
+// ---------------------------------------------------------------- mask of reading B
+// With m = 1 - lambda the pressure right-hand side -m div(phiHbyA) depends
+// on lambda directly: d rhs_P / d lambda_P = div_P(phiHbyA), and ps is the
+// adjoint of that right-hand side, so dJ/dlambda_P += ps_P div_P(phiHbyA).
+__global__ void k_adj_dlambda_mask(Grid g, Fields F, Adj A) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    int i, j, k;
+    cell_ijk(g, c, i, j, k);
+    double div = 0.0;
+    #pragma unroll
+    for (int d = 0; d < 3 && d < g.dims; ++d) {
+        long long fl = face_lo(g, d, i, j, k);
+        div += F.phiH[d][fl + face_stride(g, d)] - F.phiH[d][fl];
+    }
+    A.dlam[c] += A.ps[c] * div;
+}
+
 // ---------------------------------------------------------------- lambda chain
 namespace {
 
@@ -889,6 +907,9 @@ void launch_adj_phi(const Grid& g, const Fields& F, const Adj& A, cudaStream_t s
 }
 void launch_adj_next(const Grid& g, const Fields& F, const Adj& A, int first, cudaStream_t s) {
     k_adj_next<<<nblocks(g.N), BLOCK, 0, s>>>(g, F, A, first);
+}
+void launch_adj_dlambda_mask(const Grid& g, const Fields& F, const Adj& A, cudaStream_t s) {
+    if (g.mask_b) k_adj_dlambda_mask<<<nblocks(g.N), BLOCK, 0, s>>>(g, F, A);
 }
 void launch_adj_drag_value(const Grid& g, const Fields& F, const Adj& A, cudaStream_t s) {
     k_adj_drag_value<<<nblocks(g.N), BLOCK, 0, s>>>(g, F, A);

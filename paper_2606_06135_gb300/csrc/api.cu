@@ -1062,6 +1062,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
     if (o.precond < 0 || o.precond > 1 || o.p_check < 0 || o.mg_coarse_sweeps < 0) return HFDIB_ERR_INVALID_ARG;
     if (o.precision < 0 || o.precision > 1) return HFDIB_ERR_INVALID_ARG;
     if (o.wall_distance < 0 || o.wall_distance > 1) return HFDIB_ERR_INVALID_ARG;
+    if (o.continuity_mask < 0 || o.continuity_mask > 1) return HFDIB_ERR_INVALID_ARG;
     // the mixed path runs its FP32 V-cycle inside the persistent CG kernel
     if (o.precision == 1 && (o.p_persistent == 0 || o.precond != 1)) return HFDIB_ERR_INVALID_ARG;
     if (o.p_maxiter > 100000 || o.freeze_switch < 0) return HFDIB_ERR_INVALID_ARG;
@@ -1105,6 +1106,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
     g.nface[0] = (long long)(g.nx + 1) * g.ny * g.nz;
     g.nface[1] = (long long)g.nx * (g.ny + 1) * g.nz;
     g.nface[2] = (long long)g.nx * g.ny * (g.nz + 1);
+    g.mask_b = o.continuity_mask;
     Params& P = h->P;
     P.model = model;
     P.urf_u = o.urf_u; P.urf_p = o.urf_p; P.urf_turb = o.urf_turb;
@@ -1170,6 +1172,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
             if (M.lv[l].N <= TAIL_CELLS) { h->tail_from = l; break; }
     }
     F.mixed = o.precision == 1 ? 1 : 0;
+    F.lam = h->lam;
     if (!rc && F.mixed) {
         for (int d = 0; d < 3; ++d) { A(F.phi32[d], g.nface[d]); A(F.r32[d], N); A(F.d32[d], N); }
         A(F.nut32, N); A(F.gam32, N); A(F.gamk32, N); A(F.diag32, N); A(F.z32, N);
@@ -1611,6 +1614,7 @@ int hfdib_adjoint_grad(hfdib_handle hh, int objective, double tol, int max_iter,
     if (change_out) *change_out = change;
     CK(cudaMemsetAsync(A.dlam, 0, g.N * sizeof(double), s));
     launch_adj_dlambda(g, F, h->bl, h->lam, A, s);
+    launch_adj_dlambda_mask(g, F, A, s);
     if (drag) {
         // plus the explicit dependence of the drag on lambda through u_ib
         Adj Ae = A;

@@ -68,7 +68,20 @@ struct Grid {
     double nu;
     long long stride[3];
     long long nface[3];
+    int mask_b;      // continuity mask: 0 reading A m = [lambda < 1], 1 reading B m = 1 - lambda
 };
+
+// m div(phiHbyA), the source of the pressure equation (Eq. hfdibrans_2 with
+// its (1 - lambda) factor): reading A m = [lambda < 1] (flag F_M), reading B
+// m = 1 - lambda
+__device__ inline double masked_div(const Grid& g, const double* lam, uint16_t f, long long c, double div) {
+    if (g.mask_b) return (1.0 - lam[c]) * div;
+    return (f & F_M) ? div : 0.0;
+}
+__device__ inline double cont_mask(const Grid& g, const double* lam, uint16_t f, long long c) {
+    if (g.mask_b) return 1.0 - lam[c];
+    return (f & F_M) ? 1.0 : 0.0;
+}
 
 __host__ __device__ inline int tag_of(uint16_t f) { return f & F_TAG; }
 __host__ __device__ inline bool closed_side(uint16_t f, int s) { return (f >> (F_CLOSED_SHIFT + s)) & 1u; }

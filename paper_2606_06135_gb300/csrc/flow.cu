@@ -429,7 +429,7 @@ __global__ void k_update(Grid g, Params P, Fields F, Level L0) {
             }
             div += fhi - flo;
         }
-        red[0] += (f & F_M) ? fabs(div) : 0.0;
+        red[0] += fabs(masked_div(g, F.lam, f, c, div));
         // relaxed pressure and the velocity update
         double a = P.urf_p;
         double prP = prelax(F.p, F.pn, c, a);

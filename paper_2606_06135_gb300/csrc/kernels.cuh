@@ -80,6 +80,7 @@ struct Fields {
     double* sp;        // extra implicit diagonal (integrated)
     double* src;       // explicit source (integrated)
     double* asus;      // realizable k-eps: A_s U* of the velocity gradient (for nu_t)
+    const double* lam; // lambda (the continuity mask of reading B)
     double* bt;        // relaxed right-hand side
     double* diag;      // relaxed diagonal
     double* ywall;
@@ -257,6 +258,7 @@ void launch_adj_gradu(const Grid& g, const Fields& F, const BcList& bl, const Ad
 void launch_adj_phi(const Grid& g, const Fields& F, const Adj& A, cudaStream_t s);
 void launch_adj_next(const Grid& g, const Fields& F, const Adj& A, int first, cudaStream_t s);
 void launch_adj_objective(const Grid& g, const Fields& F, const Adj& A, cudaStream_t s);
+void launch_adj_dlambda_mask(const Grid& g, const Fields& F, const Adj& A, cudaStream_t s);
 void launch_adj_drag_value(const Grid& g, const Fields& F, const Adj& A, cudaStream_t s);
 void launch_adj_drag_seed(const Grid& g, const Fields& F, const Adj& A, cudaStream_t s);
 void launch_adj_dlambda(const Grid& g, const Fields& F, const BcList& bl, const double* lam, const Adj& A,

@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(1024) k_pressure_batched(PcgbArgs<MT> A) {
                     A1 += L0.cf[d][fl + fs];
                 }
             }
-            double rhs = -((f & F_M) ? div : 0.0) + bout;
+            double rhs = -masked_div(g, F.lam, f, c, div) + bout;
             double Ap = L0.diag[c] * F.p[c] - pl_offsum(L0, g.dims, F.p, c, i, j, k);
             double r = rhs - Ap;
             F.r[c] = r;

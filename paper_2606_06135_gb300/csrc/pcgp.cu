@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_pressure_persistent(PcgpArgs<MT>
                 A1 += L0.cf[d][fl + fs];
             }
         }
-        double rhs = -((f & F_M) ? div : 0.0) + bout;
+        double rhs = -masked_div(g, F.lam, f, c, div) + bout;
         double Ap = L0.diag[c] * F.p[c] - pl_offsum(L0, g.dims, F.p, c, i, j, k);
         double r = rhs - Ap;
         F.r[c] = r;

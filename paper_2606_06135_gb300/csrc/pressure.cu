@@ -347,7 +347,7 @@ __global__ void k_pcg_init(Grid g, Fields F, Level L0, int jacobi) {
                 A1 += L0.cf[d][fl + fs];
             }
         }
-        double rhs = -((f & F_M) ? div : 0.0) + bout;
+        double rhs = -masked_div(g, F.lam, f, c, div) + bout;
         double dg = L0.diag[c];
         double Ap = dg * F.p[c] - lv_offsum(L0, g.dims, F.p, c, i, j, k);
         double r = rhs - Ap;

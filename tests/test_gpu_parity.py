@@ -91,6 +91,7 @@ SWEEP_CASES = {
     "cylinder_komega": lambda: G.case_cylinder(48, 24, model="komega"),
     "cylinder_rke": lambda: G.case_cylinder(48, 24, model="realizableke"),
     "bfs_keps_yperp": lambda: G.case_bfs(64, 16, model="kepsilon"),
+    "cylinder_keps_maskB": lambda: G.case_cylinder(48, 24),
 }
 
 EXACT = dict(n_u=600, n_turb=600, p_reltol=1e-15, p_maxiter=4000)
@@ -103,7 +104,8 @@ EXACT = dict(n_u=600, n_turb=600, p_reltol=1e-15, p_maxiter=4000)
 SWEEP_TOL = {"bfs_rke": 1e-8}
 
 # (GPU options, oracle options) of cases that change an option
-SWEEP_OPTS = {"bfs_keps_yperp": (dict(wall_distance=1), dict(wall_distance="y_perp"))}
+SWEEP_OPTS = {"bfs_keps_yperp": (dict(wall_distance=1), dict(wall_distance="y_perp")),
+              "cylinder_keps_maskB": (dict(continuity_mask=1), dict(continuity_mask="B"))}
 
 
 @pytest.mark.parametrize("name", sorted(SWEEP_CASES))
