@@ -141,6 +141,8 @@ class FrozenSteady:
         m = o.m
         if m.dims != 2:
             raise ValueError("the oracle adjoint covers 2D grids")
+        if o.opts.get("convection", "upwind") != "upwind":
+            raise ValueError("the oracle adjoint covers the upwind scheme")
         self.o = copy.deepcopy(o)
         o = self.o
         o.imposed_fields()          # branch and masks the next sweep would use

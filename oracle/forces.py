@@ -73,7 +73,7 @@ def ib_force(o):
     for c in range(m.dims):
         ut = imposed_velocity(o, c)
         aP, aM, aPl, b = O.assemble_transport(m, o.phi, nu_eff, o.bnd.velocity_spec(c))
-        b = b + o.transpose_source(G, nu_eff, c)
+        b = b + o.transpose_source(G, nu_eff, c) + o.momentum_convection_correction(G, c)
         rm = aP * ut + O.apply_offdiag(m, aM, aPl, ut) - b
         Ft[c] = -float(np.sum(rm[fixed]))
         Fn[c] = -float(np.sum((m.V * gradp[c])[fixed]))

@@ -91,8 +91,10 @@ TAG_FC, TAG_BC, TAG_IC = 0, 1, 2
 # wall_distance: "y_eff" (Eq. yplus, default) or "y_perp", the distance the
 # wall functions use in y+ and omega_ib (the comparison of App. A)
 # continuity_mask: "A" (default) m = 1 where lambda < 1, else 0; "B" m = 1 - lambda
+# convection: scheme of the momentum convection term, "upwind" (Sec. 3.1,
+# default) or, by deferred correction, "linearUpwind" / "vanLeer" (App. B)
 DEFAULT_OPTS = dict(urf_u=0.7, urf_p=0.3, urf_turb=0.85, freeze_switch=0, wall_distance="y_eff",
-                    continuity_mask="A")
+                    continuity_mask="A", convection="upwind")
 
 
 def _zeros(shape, *like):
@@ -517,6 +519,57 @@ def assemble_transport(m: Mesh, phi, gamma, spec):
     return aP, aM, aPl, b
 
 
+CONV_SCHEMES = ("upwind", "linearUpwind", "vanLeer")
+
+
+def face_correction(m: Mesh, phi_d, f, dfdx_d, d, scheme):
+    """Scheme face value minus the upwind value, f_face - f_U, on the interior
+    faces normal to d (App. B: schemes for the convection term of momentum).
+    U is the upwind cell of the face (flux phi_d >= 0: the low cell), D the
+    other, s = +1 when D lies at +d from U.
+      linearUpwind: f_face = f_U + grad f_U . (x_face - x_U) = f_U + s (Delta/2) df/dx_d|U
+      vanLeer (TVD): f_face = f_U + psi(r) (f_D - f_U)/2, psi(r) = (r + |r|)/(1 + |r|),
+                     r = 2 (x_D - x_U) . grad f_U / (f_D - f_U) - 1 (0 where f_D = f_U)
+    with the cell gradient of the Gauss-linear scheme."""
+    ax = 2 - d
+    n = m.n[d]
+    F = phi_d[_sl(ax, 1, n)]
+    fL, fH = f[_sl(ax, 0, n - 1)], f[_sl(ax, 1, n)]
+    gL, gH = dfdx_d[_sl(ax, 0, n - 1)], dfdx_d[_sl(ax, 1, n)]
+    pos = F >= 0.0
+    fU = np.where(pos, fL, fH)
+    fD = np.where(pos, fH, fL)
+    gU = np.where(pos, gL, gH)
+    s = np.where(pos, 1.0, -1.0)
+    if scheme == "linearUpwind":
+        return s * (0.5 * m.D[d]) * gU
+    if scheme == "vanLeer":
+        dd = fD - fU
+        nz = dd != 0.0
+        r = np.where(nz, 2.0 * (s * m.D[d]) * gU / np.where(nz, dd, 1.0) - 1.0, 0.0)
+        psi = (r + np.abs(r)) / (1.0 + np.abs(r))
+        return np.where(nz, 0.5 * psi * dd, 0.0)
+    raise ValueError("convection scheme: " + str(scheme))
+
+
+def convection_correction(m: Mesh, phi, f, G, scheme):
+    """Deferred correction of the upwind convection of f (one velocity
+    component): the rows keep the bounded upwind operator and take
+    -sum_faces F_out (f_face - f_U) as an explicit source, so a converged
+    state solves the scheme's equations.  G[d] = d f / d x_d.  Boundary faces
+    keep their upwind / boundary values."""
+    out = _zeros(m.shape, f, *phi[:m.dims])
+    if scheme == "upwind":
+        return out
+    for d in range(m.dims):
+        ax = 2 - d
+        n = m.n[d]
+        corr = phi[d][_sl(ax, 1, n)] * face_correction(m, phi[d], f, G[d], d, scheme)
+        out[_sl(ax, 0, n - 1)] -= corr     # the face is the high face of the low cell
+        out[_sl(ax, 1, n)] += corr         # and the low face (outward flux -F) of the high cell
+    return out
+
+
 def to_sparse(m: Mesh, aP, aM, aPl):
     idx = np.arange(m.N).reshape(m.shape)
     rows = [idx.ravel()]
@@ -761,7 +814,7 @@ class Oracle:
         aPc, b0c = [], []
         for c in range(m.dims):
             aP, aM, aPl, b = assemble_transport(m, self.phi, nu_eff, self.bnd.velocity_spec(c))
-            b = b + self.transpose_source(G, nu_eff, c)
+            b = b + self.transpose_source(G, nu_eff, c) + self.momentum_convection_correction(G, c)
             aPc.append(aP)
             b0c.append(b)
         # ---- a4: momentum predictor (relaxed), rows u = u_ib where alpha_u = 1
@@ -814,6 +867,13 @@ class Oracle:
         self.iteration += 1
         self.history.append(res)
         return res
+
+    def momentum_convection_correction(self, G, c):
+        """Deferred correction of the convection of u_c for the scheme of
+        opts["convection"] (App. B), from u and grad u at sweep start."""
+        m = self.m
+        scheme = self.opts.get("convection", "upwind")
+        return convection_correction(m, self.phi, self.u[c], [G[d][c] for d in range(m.dims)], scheme)
 
     def transpose_source(self, G, nu_eff, c):
         """Explicit div(nu_eff (grad u)^T) for component c: face flux
