@@ -131,7 +131,12 @@ typedef struct {
                                     m = 1 where lambda < 1, else 0 (default);
                                     1 reading B, m = 1 - lambda (smooth in lambda:
                                     hfdib_adjoint_grad then differentiates it)     */
-    int32_t reserved;
+    int32_t convection;          /* momentum convection scheme (App. B): 0 upwind
+                                    (Sec. 3.1, default); 1 linearUpwind, 2 vanLeer,
+                                    both as a deferred correction of the bounded
+                                    upwind rows from the sweep-start velocity and
+                                    its Gauss-linear gradient (hfdib_adjoint_grad
+                                    needs 0)                                       */
 } hfdib_options;
 
 typedef struct hfdib_ctx* hfdib_handle;
@@ -244,7 +249,7 @@ enum { HFDIB_GMRES_MAX_RESTART = 200 };
  *                residual or change) : host pointers, nullable
  * Call it on a converged state (hfdib_solve_steady to a tight tolerance): the
  * gradient is that of the fixed point, and its error follows the residual.
- * 2D grids only (INVALID_ARG otherwise).  The state is left unchanged.
+ * 2D grids and the upwind convection scheme only (INVALID_ARG otherwise).  The state is left unchanged.
  * Returns HFDIB_OK, HFDIB_ERR_NOT_CONVERGED (gradient of the last iterate
  * still written), HFDIB_ERR_DIVERGED, HFDIB_ERR_INVALID_ARG, or CUDA/OOM errors.
  * The first call allocates about 90 doubles per cell of work arrays (plus

@@ -1063,6 +1063,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
     if (o.precision < 0 || o.precision > 1) return HFDIB_ERR_INVALID_ARG;
     if (o.wall_distance < 0 || o.wall_distance > 1) return HFDIB_ERR_INVALID_ARG;
     if (o.continuity_mask < 0 || o.continuity_mask > 1) return HFDIB_ERR_INVALID_ARG;
+    if (o.convection < 0 || o.convection > 2) return HFDIB_ERR_INVALID_ARG;
     // the mixed path runs its FP32 V-cycle inside the persistent CG kernel
     if (o.precision == 1 && (o.p_persistent == 0 || o.precond != 1)) return HFDIB_ERR_INVALID_ARG;
     if (o.p_maxiter > 100000 || o.freeze_switch < 0) return HFDIB_ERR_INVALID_ARG;
@@ -1107,6 +1108,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
     g.nface[1] = (long long)g.nx * (g.ny + 1) * g.nz;
     g.nface[2] = (long long)g.nx * g.ny * (g.nz + 1);
     g.mask_b = o.continuity_mask;
+    g.conv = o.convection;
     Params& P = h->P;
     P.model = model;
     P.urf_u = o.urf_u; P.urf_p = o.urf_p; P.urf_turb = o.urf_turb;
@@ -1527,7 +1529,7 @@ int hfdib_adjoint_grad(hfdib_handle hh, int objective, double tol, int max_iter,
     if (!h) return HFDIB_ERR_INVALID_ARG;
     if (objective != HFDIB_OBJ_PRESSURE_DROP && objective != HFDIB_OBJ_DRAG) return HFDIB_ERR_INVALID_ARG;
     const bool drag = objective == HFDIB_OBJ_DRAG;
-    if (h->g.dims != 2) return HFDIB_ERR_INVALID_ARG;
+    if (h->g.dims != 2 || h->g.conv != 0) return HFDIB_ERR_INVALID_ARG;
     if (!(tol > 0.0) || max_iter < 0 || (max_iter > 0 && !dJ_dlambda)) return HFDIB_ERR_INVALID_ARG;
     if (gmres_restart < 0 || gmres_restart > HFDIB_GMRES_MAX_RESTART) return HFDIB_ERR_INVALID_ARG;
     const Grid& g = h->g;

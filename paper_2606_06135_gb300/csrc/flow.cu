@@ -219,6 +219,51 @@ __device__ __forceinline__ double transpose_src(const Grid& g, const Fields& F, 
     return T;
 }
 
+// Deferred correction of the momentum convection (App. B schemes): the rows
+// keep bounded upwind, and -sum over interior faces of F_out (u_f - u_U)
+// goes to the right-hand side, from u and grad u at sweep start.  U is the
+// upwind cell of the face, D the other, s = +1 when D lies at +d from U.
+//   linearUpwind: u_f - u_U = s (Delta/2) du/dx_d|U
+//   vanLeer:      u_f - u_U = psi(r) (u_D - u_U)/2, psi = (r + |r|)/(1 + |r|),
+//                 r = 2 s Delta du/dx_d|U / (u_D - u_U) - 1 (no term where u_D = u_U)
+__device__ inline double conv_src(const Grid& g, const Fields& F, long long c, int i, int j, int k, int q) {
+    double corr = 0.0;
+    const double* u = F.u[q];
+    #pragma unroll
+    for (int d = 0; d < 3 && d < g.dims; ++d) {
+        long long fl = face_lo(g, d, i, j, k);
+        long long fs = face_stride(g, d);
+        const double* Gd = F.G + (long long)(3 * d + q) * g.N;   // d u_q / d x_d
+        #pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            if (!interior(g, d, side, i, j, k)) continue;
+            double Fb = F.phi[d][fl + side * fs];
+            double Fout = side ? Fb : -Fb;
+            long long n = nbr_cell(g, c, d, side);
+            bool out = Fout >= 0.0;
+            long long U = out ? c : n;
+            double s = (out == (side == 1)) ? 1.0 : -1.0;
+            double gU = Gd[U];
+            double du;
+            if (g.conv == 1) {
+                du = s * (0.5 * g.D[d]) * gU;
+            } else {
+                double uU = u[U], uD = u[out ? n : c];
+                double dd = uD - uU;
+                if (dd != 0.0) {
+                    double r = 2.0 * (s * g.D[d]) * gU / dd - 1.0;
+                    double psi = (r + fabs(r)) / (1.0 + fabs(r));
+                    du = 0.5 * psi * dd;
+                } else {
+                    du = 0.0;
+                }
+            }
+            corr += Fout * du;
+        }
+    }
+    return -corr;
+}
+
 // ---------------------------------------------------------------- a3 assembly
 __global__ void __launch_bounds__(BLOCK, 2) k_mom_asm(Grid g, Params P, Fields F) {
     double red[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -239,6 +284,7 @@ __global__ void __launch_bounds__(BLOCK, 2) k_mom_asm(Grid g, Params P, Fields F
         #pragma unroll
         for (int q = 0; q < 3 && q < g.dims; ++q) {
             double b0 = R.bnd[q] + transpose_src(g, F, c, i, j, k, q, nuP);
+            if (g.conv) b0 += conv_src(g, F, c, i, j, k, q);
             double gp = grad_p(g, F.p, c, q, i, j, k);
             double uold = F.u[q][c];
             double bfull = b0 - gp * g.V;
@@ -480,7 +526,9 @@ __global__ void k_ib_force(Grid g, Fields F) {
                 if (!vel_row_fixed(g, F, nc, q, uN)) uN = F.u[q][nc];
                 r += R.a[s] * uN;
             }
-            r -= R.bnd[q] + transpose_src(g, F, c, i, j, k, q, nuP);
+            double b0 = R.bnd[q] + transpose_src(g, F, c, i, j, k, q, nuP);
+            if (g.conv) b0 += conv_src(g, F, c, i, j, k, q);
+            r -= b0;
             v[q] -= g.V * grad_p(g, F.p, c, q, i, j, k);
             v[3 + q] -= r;
         }

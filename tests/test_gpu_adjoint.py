@@ -175,6 +175,10 @@ def test_adjoint_rejects_3d_and_unknown_objective():
     with pytest.raises(HfdibError):
         s.adjoint_grad(max_iter=10, objective=7)
     s.close()
+    s = Solver(G.case_grf(32, 16, seed=1), convection=1)
+    with pytest.raises(HfdibError):
+        s.adjoint_grad(max_iter=10)
+    s.close()
 
 
 @pytest.mark.parametrize("name", sorted(CASES))

@@ -198,3 +198,18 @@ def test_recirculation_on_the_full_step():
     assert got[2] == ref[2] and got[0] == ref[0] and got[1] == ref[1], (got, ref)
     assert got[2] > 100
     s.close()
+
+
+def test_force_with_linear_upwind_matches_oracle():
+    """The force includes the deferred convection correction of the imposed
+    rows' momentum (App. B scheme)."""
+    case = G.case_rotated_box(15.0, 16, model="laminar", Re=20.0)
+    o = O.Oracle(case, dict(convection="linearUpwind"))
+    it, res = o.solve(tol=1e-13, max_iter=8000)
+    assert o.max_residual(res) <= 1e-13
+    o.imposed_fields()
+    Fref = sum(Fo.ib_force(o))
+    s = gpu_converged(case, convection=1)
+    F = sum(s.force())
+    assert np.abs(F - Fref).max() <= 1e-9 * np.abs(Fref).max()
+    s.close()

@@ -92,6 +92,8 @@ SWEEP_CASES = {
     "cylinder_rke": lambda: G.case_cylinder(48, 24, model="realizableke"),
     "bfs_keps_yperp": lambda: G.case_bfs(64, 16, model="kepsilon"),
     "cylinder_keps_maskB": lambda: G.case_cylinder(48, 24),
+    "cylinder_keps_linup": lambda: G.case_cylinder(48, 24),
+    "bfs_sst_vanleer": lambda: G.case_bfs(64, 16),
 }
 
 EXACT = dict(n_u=600, n_turb=600, p_reltol=1e-15, p_maxiter=4000)
@@ -105,7 +107,9 @@ SWEEP_TOL = {"bfs_rke": 1e-8}
 
 # (GPU options, oracle options) of cases that change an option
 SWEEP_OPTS = {"bfs_keps_yperp": (dict(wall_distance=1), dict(wall_distance="y_perp")),
-              "cylinder_keps_maskB": (dict(continuity_mask=1), dict(continuity_mask="B"))}
+              "cylinder_keps_maskB": (dict(continuity_mask=1), dict(continuity_mask="B")),
+              "cylinder_keps_linup": (dict(convection=1), dict(convection="linearUpwind")),
+              "bfs_sst_vanleer": (dict(convection=2), dict(convection="vanLeer"))}
 
 
 @pytest.mark.parametrize("name", sorted(SWEEP_CASES))
@@ -253,4 +257,22 @@ def test_3d_converged_state_matches_oracle(precision):
     errs = {n: relL2(got[n], ref) for n, ref in (("ux", o.u[0]), ("uy", o.u[1]), ("uz", o.u[2]),
                                                   ("p", o.p), ("k", o.k), ("eps", o.eps), ("nut", o.nut))}
     assert max(errs.values()) < 1e-9, errs
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_converged_convection_schemes_match_oracle(scheme, precision):
+    """linearUpwind (1) and vanLeer (2) momentum convection (App. B, deferred
+    correction): the converged state matches the oracle's, FP64 within 1e-9,
+    mixed within 1e-4."""
+    name = {1: "linearUpwind", 2: "vanLeer"}[scheme]
+    case = G.case_cylinder(48, 24, model="laminar", Re=40.0)
+    o = O.Oracle(case, dict(convection=name))
+    _, ores = o.solve(tol=1e-12, max_iter=3000)
+    assert o.max_residual(ores) <= 1e-12
+    s = make_solver(case, convection=scheme, precision=precision)
+    rc, it, res = s.solve(tol=1e-12, max_iter=8000, check_every=20)
+    assert rc == 0, (rc, it, res)
+    compare_fields(s, o, 1e-9 if precision == 0 else 1e-4)
     s.close()
