@@ -315,8 +315,9 @@ int hfdib_set_field(hfdib_handle h, int field, const double* src);
  * hfdib_get_bc_list copies, for the n_bc boundary cells in increasing cell
  * order, device arrays (each nullable):
  *   ints     : int64 [n_bc][8] = cell, in-solid neighbour (-1 none), y_perp
- *              case (0,1,2), clamped flag, X1 base cell (i,j,k) -- then X2 base
- *              (i,j,k) follows in ints2 ;
+ *              case (0,1,2), clamped flag, X1 base cell (i,j,k), and the
+ *              wall-function branch of the last sweep (1: laminar, y+ <=
+ *              y+_lam, Eq. alphauk; 0: log) -- X2 base (i,j,k) is in ints2 ;
  *   ints2    : int64 [n_bc][3] = X2 base (i,j,k)
  *   reals    : double [n_bc][14] = n (3), y_perp, y_eff, wS, w1, w2,
  *              t1 (3), t2 (3). */

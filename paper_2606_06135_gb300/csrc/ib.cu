@@ -372,7 +372,7 @@ __global__ void k_export_bc(BcList bl, long long* ints, long long* ints2, double
     if (ints) {
         long long* o = ints + 8 * (long long)q;
         o[0] = bl.cell[q]; o[1] = bl.nbr[q]; o[2] = bl.cas[q]; o[3] = bl.clamped[q];
-        o[4] = bl.b1[3 * q]; o[5] = bl.b1[3 * q + 1]; o[6] = bl.b1[3 * q + 2]; o[7] = 0;
+        o[4] = bl.b1[3 * q]; o[5] = bl.b1[3 * q + 1]; o[6] = bl.b1[3 * q + 2]; o[7] = bl.lamb[q];
     }
     if (ints2) {
         long long* o = ints2 + 3 * (long long)q;

@@ -274,7 +274,7 @@ class Solver:
         a2 = ints2.cpu().numpy()[:nbc]
         r = reals.cpu().numpy()[:nbc]
         return dict(cell=a[:, 0], nbr=a[:, 1], case=a[:, 2], clamped=a[:, 3].astype(bool),
-                    base1=a[:, 4:7], base2=a2, n=r[:, 0:3], y_perp=r[:, 3], y_eff=r[:, 4],
+                    base1=a[:, 4:7], base2=a2, laminar=a[:, 7].astype(bool), n=r[:, 0:3], y_perp=r[:, 3], y_eff=r[:, 4],
                     wS=r[:, 5], w1=r[:, 6], w2=r[:, 7], t1=r[:, 8:11], t2=r[:, 11:14])
 
     def history(self, count=1024):

@@ -276,3 +276,40 @@ def test_converged_convection_schemes_match_oracle(scheme, precision):
     assert rc == 0, (rc, it, res)
     compare_fields(s, o, 1e-9 if precision == 0 else 1e-4)
     s.close()
+
+
+def test_oracle_residuals_at_the_full_size_converged_state():
+    """The 1024 x 256 step in the benchmark's configuration (k-omega SST,
+    mixed, one-way switch from sweep 300, pressure tolerance 0.2) solved to
+    1e-6 on the GPU.  The oracle, given that state and the GPU's wall-function
+    branches, evaluates the scaled residuals of the next sweep (App. D) and
+    finds the GPU's own: the GPU's converged state solves the oracle's
+    equations at full size."""
+    from paper_2606_06135_gb300.hfdib import Solver
+    case = G.case_bfs(1024, 256)
+    s = Solver(case, precision=1, freeze_switch=300, p_reltol=0.2)
+    rc, it, res = s.solve(tol=1e-6, max_iter=20000, check_every=100)
+    assert rc == 0, (rc, it, res)
+    m = O.Mesh(case["grid"])
+    f = s.fields()
+    phix = s.field("phix").cpu().numpy().reshape(1, m.ny, m.nx + 1)
+    phiy = s.field("phiy").cpu().numpy().reshape(1, m.ny + 1, m.nx)
+    lamb = s.bc_list()["laminar"]
+    res_gpu = s.sweep()          # evaluated at the start of the sweep: this state's
+    o = O.Oracle(case, dict(freeze_switch=1))
+    o.u = [f["ux"], f["uy"]]
+    o.p, o.phi = f["p"], [phix, phiy]
+    o.k, o.omega, o.eps, o.nut = f["k"], f["omega"], f["eps"], f["nut"]
+    o.lam_branch, o.iteration = lamb, 10 ** 6
+    r = o.sweep()
+    got = {"U0": res_gpu[0], "U1": res_gpu[1], "p": res_gpu[3], "omega": res_gpu[4], "k": res_gpu[5]}
+    print("full-size residuals, oracle vs GPU:", {k: ("%.6e" % r[k], "%.6e" % v) for k, v in got.items()})
+    # the momentum residuals are functions of the sweep-start state alone:
+    # the same numbers up to summation order
+    for key in ("U0", "U1"):
+        assert abs(r[key] - got[key]) <= 1e-6 * got[key], (key, r[key], got[key])
+    # the others follow the predictor (exact LU in the oracle, two red-black
+    # passes on the GPU) and the flow update: the same order of magnitude
+    for key in ("p", "omega", "k"):
+        assert r[key] <= 1e-5, (key, r[key], got[key])
+    assert max(got.values()) <= 2e-6
