@@ -137,6 +137,11 @@ typedef struct {
                                     upwind rows from the sweep-start velocity and
                                     its Gauss-linear gradient (hfdib_adjoint_grad
                                     needs 0)                                       */
+    int32_t mg_tail_cells;       /* persistent pressure solve: multigrid levels of at
+                                    most this many cells run inside one thread block
+                                    (in shared memory when they fit), the others
+                                    as grid-wide phases (0: the library default)   */
+    int32_t reserved;
 } hfdib_options;
 
 typedef struct hfdib_ctx* hfdib_handle;

@@ -52,6 +52,7 @@ struct Ctx {
     MgLevels mg;
     MgLevels32 mg32;
     int tail_from = 1;
+    long long tail_cells = 0;   // persistent pressure solve: largest level of block 0's tail
     int coarse_sweeps = 20;
     int use_graph = 0;
     int parity = 0;              // which of the two sweep graphs matches the p / pr buffers
@@ -242,12 +243,12 @@ void enqueue_part_a(Ctx* h, long long* L, bool with_pressure = true) {
         if (F.mixed) {
             PROF(h, HFDIB_K_PCG, launch_pressure_persistent32(g, F, M, h->mg32, h->coarse_sweeps,
                                                                h->opt.p_reltol, h->opt.p_maxiter, h->pblocks,
-                                                               h->ppart, h->pbar, h->perr, s));
+                                                               h->ppart, h->pbar, h->perr, h->tail_cells, s));
             (*L)++;
         } else {
             PROF(h, HFDIB_K_PCG, launch_pressure_persistent(g, F, M, jac, h->coarse_sweeps, h->opt.p_reltol,
                                                              h->opt.p_maxiter, h->pblocks, h->ppart, h->pbar,
-                                                             h->perr, s));
+                                                             h->perr, h->tail_cells, s));
             (*L)++;
         }
         return;
@@ -1060,6 +1061,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
         return HFDIB_ERR_INVALID_ARG;
     if (o.n_u < 1 || o.n_turb < 1 || o.p_maxiter < 0 || !(o.p_reltol >= 0)) return HFDIB_ERR_INVALID_ARG;
     if (o.precond < 0 || o.precond > 1 || o.p_check < 0 || o.mg_coarse_sweeps < 0) return HFDIB_ERR_INVALID_ARG;
+    if (o.mg_tail_cells < 0 || o.mg_tail_cells > (1 << 20)) return HFDIB_ERR_INVALID_ARG;
     if (o.precision < 0 || o.precision > 1) return HFDIB_ERR_INVALID_ARG;
     if (o.wall_distance < 0 || o.wall_distance > 1) return HFDIB_ERR_INVALID_ARG;
     if (o.continuity_mask < 0 || o.continuity_mask > 1) return HFDIB_ERR_INVALID_ARG;
@@ -1080,6 +1082,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
     h->opt = o;
     h->bc = *bc;
     h->coarse_sweeps = o.mg_coarse_sweeps > 0 ? o.mg_coarse_sweeps : 4;
+    h->tail_cells = o.mg_tail_cells > 0 ? o.mg_tail_cells : PT_DEFAULT_TAIL_CELLS;
     h->use_graph = (o.graph != 0 && o.p_check == 0) ? 1 : 0;
     h->model = model;
     Grid& g = h->g;

@@ -126,6 +126,9 @@ using Level = LevelT<double>;
 using Level32 = LevelT<float>;
 constexpr int MAX_LEVELS = 16;
 constexpr long long TAIL_CELLS = 4096;
+// persistent pressure solve: default largest level run by block 0 alone (in
+// shared memory when the levels fit; the V-cycle is the same either way)
+constexpr long long PT_DEFAULT_TAIL_CELLS = 4096;
 template <typename T>
 struct MgLevelsT {
     int nl;
@@ -184,10 +187,10 @@ void launch_pcg_body(const Grid& g, const Fields& F, const MgLevels& M, int ntai
 int pcgp_blocks(int* out);
 cudaError_t launch_pressure_persistent(const Grid& g, const Fields& F, const MgLevels& M, int jacobi,
                                        int coarse_sweeps, double reltol, int maxit, int nblk, double* part,
-                                       unsigned int* bar, int* err, cudaStream_t s);
+                                       unsigned int* bar, int* err, long long tail_cells, cudaStream_t s);
 cudaError_t launch_pressure_persistent32(const Grid& g, const Fields& F, const MgLevels& M, const MgLevels32& M32,
                                          int coarse_sweeps, double reltol, int maxit, int nblk, double* part,
-                                         unsigned int* bar, int* err, cudaStream_t s);
+                                         unsigned int* bar, int* err, long long tail_cells, cudaStream_t s);
 void launch_p_coef32(const Grid& g, const MgLevels& M, const MgLevels32& M32, cudaStream_t s);
 void launch_mom_smooth32(const Grid& g, const Params& P, const Fields& F, int colour, int zero_init, cudaStream_t s);
 void launch_scal_smooth32(const Grid& g, const Params& P, const Fields& F, int eq, int colour, int zero_init,

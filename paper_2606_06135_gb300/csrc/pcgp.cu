@@ -11,7 +11,7 @@
 // instead of waiting forever.  Reductions: every block writes its partial;
 // after the barrier every block sums all partials in the same order, so all
 // blocks hold the same bit-identical value (deterministic, no atomics on
-// floating point).  Levels of at most PT_TAIL_CELLS cells run inside block 0.
+// floating point).  Levels of at most tail_cells cells (an option) run inside block 0.
 //
 // Mixed precision (pattern "FP32 sweeps inside FP64 refinement"): the CG
 // vectors, dot products, scalars and the defect r = rhs - A p stay FP64; the
@@ -25,8 +25,6 @@
 namespace hf {
 
 constexpr int PT_THREADS = 1024;
-constexpr long long PT_TAIL_CELLS = 1024;        // block-0 tail read from global memory
-constexpr long long PT_SMEM_TAIL_CELLS = 1024;   // block-0 tail held in shared memory
 constexpr long long PT_SPIN_LIMIT = 1ll << 26;   // ~0.1-1 s of polling
 
 template <typename MT>
@@ -45,6 +43,7 @@ struct PcgpArgs {
     double* part;        // [8][gridDim.x] block partials
     unsigned int* bar;   // barrier arrival counter (zeroed before each launch)
     int* err;            // barrier timeout flag
+    long long tail_cells;  // largest level block 0 runs alone (shared memory when it fits)
 };
 
 // ---------------------------------------------------------------- barrier
@@ -110,7 +109,7 @@ __device__ inline double grid_total(const AT& A, int q) {
 }
 
 // block 0's copy of the level table whose tail levels point into dynamic
-// shared memory (set up once per solve by pl_load_tail)
+// shared memory (set up once per solve by pl_build_tail)
 template <typename MT>
 __device__ inline MgLevelsT<MT>* tail_levels() {
     __shared__ MgLevelsT<MT> table;
@@ -119,8 +118,11 @@ __device__ inline MgLevelsT<MT>* tail_levels() {
 
 extern __shared__ __align__(16) unsigned char pt_dyn_smem[];
 
+// block 0: the tail levels lf..nl-1 built directly in dynamic shared memory
+// (level lf coarsened from the grid's level lf-1, each further level from the
+// shared one above it); the grid never builds them in global memory
 template <typename MT>
-__device__ void pl_load_tail(const PcgpArgs<MT>& A) {
+__device__ void pl_build_tail(const PcgpArgs<MT>& A) {
     MgLevelsT<MT>* S = tail_levels<MT>();
     const int dims = A.g.dims;
     if (threadIdx.x == 0) {
@@ -139,18 +141,10 @@ __device__ void pl_load_tail(const PcgpArgs<MT>& A) {
     }
     __syncthreads();
     for (int l = A.lf; l < A.M.nl; ++l) {
-        const LevelT<MT>& G = A.M.lv[l];
-        const LevelT<MT>& L = S->lv[l];
-        for (long long c = threadIdx.x; c < G.N; c += blockDim.x) { L.diag[c] = G.diag[c]; L.idg[c] = G.idg[c]; }
-        long long nf[3] = {(long long)(G.nx + 1) * G.ny * G.nz, (long long)G.nx * (G.ny + 1) * G.nz,
-                           (long long)G.nx * G.ny * (G.nz + 1)};
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if (d >= dims) break;
-            for (long long f = threadIdx.x; f < nf[d]; f += blockDim.x) L.cf[d][f] = G.cf[d][f];
-        }
+        if (l == A.lf) pl_coarsen(A.M.lv[l - 1], S->lv[l], dims, threadIdx.x, blockDim.x);
+        else pl_coarsen(S->lv[l - 1], S->lv[l], dims, threadIdx.x, blockDim.x);
+        __syncthreads();
     }
-    __syncthreads();
 }
 
 // z = B r: the level-0 zero-start red half sweep has been done by the caller;
@@ -261,7 +255,9 @@ __device__ void pl_build_operator(const PcgpArgs<MT>& A) {
         if (copy) { P0.diag[c] = (MT)diag; P0.idg[c] = (MT)idg; }
     }
     grid_sync(A);
-    for (int l = 1; l < A.M.nl; ++l) {
+    // the shared-memory tail levels are built by block 0 (pl_build_tail)
+    const int lend = (A.smem_tail && A.lf < A.M.nl) ? A.lf : A.M.nl;
+    for (int l = 1; l < lend; ++l) {
         pl_coarsen(A.M.lv[l - 1], A.M.lv[l], g.dims, t0, TT);
         grid_sync(A);
     }
@@ -282,11 +278,18 @@ __global__ void __launch_bounds__(PT_THREADS) k_pressure_persistent(PcgpArgs<MT>
     const bool jac = A.jacobi != 0;
     // ---- operator hierarchy for this sweep's rAU (tail levels to shared memory)
     pl_build_operator(A);
-    if (A.smem_tail && A.lf < A.M.nl && blockIdx.x == 0) pl_load_tail(A);
-    // ---- r = rhs - A p, residual sums; z0 (Jacobi, or the level-0 red start)
+    // ---- block 0 builds the shared-memory tail while the other blocks form
+    // r = rhs - A p, the residual sums and z0 (Jacobi, or the level-0 red start)
+    const bool tail_b0 = A.smem_tail && A.lf < A.M.nl;
+    if (tail_b0 && blockIdx.x == 0) pl_build_tail(A);
+    long long rc0 = t0, RT = T;
+    if (tail_b0 && gridDim.x > 1) {
+        RT = T - blockDim.x;
+        rc0 = blockIdx.x == 0 ? g.N : t0 - blockDim.x;
+    }
     double s_rz = 0, s_rr = 0, s_bb = 0, s1 = 0, s2 = 0, s3 = 0;
     double pbar = F.scal[SC_SUM_P] * g.iN;
-    for (long long c = t0; c < g.N; c += T) {
+    for (long long c = rc0; c < g.N; c += RT) {
         int i, j, k;
         cell_ijk(g, c, i, j, k);
         uint16_t f = F.flags[c];
@@ -466,13 +469,13 @@ static cudaError_t launch_pp(PcgpArgs<MT>& A, int nblk, cudaStream_t s) {
     A.smem_tail = 0;
     size_t bytes = 0;
     for (int l = 1; l < A.M.nl; ++l) {
-        if (A.M.lv[l].N > PT_SMEM_TAIL_CELLS) continue;
+        if (A.M.lv[l].N > A.tail_cells) continue;
         size_t b = tail_bytes(A.M, A.g.dims, l);
         if (b <= PT_SMEM_BUDGET) { A.lf = l; A.smem_tail = 1; bytes = b; break; }
     }
     if (!A.smem_tail) {
         for (int l = 1; l < A.M.nl; ++l)
-            if (A.M.lv[l].N <= PT_TAIL_CELLS) { A.lf = l; break; }
+            if (A.M.lv[l].N <= A.tail_cells) { A.lf = l; break; }
     }
     if (bytes > 0) {
         cudaError_t e = cudaFuncSetAttribute(k_pressure_persistent<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -495,21 +498,21 @@ static cudaError_t launch_pp(PcgpArgs<MT>& A, int nblk, cudaStream_t s) {
 
 cudaError_t launch_pressure_persistent(const Grid& g, const Fields& F, const MgLevels& M, int jacobi,
                                        int coarse_sweeps, double reltol, int maxit, int nblk, double* part,
-                                       unsigned int* bar, int* err, cudaStream_t s) {
+                                       unsigned int* bar, int* err, long long tail_cells, cudaStream_t s) {
     PcgpArgs<double> A;
     A.g = g; A.F = F; A.L0d = M.lv[0]; A.M = M; A.zp = M.lv[0].x;
     A.coarse_sweeps = coarse_sweeps; A.jacobi = jacobi; A.reltol = reltol; A.maxit = maxit;
-    A.part = part; A.bar = bar; A.err = err;
+    A.part = part; A.bar = bar; A.err = err; A.tail_cells = tail_cells;
     return launch_pp(A, nblk, s);
 }
 
 cudaError_t launch_pressure_persistent32(const Grid& g, const Fields& F, const MgLevels& M, const MgLevels32& M32,
                                          int coarse_sweeps, double reltol, int maxit, int nblk, double* part,
-                                         unsigned int* bar, int* err, cudaStream_t s) {
+                                         unsigned int* bar, int* err, long long tail_cells, cudaStream_t s) {
     PcgpArgs<float> A;
     A.g = g; A.F = F; A.L0d = M.lv[0]; A.M = M32; A.zp = M32.lv[0].x;
     A.coarse_sweeps = coarse_sweeps; A.jacobi = 0; A.reltol = reltol; A.maxit = maxit;
-    A.part = part; A.bar = bar; A.err = err;
+    A.part = part; A.bar = bar; A.err = err; A.tail_cells = tail_cells;
     return launch_pp(A, nblk, s);
 }
 
