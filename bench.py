@@ -58,7 +58,7 @@ def PCG_ITERS_FACTOR(piters):
 # workload (dram__bytes_read.sum + dram__bytes_write.sum; mixed: the FP32
 # V-cycle variant).  At 262k cells the pressure hierarchy stays in L2, so
 # this is far below the algorithmic count.
-TRAFFIC = {("pcg", "mixed"): 10.661632e6 + 0.983808e6, ("pcg", "fp64"): 12.071168e6 + 0.745728e6}
+TRAFFIC = {("pcg", "mixed"): 10.674176e6 + 1.420288e6, ("pcg", "fp64"): 12.108800e6 + 0.996608e6}
 
 # FP64 flops of one launch of the FP64 assembly kernels on this workload
 # (ncu: 2 x DFMA + DADD + DMUL thread instructions).  These kernels are bound
