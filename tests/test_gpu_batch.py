@@ -15,18 +15,24 @@ def uneven_cases(model="kepsilon"):
             G.case_cylinder(40, 20, model=model)]
 
 
+OPTION_SETS = {"defaults": {}, "maskB_vanleer": dict(continuity_mask=1, convection=2)}
+
+
+@pytest.mark.parametrize("options", sorted(OPTION_SETS))
 @pytest.mark.parametrize("precision", [0, 1])
-def test_batch_equals_individual_solves_bit_for_bit(precision):
+def test_batch_equals_individual_solves_bit_for_bit(precision, options):
     """Same per-problem arithmetic, block partition and summation order as
-    the single-problem persistent kernel: identical results."""
+    the single-problem persistent kernel: identical results, also with
+    reading B of the continuity mask and vanLeer convection."""
     from paper_2606_06135_gb300.hfdib import BatchSolver, Solver
+    opts = OPTION_SETS[options]
     cases = uneven_cases()
-    bs = BatchSolver(cases, precision=precision)
+    bs = BatchSolver(cases, precision=precision, **opts)
     r = bs.sweep(12)
     assert r.shape == (3, 10)
     assert np.all(np.isfinite(r))
     for i, c in enumerate(cases):
-        s = Solver(c, precision=precision)
+        s = Solver(c, precision=precision, **opts)
         s.sweep(12)
         fb = bs.problem(i).fields()
         fs = s.fields()
