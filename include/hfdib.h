@@ -141,7 +141,13 @@ typedef struct {
                                     most this many cells run inside one thread block
                                     (in shared memory when they fit), the others
                                     as grid-wide phases (0: the library default)   */
-    int32_t reserved;
+    int32_t p_cg32;              /* precision = 1 only: 1 runs the pressure correction
+                                    solve's CG product and vectors in FP32 as well
+                                    (dots accumulated in FP64; the start defect
+                                    r0 = b - A p and p itself stay FP64, so the
+                                    steady state still solves the FP64 equations);
+                                    0 keeps them FP64 (default).  Single problems
+                                    only (hfdib_create_batch rejects it)          */
 } hfdib_options;
 
 typedef struct hfdib_ctx* hfdib_handle;

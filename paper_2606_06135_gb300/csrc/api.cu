@@ -243,7 +243,8 @@ void enqueue_part_a(Ctx* h, long long* L, bool with_pressure = true) {
         if (F.mixed) {
             PROF(h, HFDIB_K_PCG, launch_pressure_persistent32(g, F, M, h->mg32, h->coarse_sweeps,
                                                                h->opt.p_reltol, h->opt.p_maxiter, h->pblocks,
-                                                               h->ppart, h->pbar, h->perr, h->tail_cells, s));
+                                                               h->ppart, h->pbar, h->perr, h->tail_cells,
+                                                               h->opt.p_cg32, s));
             (*L)++;
         } else {
             PROF(h, HFDIB_K_PCG, launch_pressure_persistent(g, F, M, jac, h->coarse_sweeps, h->opt.p_reltol,
@@ -1062,6 +1063,8 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
     if (o.n_u < 1 || o.n_turb < 1 || o.p_maxiter < 0 || !(o.p_reltol >= 0)) return HFDIB_ERR_INVALID_ARG;
     if (o.precond < 0 || o.precond > 1 || o.p_check < 0 || o.mg_coarse_sweeps < 0) return HFDIB_ERR_INVALID_ARG;
     if (o.mg_tail_cells < 0 || o.mg_tail_cells > (1 << 20)) return HFDIB_ERR_INVALID_ARG;
+    // the FP32 correction solve is a variant of the mixed persistent pressure solve
+    if (o.p_cg32 < 0 || o.p_cg32 > 1 || (o.p_cg32 && o.precision != 1)) return HFDIB_ERR_INVALID_ARG;
     if (o.precision < 0 || o.precision > 1) return HFDIB_ERR_INVALID_ARG;
     if (o.wall_distance < 0 || o.wall_distance > 1) return HFDIB_ERR_INVALID_ARG;
     if (o.continuity_mask < 0 || o.continuity_mask > 1) return HFDIB_ERR_INVALID_ARG;
@@ -1181,6 +1184,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
     if (!rc && F.mixed) {
         for (int d = 0; d < 3; ++d) { A(F.phi32[d], g.nface[d]); A(F.r32[d], N); A(F.d32[d], N); }
         A(F.nut32, N); A(F.gam32, N); A(F.gamk32, N); A(F.diag32, N); A(F.z32, N);
+        if (o.p_cg32) { A(F.pd32[0], N); A(F.pd32[1], N); A(F.pq32, N); }
         // FP32 preconditioner hierarchy, same shapes as the FP64 one
         MgLevels32& M32 = h->mg32;
         memset(&M32, 0, sizeof(M32));
@@ -1653,6 +1657,7 @@ int hfdib_create_batch(int B, const hfdib_grid* grids, const double* const* lamb
     hfdib_options o;
     if (opt) o = *opt; else hfdib_default_options(&o);
     if (o.precond != 1) return HFDIB_ERR_INVALID_ARG;   // batched solve: multigrid preconditioner
+    if (o.p_cg32) return HFDIB_ERR_INVALID_ARG;         // the FP32 correction solve is single-problem
     o.p_persistent = 1;
     BatchCtx* b = new (std::nothrow) BatchCtx();
     if (!b) return HFDIB_ERR_OOM;

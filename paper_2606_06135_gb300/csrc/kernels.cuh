@@ -103,6 +103,8 @@ struct Fields {
     float* d32[3];     // FP32 correction
     float* diag32;     // relaxed diagonal of the scalar equation
     float* z32;        // preconditioned residual of the CG (mixed path)
+    float* pd32[2];    // FP32 CG search directions of the pressure solve (p_cg32)
+    float* pq32;       // FP32 A d of the pressure solve (p_cg32)
     int mixed;
     // scalars and reductions
     double* scal;
@@ -190,7 +192,8 @@ cudaError_t launch_pressure_persistent(const Grid& g, const Fields& F, const MgL
                                        unsigned int* bar, int* err, long long tail_cells, cudaStream_t s);
 cudaError_t launch_pressure_persistent32(const Grid& g, const Fields& F, const MgLevels& M, const MgLevels32& M32,
                                          int coarse_sweeps, double reltol, int maxit, int nblk, double* part,
-                                         unsigned int* bar, int* err, long long tail_cells, cudaStream_t s);
+                                         unsigned int* bar, int* err, long long tail_cells, int cg32,
+                                         cudaStream_t s);
 void launch_p_coef32(const Grid& g, const MgLevels& M, const MgLevels32& M32, cudaStream_t s);
 void launch_mom_smooth32(const Grid& g, const Params& P, const Fields& F, int colour, int zero_init, cudaStream_t s);
 void launch_scal_smooth32(const Grid& g, const Params& P, const Fields& F, int eq, int colour, int zero_init,

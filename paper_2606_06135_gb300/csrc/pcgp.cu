@@ -44,6 +44,9 @@ struct PcgpArgs {
     unsigned int* bar;   // barrier arrival counter (zeroed before each launch)
     int* err;            // barrier timeout flag
     long long tail_cells;  // largest level block 0 runs alone (shared memory when it fits)
+    int cg32;              // FP32 preconditioner only: CG vectors and product in FP32
+    float* cd32[2];        // FP32 search directions (cg32)
+    float* cq32;           // FP32 A d (cg32)
 };
 
 // ---------------------------------------------------------------- barrier
@@ -193,9 +196,11 @@ __device__ void pl_vcycle_rest(const PcgpArgs<MT>& A, int qdot) {
             grid_sync(A);
         }
     }
-    // final red half sweep of level 0 with r.z
+    // final red half sweep of level 0 with r.z (the CG residual: FP64, or
+    // under cg32 the FP32 one held in level 0's right-hand side)
     const LevelT<MT>& L0 = M.lv[0];
     const double* r = A.F.r;
+    const bool r32 = A.cg32 != 0;
     double rz = 0.0;
     const long long NP = pl_npairs(L0);
     for (long long p = t0; p < NP; p += TT) {
@@ -208,7 +213,7 @@ __device__ void pl_vcycle_rest(const PcgpArgs<MT>& A, int qdot) {
             long long c = c0 + o;
             if (((i0 + o + j + k) & 1) == 0)
                 L0.x[c] = (L0.b[c] + pl_offsum(L0, dims, L0.x, c, i0 + o, j, k)) * L0.idg[c];
-            rz += r[c] * (double)L0.x[c];
+            rz += (r32 ? (double)L0.b[c] : r[c]) * (double)L0.x[c];
         }
     }
     block_partial(A, qdot, rz);
@@ -312,6 +317,9 @@ __global__ void __launch_bounds__(PT_THREADS) k_pressure_persistent(PcgpArgs<MT>
         double r = rhs - Ap;
         F.r[c] = r;
         F.d[0][c] = 0.0;
+        if constexpr (sizeof(MT) == 4) {
+            if (A.cg32) A.cd32[0][c] = 0.0f;
+        }
         F.pn[c] = F.p[c];
         if (jac) {
             double zz = r * L0.idg[c];
@@ -360,6 +368,60 @@ __global__ void __launch_bounds__(PT_THREADS) k_pressure_persistent(PcgpArgs<MT>
         while (it < A.maxit) {
             if (*A.err) break;
             double beta = it == 0 ? 0.0 : rz / rz_prev;
+            if constexpr (sizeof(MT) == 4) {
+            if (A.cg32) {
+                // the correction solve in FP32 (P1): the product with the FP32
+                // copy of the operator, FP32 vectors, dots accumulated in FP64;
+                // the start defect (r0 above) and p stay FP64
+                const float* dold = A.cd32[it & 1];
+                float* dnew = A.cd32[(it + 1) & 1];
+                const float fb = (float)beta;
+                double s_dq = 0.0;
+                for (long long c = t0; c < g.N; c += T) {
+                    int i, j, k;
+                    cell_ijk(g, c, i, j, k);
+                    const int idx[3] = {i, j, k};
+                    float zc = (float)z[c];
+                    float acc = (float)P0.diag[c] * zc;
+                    #pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        if (d >= g.dims) break;
+                        long long fl = face_lo(g, d, i, j, k);
+                        if (idx[d] > 0) acc -= (float)P0.cf[d][fl] * (float)z[c - g.stride[d]];
+                        if (idx[d] < g.n[d] - 1) acc -= (float)P0.cf[d][fl + face_stride(g, d)] * (float)z[c + g.stride[d]];
+                    }
+                    float dP = zc + fb * dold[c];
+                    float qv = it == 0 ? acc : acc + fb * A.cq32[c];
+                    dnew[c] = dP;
+                    A.cq32[c] = qv;
+                    s_dq += (double)dP * (double)qv;
+                }
+                block_partial(A, Q_DQ, s_dq);
+                grid_sync(A);
+                double dq = grid_total(A, Q_DQ);
+                double alpha = dq != 0.0 ? rz / dq : 0.0;
+                const float fa = (float)alpha;
+                double s_r2 = 0.0;
+                for (long long c = t0; c < g.N; c += T) {
+                    F.pn[c] += alpha * (double)dnew[c];
+                    float r = (float)P0.b[c] - fa * A.cq32[c];
+                    P0.b[c] = (MT)r;
+                    s_r2 += (double)r * (double)r;
+                    int i, j, k;
+                    cell_ijk(g, c, i, j, k);
+                    if (((i + j + k) & 1) == 0) z[c] = (MT)(r * (float)P0.idg[c]);
+                }
+                block_partial(A, Q_RR, s_r2);
+                grid_sync(A);
+                double rr = grid_total(A, Q_RR);
+                rz_prev = rz;
+                pl_vcycle_rest(A, Q_RZ);
+                rz = grid_total(A, Q_RZ);
+                ++it;
+                if (!(rr > tol2)) break;
+                continue;
+            }
+            }
             const double* dold = F.d[it & 1];
             double* dnew = F.d[(it + 1) & 1];
             // d = z + beta d_old; q = A d = A z + beta q_old (linearity: the
@@ -503,16 +565,19 @@ cudaError_t launch_pressure_persistent(const Grid& g, const Fields& F, const MgL
     A.g = g; A.F = F; A.L0d = M.lv[0]; A.M = M; A.zp = M.lv[0].x;
     A.coarse_sweeps = coarse_sweeps; A.jacobi = jacobi; A.reltol = reltol; A.maxit = maxit;
     A.part = part; A.bar = bar; A.err = err; A.tail_cells = tail_cells;
+    A.cg32 = 0; A.cd32[0] = A.cd32[1] = nullptr; A.cq32 = nullptr;
     return launch_pp(A, nblk, s);
 }
 
 cudaError_t launch_pressure_persistent32(const Grid& g, const Fields& F, const MgLevels& M, const MgLevels32& M32,
                                          int coarse_sweeps, double reltol, int maxit, int nblk, double* part,
-                                         unsigned int* bar, int* err, long long tail_cells, cudaStream_t s) {
+                                         unsigned int* bar, int* err, long long tail_cells, int cg32,
+                                         cudaStream_t s) {
     PcgpArgs<float> A;
     A.g = g; A.F = F; A.L0d = M.lv[0]; A.M = M32; A.zp = M32.lv[0].x;
     A.coarse_sweeps = coarse_sweeps; A.jacobi = 0; A.reltol = reltol; A.maxit = maxit;
     A.part = part; A.bar = bar; A.err = err; A.tail_cells = tail_cells;
+    A.cg32 = cg32; A.cd32[0] = F.pd32[0]; A.cd32[1] = F.pd32[1]; A.cq32 = F.pq32;
     return launch_pp(A, nblk, s);
 }
 

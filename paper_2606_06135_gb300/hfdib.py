@@ -65,7 +65,7 @@ class Options(C.Structure):
                 ("p_check", C.c_int32), ("mg_coarse_sweeps", C.c_int32), ("graph", C.c_int32),
                 ("p_persistent", C.c_int32), ("freeze_switch", C.c_int32), ("frozen_turbulence", C.c_int32),
                 ("wall_distance", C.c_int32), ("continuity_mask", C.c_int32), ("convection", C.c_int32),
-                ("mg_tail_cells", C.c_int32), ("reserved", C.c_int32)]
+                ("mg_tail_cells", C.c_int32), ("p_cg32", C.c_int32)]
 
 
 _LIB = None

@@ -352,3 +352,27 @@ def test_degenerate_grids_match_oracle(name):
         err = float(np.linalg.norm(got[n].ravel() - np.asarray(ref).ravel()))
         assert err <= 1e-9 * max(float(np.linalg.norm(ref)), 1.0), (n, err)
     s.close()
+
+
+@pytest.mark.parametrize("name", ["cylinder_keps", "bfs_sst"])
+def test_converged_state_with_fp32_correction_solve(name):
+    """p_cg32: the pressure correction solve's CG product and vectors in FP32
+    too (P1); the start defect and p stay FP64, so the steady state still
+    solves the FP64 equations: within 1e-4 of the FP64 oracle per field, like
+    the other mixed solves."""
+    mk, maxit = CONVERGED[name]
+    case = mk()
+    o = O.Oracle(case)
+    _, ores = o.solve(tol=1e-12, max_iter=2000)
+    s = make_solver(case, precision=1, p_cg32=1)
+    rc, it, res = s.solve(tol=1e-12, max_iter=maxit, check_every=20)
+    assert rc == 0, (rc, it, res)
+    errs = compare_fields(s, o, 1e-4)
+    print("p_cg32 rel-L2 vs FP64 oracle (%s, %d sweeps):" % (name, it), {k: "%.2e" % v for k, v in errs.items()})
+    s.close()
+
+
+def test_fp32_correction_solve_needs_the_mixed_path():
+    from paper_2606_06135_gb300.hfdib import HfdibError
+    with pytest.raises(HfdibError):
+        make_solver(G.case_cylinder(32, 16), precision=0, p_cg32=1)
