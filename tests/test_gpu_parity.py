@@ -289,7 +289,8 @@ def test_oracle_residuals_at_the_full_size_converged_state():
     1e-6 on the GPU.  The oracle, given that state and the GPU's wall-function
     branches, evaluates the scaled residuals of the next sweep (App. D) and
     finds the GPU's own: the GPU's converged state solves the oracle's
-    equations at full size."""
+    equations at full size.  The same state's reattachment point is checked
+    against the paper's (Sec. 3.3)."""
     from paper_2606_06135_gb300.hfdib import Solver
     case = G.case_bfs(1024, 256)
     s = Solver(case, precision=1, freeze_switch=300, p_reltol=0.2)
@@ -318,6 +319,15 @@ def test_oracle_residuals_at_the_full_size_converged_state():
     for key in ("p", "omega", "k"):
         assert r[key] <= 1e-5, (key, r[key], got[key])
     assert max(got.values()) <= 2e-6
+    # the converged step reattaches (tau_x of the bottom wall turns positive,
+    # Sec. 3.3) within 15 % of the 4.43 step heights the paper reports for
+    # its solver (the step height is 1, its edge at x = 0)
+    from oracle import forces as Fo
+    xs = m.x0 + (np.arange(m.nx) + 0.5) * m.dx
+    tau = s.wall_shear("ymin").cpu().numpy()[0]
+    x_reat = Fo.reattachment(xs[xs > 0.0], tau[xs > 0.0])
+    print("reattachment length: %.3f step heights" % x_reat)
+    assert x_reat is not None and abs(x_reat - 4.43) <= 0.15 * 4.43, x_reat
 
 
 def _all_solid():
