@@ -369,58 +369,58 @@ __global__ void __launch_bounds__(PT_THREADS) k_pressure_persistent(PcgpArgs<MT>
             if (*A.err) break;
             double beta = it == 0 ? 0.0 : rz / rz_prev;
             if constexpr (sizeof(MT) == 4) {
-            if (A.cg32) {
-                // the correction solve in FP32 (P1): the product with the FP32
-                // copy of the operator, FP32 vectors, dots accumulated in FP64;
-                // the start defect (r0 above) and p stay FP64
-                const float* dold = A.cd32[it & 1];
-                float* dnew = A.cd32[(it + 1) & 1];
-                const float fb = (float)beta;
-                double s_dq = 0.0;
-                for (long long c = t0; c < g.N; c += T) {
-                    int i, j, k;
-                    cell_ijk(g, c, i, j, k);
-                    const int idx[3] = {i, j, k};
-                    float zc = (float)z[c];
-                    float acc = (float)P0.diag[c] * zc;
-                    #pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        if (d >= g.dims) break;
-                        long long fl = face_lo(g, d, i, j, k);
-                        if (idx[d] > 0) acc -= (float)P0.cf[d][fl] * (float)z[c - g.stride[d]];
-                        if (idx[d] < g.n[d] - 1) acc -= (float)P0.cf[d][fl + face_stride(g, d)] * (float)z[c + g.stride[d]];
+                if (A.cg32) {
+                    // the correction solve in FP32 (P1): the product with the FP32
+                    // copy of the operator, FP32 vectors, dots accumulated in FP64;
+                    // the start defect (r0 above) and p stay FP64
+                    const float* dold = A.cd32[it & 1];
+                    float* dnew = A.cd32[(it + 1) & 1];
+                    const float fb = (float)beta;
+                    double s_dq = 0.0;
+                    for (long long c = t0; c < g.N; c += T) {
+                        int i, j, k;
+                        cell_ijk(g, c, i, j, k);
+                        const int idx[3] = {i, j, k};
+                        float zc = (float)z[c];
+                        float acc = (float)P0.diag[c] * zc;
+                        #pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            if (d >= g.dims) break;
+                            long long fl = face_lo(g, d, i, j, k);
+                            if (idx[d] > 0) acc -= (float)P0.cf[d][fl] * (float)z[c - g.stride[d]];
+                            if (idx[d] < g.n[d] - 1) acc -= (float)P0.cf[d][fl + face_stride(g, d)] * (float)z[c + g.stride[d]];
+                        }
+                        float dP = zc + fb * dold[c];
+                        float qv = it == 0 ? acc : acc + fb * A.cq32[c];
+                        dnew[c] = dP;
+                        A.cq32[c] = qv;
+                        s_dq += (double)dP * (double)qv;
                     }
-                    float dP = zc + fb * dold[c];
-                    float qv = it == 0 ? acc : acc + fb * A.cq32[c];
-                    dnew[c] = dP;
-                    A.cq32[c] = qv;
-                    s_dq += (double)dP * (double)qv;
+                    block_partial(A, Q_DQ, s_dq);
+                    grid_sync(A);
+                    double dq = grid_total(A, Q_DQ);
+                    double alpha = dq != 0.0 ? rz / dq : 0.0;
+                    const float fa = (float)alpha;
+                    double s_r2 = 0.0;
+                    for (long long c = t0; c < g.N; c += T) {
+                        F.pn[c] += alpha * (double)dnew[c];
+                        float r = (float)P0.b[c] - fa * A.cq32[c];
+                        P0.b[c] = (MT)r;
+                        s_r2 += (double)r * (double)r;
+                        int i, j, k;
+                        cell_ijk(g, c, i, j, k);
+                        if (((i + j + k) & 1) == 0) z[c] = (MT)(r * (float)P0.idg[c]);
+                    }
+                    block_partial(A, Q_RR, s_r2);
+                    grid_sync(A);
+                    double rr = grid_total(A, Q_RR);
+                    rz_prev = rz;
+                    pl_vcycle_rest(A, Q_RZ);
+                    rz = grid_total(A, Q_RZ);
+                    ++it;
+                    if (!(rr > tol2)) break;
+                    continue;
                 }
-                block_partial(A, Q_DQ, s_dq);
-                grid_sync(A);
-                double dq = grid_total(A, Q_DQ);
-                double alpha = dq != 0.0 ? rz / dq : 0.0;
-                const float fa = (float)alpha;
-                double s_r2 = 0.0;
-                for (long long c = t0; c < g.N; c += T) {
-                    F.pn[c] += alpha * (double)dnew[c];
-                    float r = (float)P0.b[c] - fa * A.cq32[c];
-                    P0.b[c] = (MT)r;
-                    s_r2 += (double)r * (double)r;
-                    int i, j, k;
-                    cell_ijk(g, c, i, j, k);
-                    if (((i + j + k) & 1) == 0) z[c] = (MT)(r * (float)P0.idg[c]);
-                }
-                block_partial(A, Q_RR, s_r2);
-                grid_sync(A);
-                double rr = grid_total(A, Q_RR);
-                rz_prev = rz;
-                pl_vcycle_rest(A, Q_RZ);
-                rz = grid_total(A, Q_RZ);
-                ++it;
-                if (!(rr > tol2)) break;
-                continue;
-            }
             }
             const double* dold = F.d[it & 1];
             double* dnew = F.d[(it + 1) & 1];
