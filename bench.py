@@ -46,6 +46,24 @@ P_RELTOL = 0.2         # per-sweep pressure tolerance on this workload (time to 
                        # 0.1 -> 19.7 s, 0.2 -> 17.2 s mixed; 0.3 diverged); both legs use it
 MAX_SOLVE_SWEEPS = 20000
 
+
+def max_over_ranks(x, dist, device):
+    """The job's time is its slowest rank's: the largest of a per-rank time
+    over the process group (x itself on one rank)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank, world, seconds):
+    """Whole-job throughput of `world` replicas that each process
+    units_per_rank in `seconds` (the slowest rank's time)."""
+    return world * units_per_rank / seconds
+
+
 # Algorithmic bytes per cell for one launch group of each kernel class
 # (2D, FP64 words of 8 B, minimum traffic with perfect neighbour reuse,
 # face arrays counted as one word per cell and direction, flags 2 B).
@@ -385,10 +403,7 @@ def main():
         piters = hist[:, 7]
         fixed, per_it = s.launch_counts()
         launches = int(args.steps * fixed + per_it * piters.sum())
-        if dist is not None:
-            t = torch.tensor([t_dev], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_dev = float(t.item())
+        t_dev = max_over_ranks(t_dev, dist, dev)
         # roofline of the dominant kernel class (host-driven sweeps, event pairs)
         prof = s.profile(3)
         dname, (dus, dcalls) = max(prof.items(), key=lambda kv: kv[1][0])
@@ -423,7 +438,7 @@ def main():
                         "unit": "GFLOP/s (FP64)", "frac": alu[top]["achieved"] / FP64_PEAK_GFLOPS,
                         "peak_source": "nominal", "per_class": alu}
         s.close()
-        return dict(value=world * N * args.steps / t_dev, ms=1e3 * t_dev / args.steps, clocks=clk,
+        return dict(value=replica_rate(N * args.steps, world, t_dev), ms=1e3 * t_dev / args.steps, clocks=clk,
                     launches=launches, piters=float(piters.mean()), roofline=roof, roofline_alu=roof_alu)
 
     res = {p: timed_sweeps(p) for p in ("mixed", "fp64")}
@@ -468,15 +483,19 @@ def main():
         t_wall = time.perf_counter() - t0
         t_solve = e0.elapsed_time(e1) / 1e3
         s2.close()
+        barrier()
+        t_wall = max_over_ranks(t_wall, dist, dev)
+        t_solve = max_over_ranks(t_solve, dist, dev)
         conv = rc == 0
-        leg = {"converged": conv, "sweeps": iters, "seconds": t_solve, "solves_per_s": (world / t_solve) if conv else 0.0,
+        leg = {"converged": conv, "sweeps": iters, "seconds": t_solve,
+               "solves_per_s": replica_rate(1, world, t_solve) if conv else 0.0,
                "final_max_residual": float(max(r[:6])), "tol": TOL}
         if e2e:
             d2h = sum(v.numel() * 8 for v in host.values()) + 8 * hfdib.NRES * ((iters + 99) // 100)
-            leg["e2e"] = {"value": world * N * iters / t_wall, "unit": "cell-updates/s",
+            leg["e2e"] = {"value": replica_rate(N * iters, world, t_wall), "unit": "cell-updates/s",
                           "h2d_bytes_per_step": 2 * N * 8, "d2h_bytes_per_step": d2h,
                           "step": "host lambda/ywall -> create (IB geometry) -> solve to 1e-6 -> host fields",
-                          "solves_per_s": (world / t_wall) if conv else 0.0}
+                          "solves_per_s": replica_rate(1, world, t_wall) if conv else 0.0}
         return leg
 
     if not args.no_solve:
