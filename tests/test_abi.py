@@ -72,3 +72,43 @@ def test_force_and_wall_shear_reject_null_handles_without_touching_the_gpu(libpa
     n = C.c_int64(-5)
     assert lib.hfdib_wall_shear(None, 2, None, C.byref(n)) == -1
     assert n.value == -5
+
+
+def _header_structs():
+    """typedef struct { ... } name; of include/hfdib.h as name -> [(field,
+    c type, array length)], comments removed, in declaration order."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct\s*\{(.*?)\}\s*(\w+)\s*;", src, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            ctype, names = decl.split(" ", 1)
+            for nm in names.split(","):
+                nm = nm.strip()
+                m = re.match(r"(\w+)(?:\[(\d+)\])?$", nm)
+                fields.append((m.group(1), ctype, int(m.group(2)) if m.group(2) else 1))
+        out[name] = fields
+    return out
+
+
+def test_binding_structs_match_the_header():
+    """The ctypes mirrors of hfdib_grid, hfdib_bc, hfdib_options and
+    hfdib_tune list the header's fields in the same order with the same types
+    (an options field added on one side only would shift every later one)."""
+    import ctypes as C
+    from paper_2606_06135_gb300 import hfdib
+    ctype_of = {"int32_t": C.c_int32, "double": C.c_double}
+    structs = _header_structs()
+    for cname, pyc in (("hfdib_grid", hfdib.Grid), ("hfdib_bc", hfdib.Bc), ("hfdib_options", hfdib.Options),
+                       ("hfdib_tune", hfdib.Tune)):
+        want = structs[cname]
+        got = pyc._fields_
+        assert [f[0] for f in got] == [w[0] for w in want], cname
+        for (fname, ftype), (_, ctype, n) in zip(got, want):
+            base = ctype_of[ctype]
+            expect = base * n if n > 1 else base
+            assert ftype == expect or (n > 1 and ftype._type_ == base and ftype._length_ == n), (cname, fname)
