@@ -133,7 +133,9 @@ typedef struct {
                                     hfdib_adjoint_grad then differentiates it)     */
     int32_t convection;          /* momentum convection scheme (App. B): 0 upwind
                                     (Sec. 3.1, default); 1 linearUpwind, 2 vanLeer,
-                                    both as a deferred correction of the bounded
+                                    3 linearUpwind with each cell's gradient
+                                    scaled by its Barth-Jespersen limiter, all
+                                    as a deferred correction of the bounded
                                     upwind rows from the sweep-start velocity and
                                     its Gauss-linear gradient (hfdib_adjoint_grad
                                     needs 0)                                       */

@@ -92,7 +92,8 @@ TAG_FC, TAG_BC, TAG_IC = 0, 1, 2
 # wall functions use in y+ and omega_ib (the comparison of App. A)
 # continuity_mask: "A" (default) m = 1 where lambda < 1, else 0; "B" m = 1 - lambda
 # convection: scheme of the momentum convection term, "upwind" (Sec. 3.1,
-# default) or, by deferred correction, "linearUpwind" / "vanLeer" (App. B)
+# default) or, by deferred correction, "linearUpwind" / "vanLeer" /
+# "linearUpwindLimited" (App. B; the last with a cell-limited gradient)
 DEFAULT_OPTS = dict(urf_u=0.7, urf_p=0.3, urf_turb=0.85, freeze_switch=0, wall_distance="y_eff",
                     continuity_mask="A", convection="upwind")
 
@@ -519,7 +520,34 @@ def assemble_transport(m: Mesh, phi, gamma, spec):
     return aP, aM, aPl, b
 
 
-CONV_SCHEMES = ("upwind", "linearUpwind", "vanLeer")
+CONV_SCHEMES = ("upwind", "linearUpwind", "vanLeer", "linearUpwindLimited")
+
+
+def cell_limiter(m: Mesh, f, G):
+    """Cell-limited gradient factor l_P in [0, 1] (the Barth-Jespersen rule):
+    the largest l <= 1 for which every face extrapolation f_P + l grad f_P .
+    (x_f - x_P) = f_P +- l (Delta_d/2) df/dx_d stays within the minimum and
+    maximum of f over P and its interior neighbours.  G[d] = df/dx_d."""
+    fmax = f.copy()
+    fmin = f.copy()
+    for d in range(m.dims):
+        ax = 2 - d
+        n = m.n[d]
+        lo, hi = _sl(ax, 0, n - 1), _sl(ax, 1, n)
+        fmax[lo] = np.maximum(fmax[lo], f[hi])
+        fmin[lo] = np.minimum(fmin[lo], f[hi])
+        fmax[hi] = np.maximum(fmax[hi], f[lo])
+        fmin[hi] = np.minimum(fmin[hi], f[lo])
+    lim = np.ones(m.shape)
+    for d in range(m.dims):
+        for sgn in (1.0, -1.0):
+            delta = sgn * 0.5 * m.D[d] * G[d]
+            up = delta > 0.0
+            dn = delta < 0.0
+            with np.errstate(divide="ignore", invalid="ignore"):
+                lim = np.where(up, np.minimum(lim, (fmax - f) / np.where(up, delta, 1.0)), lim)
+                lim = np.where(dn, np.minimum(lim, (fmin - f) / np.where(dn, delta, 1.0)), lim)
+    return lim
 
 
 def face_correction(m: Mesh, phi_d, f, dfdx_d, d, scheme):
@@ -561,6 +589,11 @@ def convection_correction(m: Mesh, phi, f, G, scheme):
     out = _zeros(m.shape, f, *phi[:m.dims])
     if scheme == "upwind":
         return out
+    if scheme == "linearUpwindLimited":
+        # linearUpwind with each cell's gradient scaled by its limiter
+        lim = cell_limiter(m, f, G)
+        G = [lim * G[d] for d in range(m.dims)]
+        scheme = "linearUpwind"
     for d in range(m.dims):
         ax = 2 - d
         n = m.n[d]

@@ -217,6 +217,7 @@ void enqueue_part_a(Ctx* h, long long* L, bool with_pressure = true) {
     PROF(h, HFDIB_K_IMPOSED, launch_means(g, P, F, s));
     // a3: momentum assembly; a4: predictor; a5: correction (imposed rows)
     PROF(h, HFDIB_K_GRAD_U, launch_grad_u(g, F, s));
+    if (g.conv == 3) { PROF(h, HFDIB_K_GRAD_U, launch_conv_limit(g, F, s)); (*L)++; }
     PROF(h, HFDIB_K_MOM_ASM, launch_mom_asm(g, P, F, s));
     *L += 4;
     for (int n = 0; n < h->opt.n_u; ++n) {
@@ -1068,7 +1069,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
     if (o.precision < 0 || o.precision > 1) return HFDIB_ERR_INVALID_ARG;
     if (o.wall_distance < 0 || o.wall_distance > 1) return HFDIB_ERR_INVALID_ARG;
     if (o.continuity_mask < 0 || o.continuity_mask > 1) return HFDIB_ERR_INVALID_ARG;
-    if (o.convection < 0 || o.convection > 2) return HFDIB_ERR_INVALID_ARG;
+    if (o.convection < 0 || o.convection > 3) return HFDIB_ERR_INVALID_ARG;
     // the mixed path runs its FP32 V-cycle inside the persistent CG kernel
     if (o.precision == 1 && (o.p_persistent == 0 || o.precond != 1)) return HFDIB_ERR_INVALID_ARG;
     if (o.p_maxiter > 100000 || o.freeze_switch < 0) return HFDIB_ERR_INVALID_ARG;
@@ -1143,7 +1144,8 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
     }
     A(F.p, N); A(F.pn, N); A(F.pr, N); A(F.rAU, N);
     A(F.k, N); A(F.w, N); A(F.w2, N); A(F.nut, N); A(F.kib, N); A(F.wib, N);
-    A(F.G, 9 * N); A(F.mrow, 9 * N); A(F.Pk, N); A(F.S2, N); A(F.gam, N); A(F.gamk, N); A(F.sp, N); A(F.src, N); A(F.asus, N);
+    A(F.G, 9 * N); A(F.mrow, 9 * N);
+    if (o.convection == 3) A(F.Glim, 9 * N); A(F.Pk, N); A(F.S2, N); A(F.gam, N); A(F.gamk, N); A(F.sp, N); A(F.src, N); A(F.asus, N);
     A(F.bt, N); A(F.diag, N); A(F.ywall, N); A(F.flags, N);
     A(F.prhs, N); A(F.pdiag, N); A(F.r, N); A(F.z, N); A(F.d[0], N); A(F.d[1], N); A(F.q, N);
     A(F.scal, SC_NSCAL); A(F.partials, 16 * (long long)nb + 64); A(F.counters, 64);
@@ -1455,7 +1457,7 @@ int hfdib_get_launch_counts(hfdib_handle hh, int64_t* per_sweep, int64_t* per_pc
     bool turb = h->model != HFDIB_LAMINAR;
     int jac = h->opt.precond == 0;
     int tf = h->tail_from;
-    La = (turb ? 1 : 0) + 4 + 2 * h->opt.n_u + 2 +
+    La = (turb ? 1 : 0) + 4 + (h->g.conv == 3 ? 1 : 0) + 2 * h->opt.n_u + 2 +
          (h->pblocks > 0 ? 1 : (1 + (tf - 1) + (tf < h->mg.nl ? 1 : 0)) + 1 + (jac ? 0 : 5 * tf + 1) + 1);
     bool turb_b = turb && !h->opt.frozen_turbulence;
     Lb = 1 + (turb_b ? 4 + 2 * h->opt.n_turb + 2 + 2 * h->opt.n_turb + 1 : 0) + 1;
@@ -1484,6 +1486,7 @@ int hfdib_ib_force(hfdib_handle hh, double* force) {
                    F.uib[0], F.uib[1], F.uib[2], F.kib, F.wib, s);
     CK(cudaMemsetAsync(F.scal + SC_NLAM, 0, 2 * sizeof(double), s));
     launch_grad_u(g, F, s);
+    if (g.conv == 3) launch_conv_limit(g, F, s);
     launch_ib_force(g, F, s);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(force, F.scal + SC_FORCE, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -69,7 +69,8 @@ struct Grid {
     long long stride[3];
     long long nface[3];
     int mask_b;      // continuity mask: 0 reading A m = [lambda < 1], 1 reading B m = 1 - lambda
-    int conv;        // momentum convection: 0 upwind, 1 linearUpwind, 2 vanLeer (deferred correction)
+    int conv;        // momentum convection: 0 upwind, 1 linearUpwind, 2 vanLeer, 3 linearUpwind with a
+                     // cell-limited gradient (deferred correction)
 };
 
 // m div(phiHbyA), the source of the pressure equation (Eq. hfdibrans_2 with

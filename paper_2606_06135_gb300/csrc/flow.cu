@@ -223,9 +223,58 @@ __device__ __forceinline__ double transpose_src(const Grid& g, const Fields& F, 
 // keep bounded upwind, and -sum over interior faces of F_out (u_f - u_U)
 // goes to the right-hand side, from u and grad u at sweep start.  U is the
 // upwind cell of the face, D the other, s = +1 when D lies at +d from U.
-//   linearUpwind: u_f - u_U = s (Delta/2) du/dx_d|U
+//   linearUpwind: u_f - u_U = s (Delta/2) du/dx_d|U (scheme 3: times the
+//                 upwind cell's Barth-Jespersen limiter)
 //   vanLeer:      u_f - u_U = psi(r) (u_D - u_U)/2, psi = (r + |r|)/(1 + |r|),
 //                 r = 2 s Delta du/dx_d|U / (u_D - u_U) - 1 (no term where u_D = u_U)
+// Barth-Jespersen limiter of cell U for component q (scheme 3): the largest
+// l <= 1 keeping u_U + l (+-Delta_d/2) du/dx_d|U within the min/max of u over
+// U and its interior neighbours
+__device__ inline double conv_limiter(const Grid& g, const Fields& F, long long U, int iU, int jU, int kU, int q) {
+    const double* u = F.u[q];
+    const double uU = u[U];
+    double umax = uU, umin = uU;
+    #pragma unroll
+    for (int d = 0; d < 3 && d < g.dims; ++d) {
+        #pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            if (!interior(g, d, side, iU, jU, kU)) continue;
+            double v = u[nbr_cell(g, U, d, side)];
+            umax = fmax(umax, v);
+            umin = fmin(umin, v);
+        }
+    }
+    double l = 1.0;
+    #pragma unroll
+    for (int d = 0; d < 3 && d < g.dims; ++d) {
+        const double gd = F.G[(long long)(3 * d + q) * g.N + U];
+        #pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            double delta = (side ? -0.5 : 0.5) * g.D[d] * gd;
+            if (delta > 0.0) l = fmin(l, (umax - uU) / delta);
+            else if (delta < 0.0) l = fmin(l, (umin - uU) / delta);
+        }
+    }
+    return l;
+}
+
+// scheme 3: the cell-limited velocity gradient, Glim = l G per component
+__global__ void k_conv_limit(Grid g, Fields F) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    int i, j, k;
+    cell_ijk(g, c, i, j, k);
+    #pragma unroll
+    for (int q = 0; q < 3 && q < g.dims; ++q) {
+        double l = conv_limiter(g, F, c, i, j, k, q);
+        #pragma unroll
+        for (int d = 0; d < 3 && d < g.dims; ++d) {
+            long long e = (long long)(3 * d + q) * g.N + c;
+            F.Glim[e] = l * F.G[e];
+        }
+    }
+}
+
 __device__ inline double conv_src(const Grid& g, const Fields& F, long long c, int i, int j, int k, int q) {
     double corr = 0.0;
     const double* u = F.u[q];
@@ -233,7 +282,8 @@ __device__ inline double conv_src(const Grid& g, const Fields& F, long long c, i
     for (int d = 0; d < 3 && d < g.dims; ++d) {
         long long fl = face_lo(g, d, i, j, k);
         long long fs = face_stride(g, d);
-        const double* Gd = F.G + (long long)(3 * d + q) * g.N;   // d u_q / d x_d
+        // d u_q / d x_d (scheme 3: the limited copy written by k_conv_limit)
+        const double* Gd = (g.conv == 3 ? F.Glim : F.G) + (long long)(3 * d + q) * g.N;
         #pragma unroll
         for (int side = 0; side < 2; ++side) {
             if (!interior(g, d, side, i, j, k)) continue;
@@ -245,7 +295,7 @@ __device__ inline double conv_src(const Grid& g, const Fields& F, long long c, i
             double s = (out == (side == 1)) ? 1.0 : -1.0;
             double gU = Gd[U];
             double du;
-            if (g.conv == 1) {
+            if (g.conv != 2) {
                 du = s * (0.5 * g.D[d]) * gU;
             } else {
                 double uU = u[U], uD = u[out ? n : c];
@@ -635,6 +685,9 @@ void launch_means(const Grid& g, const Params& P, const Fields& F, cudaStream_t 
 }
 void launch_grad_u(const Grid& g, const Fields& F, cudaStream_t s) {
     k_grad_u<<<nblocks(g.N), BLOCK, 0, s>>>(g, F);
+}
+void launch_conv_limit(const Grid& g, const Fields& F, cudaStream_t s) {
+    k_conv_limit<<<nblocks(g.N), BLOCK, 0, s>>>(g, F);
 }
 void launch_mom_asm(const Grid& g, const Params& P, const Fields& F, cudaStream_t s) {
     k_mom_asm<<<rblocks(g.N), BLOCK, 0, s>>>(g, P, F);

@@ -73,6 +73,7 @@ struct Fields {
     double* kib;
     double* wib;
     double* G;         // 9*N velocity gradient, G[(3a+b)N + c] = d u_b / d x_a
+    double* Glim;      // 9*N its cell-limited copy (convection scheme 3 only)
     double* Pk;
     double* S2;
     double* gam;       // scalar equation diffusivity
@@ -165,6 +166,7 @@ void launch_init_flux(const Grid& g, const Fields& F, cudaStream_t s);
 void launch_means(const Grid& g, const Params& P, const Fields& F, cudaStream_t s);
 void launch_grad_u(const Grid& g, const Fields& F, cudaStream_t s);
 void launch_mom_asm(const Grid& g, const Params& P, const Fields& F, cudaStream_t s);
+void launch_conv_limit(const Grid& g, const Fields& F, cudaStream_t s);
 void launch_ib_force(const Grid& g, const Fields& F, cudaStream_t s);
 void launch_recirc(const Grid& g, const Fields& F, double x_rear, unsigned int* count, cudaStream_t s);
 void launch_wall_shear(const Grid& g, const Fields& F, int side, long long nf, double* tau, cudaStream_t s);

@@ -94,6 +94,8 @@ SWEEP_CASES = {
     "cylinder_keps_maskB": lambda: G.case_cylinder(48, 24),
     "cylinder_keps_linup": lambda: G.case_cylinder(48, 24),
     "bfs_sst_vanleer": lambda: G.case_bfs(64, 16),
+    "cylinder_keps_linupl": lambda: G.case_cylinder(48, 24),
+    "bfs_sst_linupl": lambda: G.case_bfs(64, 16),
     # odd sizes: the last x-pair of a row holds one cell, coarse levels round up
     "cylinder_keps_odd": lambda: G.case_cylinder(45, 23),
     "bfs_sst_odd": lambda: G.case_bfs(63, 17),
@@ -112,7 +114,9 @@ SWEEP_TOL = {"bfs_rke": 1e-8}
 SWEEP_OPTS = {"bfs_keps_yperp": (dict(wall_distance=1), dict(wall_distance="y_perp")),
               "cylinder_keps_maskB": (dict(continuity_mask=1), dict(continuity_mask="B")),
               "cylinder_keps_linup": (dict(convection=1), dict(convection="linearUpwind")),
-              "bfs_sst_vanleer": (dict(convection=2), dict(convection="vanLeer"))}
+              "bfs_sst_vanleer": (dict(convection=2), dict(convection="vanLeer")),
+              "cylinder_keps_linupl": (dict(convection=3), dict(convection="linearUpwindLimited")),
+              "bfs_sst_linupl": (dict(convection=3), dict(convection="linearUpwindLimited"))}
 
 
 @pytest.mark.parametrize("name", sorted(SWEEP_CASES))
@@ -266,12 +270,12 @@ def test_3d_converged_state_matches_oracle(precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("scheme", [1, 2])
+@pytest.mark.parametrize("scheme", [1, 2, 3])
 def test_converged_convection_schemes_match_oracle(scheme, precision):
-    """linearUpwind (1) and vanLeer (2) momentum convection (App. B, deferred
-    correction): the converged state matches the oracle's, FP64 within 1e-9,
-    mixed within 1e-4."""
-    name = {1: "linearUpwind", 2: "vanLeer"}[scheme]
+    """linearUpwind (1), vanLeer (2) and limited linearUpwind (3) momentum
+    convection (App. B, deferred correction): the converged state matches
+    the oracle's, FP64 within 1e-9, mixed within 1e-4."""
+    name = {1: "linearUpwind", 2: "vanLeer", 3: "linearUpwindLimited"}[scheme]
     case = G.case_cylinder(48, 24, model="laminar", Re=40.0)
     o = O.Oracle(case, dict(convection=name))
     _, ores = o.solve(tol=1e-12, max_iter=3000)

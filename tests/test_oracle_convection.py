@@ -118,3 +118,47 @@ def test_adjoint_refuses_other_schemes():
     o.sweep()
     with pytest.raises(ValueError):
         A.FrozenSteady(o)
+
+
+def test_cell_limiter_keeps_extrapolations_within_the_neighbour_bounds():
+    """Barth-Jespersen: l grad f extrapolated to each face stays within the
+    min/max of the cell and its neighbours; on a linear field the interior
+    limiter is 1 (the neighbours are a full cell away, the faces half)."""
+    m, _ = mesh(16, 9)
+    rng = np.random.default_rng(5)
+    f = rng.standard_normal(m.shape)
+    g = grad(m, f)
+    lim = O.cell_limiter(m, f, g)
+    assert np.all(lim >= 0.0) and np.all(lim <= 1.0)
+    fmax, fmin = f.copy(), f.copy()
+    for ax, n in ((2, m.nx), (1, m.ny)):
+        sl = lambda a, b: tuple(slice(a, b) if i == ax else slice(None) for i in range(3))
+        fmax[sl(0, n - 1)] = np.maximum(fmax[sl(0, n - 1)], f[sl(1, n)])
+        fmax[sl(1, n)] = np.maximum(fmax[sl(1, n)], f[sl(0, n - 1)])
+        fmin[sl(0, n - 1)] = np.minimum(fmin[sl(0, n - 1)], f[sl(1, n)])
+        fmin[sl(1, n)] = np.minimum(fmin[sl(1, n)], f[sl(0, n - 1)])
+    for d in range(2):
+        for sgn in (1.0, -1.0):
+            face = f + lim * sgn * 0.5 * m.D[d] * g[d]
+            assert np.all(face <= fmax + 1e-14) and np.all(face >= fmin - 1e-14)
+    X, Y, _ = G.cell_centres(G.case_uniform(16, 9)["grid"])
+    f = 0.7 * X - 1.3 * Y
+    lim = O.cell_limiter(m, f, grad(m, f))
+    assert np.all(lim[0, 1:-1, 1:-1] == 1.0)
+
+
+def test_limited_linear_upwind_keeps_symmetry_and_the_momentum_balance():
+    from test_oracle_forces import boundary_momentum_flux
+    case = G.case_cylinder(48, 24, model="laminar", Re=40.0)
+    o = O.Oracle(case, dict(convection="linearUpwindLimited"))
+    it, res = o.solve(tol=1e-10, max_iter=3000)
+    assert o.max_residual(res) <= 1e-10
+    assert np.abs(o.u[0][0] - o.u[0][0, ::-1]).max() < 1e-10
+    box = G.case_rotated_box(15.0, 16, model="laminar", Re=20.0)
+    o = O.Oracle(box, dict(convection="linearUpwindLimited"))
+    it, res = o.solve(tol=1e-13, max_iter=8000)
+    assert o.max_residual(res) <= 1e-13
+    o.imposed_fields()
+    F = sum(Fo.ib_force(o))
+    B = boundary_momentum_flux(o)
+    assert np.abs(F + B).max() <= 1e-9 * (np.abs(B).max() + np.abs(F).max())
