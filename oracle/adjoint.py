@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE, like hfdib_oracle: only tests/, the smoke check and the
 CPU arms of the benchmark may import it.  Plain FP64 (complex128 for the
-complex-step derivatives), numpy/scipy, 2D grids.
+complex-step derivatives), numpy/scipy, 2D and 3D grids.
 
 What is differentiated.  A converged state is a fixed point of the extended
 SIMPLE sweep (Fig. simplehfdibrans).  Hold fixed the turbulence fields (nu_t,
@@ -139,8 +139,6 @@ class FrozenSteady:
             raise ValueError("objective: pressure_drop or drag")
         self.kind = objective
         m = o.m
-        if m.dims != 2:
-            raise ValueError("the oracle adjoint covers 2D grids")
         if o.opts.get("convection", "upwind") != "upwind":
             raise ValueError("the oracle adjoint covers the upwind scheme")
         self.o = copy.deepcopy(o)
