@@ -142,13 +142,25 @@ CONVERGED = {
 }
 
 
+_ORACLE_STATES = {}
+
+
+def converged_oracle(name):
+    """The oracle's converged state of CONVERGED[name] (solved once per
+    module and shared read-only by the FP64, mixed and p_cg32 tests)."""
+    if name not in _ORACLE_STATES:
+        case = CONVERGED[name][0]()
+        o = O.Oracle(case)
+        _, ores = o.solve(tol=1e-12, max_iter=2000)
+        assert o.max_residual(ores) <= 1e-12
+        _ORACLE_STATES[name] = (case, o)
+    return _ORACLE_STATES[name]
+
+
 @pytest.mark.parametrize("name", sorted(CONVERGED))
 def test_converged_state_matches_oracle_fp64(name):
-    mk, maxit = CONVERGED[name]
-    case = mk()
-    o = O.Oracle(case)
-    _, ores = o.solve(tol=1e-12, max_iter=2000)
-    assert o.max_residual(ores) <= 1e-12
+    _, maxit = CONVERGED[name]
+    case, o = converged_oracle(name)
     s = make_solver(case)
     rc, it, res = s.solve(tol=1e-12, max_iter=maxit, check_every=20)
     assert rc == 0, (rc, it, res)
@@ -194,10 +206,8 @@ def test_converged_state_mixed_precision(name):
     """FP32 inner sweeps and FP32 multigrid inside FP64 refinement: the steady
     state solves the FP64 equations, so it must match the FP64 oracle within
     relative L2 1e-4 per field (it is expected far closer)."""
-    mk, maxit = CONVERGED[name]
-    case = mk()
-    o = O.Oracle(case)
-    _, ores = o.solve(tol=1e-12, max_iter=2000)
+    _, maxit = CONVERGED[name]
+    case, o = converged_oracle(name)
     s = make_solver(case, precision=1)
     rc, it, res = s.solve(tol=1e-12, max_iter=maxit, check_every=20)
     assert rc == 0, (rc, it, res)
@@ -374,10 +384,8 @@ def test_converged_state_with_fp32_correction_solve(name):
     too (P1); the start defect and p stay FP64, so the steady state still
     solves the FP64 equations: within 1e-4 of the FP64 oracle per field, like
     the other mixed solves."""
-    mk, maxit = CONVERGED[name]
-    case = mk()
-    o = O.Oracle(case)
-    _, ores = o.solve(tol=1e-12, max_iter=2000)
+    _, maxit = CONVERGED[name]
+    case, o = converged_oracle(name)
     s = make_solver(case, precision=1, p_cg32=1)
     rc, it, res = s.solve(tol=1e-12, max_iter=maxit, check_every=20)
     assert rc == 0, (rc, it, res)
