@@ -1,9 +1,11 @@
 // adjoint.cu -- reverse pass of the frozen-turbulence SIMPLE sweep, for the
-// gradient of the pressure drop with respect to the indicator lambda.
+// gradient of the pressure drop or the drag with respect to the indicator
+// lambda.
 //
 // The sweep (Fig. simplehfdibrans, steps a2-a8 with nu_t, k, eps/omega, the
 // cell groups, the wall-function branch of every bc cell, the closed faces and
-// the continuity mask held fixed) is a map G: x = (u, p, phi) -> x' whose fixed
+// the reading-A continuity mask held fixed; reading B's mask 1 - lambda is
+// differentiated) is a map G: x = (u, p, phi) -> x' whose fixed
 // point is the converged state.  The map differentiated here is the GPU sweep
 // itself, with its n_u red-black Gauss-Seidel passes of the momentum predictor
 // and with an exact pressure solve (any inner solver with the same fixed point

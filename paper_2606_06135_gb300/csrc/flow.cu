@@ -6,7 +6,12 @@
 // operator data are right-hand sides.  Discretisation (Sec. 3.1 "Numerical
 // schemes"): upwind convection in bounded form, central diffusion with the
 // arithmetic mean of the face diffusivity, Gauss-linear gradients, explicit
-// div(nu_eff (grad u)^T), implicit under-relaxation of the momentum rows.
+// div(nu_eff (grad u)^T), implicit under-relaxation of the momentum rows;
+// the schemes of App. B as a deferred correction of the convection.
+//
+// Also here, as post-processing of a state: the force of the fluid on the
+// body (Eqs. dragcoeff, dlcoeffs), the wall shear along a domain wall and the
+// recirculation region behind a body (Sec. 3.3, 3.6).
 #include "common.cuh"
 #include "kernels.cuh"
 
