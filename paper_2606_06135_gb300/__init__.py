@@ -24,7 +24,7 @@ Typical use (all compute runs in the library's CUDA kernels):
     b = BatchSolver([G.case_grf(256, 128, seed=i) for i in range(8)], precision=1)
     b.solve(tol=1e-6, max_iter=20000)
 
-    # dJ/dlambda of the converged state (frozen-turbulence adjoint, 2D)
+    # dJ/dlambda of the converged state (frozen-turbulence adjoint)
     J, dJ, iters, change, status = s.adjoint_grad(tol=1e-10, objective="drag")
 
 Options are the fields of hfdib_options (include/hfdib.h): the turbulence

@@ -1539,7 +1539,7 @@ int hfdib_adjoint_grad(hfdib_handle hh, int objective, double tol, int max_iter,
     if (!h) return HFDIB_ERR_INVALID_ARG;
     if (objective != HFDIB_OBJ_PRESSURE_DROP && objective != HFDIB_OBJ_DRAG) return HFDIB_ERR_INVALID_ARG;
     const bool drag = objective == HFDIB_OBJ_DRAG;
-    if (h->g.dims != 2 || h->g.conv != 0) return HFDIB_ERR_INVALID_ARG;
+    if (h->g.conv != 0) return HFDIB_ERR_INVALID_ARG;
     if (!(tol > 0.0) || max_iter < 0 || (max_iter > 0 && !dJ_dlambda)) return HFDIB_ERR_INVALID_ARG;
     if (gmres_restart < 0 || gmres_restart > HFDIB_GMRES_MAX_RESTART) return HFDIB_ERR_INVALID_ARG;
     const Grid& g = h->g;

@@ -165,12 +165,33 @@ def test_autograd_function_delivers_the_gradient():
     s.close()
 
 
-def test_adjoint_rejects_3d_and_unknown_objective():
-    from paper_2606_06135_gb300.hfdib import HfdibError, Solver
-    s = Solver(G.case_sphere(16, 8, 8, model="laminar"))
-    with pytest.raises(HfdibError):
-        s.adjoint_grad(max_iter=10)
+def test_3d_gradient_matches_oracle():
+    """3D (trilinear stencils, 26-neighbour normals): the GPU adjoint of a
+    sphere placed off the grid's symmetry planes against the oracle's
+    (tests/golden/adjoint3d_sphere.txt, written from oracle/ alone by
+    tests/golden/make_adjoint3d.py)."""
+    import importlib.util
+    import os
+    golden = os.path.join(os.path.dirname(__file__), "golden")
+    spec = importlib.util.spec_from_file_location("make_adjoint3d", os.path.join(golden, "make_adjoint3d.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    case = mk.sphere_off_axis()
+    vals = np.loadtxt(os.path.join(golden, "adjoint3d_sphere.txt"))
+    Jo, go = vals[0], vals[1:]
+    s = gpu_converged(case)
+    J, g, it, ch, rc = s.adjoint_grad(tol=1e-12, max_iter=40000)
+    assert rc == 0, (it, ch)
+    g = g.cpu().numpy().ravel()
+    e = rel(g, go)
+    print("3D sphere: J gpu %.15f oracle %.15f, grad rel-L2 %.2e, %d adjoint iterations" % (J, Jo, e, it))
+    assert abs(J - Jo) <= 1e-10 * abs(Jo)
+    assert e <= 1e-9
     s.close()
+
+
+def test_adjoint_rejects_unknown_objective_and_other_schemes():
+    from paper_2606_06135_gb300.hfdib import HfdibError, Solver
     s = Solver(G.case_grf(32, 16, seed=1))
     with pytest.raises(HfdibError):
         s.adjoint_grad(max_iter=10, objective=7)
