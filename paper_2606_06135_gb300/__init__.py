@@ -20,7 +20,7 @@ Typical use (all compute runs in the library's CUDA kernels):
     Cd, Cl = s.force_coefficients()
     L, V, n = s.recirculation(x_rear=0.0)        # recirculation behind x_rear
 
-    # many designs in one persistent launch per phase (2D)
+    # many designs in one persistent launch per phase
     b = BatchSolver([G.case_grf(256, 128, seed=i) for i in range(8)], precision=1)
     b.solve(tol=1e-6, max_iter=20000)
 
