@@ -262,7 +262,8 @@ enum { HFDIB_GMRES_MAX_RESTART = 200 };
  *                residual or change) : host pointers, nullable
  * Call it on a converged state (hfdib_solve_steady to a tight tolerance): the
  * gradient is that of the fixed point, and its error follows the residual.
- * 2D and 3D grids; the upwind convection scheme only (INVALID_ARG otherwise).  The state is left unchanged.
+ * 2D and 3D grids; the upwind convection scheme only (INVALID_ARG
+ * otherwise).  The state is left unchanged.
  * Returns HFDIB_OK, HFDIB_ERR_NOT_CONVERGED (gradient of the last iterate
  * still written), HFDIB_ERR_DIVERGED, HFDIB_ERR_INVALID_ARG, or CUDA/OOM errors.
  * The first call allocates about 90 doubles per cell of work arrays (plus
