@@ -797,6 +797,7 @@ class Oracle:
             Cf = (1.0 / (yplus + C_WF) ** 2 + 2.0 * yplus / C_WF ** 3 - 1.0 / C_WF ** 2)
             kvis = 2400.0 * Cf / C_EPS2 ** 2
             kS = kvis * ut ** 2
+            self.k_surface = kS      # per bc cell, kept for inspection
             v1 = interp_at(m, self.k, geo["base1"], geo["t1"])
             v2 = interp_at(m, self.k, geo["base2"], geo["t2"])
             kval = geo["wS"] * kS + geo["w1"] * v1 + geo["w2"] * v2
@@ -1067,6 +1068,13 @@ class Oracle:
         self.nut = C_MU * k * k / eps
 
     def _sst_blend(self, k, w, S2, gradk, gradw):
+        """Menter's blending functions (SST, cited in Sec. 2.1): the
+        cross-diffusion CD_kw = 2 sigma_w2 grad(k).grad(omega)/omega, F1 =
+        tanh(arg1^4) with arg1 = min(max(sqrt(k)/(beta* omega y),
+        500 nu/(y^2 omega)), 4 sigma_w2 k/(CD_kw+ y^2)), CD_kw+ = max(CD_kw,
+        1e-10), and F2 = tanh(arg2^2) with arg2 = min(max(2 sqrt(k)/(beta*
+        omega y), 500 nu/(y^2 omega)), 100).  y is the wall distance input,
+        clipped below at 1e-3 h.  Returns (CD_kw, F1, F2)."""
         m = self.m
         c = SST
         y = np.maximum(self.ywall, 1e-3 * m.h)
@@ -1081,6 +1089,29 @@ class Oracle:
                           100.0)
         F2 = np.tanh(arg2 * arg2)
         return CDkw, F1, F2
+
+    @staticmethod
+    def sst_nut(k, w, S2, F2):
+        """SST eddy viscosity with Menter's limiter: nu_t = a1 k / max(a1
+        omega, b1 F2 sqrt(2 S:S)) (S2 = 2 S:S)."""
+        c = SST
+        return c["a1"] * k / np.maximum(c["a1"] * w, c["bb1"] * F2 * np.sqrt(S2))
+
+    @staticmethod
+    def sst_k_production(G, k, w):
+        """Production in the SST k equation with Menter's limiter:
+        min(G, c1 beta* k omega)."""
+        c = SST
+        return np.minimum(G, c["c1"] * c["bstar"] * k * w)
+
+    @staticmethod
+    def sst_gbynu(S2, w, F2):
+        """G/nu_t of the SST omega source, limited consistently with
+        sst_nut and sst_k_production: min(2 S:S, (c1/a1) beta* omega
+        max(a1 omega, b1 F2 sqrt(2 S:S)))."""
+        c = SST
+        return np.minimum(S2, (c["c1"] / c["a1"]) * c["bstar"] * w
+                          * np.maximum(c["a1"] * w, c["bb1"] * F2 * np.sqrt(S2)))
 
     def komegasst(self, res):
         """k-omega SST (Menter) with the HFDIB treatment."""
@@ -1100,8 +1131,7 @@ class Oracle:
         # omega equation
         gamma = blend(c["g1"], c["g2"])
         beta = blend(c["b1"], c["b2"])
-        GbyNu = np.minimum(S2, (c["c1"] / c["a1"]) * c["bstar"] * w_old
-                           * np.maximum(c["a1"] * w_old, c["bb1"] * F2 * np.sqrt(S2)))
+        GbyNu = self.sst_gbynu(S2, w_old, F2)
         gam = self.nu + blend(c["aw1"], c["aw2"]) * self.nut
         aP, aM, aPl, b = assemble_transport(m, self.phi, gam, sspec(self.omega_in))
         aP = aP + beta * w_old * V
@@ -1115,7 +1145,7 @@ class Oracle:
         gam = self.nu + blend(c["ak1"], c["ak2"]) * self.nut
         aP, aM, aPl, b = assemble_transport(m, self.phi, gam, sspec(self.k_in))
         aP = aP + c["bstar"] * w * V
-        b = b + np.minimum(Gmod, c["c1"] * c["bstar"] * k_old * w) * V
+        b = b + self.sst_k_production(Gmod, k_old, w) * V
         fixed_k = self.alpha_u > 0.5
         k = self._turb_solve(aP, aM, aPl, b, k_old, fixed_k, self.k_ib, urf, "k", res)
         k = np.maximum(k, K_MIN)
@@ -1125,7 +1155,7 @@ class Oracle:
         self.eps = C_MU * k * w
         # nu_t = a1 k / max(a1 omega, b1 F2 sqrt(S2)) with the new k, omega
         _, _, F2n = self._sst_blend(np.maximum(k, K_MIN), w, S2, gradk, gradw)
-        self.nut = c["a1"] * k / np.maximum(c["a1"] * w, c["bb1"] * F2n * np.sqrt(S2))
+        self.nut = self.sst_nut(k, w, S2, F2n)
 
     def komega(self, res):
         """k-omega (Wilcox) of Eq. hfdibkomega with the HFDIB treatment (the

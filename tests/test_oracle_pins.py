@@ -139,20 +139,6 @@ def test_bilinear_interpolation_exact_for_linear_fields():
 
 
 # ---------------------------------------------------------------- wall functions
-def test_wall_function_closed_forms():
-    """Eq. kws: C_f(0) = 0; Eq. omegaws equals its substituted forms."""
-    Cf = lambda yp: 1.0 / (yp + O.C_WF) ** 2 + 2.0 * yp / O.C_WF ** 3 - 1.0 / O.C_WF ** 2
-    assert Cf(0.0) == 0.0
-    nu = 1e-3
-    for k, ye in ((1e-3, 0.01), (0.02, 0.05), (0.3, 0.2)):
-        ut = O.C_MU ** 0.25 * math.sqrt(k)
-        yp = ye * ut / nu
-        lam = (ut ** 2 / nu) * 6.0 / (O.BETA1_WF * yp ** 2)
-        log = (ut ** 2 / nu) / (O.KAPPA * math.sqrt(O.C_MU) * yp)
-        assert math.isclose(lam, 6.0 * nu / (O.BETA1_WF * ye ** 2), rel_tol=1e-13)
-        assert math.isclose(log, ut / (O.KAPPA * math.sqrt(O.C_MU) * ye), rel_tol=1e-13)
-
-
 @pytest.fixture(scope="module")
 def cyl_converged():
     case = G.case_cylinder(64, 32)
