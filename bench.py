@@ -64,19 +64,11 @@ def replica_rate(units_per_rank, world, seconds):
     return world * units_per_rank / seconds
 
 
-# Algorithmic bytes per cell for one launch group of each kernel class
-# (2D, FP64 words of 8 B, minimum traffic with perfect neighbour reuse,
-# face arrays counted as one word per cell and direction, flags 2 B).
-def PCG_ITERS_FACTOR(piters):
-    """The 'pcg' class is one launch of the whole pressure solve."""
-    return max(float(piters.mean()), 1.0)
-
-
-# DRAM bytes of one launch of the dominant kernel, from an ncu capture of this
-# workload (dram__bytes_read.sum + dram__bytes_write.sum; mixed: the FP32
-# V-cycle variant).  At 262k cells the pressure hierarchy stays in L2, so
-# this is far below the algorithmic count.
-TRAFFIC = {("pcg", "mixed"): 10.674176e6 + 1.420288e6, ("pcg", "fp64"): 12.108800e6 + 0.996608e6}
+# DRAM bytes of one launch of a class's kernel, keyed (class, precision, case
+# name), from an ncu capture of the kernel as it is now
+# (dram__bytes_read.sum + dram__bytes_write.sum); absent once the kernel
+# changed after the capture.
+TRAFFIC = {}
 
 # FP64 flops of one launch of the FP64 assembly kernels on this workload
 # (ncu: 2 x DFMA + DADD + DMUL thread instructions).  These kernels are bound
@@ -85,25 +77,81 @@ TRAFFIC = {("pcg", "mixed"): 10.674176e6 + 1.420288e6, ("pcg", "fp64"): 12.10880
 FP64_FLOPS = {"mom_asm": 4.7356e7, "turb_final": 3.1783e7, "scal_asm": 1.5748e7}
 FP64_PEAK_GFLOPS = 1250.0   # nominal GB300 FP64 rate (no measured FP64 peak is available)
 
-BYTES_PER_CELL = {
-    # u, v, p, nut, phi_x, phi_y, 4 gradient comps read; bm x2, u* x2 written
-    "mom_asm": 8 * (10 + 4) + 2,
-    # one colour: bm x2 (half the cells), u* x2, phi x2, nut read; u* x2 (half) written
-    "mom_smooth": 8 * (1 + 2 + 2 + 1 + 1) + 2,
-    # u*, bm x2, p, phi x2, nut read; HbyA x2, rAU, phiH x2 written
-    "hbya": 8 * (7 + 5) + 2,
-    "vcycle0": int(8 * 26 * 4 / 3),
-    # phiH x2, pn, p, HbyA x2, rAU, cf x2 read; phi x2, u x2, p written
-    "update": 8 * (9 + 5) + 2,
-    "grad_u": 8 * (2 + 4) + 2,
-    "turb_prep": 8 * (4 + 4 + 2 + 1 + 6) + 2,
-    "scal_asm": 8 * (2 + 1 + 2 + 2 + 2) + 2,
-    "scal_smooth": 8 * (1 + 1 + 2 + 1 + 1) + 2,
-    "imposed": 8 * 8 + 2,
-    "p_coef": 8 * (1 + 3),
-    "turb_final": 8 * (5 + 4) + 2,
-    "sweep_end": 0,
-}
+def class_bytes_per_sweep(dims, mixed, model, piters, n_u=2, n_turb=2):
+    """Algorithmic bytes per cell and SWEEP of each kernel class: every array
+    a class's kernels read or write counted once per launch (perfect
+    neighbour reuse), FP64 words 8 B, FP32 words 4 B, flags 2 B, face arrays
+    one word per cell and direction, red-black passes touching half the cells
+    of the colour-dependent arrays.  Sparse bc-list work is left out."""
+    D = dims
+    f8, f4, fl = 8, 4, 2
+    turb = model != "laminar"
+    sst = model == "komegasst"
+    w = f4 if mixed else f8
+    b = {}
+    # a1 max over bc u fc (flags, w); residual means (flags, u, p, k, w)
+    b["imposed"] = (fl + f8 if turb else 0) + fl + (D + 1 + (2 if turb else 0)) * f8
+    # flags, u -> grad u (D x D), once for the momentum rows and once for production
+    b["grad_u"] = (2 if turb else 1) * (fl + D * f8 + D * D * f8)
+    # flags, u, p, nut, phi, grad u -> rows (aP per component, 2D neighbours),
+    # b, u*, FP32 defect (mixed)
+    b["mom_asm"] = fl + (D + 1 + 1 + D + D * D) * f8 + (D + 2 * D + D + D) * f8 + (D * f4 if mixed else 0)
+    # one colour pass: flags, phi, nut, defect / b (half), the other colour's
+    # unknowns (half) read; this colour's unknowns (half) written
+    one = fl + (D + 1) * w + 3 * (D * w) / 2.0
+    b["mom_smooth"] = 2 * n_u * one
+    # HbyA: rows, b, p, u* (+ FP32 correction) -> HbyA, rAU; phiHbyA: HbyA -> faces
+    b["hbya"] = (fl + (3 * D + D + 1 + D) * f8 + (D * f4 if mixed else 0) + (D + 1) * f8) + (fl + 2 * D * f8)
+    # per CG iteration: FP64 CG vectors (13 words) and the V-cycle (26 words
+    # in the preconditioner type, x 4/3 (2D) or 8/7 (3D) for the coarse levels)
+    coarse = 4.0 / 3.0 if D == 2 else 8.0 / 7.0
+    b["pcg"] = (13 * f8 + 26 * w * coarse) * max(float(piters), 1.0)
+    # phiH, pn, p, HbyA, rAU, level-0 coefficients -> phi (+FP32), u, relaxed p
+    b["update"] = fl + (D + 1 + 1 + D + 1 + D) * f8 + (D + D + 1) * f8 + (D * f4 if mixed else 0)
+    if turb:
+        # production: grad u, nut, k, w (+ ywall) -> S2, P, gam, sp, src, gamk (+FP32
+        # copies); k prep: w (+FP32 correction), k, P -> w, sp, src
+        b["turb_prep"] = (fl + (D * D + 3 + (1 if sst else 0)) * f8 + 6 * f8 + (2 * f4 if mixed else 0)
+                          + (3 * f8 + (f4 if mixed else 0)) + 3 * f8)
+        # per equation: flags, phi, gam, sp, src, x -> bt, diag (+FP32 diag, defect)
+        b["scal_asm"] = 2 * (fl + (D + 4) * f8 + 2 * f8 + (2 * f4 if mixed else 0))
+        one = fl + (D + 1) * w + 3 * w / 2.0 + w / 2.0
+        b["scal_smooth"] = 2 * 2 * n_turb * one
+        # flags, k (+correction), w (+ywall, S2 for SST) -> k, w2, nut (+FP32 nut)
+        b["turb_final"] = fl + 2 * f8 + (f4 if mixed else 0) + (2 * f8 if sst else 0) + 3 * f8 + (f4 if mixed else 0)
+    b["sweep_end"] = 0
+    return b
+
+
+def class_roofline(prof, n_sweeps, cells, bytes_per_sweep, peak):
+    """Per kernel class: device time per sweep (event pairs), algorithmic
+    GB/s and its fraction of the HBM peak."""
+    total = sum(v[0] for v in prof.values())
+    out = {}
+    for k, (us, calls) in prof.items():
+        if calls == 0 or us <= 0:
+            continue
+        t = us * 1e-6 / n_sweeps
+        by = bytes_per_sweep.get(k)
+        row = {"us_per_sweep": round(us / n_sweeps, 2), "share": round(us / total, 4)}
+        if by:
+            gbs = by * cells / t / 1e9
+            row.update({"bytes_per_cell": round(by, 1), "gbs": round(gbs, 1), "frac": round(gbs / peak, 4)})
+        out[k] = row
+    return out
+
+
+def host_cpu():
+    """Core count and CPU model of this host (for the CPU baseline)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Vendor ID") and model is None:
+                model = ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
 
 
 def measured_peaks():
@@ -193,6 +241,46 @@ print(json.dumps({"sweeps": n, "seconds": el, "cells": %d}))
     if out.returncode != 0:
         raise RuntimeError("oracle run failed: " + out.stderr[-2000:])
     return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def oracle_rate_all_cores(sweeps=2, max_procs=16):
+    """The same oracle on all host cores: one single-threaded oracle per core
+    (at most max_procs), each sweeping its own copy of the workload, started
+    together; the rate is all cell-updates over the wall time until the last
+    one finishes (the oracle itself is serial, so its all-core form is
+    independent copies)."""
+    P = max(1, min(os.cpu_count() or 1, max_procs))
+    code = r"""
+import json, sys, time
+sys.path.insert(0, %r)
+from paper_2606_06135_gb300 import geometry as G
+from oracle import hfdib_oracle as O
+case = G.case_bfs(%d, %d)
+o = O.Oracle(case, dict(freeze_switch=%d))
+sys.stdout.write("ready\n"); sys.stdout.flush()
+sys.stdin.readline()
+t0 = time.perf_counter()
+for _ in range(%d):
+    o.sweep()
+print(json.dumps({"seconds": time.perf_counter() - t0}))
+""" % (ROOT, NX, NY, FREEZE, sweeps)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    procs = [subprocess.Popen([sys.executable, "-c", code], stdin=subprocess.PIPE, stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True, env=env) for _ in range(P)]
+    for pr in procs:
+        if pr.stdout.readline().strip() != "ready":
+            raise RuntimeError("oracle copy failed to start: " + pr.stderr.read()[-500:])
+    t0 = time.perf_counter()
+    for pr in procs:
+        pr.stdin.write("go\n")
+        pr.stdin.flush()
+    for pr in procs:
+        pr.wait(timeout=1800)
+    wall = time.perf_counter() - t0
+    if any(pr.returncode != 0 for pr in procs):
+        raise RuntimeError("oracle copy failed")
+    return {"procs": P, "sweeps_each": sweeps, "seconds": wall, "cells": NX * NY,
+            "value": P * sweeps * NX * NY / wall}
 
 
 def run_reference(args, rank):
@@ -329,6 +417,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched multi-lambda leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
+    ap.add_argument("--no-c4", action="store_true", help="skip the 3D Ahmed-body leg")
+    ap.add_argument("--no-c1", action="store_true", help="skip the 128 x 64 cylinder leg")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -375,20 +465,28 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(dev)
 
-    def timed_sweeps(precision):
-        """W warm-up + K timed sweeps; L2 flushed between timed sweeps."""
-        opts = dict(freeze_switch=FREEZE, p_reltol=P_RELTOL, precision=1 if precision == "mixed" else 0)
-        s = hfdib.Solver(case, device=str(dev), stream=stream, **opts)
+    def timed_sweeps(precision, cs=None, extra=None, steps=None):
+        """W warm-up + K timed sweeps of case cs (default: the headline step);
+        L2 flushed between timed sweeps.  Returns the rate, the per-class
+        roofline (event-timed host-driven sweeps) and the dominant class."""
+        cs = case if cs is None else cs
+        steps = args.steps if steps is None else steps
+        cells = cs["grid"]["nx"] * cs["grid"]["ny"] * cs["grid"]["nz"]
+        dims = 2 if cs["grid"]["nz"] == 1 else 3
+        opts = dict(freeze_switch=FREEZE, p_reltol=P_RELTOL) if cs is case else {}
+        opts.update(extra or {})
+        opts["precision"] = 1 if precision == "mixed" else 0
+        s = hfdib.Solver(cs, device=str(dev), stream=stream, **opts)
         for _ in range(args.warmup):
             s.sweep(1, read=False)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
+              for _ in range(steps)]
         clocks = ClockSampler(local)
         stream.synchronize()
         barrier()
         torch.cuda.synchronize(dev)
         clocks.start()
-        for k in range(args.steps):
+        for k in range(steps):
             with torch.cuda.stream(stream):
                 flush.fill_(float(k))
             ev[k][0].record(stream)
@@ -399,35 +497,30 @@ def main():
         barrier()
         clk = clocks.stop()
         t_dev = sum(a.elapsed_time(b) for a, b in ev) / 1e3
-        hist = s.history(args.steps)
+        hist = s.history(steps)
         piters = hist[:, 7]
+        res_last = hist[-1]
         fixed, per_it = s.launch_counts()
-        launches = int(args.steps * fixed + per_it * piters.sum())
+        launches = int(steps * fixed + per_it * piters.sum())
         t_dev = max_over_ranks(t_dev, dist, dev)
-        # roofline of the dominant kernel class (host-driven sweeps, event pairs)
-        prof = s.profile(3)
-        dname, (dus, dcalls) = max(prof.items(), key=lambda kv: kv[1][0])
-        avg_us = dus / max(dcalls, 1)
-        if dname == "pcg":
-            # per CG iteration: FP64 CG vectors (13 words) + the V-cycle (26
-            # words x 4/3 for the coarse levels) in the preconditioner's type
-            wv = 4 if precision == "mixed" else 8
-            bpc = (8 * (7 + 6) + int(wv * 26 * 4 / 3)) * PCG_ITERS_FACTOR(piters)
-        else:
-            bpc = BYTES_PER_CELL.get(dname, 0)
-        achieved = bpc * N / (avg_us * 1e-6) / 1e9
-        total = sum(x[0] for x in prof.values())
-        traffic = TRAFFIC.get((dname, precision))
-        roof = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
-                "traffic_note": "ncu DRAM bytes of one launch; the pressure hierarchy is L2-resident at this size"
-                if traffic else None,
-                "algorithmic_bytes_per_launch": bpc * N, "avg_launch_us": avg_us,
-                "class_share": {k: round(v[0] / total, 4) for k, v in prof.items()}}
+        # per-class roofline (host-driven sweeps, an event pair per launch group)
+        n_prof = 3
+        prof = s.profile(n_prof)
+        ph = s.history(n_prof)
+        bps = class_bytes_per_sweep(dims, precision == "mixed", cs["model"], float(ph[:, 7].mean()))
+        classes = class_roofline(prof, n_prof, cells, bps, peak)
+        dname = max(classes, key=lambda k: classes[k]["us_per_sweep"])
+        d = classes[dname]
+        traffic = TRAFFIC.get((dname, precision, cs["name"]))
+        roof = {"bound": "hbm", "kernel": dname, "achieved": d.get("gbs"), "peak": peak, "unit": "GB/s",
+                "frac": d.get("frac"), "peak_source": peak_kind, "traffic": traffic,
+                "algorithmic_bytes_per_launch": d.get("bytes_per_cell", 0) * cells,
+                "avg_launch_us": d["us_per_sweep"],
+                "class_share": {k: v["share"] for k, v in classes.items()}}
         # FP64-ALU roofline of the assembly classes (live event timing)
         alu = {}
         for cls, fl in FP64_FLOPS.items():
-            if cls in prof and prof[cls][1] > 0:
+            if cs is case and cls in prof and prof[cls][1] > 0:
                 us = prof[cls][0] / prof[cls][1]
                 gf = fl / (us * 1e-6) / 1e9
                 alu[cls] = {"achieved": gf, "avg_launch_us": us, "flops_per_launch": fl}
@@ -438,8 +531,9 @@ def main():
                         "unit": "GFLOP/s (FP64)", "frac": alu[top]["achieved"] / FP64_PEAK_GFLOPS,
                         "peak_source": "nominal", "per_class": alu}
         s.close()
-        return dict(value=replica_rate(N * args.steps, world, t_dev), ms=1e3 * t_dev / args.steps, clocks=clk,
-                    launches=launches, piters=float(piters.mean()), roofline=roof, roofline_alu=roof_alu)
+        return dict(value=replica_rate(cells * steps, world, t_dev), ms=1e3 * t_dev / steps, clocks=clk,
+                    launches=launches, piters=float(piters.mean()), roofline=roof, roofline_alu=roof_alu,
+                    classes=classes, cells=cells, max_residual=float(max(res_last[:6])))
 
     res = {p: timed_sweeps(p) for p in ("mixed", "fp64")}
     head = res["mixed"]
@@ -451,13 +545,43 @@ def main():
                       "Re_h": 36000, "precision": "mixed (FP32 inner sweeps + FP32 multigrid, FP64 defects)",
                       "l2": "flushed (512 MB write) between timed steps",
                       "parallelism": "replicas" if world > 1 else "single",
-                      "freeze_switch": FREEZE, "p_reltol": P_RELTOL, "pcg_iters_mean": head["piters"]},
+                      "freeze_switch": "%d (one-way y+ switch from sweep %d, not in the paper; the literal "
+                                       "switch stalls at scaled residual 0.2-0.4 on this grid)" % (FREEZE, FREEZE),
+                      "p_reltol": "%g (per-sweep pressure tolerance tuned for this workload; library "
+                                  "default 0.1)" % P_RELTOL,
+                      "pcg_iters_mean": head["piters"]},
            "gpu_launches": head["launches"], "clocks": head["clocks"], "roofline": head["roofline"],
-           "roofline_alu": head["roofline_alu"],
+           "roofline_alu": head["roofline_alu"], "classes": head["classes"],
            "fp64": {"value": res["fp64"]["value"], "ms_per_step": res["fp64"]["ms"],
                     "roofline": res["fp64"]["roofline"], "roofline_alu": res["fp64"]["roofline_alu"],
-                    "clocks": res["fp64"]["clocks"],
+                    "classes": res["fp64"]["classes"], "clocks": res["fp64"]["clocks"],
                     "pcg_iters_mean": res["fp64"]["piters"]}}
+
+    # the 3D Ahmed-like body: 2.36 M cells, a working set (~1.2 GB) far out
+    # of L2, where the sweep's kernels meet HBM; mixed precision, k-epsilon
+    if rank == 0 and not args.no_c4:
+        c4 = timed_sweeps("mixed", cs=G.case_ahmed(256, 96, 96), steps=min(args.steps, 10))
+        out["c4"] = {"workload": "ahmed_256x96x96_keps", "cells": c4["cells"], "precision": "mixed",
+                     "value": c4["value"], "unit": "cell-updates/s", "ms_per_sweep": c4["ms"],
+                     "sweeps_timed": min(args.steps, 10), "pcg_iters_mean": c4["piters"],
+                     "roofline": c4["roofline"], "classes": c4["classes"], "clocks": c4["clocks"],
+                     "l2": "working set > L2 (flushed between timed sweeps as well)"}
+    # the 128 x 64 cylinder, FP64, 500 sweeps from the uniform start
+    if rank == 0 and not args.no_c1:
+        c1case = G.case_cylinder(128, 64)
+        s1 = hfdib.Solver(c1case, device=str(dev), stream=stream, precision=0)
+        s1.sweep(1, read=False)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        s1.sweep(499, read=False)
+        e1.record(stream)
+        r1 = s1.sweep(0)
+        t1 = e0.elapsed_time(e1) / 1e3
+        out["c1"] = {"workload": "cylinder_128x64_keps_fp64_500", "cells": 128 * 64, "sweeps": 500,
+                     "value": 128 * 64 * 499 / t1, "unit": "cell-updates/s", "ms_per_sweep": 1e3 * t1 / 499,
+                     "seconds_500_sweeps": t1 * 500 / 499, "max_residual_after": float(max(r1[:6]))}
+        s1.close()
 
 
     # converged solves (both precisions) and the end-to-end leg (mixed, public
@@ -514,9 +638,15 @@ def main():
         pool.shutdown()
     if rank == 0 and not args.no_cpu:
         r = oracle_rate(seconds=15.0)
+        hc = host_cpu()
         out["cpu_baseline"] = {"value": r["cells"] * r["sweeps"] / r["seconds"], "unit": "cell-updates/s",
-                               "cores": 1, "kind": "oracle",
+                               "cores": 1, "kind": "oracle", "host": hc,
                                "sample": "%d full-size FP64 oracle sweeps of the same workload" % r["sweeps"]}
+        ra = oracle_rate_all_cores()
+        out["cpu_baseline_all_cores"] = {
+            "value": ra["value"], "unit": "cell-updates/s", "cores": ra["procs"], "kind": "oracle", "host": hc,
+            "sample": "%d single-threaded oracle copies, %d full-size sweeps each, started together"
+                      % (ra["procs"], ra["sweeps_each"])}
     if rank == 0:
         print(json.dumps(out))
     if dist is not None:

@@ -18,7 +18,8 @@
  *     handle stays valid (HFDIB_ERR_CUDA after a sticky CUDA error excepted).
  *   - Device pointers passed in are read on the handle's stream; the caller
  *     keeps ownership of every buffer it passes.  The handle owns its fields
- *     and scratch (allocated at create, freed at destroy).
+ *     and scratch (allocated at create from the allocator set by
+ *     hfdib_set_allocator -- cudaMalloc by default -- and freed at destroy).
  *   - All work is issued on the handle's stream (see hfdib_create); calls
  *     that return data to host memory synchronise that stream.
  */
@@ -41,7 +42,7 @@ typedef enum {
     HFDIB_ERR_DIVERGED = -5,      /* NaN / Inf in a residual                        */
     HFDIB_ERR_STATE_MISMATCH = -6,/* checkpoint from another grid / model           */
     HFDIB_ERR_TOO_LARGE = -7,     /* problem exceeds a fixed capacity (see below)   */
-    HFDIB_ERR_TIMEOUT = -8        /* a device-wide barrier gave up (should not occur) */
+    HFDIB_ERR_TIMEOUT = -8        /* a device-wide barrier wait gave up (see below)  */
 } hfdib_status;
 
 /* Turbulence closures (Sec. 2.1 names four, each with the same HFDIB
@@ -173,6 +174,31 @@ enum { HFDIB_RES_UX = 0, HFDIB_RES_UY = 1, HFDIB_RES_UZ = 2, HFDIB_RES_P = 3,
        HFDIB_RES_EPSW = 4, HFDIB_RES_K = 5, HFDIB_RES_CONT = 6, HFDIB_RES_PITER = 7,
        HFDIB_RES_NLAM = 8, HFDIB_RES_NSWITCH = 9, HFDIB_NRES = 10 };
 
+/* Device memory.  By default handles and batches allocate with cudaMalloc
+ * and free with cudaFree.  hfdib_set_allocator installs the caller's
+ * allocator instead, process-wide, for every handle and batch created
+ * afterwards; each handle and batch keeps the allocator it was created with
+ * until it is destroyed (changing the setting later does not move it).
+ *   alloc(bytes, stream, ctx)  : return device memory of at least `bytes`
+ *                                bytes, 256-byte aligned, usable on `stream`
+ *                                (the handle's stream), or NULL when there is
+ *                                none (the calling entry point then returns
+ *                                HFDIB_ERR_OOM).  Memory that is not 256-byte
+ *                                aligned is given back and the call fails
+ *                                with HFDIB_ERR_INVALID_ARG.
+ *   release(ptr, bytes, stream, ctx) : take back a block from alloc; called
+ *                                from hfdib_destroy / hfdib_destroy_batch (or
+ *                                a failing create) after the stream has been
+ *                                synchronised, so no work on the block is
+ *                                pending.
+ *   ctx                        : passed through unchanged.
+ * Both NULL restores cudaMalloc / cudaFree; exactly one NULL is
+ * INVALID_ARG.  Pinned host staging buffers are not affected.  The Python
+ * binding installs PyTorch's caching allocator. */
+typedef void* (*hfdib_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*hfdib_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+int hfdib_set_allocator(hfdib_alloc_fn alloc, hfdib_free_fn release, void* ctx);
+
 /* Fill *opt with the defaults listed in hfdib_options. */
 void hfdib_default_options(hfdib_options* opt);
 
@@ -209,6 +235,42 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
  *               the last sweep (nullable: then nothing is copied back and the
  *               call returns without waiting for the GPU). */
 int hfdib_simple_sweep(hfdib_handle h, int n_sweeps, double* residuals);
+
+/* hfdib_pressure_trace -- runs ONE sweep (host-driven, like
+ * hfdib_simple_sweep with graph capture off for that sweep; the solution
+ * advances) and records the phases of its persistent pressure kernel: after
+ * every device-wide barrier, block 0 appends a (phase, time) pair, the time
+ * from %globaltimer in ns.  Phases: 0 start, 1 level-0 operator built, 2 a
+ * coarse level built, 3 initial residual, 4 first black half sweep of
+ * level 0, 5 a restriction, 6 a black half sweep of a coarse level, 7 the
+ * one-block coarse tail, 8 a prolongation with its black half sweep, 9 a red
+ * half sweep going up, 10 the final red half sweep of level 0 (r.z), 11 the
+ * CG product (d, q, d.q), 12 the CG update (p, r, r.r), 13 end.  A
+ * measurement aid for the pressure solve (it allocates a small device
+ * buffer for the call).
+ *   out      : HOST, 2 * capacity int64: tag, ns, tag, ns, ...
+ *   capacity : pairs (1 .. 2^20); later phases are dropped
+ *   n_out    : host, pairs written (nullable)
+ * Errors: INVALID_ARG (NULL, bad capacity, a handle without the persistent
+ * pressure kernel), OOM, CUDA, and the sweep's own statuses. */
+int hfdib_pressure_trace(hfdib_handle h, int64_t* out, int capacity, int* n_out);
+
+/* Barrier timeouts.  The persistent pressure kernels (one cooperative launch
+ * per pressure solve, single problem or batch) separate their phases by
+ * device-wide barriers.  Every wait at such a barrier polls at most a fixed
+ * number of times (default 2^26, about 0.1-1 s); a wait that runs out sets
+ * the kernel's error word, every block that then finds the word set leaves
+ * the kernel at its next barrier, and the rest of the sweep runs on the
+ * partial pressure solution.  The next call that reads residuals back
+ * (hfdib_simple_sweep with a residual buffer, hfdib_solve_steady,
+ * hfdib_batch_sweep / hfdib_batch_solve_steady) returns HFDIB_ERR_TIMEOUT
+ * once and clears the flag; the handle stays usable (restore a checkpoint
+ * with hfdib_set_state to discard the incomplete sweep).  No kernel waits
+ * without a bound and none traps.
+ * hfdib_set_barrier_polls sets the poll budget of each wait (polls > 0) or
+ * restores the default (polls == 0); a budget of 1 makes every wait that is
+ * not already complete give up, which is how a timeout is exercised. */
+int hfdib_set_barrier_polls(hfdib_handle h, int64_t polls);
 
 /* hfdib_solve_steady -- sweep until the largest scaled residual (momentum,
  * pressure, turbulence) is <= tol, or max_iter sweeps.  Residuals are read
@@ -288,6 +350,19 @@ int hfdib_adjoint_grad(hfdib_handle h, int objective, double tol, int max_iter, 
  * the imposed fields and grad u, which the next sweep recomputes from the
  * same state).  Errors: INVALID_ARG (NULL), CUDA. */
 int hfdib_ib_force(hfdib_handle h, double* force);
+
+/* hfdib_force_coefficients -- drag and lift coefficients of the force of
+ * hfdib_ib_force: C_d = 2 F.v_d / (A_ref |u_in|^2) with v_d = (1, 0, 0)
+ * (Eq. dragcoeff) and C_l = 2 F.v_l / (A_ref |u_in|^2) with v_l =
+ * (-sin gamma, cos gamma, 0) (Eq. dlcoeffs), F = f_n + f_t.
+ *   A_ref  : reference area; 0 selects the paper's l_ref dz, the reference
+ *            length times the cell depth (one-cell-thick 2D grids only)
+ *   gamma  : angle of attack in radians (the lift direction)
+ *   coeffs : HOST pointer, 2 doubles: C_d, C_l
+ * Waits for the handle's stream; leaves the state unchanged (as
+ * hfdib_ib_force).  Errors: INVALID_ARG (NULL, A_ref < 0, A_ref = 0 on a 3D
+ * grid, zero inlet velocity, non-finite gamma), CUDA. */
+int hfdib_force_coefficients(hfdib_handle h, double A_ref, double gamma, double* coeffs);
 
 /* hfdib_wall_shear -- wall shear stress along one no-slip domain side
  * (Sec. 3.3, tau_w = nu du/dn at the wall): the shear of the discrete wall
@@ -396,9 +471,14 @@ int hfdib_profile_sweeps(hfdib_handle h, int n_sweeps, double* total_us, int64_t
  *   bc_cells  : device, bc_capacity int32 out: the bc cells in increasing
  *               cell order, identical to the cell column of hfdib_get_bc_list.
  *   n_bc      : host, receives the number of bc cells.
- *   stream    : cudaStream_t; the call synchronises it before returning.
- * Errors: INVALID_ARG; TOO_LARGE when nx*ny*nz > 2^24, or when n_bc >
- * bc_capacity (*n_bc is then set and the list is truncated); CUDA.
+ *   stream    : cudaStream_t of the current device; the call synchronises
+ *               it before returning.
+ * Errors: INVALID_ARG (NULL pointers, bad sizes, a stream of another device,
+ * or a lambda value outside [0, 1] or NaN -- *n_bc is then 0 -- as
+ * hfdib_create rejects such a field); TOO_LARGE when nx*ny*nz > 2^24, or when
+ * n_bc > bc_capacity (*n_bc is then set and the list is truncated); CUDA
+ * (checked right after the launches, which also consumes a launch error an
+ * earlier, unrelated call may have left pending).
  * The first call on a device looks up the fixed array's device address and
  * should not be made inside a stream capture.  Calls share the array: two
  * calls that overlap on the GPU (unordered streams) race. */
@@ -444,6 +524,8 @@ typedef struct {
     int32_t candidates;
 } hfdib_tune;
 int hfdib_batch_autotune(hfdib_batch b, int trial_sweeps, hfdib_tune* best);
+/* the batch's barrier poll budget, as hfdib_set_barrier_polls */
+int hfdib_batch_set_barrier_polls(hfdib_batch b, int64_t polls);
 void hfdib_destroy_batch(hfdib_batch b);
 
 const char* hfdib_error_string(int code);

@@ -19,6 +19,61 @@ using namespace hf;
 namespace {
 
 constexpr int HIST = 1024;
+
+// ---------------------------------------------------------------- device memory
+// Every device buffer of a handle or batch comes from the allocator that was
+// current when the handle or batch was created: cudaMalloc / cudaFree, or
+// the caller's hook set by hfdib_set_allocator (a framework's caching
+// allocator, a fixed pool).  The handle keeps that allocator until it is
+// destroyed, so each buffer goes back where it came from.
+struct DevAlloc {
+    hfdib_alloc_fn alloc = nullptr;
+    hfdib_free_fn release = nullptr;
+    void* ctx = nullptr;
+};
+struct DevBlock {
+    void* p;
+    size_t bytes;
+};
+std::mutex& alloc_mu() {
+    static std::mutex m;
+    return m;
+}
+DevAlloc& alloc_setting() {
+    static DevAlloc a;
+    return a;
+}
+DevAlloc current_alloc() {
+    std::lock_guard<std::mutex> lock(alloc_mu());
+    return alloc_setting();
+}
+// bytes > 0; HFDIB_ERR_OOM when the allocator has no memory, INVALID_ARG when
+// a hook returns memory that is not 256-byte aligned
+int dev_alloc(const DevAlloc& A, cudaStream_t s, size_t bytes, void** out) {
+    *out = nullptr;
+    if (A.alloc) {
+        void* p = A.alloc(bytes, (void*)s, A.ctx);
+        if (!p) return HFDIB_ERR_OOM;
+        if ((uintptr_t)p & 255u) {
+            A.release(p, bytes, (void*)s, A.ctx);
+            return HFDIB_ERR_INVALID_ARG;
+        }
+        *out = p;
+        return HFDIB_OK;
+    }
+    cudaError_t e = cudaMalloc(out, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        return e == cudaErrorMemoryAllocation ? HFDIB_ERR_OOM : HFDIB_ERR_CUDA;
+    }
+    return HFDIB_OK;
+}
+void dev_free(const DevAlloc& A, cudaStream_t s, const DevBlock& b) {
+    if (!b.p) return;
+    if (A.release) A.release(b.p, b.bytes, (void*)s, A.ctx);
+    else cudaFree(b.p);
+}
 constexpr uint64_t STATE_MAGIC = 0x48464449425354ull;  // "HFDIBST"
 
 // Optional per-class kernel timing (host-driven sweeps only): an event pair
@@ -64,11 +119,15 @@ struct Ctx {
     double* ppart = nullptr;     // its block partials
     unsigned int* pbar = nullptr;
     int* perr = nullptr;
+    const int* err_src = nullptr;  // error word of the pressure kernel this handle's sweeps run
+    long long spin_limit = BARRIER_POLLS;
+    long long* trace = nullptr;    // set during hfdib_pressure_trace only
+    int trace_cap = 0;
     double* lam = nullptr;
     double* hist = nullptr;      // device [HIST][HFDIB_NRES]
-    double* res_dev = nullptr;   // device [HFDIB_NRES]
+    double* res_dev = nullptr;   // device [HFDIB_NRES + 1]: residuals, then the barrier-timeout flag
     int* cnt_scratch = nullptr;  // compaction scratch
-    std::vector<void*> allocs;
+    std::vector<DevBlock> allocs;
     long long sweeps = 0;
     long long launches = 0;
     int last_piters = 0;
@@ -77,6 +136,7 @@ struct Ctx {
     AdjGmres gm;                 // GMRES workspace of the adjoint
     cudaGraph_t adj_graph = nullptr;
     cudaGraphExec_t adj_gexec = nullptr;
+    DevAlloc al;                 // the allocator of every block in `allocs`
     bool adj_ready = false;
     long long adj_tcap = 0;      // capacity of adj.tent
 };
@@ -89,13 +149,9 @@ struct Ctx {
 
 int dalloc(Ctx* h, void** p, size_t bytes) {
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(p, bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        *p = nullptr;
-        return e == cudaErrorMemoryAllocation ? HFDIB_ERR_OOM : HFDIB_ERR_CUDA;
-    }
-    h->allocs.push_back(*p);
+    int rc = dev_alloc(h->al, h->stream, bytes, p);
+    if (rc) return rc;
+    h->allocs.push_back({*p, bytes});
     if (cudaMemsetAsync(*p, 0, bytes, h->stream) != cudaSuccess) return HFDIB_ERR_CUDA;
     return HFDIB_OK;
 }
@@ -118,7 +174,8 @@ void free_all(Ctx* h) {
     if (h->adj_graph) cudaGraphDestroy(h->adj_graph);
     h->adj_gexec = nullptr;
     h->adj_graph = nullptr;
-    for (void* p : h->allocs) cudaFree(p);
+    if (h->stream) cudaStreamSynchronize(h->stream);   // no pending work on blocks about to be released
+    for (const DevBlock& b : h->allocs) dev_free(h->al, h->stream, b);
     h->allocs.clear();
     if (h->pinned) cudaFreeHost(h->pinned);
     h->pinned = nullptr;
@@ -164,6 +221,23 @@ int sync_read(Ctx* h, const double* dev, double* host, int n) {
     CK(cudaMemcpyAsync(h->pinned, dev, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     memcpy(host, h->pinned, n * sizeof(double));
+    return HFDIB_OK;
+}
+
+// Residuals of the last sweep (HFDIB_NRES doubles).  HFDIB_ERR_TIMEOUT when a
+// barrier wait of a persistent pressure kernel gave up since the last read
+// (the flag is then cleared, so it is reported once).
+int read_residuals(Ctx* h, double* res) {
+    double tmp[HFDIB_NRES + 1];
+    int rc = sync_read(h, h->res_dev, tmp, HFDIB_NRES + 1);
+    if (rc) return rc;
+    memcpy(res, tmp, HFDIB_NRES * sizeof(double));
+    if (tmp[HFDIB_NRES] != 0.0) {
+        CK(cudaMemsetAsync(h->F.scal + SC_TIMEOUT, 0, sizeof(double), h->stream));
+        CK(cudaMemsetAsync(h->res_dev + HFDIB_NRES, 0, sizeof(double), h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        return HFDIB_ERR_TIMEOUT;
+    }
     return HFDIB_OK;
 }
 
@@ -241,16 +315,19 @@ void enqueue_part_a(Ctx* h, long long* L, bool with_pressure = true) {
     if (h->pblocks > 0) {
         // the whole solve, operator hierarchy included, in one cooperative launch
         cudaMemsetAsync(h->pbar, 0, sizeof(unsigned int), s);
+        cudaMemsetAsync(h->perr, 0, sizeof(int), s);
         if (F.mixed) {
             PROF(h, HFDIB_K_PCG, launch_pressure_persistent32(g, F, M, h->mg32, h->coarse_sweeps,
                                                                h->opt.p_reltol, h->opt.p_maxiter, h->pblocks,
-                                                               h->ppart, h->pbar, h->perr, h->tail_cells,
-                                                               h->opt.p_cg32, s));
+                                                               h->ppart, h->pbar, h->perr, h->spin_limit,
+                                                               h->tail_cells, h->opt.p_cg32, h->trace,
+                                                               h->trace_cap, s));
             (*L)++;
         } else {
             PROF(h, HFDIB_K_PCG, launch_pressure_persistent(g, F, M, jac, h->coarse_sweeps, h->opt.p_reltol,
                                                              h->opt.p_maxiter, h->pblocks, h->ppart, h->pbar,
-                                                             h->perr, h->tail_cells, s));
+                                                             h->perr, h->spin_limit, h->tail_cells, h->trace,
+                                                             h->trace_cap, s));
             (*L)++;
         }
         return;
@@ -325,7 +402,7 @@ void enqueue_part_b(Ctx* h, long long* L) {
     }
     Params Pe = P;
     if (!turb) Pe.model = HFDIB_LAMINAR;  // frozen turbulence: no k / eps|omega residuals
-    PROF(h, HFDIB_K_SWEEP_END, launch_sweep_end(Pe, F, g.dims, h->res_dev, h->hist, HIST, s));
+    PROF(h, HFDIB_K_SWEEP_END, launch_sweep_end(Pe, F, g.dims, h->err_src, h->res_dev, h->hist, HIST, s));
     (*L)++;
 }
 
@@ -452,11 +529,13 @@ struct BatchCtx {
     cudaEvent_t ef = nullptr;
     void* desc[2] = {nullptr, nullptr};   // device descriptor arrays (parity 0 / 1)
     std::vector<unsigned char> hdesc[2];
-    std::vector<void*> allocs;
+    DevAlloc al;                          // the allocator of every block in `allocs`
+    std::vector<DevBlock> allocs;
     std::vector<double*> parts;
     unsigned int* bar = nullptr;
     int* err = nullptr;
     int nblk = 0, threads = 1024, coarse_sweeps = 4, maxlev = 1;
+    long long spin_limit = BARRIER_POLLS;
     long long tail_cells = 1024;
     size_t smem = 0;
     int parity = 0;
@@ -515,9 +594,10 @@ void batch_enqueue(BatchCtx* b) {
         cudaStreamWaitEvent(s, b->ej[i], 0);
     }
     cudaMemsetAsync(b->bar, 0, sizeof(unsigned int), s);
+    cudaMemsetAsync(b->err, 0, sizeof(int), s);
     const Ctx* h0 = b->d[0];
     launch_pressure_batched(b->mixed, b->desc[b->parity], b->B, b->maxlev, b->coarse_sweeps, h0->opt.p_reltol,
-                            h0->opt.p_maxiter, b->nblk, b->threads, b->smem, b->bar, b->err, s);
+                            h0->opt.p_maxiter, b->nblk, b->threads, b->smem, b->bar, b->err, b->spin_limit, s);
     cudaEventRecord(b->ef, s);
     for (int i = 0; i < b->B; ++i) {
         cudaStreamWaitEvent(b->ws[i], b->ef, 0);
@@ -568,12 +648,27 @@ int batch_sweep_once(BatchCtx* b) {
     return HFDIB_OK;
 }
 
+// residuals of every problem; HFDIB_ERR_TIMEOUT (after clearing the flags)
+// when a barrier wait of the batched pressure kernel gave up since the last read
 int batch_read_residuals(BatchCtx* b, double* out) {
+    const size_t R = HFDIB_NRES + 1;
     for (int i = 0; i < b->B; ++i)
-        CK(cudaMemcpyAsync(b->pinned + (size_t)i * HFDIB_NRES, b->d[i]->res_dev, HFDIB_NRES * sizeof(double),
+        CK(cudaMemcpyAsync(b->pinned + (size_t)i * R, b->d[i]->res_dev, R * sizeof(double),
                            cudaMemcpyDeviceToHost, b->stream));
     CK(cudaStreamSynchronize(b->stream));
-    memcpy(out, b->pinned, sizeof(double) * HFDIB_NRES * b->B);
+    bool timeout = false;
+    for (int i = 0; i < b->B; ++i) {
+        memcpy(out + (size_t)i * HFDIB_NRES, b->pinned + (size_t)i * R, sizeof(double) * HFDIB_NRES);
+        if (b->pinned[(size_t)i * R + HFDIB_NRES] != 0.0) timeout = true;
+    }
+    if (timeout) {
+        for (Ctx* h : b->d) {
+            CK(cudaMemsetAsync(h->F.scal + SC_TIMEOUT, 0, sizeof(double), b->stream));
+            CK(cudaMemsetAsync(h->res_dev + HFDIB_NRES, 0, sizeof(double), b->stream));
+        }
+        CK(cudaStreamSynchronize(b->stream));
+        return HFDIB_ERR_TIMEOUT;
+    }
     return HFDIB_OK;
 }
 
@@ -583,7 +678,7 @@ void batch_free(BatchCtx* b) {
     batch_drop_graphs(b);
     for (Ctx* h : b->d)
         if (h) hfdib_destroy((hfdib_handle)h);
-    for (void* p : b->allocs) cudaFree(p);
+    for (const DevBlock& blk : b->allocs) dev_free(b->al, b->stream, blk);
     for (cudaEvent_t e : b->ej) cudaEventDestroy(e);
     if (b->ef) cudaEventDestroy(b->ef);
     for (cudaStream_t w : b->ws) cudaStreamDestroy(w);
@@ -1006,6 +1101,16 @@ int adj_gmres(Ctx* h, int m, double tol, int max_mv, int* mv_out, double* rel_ou
 
 extern "C" {
 
+int hfdib_set_allocator(hfdib_alloc_fn alloc, hfdib_free_fn release, void* ctx) {
+    if ((alloc == nullptr) != (release == nullptr)) return HFDIB_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(alloc_mu());
+    DevAlloc& a = alloc_setting();
+    a.alloc = alloc;
+    a.release = release;
+    a.ctx = alloc ? ctx : nullptr;
+    return HFDIB_OK;
+}
+
 void hfdib_default_options(hfdib_options* o) {
     if (!o) return;
     memset(o, 0, sizeof(*o));
@@ -1077,6 +1182,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
 
     Ctx* h = new (std::nothrow) Ctx();
     if (!h) return HFDIB_ERR_OOM;
+    h->al = current_alloc();
     h->stream = (cudaStream_t)stream;
     if (!h->stream) {
         // graph capture needs a real stream: own a non-blocking one
@@ -1149,7 +1255,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
     A(F.bt, N); A(F.diag, N); A(F.ywall, N); A(F.flags, N);
     A(F.prhs, N); A(F.pdiag, N); A(F.r, N); A(F.z, N); A(F.d[0], N); A(F.d[1], N); A(F.q, N);
     A(F.scal, SC_NSCAL); A(F.partials, 16 * (long long)nb + 64); A(F.counters, 64);
-    A(h->hist, HIST * HFDIB_NRES); A(h->res_dev, HFDIB_NRES);
+    A(h->hist, HIST * HFDIB_NRES); A(h->res_dev, HFDIB_NRES + 1);
     A(h->cnt_scratch, (long long)nb + 2);
     // multigrid hierarchy of the pressure operator: level 0 is the grid
     // itself (x = z, b = r); coarsen by 2 while every dimension is >= 4
@@ -1210,6 +1316,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
         A(h->ppart, 8 * (long long)nbk + 8);
         A(h->pbar, 2);
         A(h->perr, 1);
+        h->err_src = h->perr;
     }
 #undef A
     if (!rc && cudaMallocHost((void**)&h->pinned, 64 * sizeof(double)) != cudaSuccess) rc = HFDIB_ERR_OOM;
@@ -1267,7 +1374,7 @@ int hfdib_simple_sweep(hfdib_handle hh, int n_sweeps, double* residuals) {
         if (rc) return rc;
     }
     if (residuals) {
-        int rc = sync_read(h, h->res_dev, residuals, HFDIB_NRES);
+        int rc = read_residuals(h, residuals);
         if (rc) return rc;
         for (int q = 0; q < HFDIB_NRES; ++q)
             if (!isfinite(residuals[q])) return HFDIB_ERR_DIVERGED;
@@ -1289,7 +1396,7 @@ int hfdib_solve_steady(hfdib_handle hh, double tol, int max_iter, int check_ever
         if (rc) return rc;
         ++it;
         if (it % check_every == 0 || it == max_iter) {
-            rc = sync_read(h, h->res_dev, res, HFDIB_NRES);
+            rc = read_residuals(h, res);
             if (rc) return rc;
             double mx = 0.0;
             bool bad = false;
@@ -1494,6 +1601,25 @@ int hfdib_ib_force(hfdib_handle hh, double* force) {
     return HFDIB_OK;
 }
 
+int hfdib_force_coefficients(hfdib_handle hh, double A_ref, double gamma, double* coeffs) {
+    Ctx* h = (Ctx*)hh;
+    if (!h || !coeffs || !isfinite(gamma) || !(A_ref >= 0.0)) return HFDIB_ERR_INVALID_ARG;
+    const Grid& g = h->g;
+    if (A_ref == 0.0) {
+        // Eqs. dragcoeff, dlcoeffs: A_ref = l_ref dz on a one-cell-thick grid
+        if (g.dims != 2) return HFDIB_ERR_INVALID_ARG;
+        A_ref = h->bc.l_ref * g.D[2];
+    }
+    double U2 = g.u_in[0] * g.u_in[0] + g.u_in[1] * g.u_in[1] + g.u_in[2] * g.u_in[2];
+    if (!(U2 > 0.0)) return HFDIB_ERR_INVALID_ARG;
+    double force[6];
+    int rc = hfdib_ib_force(hh, force);
+    if (rc) return rc;
+    launch_force_coefficients(h->F, A_ref, U2, gamma, h->stream);
+    CK(cudaGetLastError());
+    return sync_read(h, h->F.scal + SC_COEF, coeffs, 2);
+}
+
 int hfdib_wall_shear(hfdib_handle hh, int side, double* tau, int64_t* n_faces_out) {
     Ctx* h = (Ctx*)hh;
     if (!h || side < 0 || side > 5) return HFDIB_ERR_INVALID_ARG;
@@ -1643,6 +1769,56 @@ int hfdib_adjoint_grad(hfdib_handle hh, int objective, double tol, int max_iter,
     return rc;
 }
 
+int hfdib_pressure_trace(hfdib_handle hh, int64_t* out, int capacity, int* n_out) {
+    Ctx* h = (Ctx*)hh;
+    if (!h || !out || capacity < 1 || capacity > (1 << 20)) return HFDIB_ERR_INVALID_ARG;
+    if (h->pblocks <= 0) return HFDIB_ERR_INVALID_ARG;    // needs the persistent pressure kernel
+    long long* dev = nullptr;
+    size_t bytes = (1 + 2 * (size_t)capacity) * sizeof(long long);
+    int rc = dev_alloc(h->al, h->stream, bytes, (void**)&dev);
+    if (rc) return rc;
+    if (cudaMemsetAsync(dev, 0, bytes, h->stream) != cudaSuccess) rc = HFDIB_ERR_CUDA;
+    std::vector<long long> host(1 + 2 * (size_t)capacity);
+    if (!rc) {
+        h->trace = dev;
+        h->trace_cap = capacity;
+        int ug = h->use_graph;
+        h->use_graph = 0;       // one host-driven sweep: the trace pointer is a launch argument
+        rc = run_sweep_host(h);
+        h->use_graph = ug;
+        h->trace = nullptr;
+        h->trace_cap = 0;
+    }
+    if (!rc && (cudaMemcpyAsync(host.data(), dev, bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+                cudaStreamSynchronize(h->stream) != cudaSuccess))
+        rc = HFDIB_ERR_CUDA;
+    cudaStreamSynchronize(h->stream);
+    dev_free(h->al, h->stream, DevBlock{dev, bytes});
+    if (rc) return rc;
+    int n = (int)host[0];
+    for (int i = 0; i < 2 * n; ++i) out[i] = host[1 + i];
+    if (n_out) *n_out = n;
+    return HFDIB_OK;
+}
+
+int hfdib_set_barrier_polls(hfdib_handle hh, int64_t polls) {
+    Ctx* h = (Ctx*)hh;
+    if (!h || polls < 0) return HFDIB_ERR_INVALID_ARG;
+    long long v = polls > 0 ? (long long)polls : BARRIER_POLLS;
+    if (v != h->spin_limit) {
+        h->spin_limit = v;
+        // the limit is a launch argument of the captured sweep: recapture
+        CK(cudaStreamSynchronize(h->stream));
+        for (int q = 0; q < 2; ++q) {
+            if (h->gexec[q]) cudaGraphExecDestroy(h->gexec[q]);
+            if (h->graph[q]) cudaGraphDestroy(h->graph[q]);
+            h->gexec[q] = nullptr;
+            h->graph[q] = nullptr;
+        }
+    }
+    return HFDIB_OK;
+}
+
 void hfdib_destroy(hfdib_handle hh) {
     Ctx* h = (Ctx*)hh;
     if (!h) return;
@@ -1664,6 +1840,7 @@ int hfdib_create_batch(int B, const hfdib_grid* grids, const double* const* lamb
     o.p_persistent = 1;
     BatchCtx* b = new (std::nothrow) BatchCtx();
     if (!b) return HFDIB_ERR_OOM;
+    b->al = current_alloc();
     b->B = B;
     b->mixed = o.precision == 1 ? 1 : 0;
     b->stream = (cudaStream_t)stream;
@@ -1690,28 +1867,36 @@ int hfdib_create_batch(int B, const hfdib_grid* grids, const double* const* lamb
                 cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess))
         rc = HFDIB_ERR_CUDA;
     b->nblk = sms;
+    if (!rc) {
+        void *pb = nullptr, *pe = nullptr;
+        rc = dev_alloc(b->al, b->stream, 256, &pb);
+        if (!rc) { b->allocs.push_back({pb, 256}); rc = dev_alloc(b->al, b->stream, 256, &pe); }
+        if (!rc) {
+            b->allocs.push_back({pe, 256});
+            b->bar = (unsigned int*)pb;
+            b->err = (int*)pe;
+            cudaMemsetAsync(b->bar, 0, 256, b->stream);
+            cudaMemsetAsync(b->err, 0, 256, b->stream);
+            for (Ctx* h : b->d) h->err_src = b->err;
+        }
+    }
     for (int i = 0; i < B && !rc; ++i) {
-        double* p = nullptr;
-        if (cudaMalloc(&p, sizeof(double) * 8 * (size_t)sms) != cudaSuccess) { rc = HFDIB_ERR_OOM; break; }
-        b->allocs.push_back(p);
-        b->parts.push_back(p);
+        void* p = nullptr;
+        size_t by = sizeof(double) * 8 * (size_t)sms;
+        rc = dev_alloc(b->al, b->stream, by, &p);
+        if (rc) break;
+        b->allocs.push_back({p, by});
+        b->parts.push_back((double*)p);
         if (b->d[i]->mg.nl > b->maxlev) b->maxlev = b->d[i]->mg.nl;
     }
     size_t dsz = pcgb_desc_size(b->mixed);
     for (int q = 0; q < 2 && !rc; ++q) {
-        if (cudaMalloc(&b->desc[q], dsz * B) != cudaSuccess) { rc = HFDIB_ERR_OOM; break; }
-        b->allocs.push_back(b->desc[q]);
+        rc = dev_alloc(b->al, b->stream, dsz * B, &b->desc[q]);
+        if (rc) break;
+        b->allocs.push_back({b->desc[q], dsz * B});
     }
-    if (!rc) {
-        if (cudaMalloc(&b->bar, 256) != cudaSuccess || cudaMalloc(&b->err, 256) != cudaSuccess) rc = HFDIB_ERR_OOM;
-        else {
-            b->allocs.push_back(b->bar);
-            b->allocs.push_back(b->err);
-            cudaMemsetAsync(b->bar, 0, 256, b->stream);
-            cudaMemsetAsync(b->err, 0, 256, b->stream);
-        }
-    }
-    if (!rc && cudaMallocHost((void**)&b->pinned, sizeof(double) * HFDIB_NRES * B) != cudaSuccess) rc = HFDIB_ERR_OOM;
+    if (!rc && cudaMallocHost((void**)&b->pinned, sizeof(double) * (HFDIB_NRES + 1) * B) != cudaSuccess)
+        rc = HFDIB_ERR_OOM;
     b->coarse_sweeps = o.mg_coarse_sweeps > 0 ? o.mg_coarse_sweeps : 4;
     b->use_graph = o.graph != 0;
     // shape key of the autotuner cache
@@ -1844,6 +2029,18 @@ int hfdib_batch_autotune(hfdib_batch bb, int trial_sweeps, hfdib_tune* best_out)
         tune_cache()[b->key] = best;
     }
     if (best_out) *best_out = best;
+    return HFDIB_OK;
+}
+
+int hfdib_batch_set_barrier_polls(hfdib_batch bb, int64_t polls) {
+    BatchCtx* b = (BatchCtx*)bb;
+    if (!b || polls < 0) return HFDIB_ERR_INVALID_ARG;
+    long long v = polls > 0 ? (long long)polls : BARRIER_POLLS;
+    if (v != b->spin_limit) {
+        b->spin_limit = v;
+        CK(cudaStreamSynchronize(b->stream));
+        batch_drop_graphs(b);   // the limit is a launch argument of the captured kernel
+    }
     return HFDIB_OK;
 }
 

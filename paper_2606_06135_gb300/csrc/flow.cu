@@ -591,6 +591,17 @@ __global__ void k_ib_force(Grid g, Fields F) {
     grid_reduce<6, false>(v, F.partials, F.counters + 12, F.scal + SC_FORCE);
 }
 
+// Eq. dragcoeff: C_d = 2 F.v_d / (A_ref |u_in|^2) with v_d = (1, 0, 0);
+// Eq. dlcoeffs: C_l the same with v_l = (-sin gamma, cos gamma, 0); F = f_n + f_t
+// (kinematic, so rho drops out)
+__global__ void k_force_coefficients(Fields F, double A_ref, double U2, double gamma) {
+    const double* f = F.scal + SC_FORCE;
+    double Fx = f[0] + f[3], Fy = f[1] + f[4];
+    double q = 2.0 / (A_ref * U2);
+    F.scal[SC_COEF] = q * Fx;
+    F.scal[SC_COEF + 1] = q * (-sin(gamma) * Fx + cos(gamma) * Fy);
+}
+
 // ---------------------------------------------------------------- wall shear
 // tau_w along one no-slip domain side (Sec. 3.3): the shear of the discrete
 // wall flux, nu_eff,P (u_P - 0)/(Delta/2) per tangential component, with
@@ -651,8 +662,11 @@ __global__ void k_recirc(Grid g, Fields F, double x_rear, unsigned int* count) {
 }
 
 // ---------------------------------------------------------------- sweep end
-__global__ void k_sweep_end(Fields F, int dims, int model, double* res_out, double* hist, int nhist) {
+__global__ void k_sweep_end(Fields F, int dims, int model, const int* err, double* res_out, double* hist,
+                            int nhist) {
     double* s = F.scal;
+    if (err && *err) s[SC_TIMEOUT] = 1.0;
+    res_out[HFDIB_NRES] = s[SC_TIMEOUT];
     auto sc = [](double r, double n1, double n2) { return r / ((n1 + n2) + 1e-20); };
     double res[HFDIB_NRES];
     for (int q = 0; q < 3; ++q)
@@ -715,15 +729,18 @@ void launch_update(const Grid& g, const Params& P, const Fields& F, const Level&
 void launch_ib_force(const Grid& g, const Fields& F, cudaStream_t s) {
     k_ib_force<<<rblocks(g.N), BLOCK, 0, s>>>(g, F);
 }
+void launch_force_coefficients(const Fields& F, double A_ref, double U2, double gamma, cudaStream_t s) {
+    k_force_coefficients<<<1, 1, 0, s>>>(F, A_ref, U2, gamma);
+}
 void launch_wall_shear(const Grid& g, const Fields& F, int side, long long nf, double* tau, cudaStream_t s) {
     if (nf > 0) k_wall_shear<<<nblocks(nf), BLOCK, 0, s>>>(g, F, side, nf, tau);
 }
 void launch_recirc(const Grid& g, const Fields& F, double x_rear, unsigned int* count, cudaStream_t s) {
     k_recirc<<<rblocks(g.N), BLOCK, 0, s>>>(g, F, x_rear, count);
 }
-void launch_sweep_end(const Params& P, const Fields& F, int dims, double* res_out, double* hist, int nhist,
-                      cudaStream_t s) {
-    k_sweep_end<<<1, 1, 0, s>>>(F, dims, P.model, res_out, hist, nhist);
+void launch_sweep_end(const Params& P, const Fields& F, int dims, const int* err, double* res_out, double* hist,
+                      int nhist, cudaStream_t s) {
+    k_sweep_end<<<1, 1, 0, s>>>(F, dims, P.model, err, res_out, hist, nhist);
 }
 
 }  // namespace hf

@@ -49,6 +49,7 @@ enum {
     SC_PCG_INIT = 40,            // r0.z0, r0.r0, b.b, then the 3 scaled-residual sums of p
     SC_FORCE = 52,               // 6: force on the body, pressure part xyz then the rest xyz
     SC_RECIRC = 58,              // largest x - x_rear of a recirculating cell
+    SC_COEF = 60,                // 2: drag and lift coefficients of the force
     SC_NSCAL = 64
 };
 
@@ -168,14 +169,19 @@ void launch_grad_u(const Grid& g, const Fields& F, cudaStream_t s);
 void launch_mom_asm(const Grid& g, const Params& P, const Fields& F, cudaStream_t s);
 void launch_conv_limit(const Grid& g, const Fields& F, cudaStream_t s);
 void launch_ib_force(const Grid& g, const Fields& F, cudaStream_t s);
+// C_d, C_l (Eqs. dragcoeff, dlcoeffs) from the force in scal[SC_FORCE..]: into scal[SC_COEF..]
+void launch_force_coefficients(const Fields& F, double A_ref, double U2, double gamma, cudaStream_t s);
 void launch_recirc(const Grid& g, const Fields& F, double x_rear, unsigned int* count, cudaStream_t s);
 void launch_wall_shear(const Grid& g, const Fields& F, int side, long long nf, double* tau, cudaStream_t s);
 void launch_mom_smooth(const Grid& g, const Params& P, const Fields& F, int colour, cudaStream_t s);
 void launch_hbya(const Grid& g, const Params& P, const Fields& F, cudaStream_t s);
 void launch_phiH(const Grid& g, const Fields& F, cudaStream_t s);
 void launch_update(const Grid& g, const Params& P, const Fields& F, const Level& L0, cudaStream_t s);
-void launch_sweep_end(const Params& P, const Fields& F, int dims, double* res_out, double* hist, int nhist,
-                      cudaStream_t s);
+// res_out: HFDIB_NRES residuals then one slot that is 1 once a persistent
+// kernel's barrier wait gave up (err: that kernel's error word, nullable);
+// the flag stays set in the scalars until the host clears it
+void launch_sweep_end(const Params& P, const Fields& F, int dims, const int* err, double* res_out, double* hist,
+                      int nhist, cudaStream_t s);
 
 // pressure.cu
 void launch_p_coef(const Grid& g, const MgLevels& M, const double* rAU, int ntail_from, cudaStream_t s);
@@ -189,13 +195,21 @@ void launch_pcg_body(const Grid& g, const Fields& F, const MgLevels& M, int ntai
 
 // pcgp.cu
 int pcgp_blocks(int* out);
+// Default poll budget of one wait at a persistent kernel's grid barrier
+// (about 0.1-1 s); a wait that runs out sets the kernel's error word.
+constexpr long long BARRIER_POLLS = 1ll << 26;
+// Phase tags of the persistent pressure kernel's trace (see hfdib_pressure_trace)
+enum { PH_START = 0, PH_BUILD0 = 1, PH_COARSEN = 2, PH_R0 = 3, PH_VC_SMOOTH0 = 4, PH_VC_RESTRICT = 5,
+       PH_VC_SMOOTH = 6, PH_VC_TAIL = 7, PH_VC_PROLONG = 8, PH_VC_UPSMOOTH = 9, PH_VC_FINAL = 10,
+       PH_CG_PRODUCT = 11, PH_CG_UPDATE = 12, PH_END = 13 };
 cudaError_t launch_pressure_persistent(const Grid& g, const Fields& F, const MgLevels& M, int jacobi,
                                        int coarse_sweeps, double reltol, int maxit, int nblk, double* part,
-                                       unsigned int* bar, int* err, long long tail_cells, cudaStream_t s);
+                                       unsigned int* bar, int* err, long long spin_limit, long long tail_cells,
+                                       long long* trace, int trace_cap, cudaStream_t s);
 cudaError_t launch_pressure_persistent32(const Grid& g, const Fields& F, const MgLevels& M, const MgLevels32& M32,
                                          int coarse_sweeps, double reltol, int maxit, int nblk, double* part,
-                                         unsigned int* bar, int* err, long long tail_cells, int cg32,
-                                         cudaStream_t s);
+                                         unsigned int* bar, int* err, long long spin_limit, long long tail_cells,
+                                         int cg32, long long* trace, int trace_cap, cudaStream_t s);
 void launch_p_coef32(const Grid& g, const MgLevels& M, const MgLevels32& M32, cudaStream_t s);
 void launch_mom_smooth32(const Grid& g, const Params& P, const Fields& F, int colour, int zero_init, cudaStream_t s);
 void launch_scal_smooth32(const Grid& g, const Params& P, const Fields& F, int eq, int colour, int zero_init,
@@ -210,7 +224,7 @@ size_t pcgb_desc_size(int mixed);
 int pcgb_max_batch();
 cudaError_t launch_pressure_batched(int mixed, const void* ddesc, int B, int maxlev, int coarse_sweeps,
                                     double reltol, int maxit, int nblk, int threads, size_t smem,
-                                    unsigned int* bar, int* err, cudaStream_t s);
+                                    unsigned int* bar, int* err, long long spin_limit, cudaStream_t s);
 int pcgb_fits(int mixed, int threads, size_t smem, int* blocks_per_sm);
 
 // adjoint.cu: reverse pass of the frozen-turbulence sweep (reverse fixed

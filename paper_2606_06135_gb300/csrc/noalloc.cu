@@ -11,14 +11,16 @@
 // compaction needs live in a fixed array in this file's device memory.
 //
 // That array is a file-scope __device__ symbol of NOALLOC_SCRATCH_INTS ints
-// (256 KB + 4 B), so the limit is NOALLOC_MAX_CELLS = 2^24 cells.  Every GPU
+// (256 KB + 8 B: the block counts, the total and an invalid-lambda flag), so
+// the limit is NOALLOC_MAX_CELLS = 2^24 cells.  Every GPU
 // that loads the library holds it until the process exits.  The host cannot
 // use the symbol's name as a device address; the first call on each device
 // looks up its address with cudaGetSymbolAddress (with that device current)
 // and caches it, so that first call should not be made inside a stream
-// capture.  All calls share the array and it keeps the last call's contents;
-// each call rewrites every entry it reads before reading it, and calls that
-// overlap on the GPU (different streams, no ordering) race on it.
+// capture.  The stream must belong to the current device (checked).  All
+// calls share the array and it keeps the last call's contents; each call
+// clears the flag and rewrites every count it reads before reading it, and
+// calls that overlap on the GPU (different streams, no ordering) race on it.
 #include <mutex>
 
 #include "common.cuh"
@@ -29,7 +31,9 @@ using hf::BLOCK;
 
 constexpr long long NOALLOC_MAX_CELLS = 1ll << 24;
 constexpr int NOALLOC_MAX_BLOCKS = (int)(NOALLOC_MAX_CELLS / BLOCK);
-constexpr int NOALLOC_SCRATCH_INTS = NOALLOC_MAX_BLOCKS + 1;  // block counts, then the total
+// block counts (the total follows the last used one), then the flag slot
+constexpr int NOALLOC_FLAG = NOALLOC_MAX_BLOCKS + 1;
+constexpr int NOALLOC_SCRATCH_INTS = NOALLOC_MAX_BLOCKS + 2;
 constexpr int NOALLOC_MAX_DEVICES = 64;
 
 static __device__ __align__(256) int g_noalloc_scratch[NOALLOC_SCRATCH_INTS];
@@ -53,8 +57,11 @@ int scratch_address(int** out) {
 }
 
 // cell groups of Sec. 2.3 written as bytes: 2 ic (lambda >= 0.5), 1 bc
-// (0 < lambda < 0.5, or lambda = 0 with an ic vertex neighbour), 0 fc
-__global__ void k_na_classify(int nx, int ny, int nz, const double* __restrict__ lam, uint8_t* __restrict__ tags) {
+// (0 < lambda < 0.5, or lambda = 0 with an ic vertex neighbour), 0 fc.  A
+// lambda outside [0, 1] or NaN sets *bad (the call then fails, as
+// hfdib_create does for such a field).
+__global__ void k_na_classify(int nx, int ny, int nz, const double* __restrict__ lam, uint8_t* __restrict__ tags,
+                              int* __restrict__ bad) {
     long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long N = (long long)nx * ny * nz;
     if (c >= N) return;
@@ -63,6 +70,7 @@ __global__ void k_na_classify(int nx, int ny, int nz, const double* __restrict__
     int j = (int)(r % ny);
     int k = (int)(r / ny);
     double l = lam[c];
+    if (!(l >= 0.0 && l <= 1.0)) *bad = 1;
     uint8_t t;
     if (l >= 0.5) {
         t = 2;
@@ -142,19 +150,30 @@ extern "C" int hfdib_classify_noalloc(const hfdib_grid* grid, const double* lamb
     if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return HFDIB_ERR_INVALID_ARG;
     long long N = (long long)grid->nx * grid->ny * grid->nz;
     if (N > NOALLOC_MAX_CELLS) return HFDIB_ERR_TOO_LARGE;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the scratch address below is the current device's: the stream must be on it
+    int cur = -1, sdev = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return HFDIB_ERR_CUDA;
+    if (cudaStreamGetDevice(s, &sdev) != cudaSuccess) { cudaGetLastError(); return HFDIB_ERR_INVALID_ARG; }
+    if (sdev != cur) return HFDIB_ERR_INVALID_ARG;
     int* scratch = nullptr;
     int rc = scratch_address(&scratch);
     if (rc) return rc;
-    cudaStream_t s = (cudaStream_t)stream;
     int nb = (int)((N + BLOCK - 1) / BLOCK);
-    k_na_classify<<<nb, BLOCK, 0, s>>>(grid->nx, grid->ny, grid->nz, lambda, tags);
+    if (cudaMemsetAsync(scratch + NOALLOC_FLAG, 0, sizeof(int), s) != cudaSuccess) return HFDIB_ERR_CUDA;
+    k_na_classify<<<nb, BLOCK, 0, s>>>(grid->nx, grid->ny, grid->nz, lambda, tags, scratch + NOALLOC_FLAG);
     k_na_count<<<nb, BLOCK, 0, s>>>(N, tags, scratch);
     k_na_scan<<<1, BLOCK, 0, s>>>(nb, scratch);
     k_na_scatter<<<nb, BLOCK, 0, s>>>(N, tags, scratch, bc_cells, bc_capacity);
-    int total = 0;
-    if (cudaMemcpyAsync(&total, scratch + nb, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    // a launch failure is reported here, before the copy is issued (this also
+    // consumes an error an earlier, unrelated launch may have left pending)
+    if (cudaGetLastError() != cudaSuccess) return HFDIB_ERR_CUDA;
+    int out[2] = {0, 0};
+    if (cudaMemcpyAsync(&out[0], scratch + nb, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&out[1], scratch + NOALLOC_FLAG, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return HFDIB_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return HFDIB_ERR_CUDA;
-    *n_bc = total;
-    return total > bc_capacity ? HFDIB_ERR_TOO_LARGE : HFDIB_OK;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return HFDIB_ERR_CUDA;
+    if (out[1]) { *n_bc = 0; return HFDIB_ERR_INVALID_ARG; }
+    *n_bc = out[0];
+    return out[0] > bc_capacity ? HFDIB_ERR_TOO_LARGE : HFDIB_OK;
 }

@@ -17,7 +17,6 @@
 namespace hf {
 
 constexpr int PB_MAXB = 64;
-constexpr long long PB_SPIN_LIMIT = 1ll << 26;
 
 template <typename MT>
 struct PcgbDesign {
@@ -40,7 +39,8 @@ struct PcgbArgs {
     double reltol;
     int maxit;
     unsigned int* bar;
-    int* err;
+    int* err;              // zeroed before each launch
+    long long spin_limit;  // polls of one barrier wait before giving up
 };
 
 // ---------------------------------------------------------------- sync and sums
@@ -50,8 +50,12 @@ __device__ __forceinline__ unsigned int pb_ld_acquire(const unsigned int* p) {
     return v;
 }
 
-// grid barrier: monotone arrival counter, bounded acquire polling
-__device__ inline void pb_sync(unsigned int* bar, int* err) {
+// grid barrier: monotone arrival counter, bounded acquire polling.  A wait
+// that runs out of polls sets the error word; a wait that finds it set
+// stops, and the whole block then leaves the kernel together (the host
+// reports HFDIB_ERR_TIMEOUT).
+__device__ inline void pb_sync(unsigned int* bar, int* err, long long spin_limit) {
+    __shared__ int s_abort;
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned int nb = gridDim.x;
@@ -59,11 +63,16 @@ __device__ inline void pb_sync(unsigned int* bar, int* err) {
         unsigned int old = atomicAdd(bar, 1u);
         unsigned int target = (old / nb + 1u) * nb;
         long long spins = 0;
+        int abort = 0;
         while ((int)(pb_ld_acquire(bar) - target) < 0) {
-            if (++spins > PB_SPIN_LIMIT) { atomicExch(err, 1); break; }
+            if (*(const volatile int*)err) { abort = 1; break; }
+            if (++spins > spin_limit) { atomicExch(err, 1); abort = 1; break; }
         }
+        if (!abort && *(const volatile int*)err) abort = 1;
+        s_abort = abort;
     }
     __syncthreads();
+    if (s_abort) asm volatile("exit;");
 }
 
 __device__ inline void pb_partial(double* part, int q, double v) {
@@ -149,13 +158,13 @@ __device__ void pb_build(const PcgbArgs<MT>& A, long long t0, long long TT) {
             if (copy) { P0.diag[c] = (MT)diag; P0.idg[c] = (MT)idg; }
         }
     }
-    pb_sync(A.bar, A.err);
+    pb_sync(A.bar, A.err, A.spin_limit);
     for (int l = 1; l < A.maxlev; ++l) {
         for (int b = 0; b < A.B; ++b) {
             const PcgbDesign<MT>& D = A.D[b];
             if (l < D.M.nl) pl_coarsen(D.M.lv[l - 1], D.M.lv[l], D.g.dims, t0, TT);
         }
-        pb_sync(A.bar, A.err);
+        pb_sync(A.bar, A.err, A.spin_limit);
     }
 }
 
@@ -206,7 +215,7 @@ __device__ void pb_vcycle(const PcgbArgs<MT>& A, const PbState& S, long long t0,
     const int B = A.B;
     for (int b = 0; b < B; ++b)
         if (!S.done[b]) pl_smooth(A.D[b].M.lv[0], A.D[b].g.dims, 1, t0, TT);
-    pb_sync(A.bar, A.err);
+    pb_sync(A.bar, A.err, A.spin_limit);
     for (int l = 0; l + 1 < A.maxlev; ++l) {
         bool any = false;
         for (int b = 0; b < B; ++b) {
@@ -216,12 +225,12 @@ __device__ void pb_vcycle(const PcgbArgs<MT>& A, const PbState& S, long long t0,
             else if (l + 1 == D.lf && D.lf < D.M.nl) { pl_restrict(D.M.lv[l], D.M.lv[l + 1], D.g.dims, false, t0, TT); any = true; }
         }
         if (!any) break;
-        pb_sync(A.bar, A.err);
+        pb_sync(A.bar, A.err, A.spin_limit);
         for (int b = 0; b < B; ++b) {
             const PcgbDesign<MT>& D = A.D[b];
             if (!S.done[b] && l + 1 < D.lf) pl_smooth(D.M.lv[l + 1], D.g.dims, 1, t0, TT);
         }
-        pb_sync(A.bar, A.err);
+        pb_sync(A.bar, A.err, A.spin_limit);
     }
     // coarse tails, problem b on block b % gridDim.x
     for (int b = 0; b < B; ++b) {
@@ -238,7 +247,7 @@ __device__ void pb_vcycle(const PcgbArgs<MT>& A, const PbState& S, long long t0,
             pl_tail(D.M, D.g.dims, D.lf, A.coarse_sweeps);
         }
     }
-    pb_sync(A.bar, A.err);
+    pb_sync(A.bar, A.err, A.spin_limit);
     for (int l = A.maxlev - 1; l >= 0; --l) {
         bool any = false;
         for (int b = 0; b < B; ++b) {
@@ -249,13 +258,13 @@ __device__ void pb_vcycle(const PcgbArgs<MT>& A, const PbState& S, long long t0,
             else pl_smooth(D.M.lv[l], D.g.dims, 1, t0, TT);
         }
         if (!any) continue;
-        pb_sync(A.bar, A.err);
+        pb_sync(A.bar, A.err, A.spin_limit);
         if (l > 0) {
             for (int b = 0; b < B; ++b) {
                 const PcgbDesign<MT>& D = A.D[b];
                 if (!S.done[b] && l < D.lf) pl_smooth(D.M.lv[l], D.g.dims, 0, t0, TT);
             }
-            pb_sync(A.bar, A.err);
+            pb_sync(A.bar, A.err, A.spin_limit);
         }
     }
     // last red half sweep of level 0 with r.z
@@ -281,7 +290,7 @@ __device__ void pb_vcycle(const PcgbArgs<MT>& A, const PbState& S, long long t0,
         }
         pb_partial(D.part, QB_RZ, rz);
     }
-    pb_sync(A.bar, A.err);
+    pb_sync(A.bar, A.err, A.spin_limit);
 }
 
 template <typename MT>
@@ -343,7 +352,7 @@ __global__ void __launch_bounds__(1024) k_pressure_batched(PcgbArgs<MT> A) {
         pb_partial(D.part, QB_R2, s2);
         pb_partial(D.part, QB_R3, s3);
     }
-    pb_sync(A.bar, A.err);
+    pb_sync(A.bar, A.err, A.spin_limit);
     for (int b = 0; b < B; ++b) {
         const PcgbDesign<MT>& D = A.D[b];
         double rr0 = pb_total(D.part, QB_RR);
@@ -371,7 +380,7 @@ __global__ void __launch_bounds__(1024) k_pressure_batched(PcgbArgs<MT> A) {
     for (int iter = 0; iter < A.maxit; ++iter) {
         bool all = true;
         for (int b = 0; b < B; ++b) all = all && S.done[b];
-        if (all || *A.err) break;
+        if (all) break;
         // d = z + beta d_old; q = A d = A z + beta q_old (linearity: the
         // neighbours' d need not be rebuilt); d.q
         for (int b = 0; b < B; ++b) {
@@ -407,7 +416,7 @@ __global__ void __launch_bounds__(1024) k_pressure_batched(PcgbArgs<MT> A) {
             }
             pb_partial(D.part, QB_DQ, s_dq);
         }
-        pb_sync(A.bar, A.err);
+        pb_sync(A.bar, A.err, A.spin_limit);
         for (int b = 0; b < B; ++b) {
             if (S.done[b]) continue;
             double dq = pb_total(A.D[b].part, QB_DQ);
@@ -438,7 +447,7 @@ __global__ void __launch_bounds__(1024) k_pressure_batched(PcgbArgs<MT> A) {
             }
             pb_partial(D.part, QB_RR, s_r2);
         }
-        pb_sync(A.bar, A.err);
+        pb_sync(A.bar, A.err, A.spin_limit);
         for (int b = 0; b < B; ++b) {
             if (S.done[b]) continue;
             double rr = pb_total(A.D[b].part, QB_RR);
@@ -465,7 +474,6 @@ __global__ void __launch_bounds__(1024) k_pressure_batched(PcgbArgs<MT> A) {
             const Fields& F = A.D[b].F;
             F.scal[SC_PCG_ITERS] = (double)S.it[b];
             F.scal[SC_PCG_DONE] = 1.0;
-            if (*A.err) F.scal[SC_TIMEOUT] = 1.0;
         }
     }
 }
@@ -519,7 +527,7 @@ int pcgb_max_batch() { return PB_MAXB; }
 
 cudaError_t launch_pressure_batched(int mixed, const void* ddesc, int B, int maxlev, int coarse_sweeps,
                                     double reltol, int maxit, int nblk, int threads, size_t smem,
-                                    unsigned int* bar, int* err, cudaStream_t s) {
+                                    unsigned int* bar, int* err, long long spin_limit, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nblk);
     cfg.blockDim = dim3(threads);
@@ -531,14 +539,16 @@ cudaError_t launch_pressure_batched(int mixed, const void* ddesc, int B, int max
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (mixed) {
-        PcgbArgs<float> A{(const PcgbDesign<float>*)ddesc, B, maxlev, coarse_sweeps, reltol, maxit, bar, err};
+        PcgbArgs<float> A{(const PcgbDesign<float>*)ddesc, B, maxlev, coarse_sweeps, reltol, maxit, bar, err,
+                          spin_limit};
         cudaError_t e = cudaFuncSetAttribute(k_pressure_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         void* args[] = {&A};
         return cudaLaunchKernelExC(&cfg, (const void*)k_pressure_batched<float>, args);
     }
-    PcgbArgs<double> A{(const PcgbDesign<double>*)ddesc, B, maxlev, coarse_sweeps, reltol, maxit, bar, err};
+    PcgbArgs<double> A{(const PcgbDesign<double>*)ddesc, B, maxlev, coarse_sweeps, reltol, maxit, bar, err,
+                       spin_limit};
     cudaError_t e = cudaFuncSetAttribute(k_pressure_batched<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;

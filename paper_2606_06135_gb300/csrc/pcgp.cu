@@ -6,12 +6,15 @@
 // coefficients, same V-cycle: red-black Gauss-Seidel, piecewise-constant
 // transfers, coarse coefficients half the covered fine faces); only the
 // execution differs: phases separated by a grid barrier instead of kernel
-// boundaries.  The launch is cooperative (all blocks resident), the barrier
-// spins with an iteration limit and records a timeout in the error word
-// instead of waiting forever.  Reductions: every block writes its partial;
-// after the barrier every block sums all partials in the same order, so all
-// blocks hold the same bit-identical value (deterministic, no atomics on
-// floating point).  Levels of at most tail_cells cells (an option) run inside block 0.
+// boundaries.  The launch is cooperative (all blocks resident).  Each wait
+// at the grid barrier is bounded: a block whose poll budget runs out sets the
+// error word, and every block that finds the error word set at a barrier
+// leaves the kernel there (no further phase runs on incomplete data).  The
+// host reads the word after the sweep and reports HFDIB_ERR_TIMEOUT.
+// Reductions: every block writes its partial; after the barrier every block
+// sums all partials in the same order, so all blocks hold the same
+// bit-identical value (deterministic, no atomics on floating point).  Levels
+// of at most tail_cells cells (an option) run inside block 0.
 //
 // Mixed precision (pattern "FP32 sweeps inside FP64 refinement"): the CG
 // vectors, dot products, scalars and the defect r = rhs - A p stay FP64; the
@@ -25,7 +28,6 @@
 namespace hf {
 
 constexpr int PT_THREADS = 1024;
-constexpr long long PT_SPIN_LIMIT = 1ll << 26;   // ~0.1-1 s of polling
 
 template <typename MT>
 struct PcgpArgs {
@@ -42,11 +44,14 @@ struct PcgpArgs {
     int maxit;
     double* part;        // [8][gridDim.x] block partials
     unsigned int* bar;   // barrier arrival counter (zeroed before each launch)
-    int* err;            // barrier timeout flag
+    int* err;            // barrier timeout flag (zeroed before each launch)
+    long long spin_limit;  // polls of one barrier wait before giving up
     long long tail_cells;  // largest level block 0 runs alone (shared memory when it fits)
     int cg32;              // FP32 preconditioner only: CG vectors and product in FP32
     float* cd32[2];        // FP32 search directions (cg32)
     float* cq32;           // FP32 A d (cg32)
+    long long* trace;      // nullable: block 0 records (phase, %globaltimer) pairs here
+    int trace_cap;         // pairs that fit after the count in trace[0]
 };
 
 // ---------------------------------------------------------------- barrier
@@ -58,8 +63,37 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
     return v;
 }
 
+__device__ __forceinline__ int ld_volatile_i32(const int* p) {
+    return *(const volatile int*)p;
+}
+
+// Phase trace: with A.trace set, thread 0 of block 0 appends (phase tag,
+// %globaltimer in ns) after every barrier; trace[0] counts the pairs.
+__device__ __forceinline__ long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return (long long)t;
+}
 template <typename AT>
-__device__ inline void grid_sync(const AT& A) {
+__device__ inline void trace_mark(const AT& A, int tag) {
+    if (A.trace && blockIdx.x == 0 && threadIdx.x == 0) {
+        long long n = A.trace[0];
+        if (n < A.trace_cap) {
+            A.trace[1 + 2 * n] = tag;
+            A.trace[2 + 2 * n] = global_ns();
+            A.trace[0] = n + 1;
+        }
+    }
+}
+
+// Grid barrier.  Thread 0 arrives and polls; a wait that runs out of polls
+// sets the error word, and a wait that sees the error word set stops.  Then
+// the whole block either continues or, on an error, leaves the kernel
+// together (block-uniform, after the block barrier, so no thread is left
+// waiting at a later __syncthreads).
+template <typename AT>
+__device__ inline void grid_sync(const AT& A, int tag) {
+    __shared__ int s_abort;
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned int nb = gridDim.x;
@@ -67,11 +101,17 @@ __device__ inline void grid_sync(const AT& A) {
         unsigned int old = atomicAdd(A.bar, 1u);
         unsigned int target = (old / nb + 1u) * nb;
         long long spins = 0;
+        int abort = 0;
         while ((int)(ld_acquire_u32(A.bar) - target) < 0) {
-            if (++spins > PT_SPIN_LIMIT) { atomicExch(A.err, 1); break; }
+            if (ld_volatile_i32(A.err)) { abort = 1; break; }
+            if (++spins > A.spin_limit) { atomicExch(A.err, 1); abort = 1; break; }
         }
+        if (!abort && ld_volatile_i32(A.err)) abort = 1;
+        s_abort = abort;
     }
     __syncthreads();
+    if (s_abort) asm volatile("exit;");
+    trace_mark(A, tag);
 }
 
 // block partial of v into slot q; returns nothing (combined after a barrier)
@@ -160,16 +200,16 @@ __device__ void pl_vcycle_rest(const PcgpArgs<MT>& A, int qdot) {
     const long long TT = (long long)gridDim.x * blockDim.x;
     const int lf = A.lf;
     pl_smooth(M.lv[0], dims, 1, t0, TT);
-    grid_sync(A);
+    grid_sync(A, PH_VC_SMOOTH0);
     for (int l = 0; l + 1 < lf; ++l) {
         pl_restrict(M.lv[l], M.lv[l + 1], dims, true, t0, TT);
-        grid_sync(A);
+        grid_sync(A, PH_VC_RESTRICT);
         pl_smooth(M.lv[l + 1], dims, 1, t0, TT);
-        grid_sync(A);
+        grid_sync(A, PH_VC_SMOOTH);
     }
     if (lf < M.nl) {
         pl_restrict(M.lv[lf - 1], M.lv[lf], dims, false, t0, TT);
-        grid_sync(A);
+        grid_sync(A, PH_VC_RESTRICT);
         if (blockIdx.x == 0) {
             if (A.smem_tail) {
                 // the tail levels live in shared memory: bring b of level lf in,
@@ -184,16 +224,16 @@ __device__ void pl_vcycle_rest(const PcgpArgs<MT>& A, int qdot) {
                 pl_tail(M, dims, lf, A.coarse_sweeps);
             }
         }
-        grid_sync(A);
+        grid_sync(A, PH_VC_TAIL);
     }
     for (int l = lf - 1; l >= 0; --l) {
         const LevelT<MT>& L = M.lv[l];
         if (l + 1 < M.nl) pl_prolong_black(L, M.lv[l + 1], dims, t0, TT);
         else pl_smooth(L, dims, 1, t0, TT);
-        grid_sync(A);
+        grid_sync(A, PH_VC_PROLONG);
         if (l > 0) {
             pl_smooth(L, dims, 0, t0, TT);
-            grid_sync(A);
+            grid_sync(A, PH_VC_UPSMOOTH);
         }
     }
     // final red half sweep of level 0 with r.z (the CG residual: FP64, or
@@ -217,7 +257,7 @@ __device__ void pl_vcycle_rest(const PcgpArgs<MT>& A, int qdot) {
         }
     }
     block_partial(A, qdot, rz);
-    grid_sync(A);
+    grid_sync(A, PH_VC_FINAL);
 }
 
 // level-0 operator from rAU (FP64, also used by the flux correction), its
@@ -259,12 +299,12 @@ __device__ void pl_build_operator(const PcgpArgs<MT>& A) {
         L.idg[c] = idg;
         if (copy) { P0.diag[c] = (MT)diag; P0.idg[c] = (MT)idg; }
     }
-    grid_sync(A);
+    grid_sync(A, PH_BUILD0);
     // the shared-memory tail levels are built by block 0 (pl_build_tail)
     const int lend = (A.smem_tail && A.lf < A.M.nl) ? A.lf : A.M.nl;
     for (int l = 1; l < lend; ++l) {
         pl_coarsen(A.M.lv[l - 1], A.M.lv[l], g.dims, t0, TT);
-        grid_sync(A);
+        grid_sync(A, PH_COARSEN);
     }
 }
 
@@ -281,6 +321,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_pressure_persistent(PcgpArgs<MT>
     const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long T = (long long)gridDim.x * blockDim.x;
     const bool jac = A.jacobi != 0;
+    trace_mark(A, PH_START);
     // ---- operator hierarchy for this sweep's rAU (tail levels to shared memory)
     pl_build_operator(A);
     // ---- block 0 builds the shared-memory tail while the other blocks form
@@ -342,7 +383,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_pressure_persistent(PcgpArgs<MT>
     block_partial(A, Q_R1, s1);
     block_partial(A, Q_R2, s2);
     block_partial(A, Q_R3, s3);
-    grid_sync(A);
+    grid_sync(A, PH_R0);
     double rr0 = grid_total(A, Q_RR);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         F.scal[SC_PCG_INIT + 1] = rr0;
@@ -366,7 +407,6 @@ __global__ void __launch_bounds__(PT_THREADS) k_pressure_persistent(PcgpArgs<MT>
         }
         double rz_prev = 1.0;
         while (it < A.maxit) {
-            if (*A.err) break;
             double beta = it == 0 ? 0.0 : rz / rz_prev;
             if constexpr (sizeof(MT) == 4) {
                 if (A.cg32) {
@@ -397,7 +437,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_pressure_persistent(PcgpArgs<MT>
                         s_dq += (double)dP * (double)qv;
                     }
                     block_partial(A, Q_DQ, s_dq);
-                    grid_sync(A);
+                    grid_sync(A, PH_CG_PRODUCT);
                     double dq = grid_total(A, Q_DQ);
                     double alpha = dq != 0.0 ? rz / dq : 0.0;
                     const float fa = (float)alpha;
@@ -412,7 +452,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_pressure_persistent(PcgpArgs<MT>
                         if (((i + j + k) & 1) == 0) z[c] = (MT)(r * (float)P0.idg[c]);
                     }
                     block_partial(A, Q_RR, s_r2);
-                    grid_sync(A);
+                    grid_sync(A, PH_CG_UPDATE);
                     double rr = grid_total(A, Q_RR);
                     rz_prev = rz;
                     pl_vcycle_rest(A, Q_RZ);
@@ -447,7 +487,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_pressure_persistent(PcgpArgs<MT>
                 s_dq += dP * qv;
             }
             block_partial(A, Q_DQ, s_dq);
-            grid_sync(A);
+            grid_sync(A, PH_CG_PRODUCT);
             double dq = grid_total(A, Q_DQ);
             double alpha = dq != 0.0 ? rz / dq : 0.0;
             // p += alpha d; r -= alpha q; r.r; z start
@@ -471,7 +511,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_pressure_persistent(PcgpArgs<MT>
             }
             block_partial(A, Q_RR, s_r2);
             if (jac) block_partial(A, Q_RZ, s_z);
-            grid_sync(A);
+            grid_sync(A, PH_CG_UPDATE);
             double rr = grid_total(A, Q_RR);
             rz_prev = rz;
             if (jac) {
@@ -489,8 +529,8 @@ __global__ void __launch_bounds__(PT_THREADS) k_pressure_persistent(PcgpArgs<MT>
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         F.scal[SC_PCG_ITERS] = (double)it;
         F.scal[SC_PCG_DONE] = 1.0;
-        if (*A.err) F.scal[SC_TIMEOUT] = 1.0;
     }
+    trace_mark(A, PH_END);
 }
 
 // ---------------------------------------------------------------- launcher
@@ -560,24 +600,27 @@ static cudaError_t launch_pp(PcgpArgs<MT>& A, int nblk, cudaStream_t s) {
 
 cudaError_t launch_pressure_persistent(const Grid& g, const Fields& F, const MgLevels& M, int jacobi,
                                        int coarse_sweeps, double reltol, int maxit, int nblk, double* part,
-                                       unsigned int* bar, int* err, long long tail_cells, cudaStream_t s) {
+                                       unsigned int* bar, int* err, long long spin_limit, long long tail_cells,
+                                       long long* trace, int trace_cap, cudaStream_t s) {
     PcgpArgs<double> A;
     A.g = g; A.F = F; A.L0d = M.lv[0]; A.M = M; A.zp = M.lv[0].x;
     A.coarse_sweeps = coarse_sweeps; A.jacobi = jacobi; A.reltol = reltol; A.maxit = maxit;
-    A.part = part; A.bar = bar; A.err = err; A.tail_cells = tail_cells;
+    A.part = part; A.bar = bar; A.err = err; A.spin_limit = spin_limit; A.tail_cells = tail_cells;
     A.cg32 = 0; A.cd32[0] = A.cd32[1] = nullptr; A.cq32 = nullptr;
+    A.trace = trace; A.trace_cap = trace_cap;
     return launch_pp(A, nblk, s);
 }
 
 cudaError_t launch_pressure_persistent32(const Grid& g, const Fields& F, const MgLevels& M, const MgLevels32& M32,
                                          int coarse_sweeps, double reltol, int maxit, int nblk, double* part,
-                                         unsigned int* bar, int* err, long long tail_cells, int cg32,
-                                         cudaStream_t s) {
+                                         unsigned int* bar, int* err, long long spin_limit, long long tail_cells,
+                                         int cg32, long long* trace, int trace_cap, cudaStream_t s) {
     PcgpArgs<float> A;
     A.g = g; A.F = F; A.L0d = M.lv[0]; A.M = M32; A.zp = M32.lv[0].x;
     A.coarse_sweeps = coarse_sweeps; A.jacobi = 0; A.reltol = reltol; A.maxit = maxit;
-    A.part = part; A.bar = bar; A.err = err; A.tail_cells = tail_cells;
+    A.part = part; A.bar = bar; A.err = err; A.spin_limit = spin_limit; A.tail_cells = tail_cells;
     A.cg32 = cg32; A.cd32[0] = F.pd32[0]; A.cd32[1] = F.pd32[1]; A.cq32 = F.pq32;
+    A.trace = trace; A.trace_cap = trace_cap;
     return launch_pp(A, nblk, s);
 }
 

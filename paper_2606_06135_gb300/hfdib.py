@@ -8,7 +8,6 @@ fallback -- load_library() raises when it is missing.
 from __future__ import annotations
 
 import ctypes as C
-import math
 import os
 
 import numpy as np
@@ -29,10 +28,13 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "out of memory"
           -4: "not converged", -5: "diverged", -6: "state mismatch", -7: "too large", -8: "timeout"}
 
 OBJECTIVES = {"pressure_drop": 0, "drag": 1}
+PRESSURE_PHASES = ("start", "build0", "coarsen", "r0", "vc_smooth0", "vc_restrict", "vc_smooth", "vc_tail",
+                   "vc_prolong", "vc_upsmooth", "vc_final", "cg_product", "cg_update", "end")
 WALL_SIDES = ("xmin", "xmax", "ymin", "ymax", "zmin", "zmax")
 
 ERR_NOT_CONVERGED = -4
 STATUS_TOO_LARGE = -7
+ERR_TIMEOUT = -8
 
 
 class HfdibError(RuntimeError):
@@ -70,13 +72,20 @@ class Options(C.Structure):
 
 _LIB = None
 
+# hfdib_alloc_fn / hfdib_free_fn of include/hfdib.h
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_ALLOCATOR = None     # the installed callbacks (kept alive while installed)
+
 EXPORTED = ("hfdib_default_options", "hfdib_create", "hfdib_simple_sweep", "hfdib_solve_steady",
             "hfdib_get_field", "hfdib_set_field", "hfdib_get_tags", "hfdib_get_bc_list",
             "hfdib_get_history", "hfdib_get_state", "hfdib_set_state", "hfdib_get_counters",
             "hfdib_error_string", "hfdib_destroy", "hfdib_profile_sweeps", "hfdib_get_launch_counts",
             "hfdib_classify_noalloc", "hfdib_create_batch", "hfdib_batch_sweep", "hfdib_batch_solve_steady",
             "hfdib_batch_handle", "hfdib_batch_autotune", "hfdib_destroy_batch", "hfdib_adjoint_grad",
-            "hfdib_ib_force", "hfdib_wall_shear", "hfdib_recirculation")
+            "hfdib_ib_force", "hfdib_wall_shear", "hfdib_recirculation", "hfdib_set_barrier_polls",
+            "hfdib_batch_set_barrier_polls", "hfdib_force_coefficients", "hfdib_pressure_trace",
+            "hfdib_set_allocator")
 KERNEL_CLASSES = ("imposed", "grad_u", "mom_asm", "mom_smooth", "hbya", "p_coef", "pcg", "vcycle0",
                   "update", "turb_prep", "scal_asm", "scal_smooth", "turb_final", "sweep_end")
 
@@ -130,6 +139,16 @@ def load_library(path=LIBPATH):
     lib.hfdib_wall_shear.restype = i32
     lib.hfdib_recirculation.argtypes = [vp, dbl, vp]
     lib.hfdib_recirculation.restype = i32
+    lib.hfdib_force_coefficients.argtypes = [vp, dbl, dbl, vp]
+    lib.hfdib_force_coefficients.restype = i32
+    lib.hfdib_set_allocator.argtypes = [ALLOC_FN, FREE_FN, vp]
+    lib.hfdib_set_allocator.restype = i32
+    lib.hfdib_pressure_trace.argtypes = [vp, vp, i32, C.POINTER(i32)]
+    lib.hfdib_pressure_trace.restype = i32
+    lib.hfdib_set_barrier_polls.argtypes = [vp, i64]
+    lib.hfdib_set_barrier_polls.restype = i32
+    lib.hfdib_batch_set_barrier_polls.argtypes = [vp, i64]
+    lib.hfdib_batch_set_barrier_polls.restype = i32
     lib.hfdib_error_string.argtypes = [i32]
     lib.hfdib_error_string.restype = C.c_char_p
     lib.hfdib_destroy.argtypes = [vp]
@@ -143,6 +162,44 @@ def load_library(path=LIBPATH):
             f.restype = C.c_int
     _LIB = lib
     return lib
+
+
+def use_torch_allocator():
+    """Device memory of the handles and batches created from now on comes from
+    PyTorch's caching allocator (hfdib_set_allocator): blocks are allocated
+    on the handle's stream and returned at destroy."""
+    global _ALLOCATOR
+    if _ALLOCATOR is not None and _ALLOCATOR[0] == "torch":
+        return
+    import torch
+    lib = load_library()
+
+    def alloc(nbytes, stream, ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0)))
+        except Exception:
+            return None        # out of memory: the library reports HFDIB_ERR_OOM
+
+    def free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    cbs = ("torch", ALLOC_FN(alloc), FREE_FN(free))
+    _check(lib.hfdib_set_allocator(cbs[1], cbs[2], None), "hfdib_set_allocator")
+    _ALLOCATOR = cbs
+
+
+def use_cuda_malloc():
+    """Handles and batches created from now on allocate with cudaMalloc."""
+    global _ALLOCATOR
+    lib = load_library()
+    _check(lib.hfdib_set_allocator(ALLOC_FN(), FREE_FN(), None), "hfdib_set_allocator")
+    # the old callbacks may still serve handles made while they were installed
+    if _ALLOCATOR is not None:
+        _RETIRED.append(_ALLOCATOR)
+    _ALLOCATOR = ("cuda", None, None)
+
+
+_RETIRED = []
 
 
 def default_options(**kw):
@@ -206,6 +263,8 @@ class Solver:
         lam = dev_array(case["lam"])
         yw = dev_array(case.get("ywall"))
         torch.cuda.synchronize(self.device)
+        if _ALLOCATOR is None:
+            use_torch_allocator()
         self._opts = default_options(**opts)
         h = C.c_void_p()
         rc = self.lib.hfdib_create(C.byref(grid_struct(g)), C.c_void_p(lam.data_ptr()),
@@ -221,6 +280,24 @@ class Solver:
         rc = self.lib.hfdib_simple_sweep(self.h, int(n), res.ctypes.data if read else None)
         _check(rc, "hfdib_simple_sweep")
         return res
+
+    def pressure_trace(self, capacity=4096):
+        """One sweep with the persistent pressure kernel's phase trace:
+        a list of (phase name, ns since the kernel started)."""
+        buf = np.zeros(2 * capacity, dtype=np.int64)
+        n = C.c_int(0)
+        self.stream.synchronize()
+        _check(self.lib.hfdib_pressure_trace(self.h, buf.ctypes.data, int(capacity), C.byref(n)),
+               "hfdib_pressure_trace")
+        pairs = buf[: 2 * n.value].reshape(-1, 2)
+        t0 = pairs[0, 1] if len(pairs) else 0
+        return [(PRESSURE_PHASES[int(t)], int(ns - t0)) for t, ns in pairs]
+
+    def set_barrier_polls(self, polls=0):
+        """Poll budget of each wait at the persistent pressure kernel's grid
+        barrier (0: the default); a wait that runs out makes the next
+        residual read return HFDIB_ERR_TIMEOUT."""
+        _check(self.lib.hfdib_set_barrier_polls(self.h, int(polls)), "hfdib_set_barrier_polls")
 
     def solve(self, tol=1e-6, max_iter=1000, check_every=10, raise_on_fail=False):
         it = C.c_int(0)
@@ -342,18 +419,13 @@ class Solver:
         return out[:3].copy(), out[3:].copy()
 
     def force_coefficients(self, A_ref=None, gamma=0.0):
-        """(C_d, C_l) of Eqs. dragcoeff and dlcoeffs.  A_ref defaults, on a 2D
-        grid, to l_ref times the cell depth dz."""
-        if A_ref is None:
-            if self.dims != 2:
-                raise ValueError("A_ref is required on a 3D grid")
-            A_ref = self.case["l_ref"] * self.case["grid"]["dz"]
-        Fn, Ft = self.force()
-        F = Fn + Ft
-        u_in = np.asarray(self.case["u_in"], dtype=np.float64)
-        q = 0.5 * A_ref * float(u_in @ u_in)
-        vl = np.array([-math.sin(gamma), math.cos(gamma), 0.0])
-        return float(F[0]) / q, float(F @ vl) / q
+        """(C_d, C_l) of Eqs. dragcoeff and dlcoeffs (hfdib_force_coefficients).
+        A_ref None: l_ref times the cell depth dz (2D grids)."""
+        out = np.zeros(2)
+        self.stream.synchronize()
+        _check(self.lib.hfdib_force_coefficients(self.h, 0.0 if A_ref is None else float(A_ref), float(gamma),
+                                                 out.ctypes.data), "hfdib_force_coefficients")
+        return float(out[0]), float(out[1])
 
     def wall_shear(self, side):
         """tau_w along a no-slip domain side ('ymin', ...): device tensor
@@ -446,6 +518,8 @@ class BatchSolver:
         self._lam = [dev(c["lam"]) for c in self.cases]
         self._yw = [dev(c.get("ywall")) for c in self.cases]
         torch.cuda.synchronize(self.device)
+        if _ALLOCATOR is None:
+            use_torch_allocator()
         B = self.B
         grids = (Grid * B)(*[grid_struct(c["grid"]) for c in self.cases])
         bcs = (Bc * B)(*[bc_struct(c) for c in self.cases])
@@ -472,6 +546,9 @@ class BatchSolver:
         if rc not in (0, ERR_NOT_CONVERGED):
             _check(rc, "hfdib_batch_solve_steady")
         return rc, it, res
+
+    def set_barrier_polls(self, polls=0):
+        _check(self.lib.hfdib_batch_set_barrier_polls(self.h, int(polls)), "hfdib_batch_set_barrier_polls")
 
     def problem(self, i):
         hh = C.c_void_p()

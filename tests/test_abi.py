@@ -112,3 +112,14 @@ def test_binding_structs_match_the_header():
             base = ctype_of[ctype]
             expect = base * n if n > 1 else base
             assert ftype == expect or (n > 1 and ftype._type_ == base and ftype._length_ == n), (cname, fname)
+
+
+def test_set_allocator_rejects_half_a_hook(libpath):
+    """hfdib_set_allocator takes both callbacks or neither (no GPU touched)."""
+    from paper_2606_06135_gb300 import hfdib
+    lib = hfdib.load_library(libpath)
+    keep = hfdib.FREE_FN(lambda p, n, s, c: None)
+    assert lib.hfdib_set_allocator(hfdib.ALLOC_FN(), keep, None) == -1
+    keep2 = hfdib.ALLOC_FN(lambda n, s, c: None)
+    assert lib.hfdib_set_allocator(keep2, hfdib.FREE_FN(), None) == -1
+    assert lib.hfdib_set_allocator(hfdib.ALLOC_FN(), hfdib.FREE_FN(), None) == 0

@@ -165,10 +165,13 @@ def test_autograd_function_delivers_the_gradient():
     s.close()
 
 
-def test_3d_gradient_matches_oracle():
+@pytest.mark.parametrize("golden_name", ["adjoint3d_sphere.txt", "adjoint3d_sphere_drag.txt",
+                                         "adjoint3d_sphere_keps_drag.txt"])
+def test_3d_gradient_matches_oracle(golden_name):
     """3D (trilinear stencils, 26-neighbour normals): the GPU adjoint of a
-    sphere placed off the grid's symmetry planes against the oracle's
-    (tests/golden/adjoint3d_sphere.txt, written from oracle/ alone by
+    sphere placed off the grid's symmetry planes against the oracle's, for the
+    pressure drop and the drag (laminar) and the drag with frozen k-epsilon
+    turbulence (goldens written from oracle/ alone by
     tests/golden/make_adjoint3d.py)."""
     import importlib.util
     import os
@@ -176,15 +179,17 @@ def test_3d_gradient_matches_oracle():
     spec = importlib.util.spec_from_file_location("make_adjoint3d", os.path.join(golden, "make_adjoint3d.py"))
     mk = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mk)
-    case = mk.sphere_off_axis()
-    vals = np.loadtxt(os.path.join(golden, "adjoint3d_sphere.txt"))
+    model, Re, objective = mk.GOLDENS[golden_name]
+    case = mk.sphere_off_axis(model, Re)
+    vals = np.loadtxt(os.path.join(golden, golden_name))
     Jo, go = vals[0], vals[1:]
     s = gpu_converged(case)
-    J, g, it, ch, rc = s.adjoint_grad(tol=1e-12, max_iter=40000)
+    J, g, it, ch, rc = s.adjoint_grad(tol=1e-12, max_iter=40000, objective=objective)
     assert rc == 0, (it, ch)
     g = g.cpu().numpy().ravel()
     e = rel(g, go)
-    print("3D sphere: J gpu %.15f oracle %.15f, grad rel-L2 %.2e, %d adjoint iterations" % (J, Jo, e, it))
+    print("3D sphere %s: J gpu %.15f oracle %.15f, grad rel-L2 %.2e, %d adjoint iterations"
+          % (golden_name, J, Jo, e, it))
     assert abs(J - Jo) <= 1e-10 * abs(Jo)
     assert e <= 1e-9
     s.close()

@@ -68,6 +68,11 @@ def test_force_matches_oracle(name):
     Cd_o, Cl_o = Fo.force_coefficients(Fn_o + Ft_o, A_ref, case["u_in"])
     assert abs(Cd - Cd_o) <= 1e-9 * (abs(Cd_o) + abs(Cl_o))
     assert abs(Cl - Cl_o) <= 1e-9 * (abs(Cd_o) + abs(Cl_o))
+    # a rotated lift direction and an explicit reference area (Eq. dlcoeffs)
+    Cd, Cl = s.force_coefficients(A_ref=0.7, gamma=0.3)
+    Cd_o, Cl_o = Fo.force_coefficients(Fn_o + Ft_o, 0.7, case["u_in"], gamma=0.3)
+    assert abs(Cd - Cd_o) <= 1e-9 * (abs(Cd_o) + abs(Cl_o))
+    assert abs(Cl - Cl_o) <= 1e-9 * (abs(Cd_o) + abs(Cl_o))
     # hfdib_ib_force leaves the state a fixed point: the next sweep's residual stays converged
     res = s.sweep()
     assert max(res[:4]) <= 1e-11
