@@ -324,6 +324,7 @@ print(json.dumps({"seconds": time.perf_counter() - t0}))
 # ---------------------------------------------------------------- extra legs
 NACA_NX, NACA_NY, NACA_AOAS = 2048, 1024, 16   # batched multi-lambda workload (16 angles of attack)
 ADJ_DESIGNS = 2                                # random-obstacle designs for the adjoint leg
+C5_DESIGNS = 32                                # random-obstacle designs of the batched-gradient leg (--c5)
 
 
 def _naca_case(aoa):
@@ -379,6 +380,31 @@ def batch_leg(hfdib, torch, cases, dev, steps, warmup):
             "l2": "working set %.0f MB per field set > L2" % (N * 8 / 1e6)}
 
 
+def c5_leg(torch, cases, dev):
+    """32 random-obstacle designs of uneven size (256 x 128 ... 512 x 256,
+    k-epsilon, Re 1000) through the batched autograd path: the forward pass
+    converges all steady states as one batch (mixed precision, the stop test
+    on the device), the backward pass runs each design's frozen-turbulence
+    adjoint of the pressure drop."""
+    import time as _t
+    from paper_2606_06135_gb300.autograd import pressure_drops
+    lams = [torch.tensor(c["lam"], dtype=torch.float64, device=dev, requires_grad=True) for c in cases]
+    torch.cuda.synchronize(dev)
+    t0 = _t.perf_counter()
+    J = pressure_drops(lams, cases, solve_tol=1e-10, max_sweeps=40000, adj_tol=1e-9, adj_max_iter=40000,
+                       precision=1)
+    torch.cuda.synchronize(dev)
+    t1 = _t.perf_counter()
+    J.sum().backward()
+    torch.cuda.synchronize(dev)
+    t2 = _t.perf_counter()
+    N = sum(c["grid"]["nx"] * c["grid"]["ny"] for c in cases)
+    return {"workload": "grf_channel_keps_designs_%d" % len(cases), "designs": len(cases), "cells": N,
+            "solve_tol": 1e-10, "adjoint_tol": 1e-9, "forward_seconds": t1 - t0, "backward_seconds": t2 - t1,
+            "gradients_per_s": len(cases) / (t2 - t0),
+            "grad_norms_finite": bool(all(torch.isfinite(l.grad).all().item() for l in lams))}
+
+
 def adjoint_leg(hfdib, torch, cases, dev):
     """Designs solved together to 1e-10 (FP64), then one frozen-turbulence
     adjoint gradient dJ/dlambda (pressure drop) per design."""
@@ -419,6 +445,10 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     ap.add_argument("--no-c4", action="store_true", help="skip the 3D Ahmed-body leg")
     ap.add_argument("--no-c1", action="store_true", help="skip the 128 x 64 cylinder leg")
+    ap.add_argument("--c5", action="store_true", help="run the 32-design batched-gradient leg (minutes)")
+    ap.add_argument("--only", choices=["c2", "c4"], default=None,
+                    help="profiling aid: run only the mixed timed sweeps of the 1024 x 256 step (c2) or of "
+                         "the 3D Ahmed-like body (c4), print that leg's numbers and stop")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -430,8 +460,8 @@ def main():
 
     # geometry of the extra legs, generated by spawned workers while the
     # GPU legs run (the pool starts before the first CUDA call)
-    pool, fut_naca, fut_grf = None, [], []
-    if rank == 0 and (not args.no_batch or not args.no_adjoint):
+    pool, fut_naca, fut_grf, fut_c5 = None, [], [], []
+    if rank == 0 and not args.only and (not args.no_batch or not args.no_adjoint or args.c5):
         import multiprocessing as mp
         from concurrent.futures import ProcessPoolExecutor
         pool = ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1), mp_context=mp.get_context("spawn"))
@@ -439,6 +469,8 @@ def main():
             fut_naca = [pool.submit(_naca_case, a) for a in range(NACA_AOAS)]
         if not args.no_adjoint:
             fut_grf = [pool.submit(_grf_case, b) for b in range(ADJ_DESIGNS)]
+        if args.c5:
+            fut_c5 = [pool.submit(_grf_case, b) for b in range(C5_DESIGNS)]
 
     import numpy as np
     import torch
@@ -535,6 +567,15 @@ def main():
                     launches=launches, piters=float(piters.mean()), roofline=roof, roofline_alu=roof_alu,
                     classes=classes, cells=cells, max_residual=float(max(res_last[:6])))
 
+    if args.only:
+        cs = None if args.only == "c2" else G.case_ahmed(256, 96, 96)
+        leg = timed_sweeps("mixed", cs=cs, steps=min(args.steps, 10) if cs is not None else None)
+        if rank == 0:
+            print(json.dumps({"only": args.only, "ms_per_sweep": leg["ms"], "value": leg["value"],
+                              "classes": leg["classes"], "pcg_iters_mean": leg["piters"]}))
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
     res = {p: timed_sweeps(p) for p in ("mixed", "fp64")}
     head = res["mixed"]
     out = {"metric": METRIC, "value": head["value"], "unit": "cell-updates/s", "n_gpus": world,
@@ -634,6 +675,8 @@ def main():
         out["batch"] = batch_leg(hfdib, torch, [f.result() for f in fut_naca], dev, args.steps, args.warmup)
     if rank == 0 and fut_grf:
         out["adjoint"] = adjoint_leg(hfdib, torch, [f.result() for f in fut_grf], dev)
+    if rank == 0 and fut_c5:
+        out["c5"] = c5_leg(torch, [f.result() for f in fut_c5], dev)
     if pool is not None:
         pool.shutdown()
     if rank == 0 and not args.no_cpu:

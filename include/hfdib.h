@@ -98,13 +98,18 @@ typedef struct {
     double p_reltol;             /* pressure solve: |r| <= p_reltol |r0| (0.1)    */
     int32_t p_maxiter;           /* pressure solve iteration cap (50)             */
     int32_t precision;           /* 0: FP64 throughout (default).  1: mixed -- FP64
-                                    state, assembly, defects (residuals), CG vectors
-                                    and reductions; the red-black inner sweeps of the
-                                    momentum and turbulence equations and the
-                                    multigrid preconditioner run in FP32 on FP32
-                                    corrections (needs p_persistent = 1, precond = 1);
-                                    the steady state solves the FP64 equations      */
-    int32_t precond;             /* pressure preconditioner: 0 Jacobi, 1 GMG V-cycle (1) */
+                                    state, assembly and defects (residuals); the
+                                    red-black inner sweeps of the momentum and
+                                    turbulence equations and the pressure
+                                    correction solve (CG vectors and product, the
+                                    multigrid V-cycle) run in FP32 on FP32
+                                    corrections, with FP64 CG scalars and FP64 sums
+                                    across warps and blocks; the correction solve
+                                    stops at max(p_reltol, 1e-6) (needs
+                                    p_persistent = 1, precond = 1); the steady state
+                                    solves the FP64 equations                      */
+    int32_t precond;             /* pressure preconditioner: 0 Jacobi (one launch per
+                                    CG step), 1 GMG V-cycle (1)                    */
     int32_t p_check;             /* host-driven solve: read the convergence flag every
                                     p_check CG iterations; 0 = no host reads: the loop
                                     stops on the device (0) */
@@ -144,13 +149,11 @@ typedef struct {
                                     most this many cells run inside one thread block
                                     (in shared memory when they fit), the others
                                     as grid-wide phases (0: the library default)   */
-    int32_t p_cg32;              /* precision = 1 only: 1 runs the pressure correction
-                                    solve's CG product and vectors in FP32 as well
-                                    (dots accumulated in FP64; the start defect
-                                    r0 = b - A p and p itself stay FP64, so the
-                                    steady state still solves the FP64 equations);
-                                    0 keeps them FP64 (default).  Single problems
-                                    only (hfdib_create_batch rejects it)          */
+    int32_t p_cg32;              /* precision = 1 only, kept for compatibility: the
+                                    mixed pressure correction solve always runs its
+                                    CG product and vectors in FP32 now, so 0 and 1
+                                    behave the same.  Single problems only
+                                    (hfdib_create_batch rejects 1)                */
 } hfdib_options;
 
 typedef struct hfdib_ctx* hfdib_handle;
@@ -245,7 +248,11 @@ int hfdib_simple_sweep(hfdib_handle h, int n_sweeps, double* residuals);
  * level 0, 5 a restriction, 6 a black half sweep of a coarse level, 7 the
  * one-block coarse tail, 8 a prolongation with its black half sweep, 9 a red
  * half sweep going up, 10 the final red half sweep of level 0 (r.z), 11 the
- * CG product (d, q, d.q), 12 the CG update (p, r, r.r), 13 end.  A
+ * CG product (d, q, d.q), 12 the CG update (p, r, r.r), 13 end; and, within
+ * block 0 without a barrier, 14 its share of the initial residual done, 15
+ * its tail table set up, 16 a tail level built, 17 the tail input copied
+ * in, 18 the tail computed, and inside the tail 19 a level down (block
+ * wide), 20 the coarsest levels, 21 a level up (block wide).  A
  * measurement aid for the pressure solve (it allocates a small device
  * buffer for the call).
  *   out      : HOST, 2 * capacity int64: tag, ns, tag, ns, ...

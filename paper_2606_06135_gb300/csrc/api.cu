@@ -1,6 +1,7 @@
 // api.cu -- C ABI of the HFDIB SIMPLE solver: handle set-up, the sweep
 // schedule (Fig. simplehfdibrans), steady solve, field access, checkpoints.
 #include <math.h>
+#include <stddef.h>
 #include <cmath>
 #include <stdio.h>
 #include <string.h>
@@ -13,6 +14,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "batch.cuh"
 
 using namespace hf;
 
@@ -107,7 +109,7 @@ struct Ctx {
     MgLevels mg;
     MgLevels32 mg32;
     int tail_from = 1;
-    long long tail_cells = 0;   // persistent pressure solve: largest level of block 0's tail
+    long long tail_cells = 0;   // persistent pressure solve: largest level of the one-block tail
     int coarse_sweeps = 20;
     int use_graph = 0;
     int parity = 0;              // which of the two sweep graphs matches the p / pr buffers
@@ -117,6 +119,10 @@ struct Ctx {
     Prof prof;
     int pblocks = 0;             // persistent pressure kernel grid (0: not used)
     double* ppart = nullptr;     // its block partials
+    void* pdesc[2] = {nullptr, nullptr};  // its problem descriptor, per p / pr parity
+    double* pbuf0 = nullptr;     // the buffer that is F.p at parity 0
+    double* pbuf1 = nullptr;     // the buffer that is F.pr at parity 0
+    size_t psmem = 0;            // its dynamic shared memory (the tail levels)
     unsigned int* pbar = nullptr;
     int* perr = nullptr;
     const int* err_src = nullptr;  // error word of the pressure kernel this handle's sweeps run
@@ -296,8 +302,9 @@ void enqueue_part_a(Ctx* h, long long* L, bool with_pressure = true) {
     *L += 4;
     for (int n = 0; n < h->opt.n_u; ++n) {
         if (F.mixed) {
-            PROF(h, HFDIB_K_MOM_SMOOTH, launch_mom_smooth32(g, P, F, 0, n == 0, s));
-            PROF(h, HFDIB_K_MOM_SMOOTH, launch_mom_smooth32(g, P, F, 1, 0, s));
+            const int last = n == h->opt.n_u - 1;
+            PROF(h, HFDIB_K_MOM_SMOOTH, launch_mom_smooth32(g, P, F, 0, n == 0, last, s));
+            PROF(h, HFDIB_K_MOM_SMOOTH, launch_mom_smooth32(g, P, F, 1, 0, last, s));
         } else {
             PROF(h, HFDIB_K_MOM_SMOOTH, launch_mom_smooth(g, P, F, 0, s));
             PROF(h, HFDIB_K_MOM_SMOOTH, launch_mom_smooth(g, P, F, 1, s));
@@ -316,20 +323,11 @@ void enqueue_part_a(Ctx* h, long long* L, bool with_pressure = true) {
         // the whole solve, operator hierarchy included, in one cooperative launch
         cudaMemsetAsync(h->pbar, 0, sizeof(unsigned int), s);
         cudaMemsetAsync(h->perr, 0, sizeof(int), s);
-        if (F.mixed) {
-            PROF(h, HFDIB_K_PCG, launch_pressure_persistent32(g, F, M, h->mg32, h->coarse_sweeps,
-                                                               h->opt.p_reltol, h->opt.p_maxiter, h->pblocks,
-                                                               h->ppart, h->pbar, h->perr, h->spin_limit,
-                                                               h->tail_cells, h->opt.p_cg32, h->trace,
-                                                               h->trace_cap, s));
-            (*L)++;
-        } else {
-            PROF(h, HFDIB_K_PCG, launch_pressure_persistent(g, F, M, jac, h->coarse_sweeps, h->opt.p_reltol,
-                                                             h->opt.p_maxiter, h->pblocks, h->ppart, h->pbar,
-                                                             h->perr, h->spin_limit, h->tail_cells, h->trace,
-                                                             h->trace_cap, s));
-            (*L)++;
-        }
+        PROF(h, HFDIB_K_PCG, launch_pressure_batched(F.mixed, g.dims, h->pdesc[h->parity], 1, M.nl, h->coarse_sweeps,
+                                                     h->opt.p_reltol, h->opt.p_maxiter, h->pblocks, PT_THREADS,
+                                                     h->psmem, h->pbar, h->perr, h->spin_limit, h->trace,
+                                                     h->trace_cap, 0, s));
+        (*L)++;
         return;
     }
     PROF(h, HFDIB_K_P_COEF, launch_p_coef(g, M, F.rAU, h->tail_from, s));
@@ -513,138 +511,263 @@ int run_sweep(Ctx* h) {
 }
 
 // ---------------------------------------------------------------- batches
-// A batch holds B problems (each a full handle on its own worker stream) and
-// advances them together: parts A of all problems run concurrently on the
-// worker streams, then ONE persistent cooperative launch solves all their
-// pressure equations, then parts B run concurrently.  The whole batched sweep
-// is captured as one CUDA graph (two, alternating the p / pr buffers).
+// A batch holds B problems (each a full handle on the batch's stream) and
+// advances them together, one launch per phase for all of them: every phase
+// of the sweep (a1-a6, a8-a12) is a batched launch in which problem b owns a
+// range of blocks (batch.cuh), and the pressure equations of all problems are
+// solved by ONE persistent cooperative launch (pcgb.cu).  The problems'
+// launch arguments live in two device tables (sweep phases, pressure solve);
+// the p / pr buffers of a problem are swapped in both tables on the device at
+// the end of each sweep it runs, so one captured graph serves every sweep.  A
+// batch solve runs that sweep inside a device-controlled while loop: each
+// problem's sweep end applies the stop test to its largest scaled residual,
+// a problem that has stopped skips every later phase, and the loop ends when
+// all have stopped or after max_iter sweeps.
 struct BatchCtx {
     int B = 0;
     int mixed = 0;
+    int dims = 2;
     std::vector<Ctx*> d;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    std::vector<cudaStream_t> ws;
-    std::vector<cudaEvent_t> ej;
-    cudaEvent_t ef = nullptr;
-    void* desc[2] = {nullptr, nullptr};   // device descriptor arrays (parity 0 / 1)
-    std::vector<unsigned char> hdesc[2];
     DevAlloc al;                          // the allocator of every block in `allocs`
     std::vector<DevBlock> allocs;
     std::vector<double*> parts;
+    void* desc = nullptr;                 // device: pressure descriptors [B]
+    SweepProblem* probs = nullptr;        // device: sweep-phase problem table [B]
+    int* start = nullptr;                 // device: block offsets [BK_KINDS][B + 1]
+    int tot[BK_KINDS] = {0, 0, 0, 0, 0};  // blocks of each launch kind
     unsigned int* bar = nullptr;
     int* err = nullptr;
+    unsigned int* loop = nullptr;         // device: [0] sweeps of the running solve, [1] its max_iter
     int nblk = 0, threads = 1024, coarse_sweeps = 4, maxlev = 1;
     long long spin_limit = BARRIER_POLLS;
-    long long tail_cells = 1024;
+    long long tail_cells = PT_DEFAULT_TAIL_CELLS;
     size_t smem = 0;
-    int parity = 0;
     int use_graph = 1;
-    cudaGraph_t graph[2] = {nullptr, nullptr};
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaGraph_t graph = nullptr;          // one sweep
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t sgraph = nullptr;         // the solve loop
+    cudaGraphExec_t sgexec = nullptr;
     long long sweeps = 0;
     double* pinned = nullptr;
+    std::vector<SweepProblem> hprobs;
+    bool described = false;               // the device tables hold the problems
     std::string key;
 };
 
-constexpr size_t BATCH_SMEM_BUDGET = 160 * 1024;
+constexpr size_t BATCH_SMEM_BUDGET = PT_SMEM_BUDGET;
 
 void batch_drop_graphs(BatchCtx* b) {
-    for (int q = 0; q < 2; ++q) {
-        if (b->gexec[q]) cudaGraphExecDestroy(b->gexec[q]);
-        if (b->graph[q]) cudaGraphDestroy(b->graph[q]);
-        b->gexec[q] = nullptr;
-        b->graph[q] = nullptr;
-    }
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->sgexec) cudaGraphExecDestroy(b->sgexec);
+    if (b->sgraph) cudaGraphDestroy(b->sgraph);
+    b->gexec = nullptr;
+    b->graph = nullptr;
+    b->sgexec = nullptr;
+    b->sgraph = nullptr;
 }
 
-// (re)build both descriptor arrays for the current launch parameters
-int batch_describe(BatchCtx* b) {
-    size_t dsz = pcgb_desc_size(b->mixed);
-    size_t smem = 0;
-    for (int q = 0; q < 2; ++q) {
-        b->hdesc[q].assign(dsz * b->B, 0);
-        for (int i = 0; i < b->B; ++i) {
-            Ctx* h = b->d[i];
-            Fields F = h->F;
-            if (q == 1) std::swap(F.p, F.pr);   // the other parity of the p / pr buffers
-            void* dst = b->hdesc[q].data() + dsz * i;
-            size_t by = b->mixed ? pcgb_describe32(dst, h->g, F, h->mg, h->mg32, b->parts[i], b->tail_cells,
-                                                   BATCH_SMEM_BUDGET)
-                                 : pcgb_describe64(dst, h->g, F, h->mg, b->parts[i], b->tail_cells, BATCH_SMEM_BUDGET);
-            if (by > smem) smem = by;
-        }
-        CK(cudaMemcpyAsync(b->desc[q], b->hdesc[q].data(), dsz * b->B, cudaMemcpyHostToDevice, b->stream));
-    }
+BatchTab batch_tab(const BatchCtx* b, int skip) { return BatchTab{b->probs, b->start, b->B, skip}; }
+
+// The host handles follow the device tables: their p / pr pointers, parity
+// and sweep count (after every batch call, before any re-description).
+int batch_sync_host(BatchCtx* b) {
+    if (!b->probs || !b->described) return HFDIB_OK;
+    CK(cudaMemcpyAsync(b->hprobs.data(), b->probs, sizeof(SweepProblem) * b->B, cudaMemcpyDeviceToHost, b->stream));
+    for (int i = 0; i < b->B; ++i)
+        CK(cudaMemcpyAsync(b->pinned + i, b->d[i]->F.scal + SC_NSWEEP, sizeof(double), cudaMemcpyDeviceToHost,
+                           b->stream));
     CK(cudaStreamSynchronize(b->stream));
+    for (int i = 0; i < b->B; ++i) {
+        Ctx* h = b->d[i];
+        const double* p = b->hprobs[i].F.p;
+        const double* pr = b->hprobs[i].F.pr;
+        // the two pressure buffers of this problem, in either order
+        if (!((p == h->pbuf0 && pr == h->pbuf1) || (p == h->pbuf1 && pr == h->pbuf0))) return HFDIB_ERR_CUDA;
+        h->F.p = b->hprobs[i].F.p;
+        h->F.pr = b->hprobs[i].F.pr;
+        h->parity = h->F.p == h->pbuf0 ? 0 : 1;
+        h->sweeps = (long long)b->pinned[i];
+    }
+    return HFDIB_OK;
+}
+
+// (re)build the problem table, the block offsets and the pressure
+// descriptors for the current launch parameters and the current p / pr
+int batch_describe(BatchCtx* b) {
+    int rc = batch_sync_host(b);
+    if (rc) return rc;
+    batch_drop_graphs(b);
+    const int B = b->B;
+    size_t dsz = pcgb_desc_size(b->mixed);
+    size_t foff = pcgb_fields_offset(b->mixed);
+    std::vector<unsigned char> hdesc(dsz * B, 0);
+    std::vector<int> st((size_t)BK_KINDS * (B + 1), 0);
+    size_t smem = 0;
+    for (int i = 0; i < B; ++i) {
+        Ctx* h = b->d[i];
+        void* dst = hdesc.data() + dsz * i;
+        size_t by = b->mixed ? pcgb_describe32(dst, h->g, h->F, h->mg, h->mg32, b->parts[i], b->tail_cells,
+                                               BATCH_SMEM_BUDGET)
+                             : pcgb_describe64(dst, h->g, h->F, h->mg, b->parts[i], b->tail_cells, BATCH_SMEM_BUDGET);
+        if (by > smem) smem = by;
+        SweepProblem& sp = b->hprobs[i];
+        memset((void*)&sp, 0, sizeof(sp));
+        sp.g = h->g;
+        sp.P = h->P;
+        sp.F = h->F;
+        sp.bl = h->bl;
+        sp.L0 = h->mg.lv[0];
+        sp.freeze = h->opt.freeze_switch;
+        bool turb_b = h->model != HFDIB_LAMINAR && !h->opt.frozen_turbulence;
+        sp.model_end = turb_b ? h->model : HFDIB_LAMINAR;
+        sp.err = b->err;
+        sp.res_out = h->res_dev;
+        sp.hist = h->hist;
+        sp.nhist = HIST;
+        sp.done = h->F.scal + SC_DONE;
+        char* pe = (char*)&b->probs[i];
+        char* de = (char*)b->desc + dsz * i + foff;
+        sp.swap_p[0] = (double**)(pe + offsetof(SweepProblem, F) + offsetof(Fields, p));
+        sp.swap_pr[0] = (double**)(pe + offsetof(SweepProblem, F) + offsetof(Fields, pr));
+        sp.swap_p[1] = (double**)(de + offsetof(Fields, p));
+        sp.swap_pr[1] = (double**)(de + offsetof(Fields, pr));
+        const long long n[BK_KINDS] = {nblocks(h->g.N), rblocks(h->g.N), nblocks(npairs(h->g)),
+                                       h->bl.nbc > 0 ? nblocks(h->bl.nbc) : 0, 1};
+        for (int k = 0; k < BK_KINDS; ++k) st[(size_t)k * (B + 1) + i + 1] = st[(size_t)k * (B + 1) + i] + (int)n[k];
+    }
+    for (int k = 0; k < BK_KINDS; ++k) b->tot[k] = st[(size_t)k * (B + 1) + B];
+    CK(cudaMemcpyAsync(b->desc, hdesc.data(), dsz * B, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->probs, b->hprobs.data(), sizeof(SweepProblem) * B, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->start, st.data(), st.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    b->described = true;
     int bps = 0;
-    if (pcgb_fits(b->mixed, b->threads, smem, &bps) != 0 || bps < 1) return HFDIB_ERR_INVALID_ARG;
+    if (pcgb_fits(b->mixed, b->dims, b->threads, smem, &bps) != 0 || bps < 1) return HFDIB_ERR_INVALID_ARG;
     b->smem = smem;
     return HFDIB_OK;
 }
 
-void batch_enqueue(BatchCtx* b) {
+// one sweep of every problem (skip: problems whose stop flag is set sit out)
+void batch_enqueue(BatchCtx* b, int skip) {
     cudaStream_t s = b->stream;
-    long long L = 0;
-    cudaEventRecord(b->ef, s);
-    for (int i = 0; i < b->B; ++i) {
-        cudaStreamWaitEvent(b->ws[i], b->ef, 0);
-        enqueue_part_a(b->d[i], &L, false);
-        cudaEventRecord(b->ej[i], b->ws[i]);
-        cudaStreamWaitEvent(s, b->ej[i], 0);
-    }
-    cudaMemsetAsync(b->bar, 0, sizeof(unsigned int), s);
-    cudaMemsetAsync(b->err, 0, sizeof(int), s);
+    const BatchTab T = batch_tab(b, skip);
+    const int* tot = b->tot;
     const Ctx* h0 = b->d[0];
-    launch_pressure_batched(b->mixed, b->desc[b->parity], b->B, b->maxlev, b->coarse_sweeps, h0->opt.p_reltol,
-                            h0->opt.p_maxiter, b->nblk, b->threads, b->smem, b->bar, b->err, b->spin_limit, s);
-    cudaEventRecord(b->ef, s);
-    for (int i = 0; i < b->B; ++i) {
-        cudaStreamWaitEvent(b->ws[i], b->ef, 0);
-        enqueue_part_b(b->d[i], &L);
-        cudaEventRecord(b->ej[i], b->ws[i]);
-        cudaStreamWaitEvent(s, b->ej[i], 0);
+    const bool turb = h0->model != HFDIB_LAMINAR;
+    const bool turb_b = turb && !h0->opt.frozen_turbulence;
+    const bool mixed = b->mixed != 0;
+    // a1, a2, the residual means
+    if (turb) launchb_max_not_ic(T, tot, s);
+    launchb_imposed(T, tot, s);
+    launchb_means(T, tot, s);
+    // a3 assembly, a4/a5 predictor with the imposed rows
+    launchb_grad_u(T, tot, s);
+    if (h0->g.conv == 3) launchb_conv_limit(T, tot, s);
+    launchb_mom_asm(T, tot, s);
+    for (int n = 0; n < h0->opt.n_u; ++n) {
+        if (mixed) {
+            const int last = n == h0->opt.n_u - 1;
+            launchb_mom_smooth32(T, tot, 0, n == 0, last, s);
+            launchb_mom_smooth32(T, tot, 1, 0, last, s);
+        } else {
+            launchb_mom_smooth(T, tot, 0, s);
+            launchb_mom_smooth(T, tot, 1, s);
+        }
     }
-}
-
-void batch_advance(BatchCtx* b) {
-    for (Ctx* h : b->d) {
-        std::swap(h->F.p, h->F.pr);
-        h->parity ^= 1;
-        h->sweeps++;
+    // a6
+    launchb_hbya(T, tot, s);
+    launchb_phiH(T, tot, s);
+    // a7: every pressure equation in one persistent launch
+    launch_pressure_reset(b->bar, b->err, s);
+    launch_pressure_batched(b->mixed, b->dims, b->desc, b->B, b->maxlev, b->coarse_sweeps, h0->opt.p_reltol,
+                            h0->opt.p_maxiter, b->nblk, b->threads, b->smem, b->bar, b->err, b->spin_limit, nullptr,
+                            0, skip, s);
+    // a8
+    launchb_update(T, tot, s);
+    if (turb_b) {
+        // a9 production, P_ib; a10 eps / omega; a11 k; a12 nu_t
+        launchb_grad_u(T, tot, s);
+        launchb_turb_prep(T, tot, s);
+        launchb_bc_prod(T, tot, s);
+        launchb_scal_asm(T, tot, 0, s);
+        for (int n = 0; n < h0->opt.n_turb; ++n) {
+            if (mixed) {
+                launchb_scal_smooth32(T, tot, 0, 0, n == 0, s);
+                launchb_scal_smooth32(T, tot, 0, 1, 0, s);
+            } else {
+                launchb_scal_smooth(T, tot, 0, 0, s);
+                launchb_scal_smooth(T, tot, 0, 1, s);
+            }
+        }
+        launchb_k_prep(T, tot, s);
+        launchb_scal_asm(T, tot, 1, s);
+        for (int n = 0; n < h0->opt.n_turb; ++n) {
+            if (mixed) {
+                launchb_scal_smooth32(T, tot, 1, 0, n == 0, s);
+                launchb_scal_smooth32(T, tot, 1, 1, 0, s);
+            } else {
+                launchb_scal_smooth(T, tot, 1, 0, s);
+                launchb_scal_smooth(T, tot, 1, 1, s);
+            }
+        }
+        launchb_turb_final(T, tot, s);
     }
-    b->parity ^= 1;
-    b->sweeps++;
+    // residual record, stop test (solves), p / pr swap
+    launchb_sweep_end(T, tot, s);
 }
 
 int batch_sweep_once(BatchCtx* b) {
-    if (b->use_graph) {
-        if (!b->gexec[b->parity]) {
-            cudaGraph_t g;
-            bool ok = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-            if (ok) {
-                batch_enqueue(b);
-                ok = cudaStreamEndCapture(b->stream, &g) == cudaSuccess;
-            }
-            cudaGraphExec_t ex = nullptr;
-            if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
-            if (!ok) {
-                cudaGetLastError();
-                b->use_graph = 0;
-            } else {
-                b->graph[b->parity] = g;
-                b->gexec[b->parity] = ex;
-            }
+    if (b->use_graph && !b->gexec) {
+        cudaGraph_t g = nullptr;
+        bool ok = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            batch_enqueue(b, 0);
+            ok = cudaStreamEndCapture(b->stream, &g) == cudaSuccess;
         }
-        if (b->use_graph) {
-            CK(cudaGraphLaunch(b->gexec[b->parity], b->stream));
-            batch_advance(b);
-            return HFDIB_OK;
+        cudaGraphExec_t ex = nullptr;
+        if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+        if (!ok) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            b->use_graph = 0;
+        } else {
+            b->graph = g;
+            b->gexec = ex;
         }
     }
-    batch_enqueue(b);
+    if (b->use_graph) CK(cudaGraphLaunch(b->gexec, b->stream));
+    else batch_enqueue(b, 0);
     CK(cudaGetLastError());
-    batch_advance(b);
+    b->sweeps++;
+    return HFDIB_OK;
+}
+
+// the solve loop as one graph: a device-controlled while node around one
+// sweep (stop flags honoured) and the loop's end-of-sweep test
+int batch_build_solve_graph(BatchCtx* b) {
+    cudaStream_t s = b->stream;
+    cudaGraph_t graph;
+    CK(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle hc;
+    CK(cudaGraphConditionalHandleCreate(&hc, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = hc;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    CK(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    batch_enqueue(b, 1);
+    launchb_next(batch_tab(b, 1), b->loop, b->loop + 1, hc, s);
+    CK(cudaStreamEndCapture(s, &body));
+    cudaGraphExec_t exec;
+    CK(cudaGraphInstantiate(&exec, graph, 0));
+    b->sgraph = graph;
+    b->sgexec = exec;
     return HFDIB_OK;
 }
 
@@ -679,9 +802,6 @@ void batch_free(BatchCtx* b) {
     for (Ctx* h : b->d)
         if (h) hfdib_destroy((hfdib_handle)h);
     for (const DevBlock& blk : b->allocs) dev_free(b->al, b->stream, blk);
-    for (cudaEvent_t e : b->ej) cudaEventDestroy(e);
-    if (b->ef) cudaEventDestroy(b->ef);
-    for (cudaStream_t w : b->ws) cudaStreamDestroy(w);
     if (b->pinned) cudaFreeHost(b->pinned);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
@@ -1177,6 +1297,8 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
     if (o.convection < 0 || o.convection > 3) return HFDIB_ERR_INVALID_ARG;
     // the mixed path runs its FP32 V-cycle inside the persistent CG kernel
     if (o.precision == 1 && (o.p_persistent == 0 || o.precond != 1)) return HFDIB_ERR_INVALID_ARG;
+    // the persistent solve is multigrid-preconditioned; Jacobi-PCG runs one launch per step
+    if (o.precond == 0) o.p_persistent = 0;
     if (o.p_maxiter > 100000 || o.freeze_switch < 0) return HFDIB_ERR_INVALID_ARG;
     if (o.frozen_turbulence < 0 || o.frozen_turbulence > 1) return HFDIB_ERR_INVALID_ARG;
 
@@ -1289,10 +1411,13 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
     }
     F.mixed = o.precision == 1 ? 1 : 0;
     F.lam = h->lam;
+    h->pbuf0 = F.p;
+    h->pbuf1 = F.pr;
+    if (!rc && !F.mixed) A(F.r_alt, N);
     if (!rc && F.mixed) {
         for (int d = 0; d < 3; ++d) { A(F.phi32[d], g.nface[d]); A(F.r32[d], N); A(F.d32[d], N); }
         A(F.nut32, N); A(F.gam32, N); A(F.gamk32, N); A(F.diag32, N); A(F.z32, N);
-        if (o.p_cg32) { A(F.pd32[0], N); A(F.pd32[1], N); A(F.pq32, N); }
+        A(F.pd32[0], N); A(F.pd32[1], N); A(F.pq32, N); A(F.px32, N); A(F.pr32, N);
         // FP32 preconditioner hierarchy, same shapes as the FP64 one
         MgLevels32& M32 = h->mg32;
         memset(&M32, 0, sizeof(M32));
@@ -1310,13 +1435,31 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
         }
     }
     if (!rc && o.p_persistent) {
-        int nbk = 0;
-        if (pcgp_blocks(&nbk) != 0 || nbk <= 0) rc = HFDIB_ERR_CUDA;
-        h->pblocks = nbk;
+        int dev = 0, nbk = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nbk, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nbk <= 0)
+            rc = HFDIB_ERR_CUDA;
+        h->pblocks = nbk;   // one block per SM: fewer arrivals per grid barrier
         A(h->ppart, 8 * (long long)nbk + 8);
         A(h->pbar, 2);
         A(h->perr, 1);
         h->err_src = h->perr;
+        size_t dsz = pcgb_desc_size(F.mixed);
+        for (int q = 0; q < 2 && !rc; ++q) rc = dalloc(h, &h->pdesc[q], dsz);
+        // the problem's descriptor of the persistent solve, one per parity of
+        // the p / pr buffers (a batch of one)
+        std::vector<unsigned char> hd(dsz);
+        for (int q = 0; q < 2 && !rc; ++q) {
+            Fields Fq = F;
+            if (q == 1) std::swap(Fq.p, Fq.pr);
+            size_t by = F.mixed ? pcgb_describe32(hd.data(), g, Fq, h->mg, h->mg32, h->ppart, h->tail_cells,
+                                                  PT_SMEM_BUDGET)
+                                : pcgb_describe64(hd.data(), g, Fq, h->mg, h->ppart, h->tail_cells, PT_SMEM_BUDGET);
+            h->psmem = by;
+            if (cudaMemcpy(h->pdesc[q], hd.data(), dsz, cudaMemcpyHostToDevice) != cudaSuccess) rc = HFDIB_ERR_CUDA;
+        }
+        int bps = 0;
+        if (!rc && (pcgb_fits(F.mixed, g.dims, PT_THREADS, h->psmem, &bps) != 0 || bps < 1)) rc = HFDIB_ERR_CUDA;
     }
 #undef A
     if (!rc && cudaMallocHost((void**)&h->pinned, 64 * sizeof(double)) != cudaSuccess) rc = HFDIB_ERR_OOM;
@@ -1772,7 +1915,7 @@ int hfdib_adjoint_grad(hfdib_handle hh, int objective, double tol, int max_iter,
 int hfdib_pressure_trace(hfdib_handle hh, int64_t* out, int capacity, int* n_out) {
     Ctx* h = (Ctx*)hh;
     if (!h || !out || capacity < 1 || capacity > (1 << 20)) return HFDIB_ERR_INVALID_ARG;
-    if (h->pblocks <= 0) return HFDIB_ERR_INVALID_ARG;    // needs the persistent pressure kernel
+    if (h->pblocks <= 0 || !h->pdesc[0]) return HFDIB_ERR_INVALID_ARG;    // needs the persistent pressure kernel
     long long* dev = nullptr;
     size_t bytes = (1 + 2 * (size_t)capacity) * sizeof(long long);
     int rc = dev_alloc(h->al, h->stream, bytes, (void**)&dev);
@@ -1838,6 +1981,8 @@ int hfdib_create_batch(int B, const hfdib_grid* grids, const double* const* lamb
     if (o.precond != 1) return HFDIB_ERR_INVALID_ARG;   // batched solve: multigrid preconditioner
     if (o.p_cg32) return HFDIB_ERR_INVALID_ARG;         // the FP32 correction solve is single-problem
     o.p_persistent = 1;
+    for (int i = 1; i < B; ++i)
+        if ((grids[i].nz == 1) != (grids[0].nz == 1)) return HFDIB_ERR_INVALID_ARG;   // all 2D or all 3D
     BatchCtx* b = new (std::nothrow) BatchCtx();
     if (!b) return HFDIB_ERR_OOM;
     b->al = current_alloc();
@@ -1849,55 +1994,62 @@ int hfdib_create_batch(int B, const hfdib_grid* grids, const double* const* lamb
         b->own_stream = true;
     }
     int rc = HFDIB_OK;
-    if (cudaEventCreateWithFlags(&b->ef, cudaEventDisableTiming) != cudaSuccess) rc = HFDIB_ERR_CUDA;
+    // every problem is a handle on the batch's stream
     for (int i = 0; i < B && !rc; ++i) {
-        cudaStream_t w;
-        cudaEvent_t e;
-        if (cudaStreamCreateWithFlags(&w, cudaStreamNonBlocking) != cudaSuccess) { rc = HFDIB_ERR_CUDA; break; }
-        b->ws.push_back(w);
-        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) { rc = HFDIB_ERR_CUDA; break; }
-        b->ej.push_back(e);
         hfdib_handle h = nullptr;
-        rc = hfdib_create(&grids[i], lambdas[i], ywalls ? ywalls[i] : nullptr, model, Re[i], &bcs[i], &o, w, &h);
+        rc = hfdib_create(&grids[i], lambdas[i], ywalls ? ywalls[i] : nullptr, model, Re[i], &bcs[i], &o, b->stream,
+                          &h);
         if (rc) break;
         b->d.push_back((Ctx*)h);
     }
+    if (!rc) b->dims = b->d[0]->g.dims;
     int dev = 0, sms = 0;
     if (!rc && (cudaGetDevice(&dev) != cudaSuccess ||
                 cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess))
         rc = HFDIB_ERR_CUDA;
     b->nblk = sms;
-    if (!rc) {
-        void *pb = nullptr, *pe = nullptr;
-        rc = dev_alloc(b->al, b->stream, 256, &pb);
-        if (!rc) { b->allocs.push_back({pb, 256}); rc = dev_alloc(b->al, b->stream, 256, &pe); }
+    if (!rc && B > sms) rc = HFDIB_ERR_TOO_LARGE;   // problem b's tail runs on block b
+    auto balloc = [&](void** p, size_t by) {
+        if (rc) return;
+        rc = dev_alloc(b->al, b->stream, by, p);
+        if (!rc) b->allocs.push_back({*p, by});
+    };
+    {
+        void *pb = nullptr, *pe = nullptr, *pl = nullptr;
+        balloc(&pb, 256);
+        balloc(&pe, 256);
+        balloc(&pl, 256);
         if (!rc) {
-            b->allocs.push_back({pe, 256});
             b->bar = (unsigned int*)pb;
             b->err = (int*)pe;
+            b->loop = (unsigned int*)pl;
             cudaMemsetAsync(b->bar, 0, 256, b->stream);
             cudaMemsetAsync(b->err, 0, 256, b->stream);
+            cudaMemsetAsync(b->loop, 0, 256, b->stream);
             for (Ctx* h : b->d) h->err_src = b->err;
         }
     }
     for (int i = 0; i < B && !rc; ++i) {
         void* p = nullptr;
-        size_t by = sizeof(double) * 8 * (size_t)sms;
-        rc = dev_alloc(b->al, b->stream, by, &p);
+        balloc(&p, sizeof(double) * 8 * (size_t)sms);
         if (rc) break;
-        b->allocs.push_back({p, by});
         b->parts.push_back((double*)p);
         if (b->d[i]->mg.nl > b->maxlev) b->maxlev = b->d[i]->mg.nl;
     }
-    size_t dsz = pcgb_desc_size(b->mixed);
-    for (int q = 0; q < 2 && !rc; ++q) {
-        rc = dev_alloc(b->al, b->stream, dsz * B, &b->desc[q]);
-        if (rc) break;
-        b->allocs.push_back({b->desc[q], dsz * B});
+    balloc(&b->desc, pcgb_desc_size(b->mixed) * B);
+    {
+        void* p = nullptr;
+        balloc(&p, sizeof(SweepProblem) * B);
+        b->probs = (SweepProblem*)p;
+        void* q = nullptr;
+        balloc(&q, sizeof(int) * BK_KINDS * (B + 1));
+        b->start = (int*)q;
     }
+    b->hprobs.resize(B);
     if (!rc && cudaMallocHost((void**)&b->pinned, sizeof(double) * (HFDIB_NRES + 1) * B) != cudaSuccess)
         rc = HFDIB_ERR_OOM;
     b->coarse_sweeps = o.mg_coarse_sweeps > 0 ? o.mg_coarse_sweeps : 4;
+    b->tail_cells = o.mg_tail_cells > 0 ? o.mg_tail_cells : PT_DEFAULT_TAIL_CELLS;   // as a single problem
     b->use_graph = o.graph != 0;
     // shape key of the autotuner cache
     if (!rc) {
@@ -1926,6 +2078,8 @@ int hfdib_batch_sweep(hfdib_batch bb, int n_sweeps, double* residuals) {
         int rc = batch_sweep_once(b);
         if (rc) return rc;
     }
+    int rs = batch_sync_host(b);
+    if (rs) return rs;
     if (residuals) {
         int rc = batch_read_residuals(b, residuals);
         if (rc) return rc;
@@ -1940,33 +2094,83 @@ int hfdib_batch_solve_steady(hfdib_batch bb, double tol, int max_iter, int check
     BatchCtx* b = (BatchCtx*)bb;
     if (!b || max_iter < 0 || !(tol >= 0)) return HFDIB_ERR_INVALID_ARG;
     if (check_every <= 0) check_every = 10;
-    std::vector<double> res((size_t)HFDIB_NRES * b->B, 0.0);
-    std::vector<int> conv_at(b->B, -1);
-    int it = 0, status = HFDIB_ERR_NOT_CONVERGED;
-    while (it < max_iter) {
-        int rc = batch_sweep_once(b);
-        if (rc) return rc;
-        ++it;
-        if (it % check_every == 0 || it == max_iter) {
-            rc = batch_read_residuals(b, res.data());
-            if (rc) return rc;
-            bool all = true, bad = false;
-            for (int i = 0; i < b->B; ++i) {
-                double mx = 0.0;
-                for (int q = 0; q <= HFDIB_RES_K; ++q) {
-                    double v = res[(size_t)i * HFDIB_NRES + q];
-                    if (!isfinite(v)) bad = true;
-                    mx = fmax(mx, v);
-                }
-                if (mx <= tol) { if (conv_at[i] < 0) conv_at[i] = it; }
-                else all = false;
-            }
-            if (bad) { status = HFDIB_ERR_DIVERGED; break; }
-            if (all) { status = HFDIB_OK; break; }
-        }
+    const int B = b->B;
+    std::vector<double> res((size_t)HFDIB_NRES * B, 0.0);
+    std::vector<long long> start_sweeps(B);
+    for (int i = 0; i < B; ++i) start_sweeps[i] = b->d[i]->sweeps;
+    // arm each problem's stop test, zero the loop counter
+    {
+        double arm[4] = {tol, 1.0, 0.0, 0.0};   // SC_STOP_TOL, SC_STOP_ON, SC_DONE, SC_DONE_AT
+        for (Ctx* h : b->d) CK(cudaMemcpyAsync(h->F.scal + SC_STOP_TOL, arm, sizeof(arm), cudaMemcpyHostToDevice,
+                                               b->stream));
+        unsigned int lp[2] = {0u, (unsigned int)max_iter};
+        CK(cudaMemcpyAsync(b->loop, lp, sizeof(lp), cudaMemcpyHostToDevice, b->stream));
+        CK(cudaStreamSynchronize(b->stream));
     }
+    long long ran = 0;
+    if (max_iter > 0) {
+        if (b->use_graph && !b->sgexec) {
+            if (batch_build_solve_graph(b) != HFDIB_OK) {
+                cudaStreamCaptureStatus st;
+                if (cudaStreamIsCapturing(b->stream, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+                    cudaGraph_t g = nullptr;
+                    cudaStreamEndCapture(b->stream, &g);
+                    if (g) cudaGraphDestroy(g);
+                }
+                cudaGetLastError();
+                b->use_graph = 0;
+            }
+        }
+        if (b->use_graph) {
+            // the whole solve: one graph launch, the loop and its stop test on the device
+            CK(cudaGraphLaunch(b->sgexec, b->stream));
+            unsigned int lp[2];
+            CK(cudaMemcpyAsync(lp, b->loop, sizeof(lp), cudaMemcpyDeviceToHost, b->stream));
+            CK(cudaStreamSynchronize(b->stream));
+            ran = lp[0];
+        } else {
+            // host-driven fallback: the same sweeps, the stop flags read every check_every sweeps
+            std::vector<double> done(B);
+            while (ran < max_iter) {
+                batch_enqueue(b, 1);
+                CK(cudaGetLastError());
+                ++ran;
+                if (ran % check_every == 0 || ran == max_iter) {
+                    for (int i = 0; i < B; ++i)
+                        CK(cudaMemcpyAsync(b->pinned + i, b->d[i]->F.scal + SC_DONE, sizeof(double),
+                                           cudaMemcpyDeviceToHost, b->stream));
+                    CK(cudaStreamSynchronize(b->stream));
+                    bool all = true;
+                    for (int i = 0; i < B; ++i) all = all && b->pinned[i] != 0.0;
+                    if (all) break;
+                }
+            }
+        }
+        b->sweeps += ran;
+    }
+    // disarm, read back the stop flags, the sweep counts and the residuals
+    std::vector<double> flags(2 * (size_t)B);
+    for (int i = 0; i < B; ++i) {
+        CK(cudaMemcpyAsync(b->pinned + 2 * i, b->d[i]->F.scal + SC_DONE, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                           b->stream));
+        CK(cudaMemsetAsync(b->d[i]->F.scal + SC_STOP_ON, 0, sizeof(double), b->stream));
+    }
+    CK(cudaStreamSynchronize(b->stream));
+    memcpy(flags.data(), b->pinned, flags.size() * sizeof(double));
+    int rc = batch_sync_host(b);
+    if (rc) return rc;
+    rc = batch_read_residuals(b, res.data());
+    if (rc) return rc;
+    int status = HFDIB_OK;
+    for (int i = 0; i < B; ++i) {
+        if (flags[2 * i] == 2.0) status = HFDIB_ERR_DIVERGED;
+        else if (flags[2 * i] == 0.0 && status == HFDIB_OK) status = HFDIB_ERR_NOT_CONVERGED;
+    }
+    if (max_iter == 0) status = HFDIB_ERR_NOT_CONVERGED;
     if (iters_out)
-        for (int i = 0; i < b->B; ++i) iters_out[i] = conv_at[i] >= 0 ? conv_at[i] : it;
+        for (int i = 0; i < B; ++i)
+            iters_out[i] = flags[2 * i] != 0.0 ? (int)((long long)flags[2 * i + 1] - start_sweeps[i])
+                                               : (int)(b->d[i]->sweeps - start_sweeps[i]);
     if (final_res) memcpy(final_res, res.data(), sizeof(double) * res.size());
     return status;
 }

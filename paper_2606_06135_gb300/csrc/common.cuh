@@ -154,15 +154,29 @@ __device__ inline bool scal_fixed(const Grid& g, uint16_t f, int s) {
 }
 __device__ inline bool p_fixed(const Grid& g, int s) { return g.kind[s] == HFDIB_BC_OUTLET; }
 
+// ---- block position -------------------------------------------------------
+// The blocks that work on one problem: a plain launch gives the whole grid
+// to one problem (block blockIdx.x of gridDim.x); a batched launch gives each
+// problem its own consecutive range of blocks, and Pos is the block's place
+// in its problem's range.  Kernel bodies index cells with Pos only, so a
+// problem sees the same block partition, and reduces in the same order,
+// alone or in a batch.
+struct Pos {
+    int bid;    // this block among its problem's blocks
+    int nblk;   // the problem's blocks
+};
+__device__ __forceinline__ Pos grid_pos() { return Pos{(int)blockIdx.x, (int)gridDim.x}; }
+
 // ---- deterministic grid reduction (last block finishes) -------------------
 template <bool MAX>
 __device__ inline double rop(double a, double b) { return MAX ? fmax(a, b) : a + b; }
 
-// Reduce v[NV] over the whole grid.  Every block writes its partials; the
-// block that finishes last combines all partials in a fixed order, so the
-// result does not depend on scheduling.  blockDim.x must be BLOCK.
+// Reduce v[NV] over the problem's blocks.  Every block writes its partials;
+// the block that finishes last combines all partials in a fixed order, so
+// the result does not depend on scheduling.  blockDim.x must be BLOCK.
 template <int NV, bool MAX>
-__device__ void grid_reduce(double (&v)[NV], double* partials, unsigned int* counter, double* out) {
+__device__ void grid_reduce(double (&v)[NV], double* partials, unsigned int* counter, double* out,
+                            Pos pos = grid_pos()) {
     __shared__ double sm[NV][BLOCK / 32];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -178,11 +192,11 @@ __device__ void grid_reduce(double (&v)[NV], double* partials, unsigned int* cou
         for (int q = 0; q < NV; ++q) {
             double x = sm[q][0];
             for (int w = 1; w < BLOCK / 32; ++w) x = rop<MAX>(x, sm[q][w]);
-            partials[(long long)q * gridDim.x + blockIdx.x] = x;
+            partials[(long long)q * pos.nblk + pos.bid] = x;
         }
         __threadfence();
         unsigned int t = atomicAdd(counter, 1u);
-        last = (t == gridDim.x - 1);
+        last = (t == (unsigned int)pos.nblk - 1);
     }
     __syncthreads();
     if (!last) return;
@@ -190,8 +204,8 @@ __device__ void grid_reduce(double (&v)[NV], double* partials, unsigned int* cou
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
         double x = MAX ? -1.0e308 : 0.0;
-        for (unsigned int b = threadIdx.x; b < gridDim.x; b += BLOCK)
-            x = rop<MAX>(x, __ldcg(&partials[(long long)q * gridDim.x + b]));
+        for (int b = threadIdx.x; b < pos.nblk; b += BLOCK)
+            x = rop<MAX>(x, __ldcg(&partials[(long long)q * pos.nblk + b]));
         for (int o = 16; o > 0; o >>= 1) x = rop<MAX>(x, __shfl_down_sync(0xffffffffu, x, o));
         if (lane == 0) sm[q][warp] = x;
     }

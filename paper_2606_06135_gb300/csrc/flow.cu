@@ -14,6 +14,7 @@
 // recirculation region behind a body (Sec. 3.3, 3.6).
 #include "common.cuh"
 #include "kernels.cuh"
+#include "batch.cuh"
 
 namespace hf {
 
@@ -94,10 +95,6 @@ __device__ inline void mom_row(const Grid& g, const Fields& F, long long c, int 
     mom_row_t<double>(g, F.phi, F.nut, c, i, j, k, f, R);
 }
 
-// predictor value u* = initial guess + (mixed path) FP32 correction
-__device__ inline double ustar(const Fields& F, int q, long long c) {
-    return F.mixed ? F.us[q][c] + (double)F.d32[q][c] : F.us[q][c];
-}
 
 // Gauss-linear gradient of the pressure-like field p at cell c (outlet faces
 // carry p_out, the rest zero gradient)
@@ -153,10 +150,10 @@ __global__ void k_face_flux(Grid g, const uint16_t* __restrict__ flags, const do
 // ---------------------------------------------------------------- means
 // Sums of the fields the residual normalisation needs, with imposed rows
 // replaced by their imposed values.
-__global__ void k_means(Grid g, Params P, Fields F) {
+__device__ __forceinline__ void b_means(Pos pos, const Grid& g, const Params& P, const Fields& F) {
     double v[6] = {0, 0, 0, 0, 0, 0};
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < g.N;
-         c += (long long)gridDim.x * blockDim.x) {
+    for (long long c = (long long)pos.bid * blockDim.x + threadIdx.x; c < g.N;
+         c += (long long)pos.nblk * blockDim.x) {
         uint16_t f = F.flags[c];
         int tag = tag_of(f);
         #pragma unroll
@@ -171,12 +168,15 @@ __global__ void k_means(Grid g, Params P, Fields F) {
             v[5] += tag == TAG_IC ? F.scal[SC_WMAX] : (tag == TAG_BC ? F.wib[c] : F.w[c]);
         }
     }
-    grid_reduce<6, false>(v, F.partials, F.counters + 1, F.scal + SC_SUM_U);
+    grid_reduce<6, false>(v, F.partials, F.counters + 1, F.scal + SC_SUM_U, pos);
+}
+__global__ void k_means(Grid g, Params P, Fields F) {
+    b_means(grid_pos(), g, P, F);
 }
 
 // ---------------------------------------------------------------- grad u
-__global__ void k_grad_u(Grid g, Fields F) {
-    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void b_grad_u(Pos pos, const Grid& g, const Fields& F) {
+    long long c = (long long)pos.bid * blockDim.x + threadIdx.x;
     if (c >= g.N) return;
     int i, j, k;
     cell_ijk(g, c, i, j, k);
@@ -195,6 +195,9 @@ __global__ void k_grad_u(Grid g, Fields F) {
             F.G[(long long)(3 * a + b) * g.N + c] = (hi - lo) * g.iD[a];
         }
     }
+}
+__global__ void k_grad_u(Grid g, Fields F) {
+    b_grad_u(grid_pos(), g, F);
 }
 
 // explicit div(nu_eff (grad u)^T) of cell c, component q: face flux
@@ -264,8 +267,8 @@ __device__ inline double conv_limiter(const Grid& g, const Fields& F, long long 
 }
 
 // scheme 3: the cell-limited velocity gradient, Glim = l G per component
-__global__ void k_conv_limit(Grid g, Fields F) {
-    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void b_conv_limit(Pos pos, const Grid& g, const Fields& F) {
+    long long c = (long long)pos.bid * blockDim.x + threadIdx.x;
     if (c >= g.N) return;
     int i, j, k;
     cell_ijk(g, c, i, j, k);
@@ -278,6 +281,9 @@ __global__ void k_conv_limit(Grid g, Fields F) {
             F.Glim[e] = l * F.G[e];
         }
     }
+}
+__global__ void k_conv_limit(Grid g, Fields F) {
+    b_conv_limit(grid_pos(), g, F);
 }
 
 __device__ inline double conv_src(const Grid& g, const Fields& F, long long c, int i, int j, int k, int q) {
@@ -320,48 +326,99 @@ __device__ inline double conv_src(const Grid& g, const Fields& F, long long c, i
 }
 
 // ---------------------------------------------------------------- a3 assembly
-__global__ void __launch_bounds__(BLOCK, 2) k_mom_asm(Grid g, Params P, Fields F) {
+// The viscosity of each interior face, nu_f = (nu_eff,P + nu_eff,N)/2, is
+// formed once and serves the row of every component and the explicit
+// transpose term: FP64 arithmetic is the limit of this kernel on GB300.
+__device__ __forceinline__ void b_mom_asm(Pos pos, const Grid& g, const Params& P, const Fields& F) {
     double red[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < g.N;
-         c += (long long)gridDim.x * blockDim.x) {
+    const long long N = g.N;
+    for (long long c = (long long)pos.bid * blockDim.x + threadIdx.x; c < N;
+         c += (long long)pos.nblk * blockDim.x) {
         int i, j, k;
         cell_ijk(g, c, i, j, k);
-        uint16_t f = F.flags[c];
-        MomRow R;
-        mom_row(g, F, c, i, j, k, f, R);
-        // keep the row for HbyA (same phi and nu_t later in the sweep)
+        const uint16_t f = F.flags[c];
+        const double nuP = g.nu + F.nut[c];
+        const int idx[3] = {i, j, k};
+        // faces s = 2d + side: neighbour, row coefficient, outflow, transpose weight nu_f S/2
+        double a[6], fo[6], w[6];
+        long long nb[6];
+        bool has[6];
+        double aPi = 0.0;   // the interior-face part of aP, common to the components
+        double A1n = 0.0;   // sum of the neighbour coefficients
         #pragma unroll
-        for (int q = 0; q < 3 && q < g.dims; ++q) F.mrow[(long long)q * g.N + c] = R.aP[q];
+        for (int s = 0; s < 6; ++s) {
+            const int d = s >> 1, side = s & 1;
+            has[s] = false;
+            a[s] = 0.0;
+            w[s] = 0.0;
+            fo[s] = 0.0;
+            nb[s] = c;
+            if (d >= g.dims) continue;
+            const double Fb = F.phi[d][face_lo(g, d, i, j, k) + (side ? face_stride(g, d) : 0)];
+            fo[s] = side ? Fb : -Fb;
+            if (!(side ? idx[d] < g.n[d] - 1 : idx[d] > 0)) continue;
+            const long long nc = side ? c + g.stride[d] : c - g.stride[d];
+            const double nuf = 0.5 * (nuP + (g.nu + F.nut[nc]));
+            const double Dif = nuf * g.SoD[d];
+            has[s] = true;
+            nb[s] = nc;
+            a[s] = fmin(fo[s], 0.0) - Dif;
+            aPi += fmax(-fo[s], 0.0) + Dif;
+            A1n += a[s];
+            w[s] = (0.5 * g.S[d]) * nuf;
+        }
+        // keep the row for the smoother (FP64 path) and HbyA (same phi and nu_t later in the sweep)
         #pragma unroll
-        for (int s = 0; s < 6 && s < 2 * g.dims; ++s) F.mrow[(long long)(3 + s) * g.N + c] = R.a[s];
-        double nuP = g.nu + F.nut[c];
-        bool fixed_row = (tag_of(f) == TAG_IC) || (f & F_AU);
+        for (int s = 0; s < 6 && s < 2 * g.dims; ++s) F.mrow[(long long)(3 + s) * N + c] = a[s];
+        const bool fixed_row = (tag_of(f) == TAG_IC) || (f & F_AU);
         #pragma unroll
         for (int q = 0; q < 3 && q < g.dims; ++q) {
-            double b0 = R.bnd[q] + transpose_src(g, F, c, i, j, k, q, nuP);
+            // boundary faces carrying a fixed value of component q
+            double aP = aPi, bnd = 0.0;
+            #pragma unroll
+            for (int s = 0; s < 6 && s < 2 * g.dims; ++s) {
+                double val;
+                if (!has[s] && vel_fixed(g, f, s, q, val)) {
+                    const double coef = nuP * g.SoHD[s >> 1] + fmax(-fo[s], 0.0);
+                    aP += coef;
+                    bnd += coef * val;
+                }
+            }
+            F.mrow[(long long)q * N + c] = aP;
+            // explicit div(nu_eff (grad u)^T): face flux nu_f (d u_a/d x_q)_f S_a
+            // through the a-faces (the cell's values on boundary faces)
+            double T = 0.0;
+            #pragma unroll
+            for (int ad = 0; ad < 3 && ad < g.dims; ++ad) {
+                const double* Gq = F.G + (long long)(3 * q + ad) * N;
+                const double GP = Gq[c];
+                const double fb = nuP * GP * g.S[ad];
+                const double flo = has[2 * ad] ? w[2 * ad] * (GP + Gq[nb[2 * ad]]) : fb;
+                const double fhi = has[2 * ad + 1] ? w[2 * ad + 1] * (GP + Gq[nb[2 * ad + 1]]) : fb;
+                T += fhi - flo;
+            }
+            double b0 = bnd + T;
             if (g.conv) b0 += conv_src(g, F, c, i, j, k, q);
-            double gp = grad_p(g, F.p, c, q, i, j, k);
-            double uold = F.u[q][c];
-            double bfull = b0 - gp * g.V;
-            F.bm[q][c] = b0 + P.rlx_u * R.aP[q] * uold - gp * g.V;
+            const double gp = grad_p(g, F.p, c, q, i, j, k);
+            const double uold = F.u[q][c];
+            const double bfull = b0 - gp * g.V;
+            F.bm[q][c] = b0 + P.rlx_u * aP * uold - gp * g.V;
             // initial guess of the predictor: u_old, with the imposed rows
             // already at their imposed values (so an exact solution of the
             // sweep's system is left unchanged by the smoother)
             double fv;
             F.us[q][c] = vel_row_fixed(g, F, c, q, fv) ? fv : uold;
             if (!fixed_row) {
-                double xP = uold;
-                double Ax = R.aP[q] * xP, A1 = R.aP[q];
+                double Ax = aP * uold;
                 #pragma unroll
                 for (int s = 0; s < 6 && s < 2 * g.dims; ++s) {
-                    if (!R.has[s]) continue;
+                    if (!has[s]) continue;
                     double xN;
-                    long long nc = R.nb[s];
-                    if (!vel_row_fixed(g, F, nc, q, xN)) xN = F.u[q][nc];
-                    Ax += R.a[s] * xN;
-                    A1 += R.a[s];
+                    if (!vel_row_fixed(g, F, nb[s], q, xN)) xN = F.u[q][nb[s]];
+                    Ax += a[s] * xN;
                 }
-                double xbar = F.scal[SC_SUM_U + q] * g.iN;
+                const double A1 = aP + A1n;
+                const double xbar = F.scal[SC_SUM_U + q] * g.iN;
                 red[3 * q + 0] += fabs(bfull - Ax);
                 red[3 * q + 1] += fabs(Ax - A1 * xbar);
                 red[3 * q + 2] += fabs(bfull - A1 * xbar);
@@ -373,14 +430,17 @@ __global__ void __launch_bounds__(BLOCK, 2) k_mom_asm(Grid g, Params P, Fields F
             }
         }
     }
-    grid_reduce<9, false>(red, F.partials, F.counters + 2, F.scal + SC_RES_U);
+    grid_reduce<9, false>(red, F.partials, F.counters + 2, F.scal + SC_RES_U, pos);
+}
+__global__ void __launch_bounds__(BLOCK, 2) k_mom_asm(Grid g, Params P, Fields F) {
+    b_mom_asm(grid_pos(), g, P, F);
 }
 
 // ---------------------------------------------------------------- a4 smoother
 // Red-black Gauss-Seidel on the relaxed momentum rows; rows with alpha_u = 1
 // hold u = u_ib (ic: u_s), which realises the correction of Eq. (corru).
-__global__ void k_mom_smooth(Grid g, Params P, Fields F, int colour) {
-    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void b_mom_smooth(Pos pos, const Grid& g, const Params& P, const Fields& F, int colour) {
+    long long p = (long long)pos.bid * blockDim.x + threadIdx.x;
     if (p >= npairs(g)) return;
     long long c;
     int i, j, k;
@@ -396,23 +456,31 @@ __global__ void k_mom_smooth(Grid g, Params P, Fields F, int colour) {
         for (int q = 0; q < 3 && q < g.dims; ++q) F.us[q][c] = F.uib[q][c];
         return;
     }
-    MomRow R;
-    mom_row(g, F, c, i, j, k, f, R);
+    // the row of this sweep, kept by the assembly (k_mom_asm)
+    const long long N = g.N;
+    const int idx[3] = {i, j, k};
     #pragma unroll
     for (int q = 0; q < 3 && q < g.dims; ++q) {
         double acc = F.bm[q][c];
         #pragma unroll
-        for (int s = 0; s < 6 && s < 2 * g.dims; ++s)
-            if (R.has[s]) acc -= R.a[s] * F.us[q][R.nb[s]];
-        F.us[q][c] = acc * P.urf_u / R.aP[q];
+        for (int s = 0; s < 6 && s < 2 * g.dims; ++s) {
+            const int d = s >> 1, side = s & 1;
+            if (!(side ? idx[d] < g.n[d] - 1 : idx[d] > 0)) continue;
+            acc -= F.mrow[(long long)(3 + s) * N + c] * F.us[q][side ? c + g.stride[d] : c - g.stride[d]];
+        }
+        F.us[q][c] = acc * P.urf_u / F.mrow[(long long)q * N + c];
     }
+}
+__global__ void k_mom_smooth(Grid g, Params P, Fields F, int colour) {
+    b_mom_smooth(grid_pos(), g, P, F, colour);
 }
 
 // FP32 red-black sweep on the correction of the predictor (mixed path):
 // (aP/urf) d_P + sum a_N d_N = r (FP64 defect rounded), d = 0 on imposed rows.
 // zero_init: the other colour is taken as 0 (first half sweep).
-__global__ void k_mom_smooth32(Grid g, Params P, Fields F, int colour, int zero_init) {
-    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void b_mom_smooth32(Pos pos, const Grid& g, const Params& P, const Fields& F, int colour,
+                                               int zero_init, int finalize) {
+    long long p = (long long)pos.bid * blockDim.x + threadIdx.x;
     if (p >= npairs(g)) return;
     long long c;
     int i, j, k;
@@ -433,13 +501,19 @@ __global__ void k_mom_smooth32(Grid g, Params P, Fields F, int colour, int zero_
             #pragma unroll
             for (int s = 0; s < 6 && s < 2 * g.dims; ++s)
                 if (R.has[s]) acc -= R.a[s] * F.d32[q][R.nb[s]];
-        F.d32[q][c] = acc * urf / R.aP[q];
+        const float dq = acc * urf / R.aP[q];
+        F.d32[q][c] = dq;
+        // the last pass of this colour: u* = initial guess + correction, in FP64
+        if (finalize) F.us[q][c] += (double)dq;
     }
+}
+__global__ void k_mom_smooth32(Grid g, Params P, Fields F, int colour, int zero_init, int finalize) {
+    b_mom_smooth32(grid_pos(), g, P, F, colour, zero_init, finalize);
 }
 
 // ---------------------------------------------------------------- a6 HbyA
-__global__ void k_hbya(Grid g, Params P, Fields F) {
-    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void b_hbya(Pos pos, const Grid& g, const Params& P, const Fields& F) {
+    long long c = (long long)pos.bid * blockDim.x + threadIdx.x;
     if (c >= g.N) return;
     int i, j, k;
     cell_ijk(g, c, i, j, k);
@@ -460,17 +534,20 @@ __global__ void k_hbya(Grid g, Params P, Fields F) {
             int d = s >> 1, side = s & 1;
             if (!interior(g, d, side, i, j, k)) continue;
             long long nb = side ? c + g.stride[d] : c - g.stride[d];
-            off += F.mrow[(long long)(3 + s) * N + c] * ustar(F, q, nb);
+            off += F.mrow[(long long)(3 + s) * N + c] * F.us[q][nb];
         }
-        double H = br - off - (aPr[q] - aavg) * ustar(F, q, c);
+        double H = br - off - (aPr[q] - aavg) * F.us[q][c];
         F.HbyA[q][c] = H * ia;
     }
     F.rAU[c] = g.V * ia;
 }
+__global__ void k_hbya(Grid g, Params P, Fields F) {
+    b_hbya(grid_pos(), g, P, F);
+}
 
 // ---------------------------------------------------------------- phiHbyA
-__global__ void k_phiH(Grid g, Fields F) {
-    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void b_phiH(Pos pos, const Grid& g, const Fields& F) {
+    long long c = (long long)pos.bid * blockDim.x + threadIdx.x;
     if (c >= g.N) return;
     int i, j, k;
     cell_ijk(g, c, i, j, k);
@@ -487,14 +564,17 @@ __global__ void k_phiH(Grid g, Fields F) {
             F.phiH[d][fl + face_stride(g, d)] = bnd_flux_hbya(g, f, 2 * d + 1, H[c]);
     }
 }
+__global__ void k_phiH(Grid g, Fields F) {
+    b_phiH(grid_pos(), g, F);
+}
 
 // ---------------------------------------------------------------- a8 update
 // phi = phiHbyA - rAU_f (p_N - p_P)/Delta S with the new (unrelaxed) pressure;
 // p <- p + urf_p (p_new - p); u = HbyA - rAU grad(p_relaxed); continuity error.
-__global__ void k_update(Grid g, Params P, Fields F, Level L0) {
+__device__ __forceinline__ void b_update(Pos pos, const Grid& g, const Params& P, const Fields& F, const Level& L0) {
     double red[1] = {0.0};
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < g.N;
-         c += (long long)gridDim.x * blockDim.x) {
+    for (long long c = (long long)pos.bid * blockDim.x + threadIdx.x; c < g.N;
+         c += (long long)pos.nblk * blockDim.x) {
         int i, j, k;
         cell_ijk(g, c, i, j, k);
         uint16_t f = F.flags[c];
@@ -546,7 +626,10 @@ __global__ void k_update(Grid g, Params P, Fields F, Level L0) {
         }
         F.pr[c] = prP;
     }
-    grid_reduce<1, false>(red, F.partials, F.counters + 6, F.scal + SC_CONT);
+    grid_reduce<1, false>(red, F.partials, F.counters + 6, F.scal + SC_CONT, pos);
+}
+__global__ void k_update(Grid g, Params P, Fields F, Level L0) {
+    b_update(grid_pos(), g, P, F, L0);
 }
 
 // ---------------------------------------------------------------- force on the body
@@ -662,8 +745,8 @@ __global__ void k_recirc(Grid g, Fields F, double x_rear, unsigned int* count) {
 }
 
 // ---------------------------------------------------------------- sweep end
-__global__ void k_sweep_end(Fields F, int dims, int model, const int* err, double* res_out, double* hist,
-                            int nhist) {
+__device__ __forceinline__ void b_sweep_end(Pos pos, const Fields& F, int dims, int model, const int* err,
+                                            double* res_out, double* hist, int nhist) {
     double* s = F.scal;
     if (err && *err) s[SC_TIMEOUT] = 1.0;
     res_out[HFDIB_NRES] = s[SC_TIMEOUT];
@@ -693,6 +776,9 @@ __global__ void k_sweep_end(Fields F, int dims, int model, const int* err, doubl
     }
     s[SC_NSWEEP] = (double)(n + 1);
 }
+__global__ void k_sweep_end(Fields F, int dims, int model, const int* err, double* res_out, double* hist, int nhist) {
+    b_sweep_end(grid_pos(), F, dims, model, err, res_out, hist, nhist);
+}
 
 // ---------------------------------------------------------------- launchers
 void launch_init_flux(const Grid& g, const Fields& F, cudaStream_t s) {
@@ -714,8 +800,9 @@ void launch_mom_asm(const Grid& g, const Params& P, const Fields& F, cudaStream_
 void launch_mom_smooth(const Grid& g, const Params& P, const Fields& F, int colour, cudaStream_t s) {
     k_mom_smooth<<<nblocks(npairs(g)), BLOCK, 0, s>>>(g, P, F, colour);
 }
-void launch_mom_smooth32(const Grid& g, const Params& P, const Fields& F, int colour, int zero_init, cudaStream_t s) {
-    k_mom_smooth32<<<nblocks(npairs(g)), BLOCK, 0, s>>>(g, P, F, colour, zero_init);
+void launch_mom_smooth32(const Grid& g, const Params& P, const Fields& F, int colour, int zero_init, int finalize,
+                         cudaStream_t s) {
+    k_mom_smooth32<<<nblocks(npairs(g)), BLOCK, 0, s>>>(g, P, F, colour, zero_init, finalize);
 }
 void launch_hbya(const Grid& g, const Params& P, const Fields& F, cudaStream_t s) {
     k_hbya<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F);
@@ -741,6 +828,110 @@ void launch_recirc(const Grid& g, const Fields& F, double x_rear, unsigned int* 
 void launch_sweep_end(const Params& P, const Fields& F, int dims, const int* err, double* res_out, double* hist,
                       int nhist, cudaStream_t s) {
     k_sweep_end<<<1, 1, 0, s>>>(F, dims, P.model, err, res_out, hist, nhist);
+}
+
+// ---------------------------------------------------------------- batched launches
+struct OpMeans {
+    __device__ void operator()(Pos p, const SweepProblem& s) const { b_means(p, s.g, s.P, s.F); }
+};
+struct OpGradU {
+    __device__ void operator()(Pos p, const SweepProblem& s) const { b_grad_u(p, s.g, s.F); }
+};
+struct OpConvLimit {
+    __device__ void operator()(Pos p, const SweepProblem& s) const { b_conv_limit(p, s.g, s.F); }
+};
+struct OpMomAsm {
+    __device__ void operator()(Pos p, const SweepProblem& s) const { b_mom_asm(p, s.g, s.P, s.F); }
+};
+struct OpMomSmooth {
+    int colour;
+    __device__ void operator()(Pos p, const SweepProblem& s) const { b_mom_smooth(p, s.g, s.P, s.F, colour); }
+};
+struct OpMomSmooth32 {
+    int colour, zero_init, finalize;
+    __device__ void operator()(Pos p, const SweepProblem& s) const {
+        b_mom_smooth32(p, s.g, s.P, s.F, colour, zero_init, finalize);
+    }
+};
+struct OpHbyA {
+    __device__ void operator()(Pos p, const SweepProblem& s) const { b_hbya(p, s.g, s.P, s.F); }
+};
+struct OpPhiH {
+    __device__ void operator()(Pos p, const SweepProblem& s) const { b_phiH(p, s.g, s.F); }
+};
+struct OpUpdate {
+    __device__ void operator()(Pos p, const SweepProblem& s) const { b_update(p, s.g, s.P, s.F, s.L0); }
+};
+// the residual record, then (batch solves) the stop test on the largest
+// scaled residual, then the p / pr swap of this problem's device tables
+struct OpSweepEnd {
+    __device__ void operator()(Pos p, const SweepProblem& s) const {
+        if (threadIdx.x != 0) return;
+        b_sweep_end(p, s.F, s.g.dims, s.model_end, s.err, s.res_out, s.hist, s.nhist);
+        double* sc = s.F.scal;
+        if (sc[SC_STOP_ON] != 0.0 && sc[SC_DONE] == 0.0) {
+            double mx = 0.0;
+            bool bad = false;
+            for (int q = 0; q <= HFDIB_RES_K; ++q) {
+                const double v = s.res_out[q];
+                if (!isfinite(v)) bad = true;
+                mx = fmax(mx, v);
+            }
+            if (bad || mx <= sc[SC_STOP_TOL]) {
+                sc[SC_DONE] = bad ? 2.0 : 1.0;
+                sc[SC_DONE_AT] = sc[SC_NSWEEP];
+            }
+        }
+        for (int t = 0; t < 2; ++t) {
+            double* a = *s.swap_p[t];
+            *s.swap_p[t] = *s.swap_pr[t];
+            *s.swap_pr[t] = a;
+        }
+    }
+};
+__global__ void k_batch_next(BatchTab T, unsigned int* count, const unsigned int* max_iter,
+                             cudaGraphConditionalHandle h) {
+    const unsigned int n = *count + 1;
+    *count = n;
+    bool all = true;
+    for (int b = 0; b < T.B; ++b) all = all && (*T.probs[b].done != 0.0);
+    cudaGraphSetConditional(h, (!all && n < *max_iter) ? 1u : 0u);
+}
+
+void launchb_means(const BatchTab& T, const int* tot, cudaStream_t s) {
+    k_batched<BK_REDUCE, OpMeans><<<tot[BK_REDUCE], BLOCK, 0, s>>>(T, OpMeans{});
+}
+void launchb_grad_u(const BatchTab& T, const int* tot, cudaStream_t s) {
+    k_batched<BK_CELLS, OpGradU><<<tot[BK_CELLS], BLOCK, 0, s>>>(T, OpGradU{});
+}
+void launchb_conv_limit(const BatchTab& T, const int* tot, cudaStream_t s) {
+    k_batched<BK_CELLS, OpConvLimit><<<tot[BK_CELLS], BLOCK, 0, s>>>(T, OpConvLimit{});
+}
+void launchb_mom_asm(const BatchTab& T, const int* tot, cudaStream_t s) {
+    k_batched<BK_REDUCE, OpMomAsm><<<tot[BK_REDUCE], BLOCK, 0, s>>>(T, OpMomAsm{});
+}
+void launchb_mom_smooth(const BatchTab& T, const int* tot, int colour, cudaStream_t s) {
+    k_batched<BK_PAIRS, OpMomSmooth><<<tot[BK_PAIRS], BLOCK, 0, s>>>(T, OpMomSmooth{colour});
+}
+void launchb_mom_smooth32(const BatchTab& T, const int* tot, int colour, int zero_init, int finalize,
+                          cudaStream_t s) {
+    k_batched<BK_PAIRS, OpMomSmooth32><<<tot[BK_PAIRS], BLOCK, 0, s>>>(T, OpMomSmooth32{colour, zero_init, finalize});
+}
+void launchb_hbya(const BatchTab& T, const int* tot, cudaStream_t s) {
+    k_batched<BK_CELLS, OpHbyA><<<tot[BK_CELLS], BLOCK, 0, s>>>(T, OpHbyA{});
+}
+void launchb_phiH(const BatchTab& T, const int* tot, cudaStream_t s) {
+    k_batched<BK_CELLS, OpPhiH><<<tot[BK_CELLS], BLOCK, 0, s>>>(T, OpPhiH{});
+}
+void launchb_update(const BatchTab& T, const int* tot, cudaStream_t s) {
+    k_batched<BK_REDUCE, OpUpdate><<<tot[BK_REDUCE], BLOCK, 0, s>>>(T, OpUpdate{});
+}
+void launchb_sweep_end(const BatchTab& T, const int* tot, cudaStream_t s) {
+    k_batched<BK_ONE, OpSweepEnd><<<tot[BK_ONE], BLOCK, 0, s>>>(T, OpSweepEnd{});
+}
+void launchb_next(const BatchTab& T, unsigned int* count, const unsigned int* max_iter,
+                  cudaGraphConditionalHandle h, cudaStream_t s) {
+    k_batch_next<<<1, 1, 0, s>>>(T, count, max_iter, h);
 }
 
 }  // namespace hf

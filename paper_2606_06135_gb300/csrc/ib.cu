@@ -18,6 +18,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "batch.cuh"
 
 namespace hf {
 
@@ -277,12 +278,17 @@ __global__ void k_bc_geometry(Grid g, const double* __restrict__ lam, const uint
 }
 
 // ---------------------------------------------------------------- a1
-__global__ void k_max_not_ic(Grid g, const uint16_t* __restrict__ flags, const double* __restrict__ w,
-                             double* partials, unsigned int* counter, double* out) {
-    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void b_max_not_ic(Pos pos, const Grid& g, const uint16_t* __restrict__ flags,
+                                             const double* __restrict__ w, double* partials, unsigned int* counter,
+                                             double* out) {
+    long long c = (long long)pos.bid * blockDim.x + threadIdx.x;
     double v[1] = {0.0};
     if (c < g.N && tag_of(flags[c]) != TAG_IC) v[0] = w[c];
-    grid_reduce<1, true>(v, partials, counter, out);
+    grid_reduce<1, true>(v, partials, counter, out, pos);
+}
+__global__ void k_max_not_ic(Grid g, const uint16_t* __restrict__ flags, const double* __restrict__ w,
+                             double* partials, unsigned int* counter, double* out) {
+    b_max_not_ic(grid_pos(), g, flags, w, partials, counter, out);
 }
 
 // ---------------------------------------------------------------- a2
@@ -308,12 +314,13 @@ __device__ inline double interp_cell(const Grid& g, const double* f, const int* 
     return val;
 }
 
-__global__ void k_imposed(Grid g, int model, int freeze, BcList bl, uint16_t* __restrict__ flags, double* scal,
-                          const double* __restrict__ ux, const double* __restrict__ uy,
-                          const double* __restrict__ uz, const double* __restrict__ kf,
-                          double* __restrict__ uibx, double* __restrict__ uiby, double* __restrict__ uibz,
-                          double* __restrict__ kib, double* __restrict__ wib) {
-    int q = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void b_imposed(Pos pos, const Grid& g, int model, int freeze, const BcList& bl,
+                                          uint16_t* __restrict__ flags, double* scal, const double* __restrict__ ux,
+                                          const double* __restrict__ uy, const double* __restrict__ uz,
+                                          const double* __restrict__ kf, double* __restrict__ uibx,
+                                          double* __restrict__ uiby, double* __restrict__ uibz,
+                                          double* __restrict__ kib, double* __restrict__ wib) {
+    int q = pos.bid * blockDim.x + threadIdx.x;
     if (q >= bl.nbc) return;
     int c = bl.cell[q];
     const int* b1 = bl.b1 + 3 * q;
@@ -363,6 +370,12 @@ __global__ void k_imposed(Grid g, int model, int freeze, BcList bl, uint16_t* __
         // k is imposed (laminar branch), the old k_P where k is solved
         wib[c] = eps_model(model) ? C_MU * (lamb ? kimp : kP) * w : w;
     }
+}
+__global__ void k_imposed(Grid g, int model, int freeze, BcList bl, uint16_t* __restrict__ flags, double* scal,
+                          const double* __restrict__ ux, const double* __restrict__ uy, const double* __restrict__ uz,
+                          const double* __restrict__ kf, double* __restrict__ uibx, double* __restrict__ uiby,
+                          double* __restrict__ uibz, double* __restrict__ kib, double* __restrict__ wib) {
+    b_imposed(grid_pos(), g, model, freeze, bl, flags, scal, ux, uy, uz, kf, uibx, uiby, uibz, kib, wib);
 }
 
 // export of the bc list for comparison with the oracle
@@ -416,6 +429,26 @@ void launch_imposed(const Grid& g, int model, int freeze, const BcList& bl, uint
 void launch_export_bc(const BcList& bl, long long* ints, long long* ints2, double* reals, cudaStream_t s) {
     if (bl.nbc == 0) return;
     k_export_bc<<<nblocks(bl.nbc), BLOCK, 0, s>>>(bl, ints, ints2, reals);
+}
+
+// ---------------------------------------------------------------- batched launches
+struct OpMaxNotIc {
+    __device__ void operator()(Pos p, const SweepProblem& s) const {
+        b_max_not_ic(p, s.g, s.F.flags, s.F.w, s.F.partials, s.F.counters + 0, s.F.scal + SC_WMAX);
+    }
+};
+struct OpImposed {
+    __device__ void operator()(Pos p, const SweepProblem& s) const {
+        const Fields& F = s.F;
+        b_imposed(p, s.g, s.P.model, s.freeze, s.bl, F.flags, F.scal, F.u[0], F.u[1], F.u[2], F.k, F.uib[0],
+                  F.uib[1], F.uib[2], F.kib, F.wib);
+    }
+};
+void launchb_max_not_ic(const BatchTab& T, const int* tot, cudaStream_t s) {
+    k_batched<BK_CELLS, OpMaxNotIc><<<tot[BK_CELLS], BLOCK, 0, s>>>(T, OpMaxNotIc{});
+}
+void launchb_imposed(const BatchTab& T, const int* tot, cudaStream_t s) {
+    if (tot[BK_BC] > 0) k_batched<BK_BC, OpImposed><<<tot[BK_BC], BLOCK, 0, s>>>(T, OpImposed{});
 }
 
 }  // namespace hf

@@ -50,7 +50,12 @@ enum {
     SC_FORCE = 52,               // 6: force on the body, pressure part xyz then the rest xyz
     SC_RECIRC = 58,              // largest x - x_rear of a recirculating cell
     SC_COEF = 60,                // 2: drag and lift coefficients of the force
-    SC_NSCAL = 64
+    // the stop test of a batch solve, checked on the device at every sweep end
+    SC_STOP_TOL = 64,            // tolerance on the largest scaled residual
+    SC_STOP_ON = 65,             // 1 while a batch solve runs
+    SC_DONE = 66,                // 1 converged, 2 diverged (non-finite residual); the problem then skips
+    SC_DONE_AT = 67,             // the sweep count at which it stopped
+    SC_NSCAL = 72
 };
 
 struct Fields {
@@ -91,6 +96,7 @@ struct Fields {
     double* prhs;
     double* pdiag;
     double* r;
+    double* r_alt;     // FP64 path: the second CG residual buffer of the persistent solve
     double* z;
     double* d[2];
     double* q;
@@ -105,8 +111,10 @@ struct Fields {
     float* d32[3];     // FP32 correction
     float* diag32;     // relaxed diagonal of the scalar equation
     float* z32;        // preconditioned residual of the CG (mixed path)
-    float* pd32[2];    // FP32 CG search directions of the pressure solve (p_cg32)
-    float* pq32;       // FP32 A d of the pressure solve (p_cg32)
+    float* pd32[2];    // FP32 CG search directions of the pressure correction solve
+    float* pq32;       // FP32 A d of the pressure correction solve
+    float* px32;       // FP32 pressure correction (pn = p + px32)
+    float* pr32;       // the second FP32 CG residual buffer of the persistent solve
     int mixed;
     // scalars and reductions
     double* scal;
@@ -193,39 +201,45 @@ void launch_pcg_start(const Fields& F, int jacobi, double reltol, int maxit, cud
 void launch_pcg_body(const Grid& g, const Fields& F, const MgLevels& M, int ntail_from, int jacobi,
                      int coarse_sweeps, int maxit, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s);
 
-// pcgp.cu
-int pcgp_blocks(int* out);
-// Default poll budget of one wait at a persistent kernel's grid barrier
-// (about 0.1-1 s); a wait that runs out sets the kernel's error word.
+// persistent pressure solve (pcgb.cu): default poll budget of one wait at its
+// grid barrier (about 0.1-1 s); a wait that runs out sets the kernel's error word.
 constexpr long long BARRIER_POLLS = 1ll << 26;
+constexpr int PT_THREADS = 1024;                 // threads per block of a single problem's solve
+constexpr size_t PT_SMEM_BUDGET = 160 * 1024;    // shared memory of one problem's tail levels
 // Phase tags of the persistent pressure kernel's trace (see hfdib_pressure_trace)
 enum { PH_START = 0, PH_BUILD0 = 1, PH_COARSEN = 2, PH_R0 = 3, PH_VC_SMOOTH0 = 4, PH_VC_RESTRICT = 5,
        PH_VC_SMOOTH = 6, PH_VC_TAIL = 7, PH_VC_PROLONG = 8, PH_VC_UPSMOOTH = 9, PH_VC_FINAL = 10,
-       PH_CG_PRODUCT = 11, PH_CG_UPDATE = 12, PH_END = 13 };
-cudaError_t launch_pressure_persistent(const Grid& g, const Fields& F, const MgLevels& M, int jacobi,
-                                       int coarse_sweeps, double reltol, int maxit, int nblk, double* part,
-                                       unsigned int* bar, int* err, long long spin_limit, long long tail_cells,
-                                       long long* trace, int trace_cap, cudaStream_t s);
-cudaError_t launch_pressure_persistent32(const Grid& g, const Fields& F, const MgLevels& M, const MgLevels32& M32,
-                                         int coarse_sweeps, double reltol, int maxit, int nblk, double* part,
-                                         unsigned int* bar, int* err, long long spin_limit, long long tail_cells,
-                                         int cg32, long long* trace, int trace_cap, cudaStream_t s);
+       PH_CG_PRODUCT = 11, PH_CG_UPDATE = 12, PH_END = 13,
+       // within block 0 (no barrier): its r0 share done, its tail table set
+       // up, a tail level built, the tail input copied in, the tail computed
+       PH_R0_SHARE = 14, PH_TB_TABLE = 15, PH_TB_LEVEL = 16, PH_TAIL_IN = 17, PH_TAIL_DONE = 18,
+       // inside the tail (pcg_ops.cuh): a block-wide level down, the coarsest
+       // part, a block-wide level up
+       PH_TL_DOWN = 19, PH_TL_WARP = 20, PH_TL_UP = 21 };
 void launch_p_coef32(const Grid& g, const MgLevels& M, const MgLevels32& M32, cudaStream_t s);
-void launch_mom_smooth32(const Grid& g, const Params& P, const Fields& F, int colour, int zero_init, cudaStream_t s);
+// mixed path: FP32 red-black pass on the momentum correction; finalize (the
+// last pass of each colour) adds the correction to u* in FP64
+void launch_mom_smooth32(const Grid& g, const Params& P, const Fields& F, int colour, int zero_init, int finalize,
+                         cudaStream_t s);
 void launch_scal_smooth32(const Grid& g, const Params& P, const Fields& F, int eq, int colour, int zero_init,
                           cudaStream_t s);
 
-// pcgb.cu (batched pressure solve)
+// pcgb.cu: the persistent pressure solve of a batch of B >= 1 problems
+// (a single problem is a batch of one); descriptors as below, all problems of
+// a launch 2D or all 3D
 size_t pcgb_describe64(void* dst, const Grid& g, const Fields& F, const MgLevels& M, double* part,
                        long long tail_cells, size_t smem_budget);
 size_t pcgb_describe32(void* dst, const Grid& g, const Fields& F, const MgLevels& M, const MgLevels32& M32,
                        double* part, long long tail_cells, size_t smem_budget);
 size_t pcgb_desc_size(int mixed);
 int pcgb_max_batch();
-cudaError_t launch_pressure_batched(int mixed, const void* ddesc, int B, int maxlev, int coarse_sweeps,
+cudaError_t launch_pressure_batched(int mixed, int dims, const void* ddesc, int B, int maxlev, int coarse_sweeps,
                                     double reltol, int maxit, int nblk, int threads, size_t smem,
-                                    unsigned int* bar, int* err, long long spin_limit, cudaStream_t s);
-int pcgb_fits(int mixed, int threads, size_t smem, int* blocks_per_sm);
+                                    unsigned int* bar, int* err, long long spin_limit, long long* trace,
+                                    int trace_cap, int skip, cudaStream_t s);
+size_t pcgb_fields_offset(int mixed);
+void launch_pressure_reset(unsigned int* bar, int* err, cudaStream_t s);
+int pcgb_fits(int mixed, int dims, int threads, size_t smem, int* blocks_per_sm);
 
 // adjoint.cu: reverse pass of the frozen-turbulence sweep (reverse fixed
 // point of Christianson type for d(pressure drop)/d(lambda))

@@ -10,6 +10,7 @@
 // models) or omega (k-omega models), eq = 1 is k.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "batch.cuh"
 
 namespace hf {
 
@@ -37,8 +38,8 @@ __device__ inline double sst_F2(double kk, double ww, double y, double nu) {
 }
 
 // ---------------------------------------------------------------- a9 production
-__global__ void k_turb_prep(Grid g, Params P, Fields F) {
-    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void b_turb_prep(Pos pos, const Grid& g, const Params& P, const Fields& F) {
+    long long c = (long long)pos.bid * blockDim.x + threadIdx.x;
     if (c >= g.N) return;
     int i, j, k;
     cell_ijk(g, c, i, j, k);
@@ -139,10 +140,13 @@ __global__ void k_turb_prep(Grid g, Params P, Fields F) {
         if (F.mixed) { F.gam32[c] = (float)F.gam[c]; F.gamk32[c] = (float)F.gamk[c]; }
     }
 }
+__global__ void k_turb_prep(Grid g, Params P, Fields F) {
+    b_turb_prep(grid_pos(), g, P, F);
+}
 
 // P_ib in the log branch of bc cells: kappa nu y+ |n.grad u|^2 / ln^2(E y+)
-__global__ void k_bc_prod(Grid g, BcList bl, Fields F) {
-    int q = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void b_bc_prod(Pos pos, const Grid& g, const BcList& bl, const Fields& F) {
+    int q = pos.bid * blockDim.x + threadIdx.x;
     if (q >= bl.nbc) return;
     if (bl.lamb[q]) return;
     long long c = bl.cell[q];
@@ -159,6 +163,9 @@ __global__ void k_bc_prod(Grid g, BcList bl, Fields F) {
     double yp = fmax(bl.yplus[q], YPLUS_LAM);
     double L = log(E_WF * yp);
     F.Pk[c] = KAPPA * g.nu * yp * dudn2 / (L * L);
+}
+__global__ void k_bc_prod(Grid g, BcList bl, Fields F) {
+    b_bc_prod(grid_pos(), g, bl, F);
 }
 
 // ---------------------------------------------------------------- scalar rows
@@ -226,13 +233,13 @@ __device__ inline void scal_row(const Grid& g, const Fields& F, const double* ga
     scal_row_t<double>(g, F.phi, gam, xin, c, i, j, k, f, R);
 }
 
-__global__ void k_scal_asm(Grid g, Params P, Fields F, int eq) {
+__device__ __forceinline__ void b_scal_asm(Pos pos, const Grid& g, const Params& P, const Fields& F, int eq) {
     double red[3] = {0.0, 0.0, 0.0};
     double* x = eq == 0 ? F.w : F.k;
     const double* gam = eq == 0 ? F.gam : F.gamk;
     double xin = eq == 0 ? P.w_in : P.k_in;
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < g.N;
-         c += (long long)gridDim.x * blockDim.x) {
+    for (long long c = (long long)pos.bid * blockDim.x + threadIdx.x; c < g.N;
+         c += (long long)pos.nblk * blockDim.x) {
         int i, j, k;
         cell_ijk(g, c, i, j, k);
         uint16_t f = F.flags[c];
@@ -268,11 +275,15 @@ __global__ void k_scal_asm(Grid g, Params P, Fields F, int eq) {
             if (F.mixed) F.r32[0][c] = (float)(b - Ax);
         }
     }
-    grid_reduce<3, false>(red, F.partials, F.counters + 7, F.scal + (eq == 0 ? SC_RES_W : SC_RES_K));
+    grid_reduce<3, false>(red, F.partials, F.counters + 7, F.scal + (eq == 0 ? SC_RES_W : SC_RES_K), pos);
+}
+__global__ void k_scal_asm(Grid g, Params P, Fields F, int eq) {
+    b_scal_asm(grid_pos(), g, P, F, eq);
 }
 
-__global__ void k_scal_smooth(Grid g, Params P, Fields F, int eq, int colour) {
-    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void b_scal_smooth(Pos pos, const Grid& g, const Params& P, const Fields& F, int eq,
+                                              int colour) {
+    long long p = (long long)pos.bid * blockDim.x + threadIdx.x;
     if (p >= npairs(g)) return;
     long long c;
     int i, j, k;
@@ -294,11 +305,15 @@ __global__ void k_scal_smooth(Grid g, Params P, Fields F, int eq, int colour) {
         if (R.has[s]) acc -= R.a[s] * x[R.nb[s]];
     x[c] = acc / F.diag[c];
 }
+__global__ void k_scal_smooth(Grid g, Params P, Fields F, int eq, int colour) {
+    b_scal_smooth(grid_pos(), g, P, F, eq, colour);
+}
 
 // FP32 red-black sweep on the correction (mixed path): diag d_P + sum a_N d_N
 // = r (FP64 defect rounded); d = 0 on imposed rows
-__global__ void k_scal_smooth32(Grid g, Params P, Fields F, int eq, int colour, int zero_init) {
-    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void b_scal_smooth32(Pos pos, const Grid& g, const Params& P, const Fields& F, int eq,
+                                                int colour, int zero_init) {
+    long long p = (long long)pos.bid * blockDim.x + threadIdx.x;
     if (p >= npairs(g)) return;
     long long c;
     int i, j, k;
@@ -320,10 +335,13 @@ __global__ void k_scal_smooth32(Grid g, Params P, Fields F, int eq, int colour, 
             if (R.has[s]) acc -= R.a[s] * F.d32[0][R.nb[s]];
     F.d32[0][c] = acc / F.diag32[c];
 }
+__global__ void k_scal_smooth32(Grid g, Params P, Fields F, int eq, int colour, int zero_init) {
+    b_scal_smooth32(grid_pos(), g, P, F, eq, colour, zero_init);
+}
 
 // after the eps/omega solve: bound it, set the k-equation sink and source
-__global__ void k_k_prep(Grid g, Params P, Fields F) {
-    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void b_k_prep(Pos pos, const Grid& g, const Params& P, const Fields& F) {
+    long long c = (long long)pos.bid * blockDim.x + threadIdx.x;
     if (c >= g.N) return;
     double w = F.w[c];
     if (F.mixed) w += (double)F.d32[0][c];   // apply the FP32 correction
@@ -342,10 +360,13 @@ __global__ void k_k_prep(Grid g, Params P, Fields F) {
         F.src[c] = fmin(F.Pk[c], SST_C1 * SST_BSTAR * kold * w) * g.V;
     }
 }
+__global__ void k_k_prep(Grid g, Params P, Fields F) {
+    b_k_prep(grid_pos(), g, P, F);
+}
 
 // bound k, apply the k correction (Eq. corru for k), update nu_t
-__global__ void k_turb_final(Grid g, Params P, Fields F) {
-    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void b_turb_final(Pos pos, const Grid& g, const Params& P, const Fields& F) {
+    long long c = (long long)pos.bid * blockDim.x + threadIdx.x;
     if (c >= g.N) return;
     uint16_t f = F.flags[c];
     double kx = F.k[c];
@@ -375,6 +396,9 @@ __global__ void k_turb_final(Grid g, Params P, Fields F) {
     F.nut[c] = nut;
     if (F.mixed) F.nut32[c] = (float)nut;
 }
+__global__ void k_turb_final(Grid g, Params P, Fields F) {
+    b_turb_final(grid_pos(), g, P, F);
+}
 
 // ---------------------------------------------------------------- launchers
 void launch_turb_prep(const Grid& g, const Params& P, const Fields& F, cudaStream_t s) {
@@ -400,6 +424,55 @@ void launch_k_prep(const Grid& g, const Params& P, const Fields& F, cudaStream_t
 }
 void launch_turb_final(const Grid& g, const Params& P, const Fields& F, cudaStream_t s) {
     k_turb_final<<<nblocks(g.N), BLOCK, 0, s>>>(g, P, F);
+}
+
+// ---------------------------------------------------------------- batched launches
+struct OpTurbPrep {
+    __device__ void operator()(Pos p, const SweepProblem& s) const { b_turb_prep(p, s.g, s.P, s.F); }
+};
+struct OpBcProd {
+    __device__ void operator()(Pos p, const SweepProblem& s) const { b_bc_prod(p, s.g, s.bl, s.F); }
+};
+struct OpScalAsm {
+    int eq;
+    __device__ void operator()(Pos p, const SweepProblem& s) const { b_scal_asm(p, s.g, s.P, s.F, eq); }
+};
+struct OpScalSmooth {
+    int eq, colour;
+    __device__ void operator()(Pos p, const SweepProblem& s) const { b_scal_smooth(p, s.g, s.P, s.F, eq, colour); }
+};
+struct OpScalSmooth32 {
+    int eq, colour, zero_init;
+    __device__ void operator()(Pos p, const SweepProblem& s) const {
+        b_scal_smooth32(p, s.g, s.P, s.F, eq, colour, zero_init);
+    }
+};
+struct OpKPrep {
+    __device__ void operator()(Pos p, const SweepProblem& s) const { b_k_prep(p, s.g, s.P, s.F); }
+};
+struct OpTurbFinal {
+    __device__ void operator()(Pos p, const SweepProblem& s) const { b_turb_final(p, s.g, s.P, s.F); }
+};
+void launchb_turb_prep(const BatchTab& T, const int* tot, cudaStream_t s) {
+    k_batched<BK_CELLS, OpTurbPrep><<<tot[BK_CELLS], BLOCK, 0, s>>>(T, OpTurbPrep{});
+}
+void launchb_bc_prod(const BatchTab& T, const int* tot, cudaStream_t s) {
+    if (tot[BK_BC] > 0) k_batched<BK_BC, OpBcProd><<<tot[BK_BC], BLOCK, 0, s>>>(T, OpBcProd{});
+}
+void launchb_scal_asm(const BatchTab& T, const int* tot, int eq, cudaStream_t s) {
+    k_batched<BK_REDUCE, OpScalAsm><<<tot[BK_REDUCE], BLOCK, 0, s>>>(T, OpScalAsm{eq});
+}
+void launchb_scal_smooth(const BatchTab& T, const int* tot, int eq, int colour, cudaStream_t s) {
+    k_batched<BK_PAIRS, OpScalSmooth><<<tot[BK_PAIRS], BLOCK, 0, s>>>(T, OpScalSmooth{eq, colour});
+}
+void launchb_scal_smooth32(const BatchTab& T, const int* tot, int eq, int colour, int zero_init, cudaStream_t s) {
+    k_batched<BK_PAIRS, OpScalSmooth32><<<tot[BK_PAIRS], BLOCK, 0, s>>>(T, OpScalSmooth32{eq, colour, zero_init});
+}
+void launchb_k_prep(const BatchTab& T, const int* tot, cudaStream_t s) {
+    k_batched<BK_CELLS, OpKPrep><<<tot[BK_CELLS], BLOCK, 0, s>>>(T, OpKPrep{});
+}
+void launchb_turb_final(const BatchTab& T, const int* tot, cudaStream_t s) {
+    k_batched<BK_CELLS, OpTurbFinal><<<tot[BK_CELLS], BLOCK, 0, s>>>(T, OpTurbFinal{});
 }
 
 }  // namespace hf

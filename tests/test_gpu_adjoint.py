@@ -270,3 +270,21 @@ def test_reading_b_gradient_matches_oracle(name):
     # the gradient reaches the fluid far from the body
     assert np.count_nonzero(g) > 0.9 * g.size
     s.close()
+
+
+def test_batched_autograd_matches_single_designs():
+    """pressure_drops: two designs of different size solved as one batch; the
+    gradients of sum(J) are each design's own adjoint gradient."""
+    import torch
+    from paper_2606_06135_gb300.autograd import pressure_drop, pressure_drops
+    cases = [G.case_grf(32, 16, seed=1), G.case_grf(40, 20, seed=2)]
+    lams = [torch.tensor(c["lam"], dtype=torch.float64, device="cuda", requires_grad=True) for c in cases]
+    J = pressure_drops(lams, cases, solve_tol=1e-12, adj_tol=1e-11)
+    assert J.shape == (2,)
+    J.sum().backward()
+    for c, lam, Jb in zip(cases, lams, J.detach().cpu().numpy()):
+        ls = torch.tensor(c["lam"], dtype=torch.float64, device="cuda", requires_grad=True)
+        Js = pressure_drop(ls, c, solve_tol=1e-12, adj_tol=1e-11)
+        Js.backward()
+        assert abs(Js.item() - Jb) <= 1e-10 * abs(Jb)
+        assert rel(lam.grad.cpu().numpy(), ls.grad.cpu().numpy()) <= 1e-8

@@ -168,6 +168,17 @@ def test_converged_state_matches_oracle_fp64(name):
     s.close()
 
 
+def test_converged_state_jacobi_pcg_fp64():
+    """precond = 0: the pressure equation by Jacobi-preconditioned CG (one
+    launch per CG step) reaches the same steady state as the FP64 oracle."""
+    case, o = converged_oracle("cylinder_keps")
+    s = make_solver(case, precond=0, p_maxiter=200)
+    rc, it, res = s.solve(tol=1e-12, max_iter=6000, check_every=20)
+    assert rc == 0, (rc, it, res)
+    compare_fields(s, o, 1e-9)
+    s.close()
+
+
 def test_deterministic_and_checkpoint_resume():
     case = G.case_cylinder(64, 32)
     a = make_solver(case)
