@@ -252,7 +252,8 @@ int hfdib_simple_sweep(hfdib_handle h, int n_sweeps, double* residuals);
  * block 0 without a barrier, 14 its share of the initial residual done, 15
  * its tail table set up, 16 a tail level built, 17 the tail input copied
  * in, 18 the tail computed, and inside the tail 19 a level down (block
- * wide), 20 the coarsest levels, 21 a level up (block wide).  A
+ * wide), 20 the coarsest levels, 21 a level up (block wide), 22 the cell
+ * loop of a CG product or update done, 23 its block partial written.  A
  * measurement aid for the pressure solve (it allocates a small device
  * buffer for the call).
  *   out      : HOST, 2 * capacity int64: tag, ns, tag, ns, ...

@@ -1375,6 +1375,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
     A(F.G, 9 * N); A(F.mrow, 9 * N);
     if (o.convection == 3) A(F.Glim, 9 * N); A(F.Pk, N); A(F.S2, N); A(F.gam, N); A(F.gamk, N); A(F.sp, N); A(F.src, N); A(F.asus, N);
     A(F.bt, N); A(F.diag, N); A(F.ywall, N); A(F.flags, N);
+    if (model == HFDIB_KOMEGA_SST) A(F.iyw, N);
     A(F.prhs, N); A(F.pdiag, N); A(F.r, N); A(F.z, N); A(F.d[0], N); A(F.d[1], N); A(F.q, N);
     A(F.scal, SC_NSCAL); A(F.partials, 16 * (long long)nb + 64); A(F.counters, 64);
     A(h->hist, HIST * HFDIB_NRES); A(h->res_dev, HFDIB_NRES + 1);
@@ -1474,6 +1475,7 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
     double bad = 0.0;
     if (sync_read(h, F.scal + 63, &bad, 1) != HFDIB_OK) { free_all(h); delete h; return HFDIB_ERR_CUDA; }
     if (bad != 0.0) { free_all(h); delete h; return HFDIB_ERR_INVALID_ARG; }
+    if (model == HFDIB_KOMEGA_SST) launch_inv_wall_distance(g, F, s);
 
     // a0: groups, boundary-cell list and geometry
     launch_classify(g, h->lam, F.flags, s);

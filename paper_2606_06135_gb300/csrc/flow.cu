@@ -99,6 +99,10 @@ __device__ inline void mom_row(const Grid& g, const Fields& F, long long c, int 
 // Gauss-linear gradient of the pressure-like field p at cell c (outlet faces
 // carry p_out, the rest zero gradient)
 __device__ inline double grad_p(const Grid& g, const double* p, long long c, int d, int i, int j, int k) {
+    // between two interior faces (hi - lo) / Delta = (p_N - p_S) / (2 Delta):
+    // two FP64 operations instead of six
+    if (interior(g, d, 0, i, j, k) && interior(g, d, 1, i, j, k))
+        return (p[c + g.stride[d]] - p[c - g.stride[d]]) * (0.5 * g.iD[d]);
     double pP = p[c];
     double lo, hi;
     if (interior(g, d, 0, i, j, k)) lo = 0.5 * (p[c - g.stride[d]] + pP);
@@ -152,6 +156,9 @@ __global__ void k_face_flux(Grid g, const uint16_t* __restrict__ flags, const do
 // replaced by their imposed values.
 __device__ __forceinline__ void b_means(Pos pos, const Grid& g, const Params& P, const Fields& F) {
     double v[6] = {0, 0, 0, 0, 0, 0};
+    // (unrolled: the loads of four cells in flight per thread on the
+    // two-blocks-per-SM reduction grid)
+    #pragma unroll 4
     for (long long c = (long long)pos.bid * blockDim.x + threadIdx.x; c < g.N;
          c += (long long)pos.nblk * blockDim.x) {
         uint16_t f = F.flags[c];
@@ -181,18 +188,30 @@ __device__ __forceinline__ void b_grad_u(Pos pos, const Grid& g, const Fields& F
     int i, j, k;
     cell_ijk(g, c, i, j, k);
     uint16_t f = F.flags[c];
+    // between two interior faces (hi - lo) / D = (u_N - u_S) / (2 D): two FP64
+    // operations instead of six (FP64 issue is this kernel's bound)
+    double hiD[3];
+    #pragma unroll
+    for (int a = 0; a < 3 && a < g.dims; ++a) hiD[a] = 0.5 * g.iD[a];
     #pragma unroll
     for (int b = 0; b < 3 && b < g.dims; ++b) {
         const double* u = F.u[b];
         double uP = u[c];
         #pragma unroll
         for (int a = 0; a < 3 && a < g.dims; ++a) {
-            double lo, hi, val;
-            if (interior(g, a, 0, i, j, k)) lo = 0.5 * (u[c - g.stride[a]] + uP);
-            else lo = vel_fixed(g, f, 2 * a, b, val) ? val : uP;
-            if (interior(g, a, 1, i, j, k)) hi = 0.5 * (uP + u[c + g.stride[a]]);
-            else hi = vel_fixed(g, f, 2 * a + 1, b, val) ? val : uP;
-            F.G[(long long)(3 * a + b) * g.N + c] = (hi - lo) * g.iD[a];
+            const bool in_lo = interior(g, a, 0, i, j, k), in_hi = interior(g, a, 1, i, j, k);
+            double G;
+            if (in_lo && in_hi) {
+                G = (u[c + g.stride[a]] - u[c - g.stride[a]]) * hiD[a];
+            } else {
+                double lo, hi, val;
+                if (in_lo) lo = 0.5 * (u[c - g.stride[a]] + uP);
+                else lo = vel_fixed(g, f, 2 * a, b, val) ? val : uP;
+                if (in_hi) hi = 0.5 * (uP + u[c + g.stride[a]]);
+                else hi = vel_fixed(g, f, 2 * a + 1, b, val) ? val : uP;
+                G = (hi - lo) * g.iD[a];
+            }
+            F.G[(long long)(3 * a + b) * g.N + c] = G;
         }
     }
 }
@@ -332,6 +351,15 @@ __device__ inline double conv_src(const Grid& g, const Fields& F, long long c, i
 __device__ __forceinline__ void b_mom_asm(Pos pos, const Grid& g, const Params& P, const Fields& F) {
     double red[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     const long long N = g.N;
+    // loop-invariant factors: (S/Delta)/2 and S/4 per direction, the means
+    double hSoD[3], qS[3], hS[3], xbar[3];
+    #pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        hSoD[d] = 0.5 * g.SoD[d];
+        qS[d] = 0.25 * g.S[d];
+        hS[d] = 0.5 * g.S[d];
+        xbar[d] = d < g.dims ? F.scal[SC_SUM_U + d] * g.iN : 0.0;
+    }
     for (long long c = (long long)pos.bid * blockDim.x + threadIdx.x; c < N;
          c += (long long)pos.nblk * blockDim.x) {
         int i, j, k;
@@ -339,12 +367,14 @@ __device__ __forceinline__ void b_mom_asm(Pos pos, const Grid& g, const Params& 
         const uint16_t f = F.flags[c];
         const double nuP = g.nu + F.nut[c];
         const int idx[3] = {i, j, k};
-        // faces s = 2d + side: neighbour, row coefficient, outflow, transpose weight nu_f S/2
+        // faces s = 2d + side: neighbour, row coefficient, outflow, transpose
+        // weight nu_f S/2 (a boundary face: nu_P S/2 with the cell itself as
+        // the neighbour, so that w (G_P + G_N) is the flux nu_P G_P S of the
+        // cell value)
         double a[6], fo[6], w[6];
         long long nb[6];
         bool has[6];
-        double aPi = 0.0;   // the interior-face part of aP, common to the components
-        double A1n = 0.0;   // sum of the neighbour coefficients
+        double aPi = 0.0;   // the interior-face part of aP (= -sum a_N), common to the components
         #pragma unroll
         for (int s = 0; s < 6; ++s) {
             const int d = s >> 1, side = s & 1;
@@ -356,17 +386,22 @@ __device__ __forceinline__ void b_mom_asm(Pos pos, const Grid& g, const Params& 
             if (d >= g.dims) continue;
             const double Fb = F.phi[d][face_lo(g, d, i, j, k) + (side ? face_stride(g, d) : 0)];
             fo[s] = side ? Fb : -Fb;
+            w[s] = hS[d] * nuP;
             if (!(side ? idx[d] < g.n[d] - 1 : idx[d] > 0)) continue;
             const long long nc = side ? c + g.stride[d] : c - g.stride[d];
-            const double nuf = 0.5 * (nuP + (g.nu + F.nut[nc]));
-            const double Dif = nuf * g.SoD[d];
+            // nu_f = (nu_eff,P + nu_eff,N)/2 folded into the factors
+            const double nus = nuP + (g.nu + F.nut[nc]);
+            const double Dif = nus * hSoD[d];
             has[s] = true;
             nb[s] = nc;
             a[s] = fmin(fo[s], 0.0) - Dif;
-            aPi += fmax(-fo[s], 0.0) + Dif;
-            A1n += a[s];
-            w[s] = (0.5 * g.S[d]) * nuf;
+            aPi -= a[s];
+            w[s] = qS[d] * nus;
         }
+        // w_hi - w_lo per direction (the transpose term's weight of G_P)
+        double dw[3];
+        #pragma unroll
+        for (int d = 0; d < 3; ++d) dw[d] = w[2 * d + 1] - w[2 * d];
         // keep the row for the smoother (FP64 path) and HbyA (same phi and nu_t later in the sweep)
         #pragma unroll
         for (int s = 0; s < 6 && s < 2 * g.dims; ++s) F.mrow[(long long)(3 + s) * N + c] = a[s];
@@ -386,16 +421,16 @@ __device__ __forceinline__ void b_mom_asm(Pos pos, const Grid& g, const Params& 
             }
             F.mrow[(long long)q * N + c] = aP;
             // explicit div(nu_eff (grad u)^T): face flux nu_f (d u_a/d x_q)_f S_a
-            // through the a-faces (the cell's values on boundary faces)
+            // through the a-faces (the cell's values on boundary faces):
+            // w_hi (G_P + G_hi) - w_lo (G_P + G_lo), three FMAs per direction
             double T = 0.0;
             #pragma unroll
             for (int ad = 0; ad < 3 && ad < g.dims; ++ad) {
                 const double* Gq = F.G + (long long)(3 * q + ad) * N;
                 const double GP = Gq[c];
-                const double fb = nuP * GP * g.S[ad];
-                const double flo = has[2 * ad] ? w[2 * ad] * (GP + Gq[nb[2 * ad]]) : fb;
-                const double fhi = has[2 * ad + 1] ? w[2 * ad + 1] * (GP + Gq[nb[2 * ad + 1]]) : fb;
-                T += fhi - flo;
+                T = fma(-w[2 * ad], Gq[nb[2 * ad]], T);
+                T = fma(w[2 * ad + 1], Gq[nb[2 * ad + 1]], T);
+                T = fma(dw[ad], GP, T);
             }
             double b0 = bnd + T;
             if (g.conv) b0 += conv_src(g, F, c, i, j, k, q);
@@ -417,11 +452,12 @@ __device__ __forceinline__ void b_mom_asm(Pos pos, const Grid& g, const Params& 
                     if (!vel_row_fixed(g, F, nb[s], q, xN)) xN = F.u[q][nb[s]];
                     Ax += a[s] * xN;
                 }
-                const double A1 = aP + A1n;
-                const double xbar = F.scal[SC_SUM_U + q] * g.iN;
+                // row sum: the boundary part of aP (the interior part cancels
+                // the neighbour coefficients)
+                const double A1 = aP - aPi;
                 red[3 * q + 0] += fabs(bfull - Ax);
-                red[3 * q + 1] += fabs(Ax - A1 * xbar);
-                red[3 * q + 2] += fabs(bfull - A1 * xbar);
+                red[3 * q + 1] += fabs(Ax - A1 * xbar[q]);
+                red[3 * q + 2] += fabs(bfull - A1 * xbar[q]);
                 // defect of the relaxed system at the initial guess: with
                 // x_P = u_old the relaxation terms cancel, leaving b - A x
                 if (F.mixed) F.r32[q][c] = (float)(bfull - Ax);
@@ -616,12 +652,20 @@ __device__ __forceinline__ void b_update(Pos pos, const Grid& g, const Params& P
         double prP = prelax(F.p, F.pn, c, a);
         #pragma unroll
         for (int d = 0; d < 3 && d < g.dims; ++d) {
-            double lo, hi;
-            if (interior(g, d, 0, i, j, k)) lo = 0.5 * (prelax(F.p, F.pn, c - g.stride[d], a) + prP);
-            else lo = p_fixed(g, 2 * d) ? g.p_out : prP;
-            if (interior(g, d, 1, i, j, k)) hi = 0.5 * (prP + prelax(F.p, F.pn, c + g.stride[d], a));
-            else hi = p_fixed(g, 2 * d + 1) ? g.p_out : prP;
-            double gp = (hi - lo) * g.iD[d];
+            const bool in_lo = interior(g, d, 0, i, j, k), in_hi = interior(g, d, 1, i, j, k);
+            double gp;
+            if (in_lo && in_hi) {
+                // (p_N - p_S) / (2 Delta) of the relaxed pressure
+                gp = (prelax(F.p, F.pn, c + g.stride[d], a) - prelax(F.p, F.pn, c - g.stride[d], a)) *
+                     (0.5 * g.iD[d]);
+            } else {
+                double lo, hi;
+                if (in_lo) lo = 0.5 * (prelax(F.p, F.pn, c - g.stride[d], a) + prP);
+                else lo = p_fixed(g, 2 * d) ? g.p_out : prP;
+                if (in_hi) hi = 0.5 * (prP + prelax(F.p, F.pn, c + g.stride[d], a));
+                else hi = p_fixed(g, 2 * d + 1) ? g.p_out : prP;
+                gp = (hi - lo) * g.iD[d];
+            }
             F.u[d][c] = F.HbyA[d][c] - F.rAU[c] * gp;
         }
         F.pr[c] = prP;

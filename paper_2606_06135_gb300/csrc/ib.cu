@@ -330,7 +330,7 @@ __device__ __forceinline__ void b_imposed(Pos pos, const Grid& g, int model, int
     double wS = bl.wS[q], w1 = bl.w1[q], w2 = bl.w2[q], ye = bl.ywf[q];
     bool turb = model != HFDIB_LAMINAR;
     double kP = turb ? kf[c] : 0.0;
-    double ut = pow(C_MU, 0.25) * sqrt(kP);
+    double ut = sqrt(sqrt(C_MU)) * sqrt(kP);   // C_mu^(1/4) sqrt(k)
     double yplus = ye * ut / g.nu;
     bool lamb = turb ? (yplus <= YPLUS_LAM) : true;
     int old = bl.lamb[q];
@@ -340,9 +340,17 @@ __device__ __forceinline__ void b_imposed(Pos pos, const Grid& g, int model, int
     bl.yplus[q] = yplus;
     bl.lamb[q] = lamb ? 1 : 0;
     // diagnostics: branch population and changes (integer-valued sums are
-    // exact in any order)
-    if (lamb) atomicAdd(scal + SC_NLAM, 1.0);
-    if (old != (lamb ? 1 : 0)) atomicAdd(scal + SC_NSWITCH, 1.0);
+    // exact in any order), counted per warp and added once per warp: a
+    // floating-point atomic per cell on one address serialises at L2
+    {
+        const unsigned int act = __activemask();
+        const unsigned int nl = __popc(__ballot_sync(act, lamb));
+        const unsigned int ns = __popc(__ballot_sync(act, old != (lamb ? 1 : 0)));
+        if ((int)(threadIdx.x & 31) == __ffs(act) - 1) {
+            if (nl) atomicAdd(scal + SC_NLAM, (double)nl);
+            if (ns) atomicAdd(scal + SC_NSWITCH, (double)ns);
+        }
+    }
     uint16_t f = flags[c];
     f = lamb ? (uint16_t)(f | F_AU) : (uint16_t)(f & ~F_AU);
     flags[c] = f;

@@ -91,6 +91,7 @@ struct Fields {
     double* bt;        // relaxed right-hand side
     double* diag;      // relaxed diagonal
     double* ywall;
+    double* iyw;       // k-omega SST: 1 / max(ywall, 1e-3 h), set at create (ywall is fixed)
     uint16_t* flags;
     // pressure solver
     double* prhs;
@@ -215,7 +216,9 @@ enum { PH_START = 0, PH_BUILD0 = 1, PH_COARSEN = 2, PH_R0 = 3, PH_VC_SMOOTH0 = 4
        PH_R0_SHARE = 14, PH_TB_TABLE = 15, PH_TB_LEVEL = 16, PH_TAIL_IN = 17, PH_TAIL_DONE = 18,
        // inside the tail (pcg_ops.cuh): a block-wide level down, the coarsest
        // part, a block-wide level up
-       PH_TL_DOWN = 19, PH_TL_WARP = 20, PH_TL_UP = 21 };
+       PH_TL_DOWN = 19, PH_TL_WARP = 20, PH_TL_UP = 21,
+       // within block 0: the cell loop of a CG phase done, its block partial written
+       PH_B0_LOOP = 22, PH_B0_PART = 23 };
 void launch_p_coef32(const Grid& g, const MgLevels& M, const MgLevels32& M32, cudaStream_t s);
 // mixed path: FP32 red-black pass on the momentum correction; finalize (the
 // last pass of each colour) adds the correction to u* in FP64
@@ -323,5 +326,6 @@ void launch_scal_smooth(const Grid& g, const Params& P, const Fields& F, int eq,
                         cudaStream_t s);
 void launch_k_prep(const Grid& g, const Params& P, const Fields& F, cudaStream_t s);
 void launch_turb_final(const Grid& g, const Params& P, const Fields& F, cudaStream_t s);
+void launch_inv_wall_distance(const Grid& g, const Fields& F, cudaStream_t s);
 
 }  // namespace hf

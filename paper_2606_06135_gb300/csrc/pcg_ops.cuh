@@ -139,34 +139,40 @@ __device__ void pl_red_start(const LevelT<T>& Lr, int t0, int TT) {
     }
 }
 
+// sum of the residuals b - A x of the children of coarse cell (I, J, K) on
+// fine level F.  The children's loads are issued together: a missing child
+// (odd fine size) is computed on the first child, which always exists, and
+// dropped by a select, so the sum equals the sum over the existing children
+// bit for bit.  (3D: one layer of four children at a time, which bounds the
+// registers that the loads in flight take.)
+template <int D, typename T>
+__device__ __forceinline__ T pl_child_sum(const LevelT<T>& F, int I, int J, int K) {
+    T sum = T(0);
+#pragma unroll 1
+    for (int oz = 0; oz < (D == 3 ? 2 : 1); ++oz) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = 2 * I + (q & 1), j = 2 * J + (q >> 1), k = 2 * K + oz;
+            const bool in = i < F.nx && j < F.ny && (D == 2 || k < F.nz);
+            const int ic = in ? i : 2 * I, jc = in ? j : 2 * J, kc = in ? k : 2 * K;
+            const int c = (kc * F.ny + jc) * F.nx + ic;
+            const T r = F.b[c] - (F.diag[c] * F.x[c] - pl_offsum<D>(F, F.x, c, ic, jc, kc));
+            sum += in ? r : T(0);
+        }
+    }
+    return sum;
+}
+
 // b_C = sum of the children's residuals; fuse_red: also the zero-start red
-// half sweep of the coarse level (x_C = b_C / diag_C on red cells).  The
-// children's loads are issued together: a missing child (odd fine size) is
-// computed on the first child, which always exists, and dropped by a
-// select, so the sum equals the sum over the existing children bit for bit.
+// half sweep of the coarse level (x_C = b_C / diag_C on red cells)
 template <int D, typename T>
 __device__ void pl_restrict(const LevelT<T>& Fr, const LevelT<T>& Cr, bool fuse_red, int t0, int TT) {
     const LevelT<T> F = Fr, Cc = Cr;
-    constexpr int NCH = D == 3 ? 8 : 4;
     const int NC = (int)Cc.N;
     for (int C = t0; C < NC; C += TT) {
         int I, J, K;
         pl_ijk<D>(Cc, C, I, J, K);
-        T sum = T(0);
-        // (3D: one layer of four children at a time, which bounds the
-        // registers that the loads in flight take)
-#pragma unroll 1
-        for (int oz = 0; oz < NCH / 4; ++oz) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int i = 2 * I + (q & 1), j = 2 * J + (q >> 1), k = 2 * K + oz;
-                const bool in = i < F.nx && j < F.ny && (D == 2 || k < F.nz);
-                const int ic = in ? i : 2 * I, jc = in ? j : 2 * J, kc = in ? k : 2 * K;
-                const int c = (kc * F.ny + jc) * F.nx + ic;
-                const T r = F.b[c] - (F.diag[c] * F.x[c] - pl_offsum<D>(F, F.x, c, ic, jc, kc));
-                sum += in ? r : T(0);
-            }
-        }
+        const T sum = pl_child_sum<D>(F, I, J, K);
         Cc.b[C] = sum;
         if (fuse_red && ((I + J + K) & 1) == 0) Cc.x[C] = sum * Cc.idg[C];
     }
@@ -206,6 +212,56 @@ __device__ void pl_prolong_black(const LevelT<T>& Lr, const LevelT<T>& Cr, int t
             const T czm = L.cf[2][c], czp = L.cf[2][c + s];
             const T vzm = L.x[c + (km - k) * s] + Cc.x[((km >> 1) * Cc.ny + (j >> 1)) * Cc.nx + (i >> 1)];
             const T vzp = L.x[c + (kp - k) * s] + Cc.x[((kp >> 1) * Cc.ny + (j >> 1)) * Cc.nx + (i >> 1)];
+            acc = zm ? pl_fma(czm, vzm, acc) : acc;
+            acc = zp ? pl_fma(czp, vzp, acc) : acc;
+        }
+        L.x[c] = acc * L.idg[c];
+    }
+}
+
+// The value of coarse cell P = (I, J, K) after the coarse level's red half
+// sweep of the way up: stored for a black cell; for a red cell recomputed
+// from its (black) neighbours exactly as pl_smooth computes it.  Lets a
+// prolongation read the red half sweep's result without a grid phase for it.
+template <int D, typename T>
+__device__ __forceinline__ T pl_coarse_final(const LevelT<T>& C, int I, int J, int K) {
+    const int P = (K * C.ny + J) * C.nx + I;
+    if (((I + J + K) & 1) != 0) return C.x[P];
+    return (C.b[P] + pl_offsum<D>(C, C.x, P, I, J, K)) * C.idg[P];
+}
+
+// pl_prolong_black with the coarse level's red half sweep folded in: the
+// coarse values are read through pl_coarse_final (the coarse level's red
+// cells are then never written; nothing reads them before the next V-cycle
+// sets them again)
+template <int D, typename T>
+__device__ void pl_prolong_black_red(const LevelT<T>& Lr, const LevelT<T>& Cr, int t0, int TT) {
+    const LevelT<T> L = Lr, Cc = Cr;
+    const int NP = pl_npairs(L);
+    for (int p = t0; p < NP; p += TT) {
+        int i, j, k, c;
+        if (!pl_pair_cell<D>(L, p, 1, i, j, k, c)) continue;
+        const bool xm = i > 0, xp = i < L.nx - 1, ym = j > 0, yp = j < L.ny - 1;
+        const int im = xm ? i - 1 : i, ip = xp ? i + 1 : i, jm = ym ? j - 1 : j, jp = yp ? j + 1 : j;
+        const int K = k >> 1;
+        const int fx = pl_fx(L, i, j, k), fy = pl_fy(L, i, j, k);
+        const T cxm = L.cf[0][fx], cxp = L.cf[0][fx + 1], cym = L.cf[1][fy], cyp = L.cf[1][fy + L.nx];
+        const T vxm = L.x[c + (im - i)] + pl_coarse_final<D>(Cc, im >> 1, j >> 1, K);
+        const T vxp = L.x[c + (ip - i)] + pl_coarse_final<D>(Cc, ip >> 1, j >> 1, K);
+        const T vym = L.x[c + (jm - j) * L.nx] + pl_coarse_final<D>(Cc, i >> 1, jm >> 1, K);
+        const T vyp = L.x[c + (jp - j) * L.nx] + pl_coarse_final<D>(Cc, i >> 1, jp >> 1, K);
+        T acc = L.b[c];
+        acc = xm ? pl_fma(cxm, vxm, acc) : acc;
+        acc = xp ? pl_fma(cxp, vxp, acc) : acc;
+        acc = ym ? pl_fma(cym, vym, acc) : acc;
+        acc = yp ? pl_fma(cyp, vyp, acc) : acc;
+        if (D == 3) {
+            const int s = L.nx * L.ny;
+            const bool zm = k > 0, zp = k < L.nz - 1;
+            const int km = zm ? k - 1 : k, kp = zp ? k + 1 : k;
+            const T czm = L.cf[2][c], czp = L.cf[2][c + s];
+            const T vzm = L.x[c + (km - k) * s] + pl_coarse_final<D>(Cc, i >> 1, j >> 1, km >> 1);
+            const T vzp = L.x[c + (kp - k) * s] + pl_coarse_final<D>(Cc, i >> 1, j >> 1, kp >> 1);
             acc = zm ? pl_fma(czm, vzm, acc) : acc;
             acc = zp ? pl_fma(czp, vzp, acc) : acc;
         }

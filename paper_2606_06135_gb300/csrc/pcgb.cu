@@ -158,6 +158,16 @@ __device__ inline void pb_sync(const PcgbArgs<MT>& A, int tag) {
     pb_mark(A, tag);
 }
 
+// sm[0 .. n-1] (n <= 32) summed by one warp in a fixed shuffle tree; the sum
+// is valid in lane 0 (a serial sum by one thread would chain 32 FP64 adds,
+// each waiting for the last)
+__device__ __forceinline__ double pb_warp_sum(const double* sm, int n) {
+    const int lane = threadIdx.x & 31;
+    double y = lane < n ? sm[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) y += __shfl_down_sync(0xffffffffu, y, o);
+    return y;
+}
+
 // Block partial of v into slot q: summed in the type of v per thread and
 // across the lanes of a warp, in FP64 across the warps of the block.
 template <typename AT>
@@ -168,10 +178,9 @@ __device__ inline void pb_partial(double* part, int q, AT v) {
     __syncthreads();
     if (lane == 0) sm[warp] = (double)v;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double x = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += sm[w];
-        part[(long long)q * gridDim.x + blockIdx.x] = x;
+    if (warp == 0) {
+        const double x = pb_warp_sum(sm, (int)(blockDim.x >> 5));
+        if (lane == 0) part[(long long)q * gridDim.x + blockIdx.x] = x;
     }
 }
 
@@ -196,10 +205,12 @@ __device__ inline void pb_totals(const double* part, int q0, double (&out)[NV]) 
 #pragma unroll
         for (int v = 0; v < NV; ++v) sm[v][warp] = x[v];
     __syncthreads();
-    if (threadIdx.x < NV) {
-        double y = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) y += sm[threadIdx.x][w];
-        res[threadIdx.x] = y;
+    if (warp == 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const double y = pb_warp_sum(sm[v], (int)(blockDim.x >> 5));
+            if (lane == 0) res[v] = y;
+        }
     }
     __syncthreads();
 #pragma unroll
@@ -217,10 +228,9 @@ __device__ inline double pb_total(const double* part, int q) {
     __syncthreads();
     if (lane == 0) sm[warp] = x;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double y = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) y += sm[w];
-        res = y;
+    if (warp == 0) {
+        const double y = pb_warp_sum(sm, (int)(blockDim.x >> 5));
+        if (lane == 0) res = y;
     }
     __syncthreads();
     return res;
@@ -232,6 +242,9 @@ enum { QB_RZ = 0, QB_RR = 1, QB_R1 = 2, QB_R2 = 3, QB_R3 = 4, QB_DQ = 5 };
 // this launch out (its batch solve has stopped)
 struct PbState {
     double rz[PB_MAXB], rzp[PB_MAXB], tol2[PB_MAXB], dq[PB_MAXB], rr[PB_MAXB];
+    // the CG step scalars, formed once by thread 0: an FP64 division by every
+    // thread of a block costs microseconds on this GPU
+    double alpha[PB_MAXB], beta[PB_MAXB];
     int it[PB_MAXB], done[PB_MAXB], off[PB_MAXB];
 };
 
@@ -436,6 +449,11 @@ __device__ void pb_vcycle(const PcgbArgs<MT>& A, const PbState& S, int t0, int T
             if (!S.done[b]) pl_smooth<D>(pb_level(A.D[b], 0, rsel), 1, t0, TT);
         pb_sync(A, PH_VC_SMOOTH0);
     }
+    // Down: restriction (with the coarse level's zero-start red half sweep),
+    // then the black half sweep.  (Folding the black half sweep into the
+    // restriction, with each black coarse cell recomputing its red
+    // neighbours from their children, measured three times slower than the
+    // two phases.)
     for (int l = 0; l + 1 < A.maxlev; ++l) {
         bool any = false;
         for (int b = 0; b < B; ++b) {
@@ -488,18 +506,31 @@ __device__ void pb_vcycle(const PcgbArgs<MT>& A, const PbState& S, int t0, int T
         }
     }
     if (tails) pb_sync(A, PH_VC_TAIL);
+    // Up: prolongation with the black half sweep, then the red half sweep.
+    // In 2D the red half sweep of a grid level l >= 1 has no phase of its
+    // own: the prolongation into level l - 1 recomputes the red values it
+    // reads (pl_prolong_black_red), which saves one grid phase per level.
+    // (In 3D a fine black cell would recompute six coarse red cells, more
+    // work than the phase it saves.)
+    constexpr bool fold_red = D == 2;
     for (int l = A.maxlev - 1; l >= 0; --l) {
         bool any = false;
         for (int b = 0; b < B; ++b) {
             const PcgbDesign<MT>& Dz = A.D[b];
             if (S.done[b] || l >= Dz.lf) continue;
             any = true;
-            if (l + 1 < Dz.M.nl) pl_prolong_black<D>(pb_level(Dz, l, rsel), Dz.M.lv[l + 1], t0, TT);
-            else pl_smooth<D>(pb_level(Dz, l, rsel), 1, t0, TT);
+            if (l + 1 < Dz.M.nl) {
+                if (fold_red && l + 1 < Dz.lf)
+                    pl_prolong_black_red<D>(pb_level(Dz, l, rsel), Dz.M.lv[l + 1], t0, TT);
+                else
+                    pl_prolong_black<D>(pb_level(Dz, l, rsel), Dz.M.lv[l + 1], t0, TT);
+            } else {
+                pl_smooth<D>(pb_level(Dz, l, rsel), 1, t0, TT);
+            }
         }
         if (!any) continue;
         pb_sync(A, PH_VC_PROLONG);
-        if (l > 0) {
+        if (l > 0 && !fold_red) {
             for (int b = 0; b < B; ++b) {
                 const PcgbDesign<MT>& Dz = A.D[b];
                 if (!S.done[b] && l < Dz.lf) pl_smooth<D>(pb_level(Dz, l, rsel), 0, t0, TT);
@@ -651,7 +682,10 @@ __global__ void __launch_bounds__(1024, 1) k_pressure_pcg(PcgbArgs<MT> A) {
     for (int b = 0; b < B; ++b) {
         if (S.off[b]) continue;
         const double rz = pb_total(A.D[b].part, QB_RZ);
-        if (threadIdx.x == 0) S.rz[b] = rz;
+        if (threadIdx.x == 0) {
+            S.rz[b] = rz;
+            S.beta[b] = 0.0;
+        }
     }
     __syncthreads();
     for (int iter = 0; iter < A.maxit; ++iter) {
@@ -664,7 +698,7 @@ __global__ void __launch_bounds__(1024, 1) k_pressure_pcg(PcgbArgs<MT> A) {
             if (S.done[b]) continue;
             const PcgbDesign<MT>& Dz = A.D[b];
             const int it = S.it[b];
-            const double beta = it == 0 ? 0.0 : S.rz[b] / S.rzp[b];
+            const double beta = S.beta[b];
             // one x-pair per thread: both cells' loads issue before the
             // first store (a cell loop would wait for its first cell's
             // stores before loading the second)
@@ -699,7 +733,9 @@ __global__ void __launch_bounds__(1024, 1) k_pressure_pcg(PcgbArgs<MT> A) {
                         s_dq += dP[1] * qv[1];
                     }
                 }
+                pb_mark(A, PH_B0_LOOP);
                 pb_partial(Dz.part, QB_DQ, s_dq);
+                pb_mark(A, PH_B0_PART);
             } else {
                 const Fields& F = Dz.F;
                 const Level L0 = Dz.L0d;
@@ -738,7 +774,10 @@ __global__ void __launch_bounds__(1024, 1) k_pressure_pcg(PcgbArgs<MT> A) {
         for (int b = 0; b < B; ++b) {
             if (S.done[b]) continue;
             const double dq = pb_total(A.D[b].part, QB_DQ);
-            if (threadIdx.x == 0) S.dq[b] = dq;
+            if (threadIdx.x == 0) {
+                S.dq[b] = dq;
+                S.alpha[b] = dq != 0.0 ? S.rz[b] / dq : 0.0;
+            }
         }
         __syncthreads();
         // x += alpha d (FP64 path: p += alpha d); r -= alpha q into the other
@@ -749,12 +788,14 @@ __global__ void __launch_bounds__(1024, 1) k_pressure_pcg(PcgbArgs<MT> A) {
             if (S.done[b]) continue;
             const PcgbDesign<MT>& Dz = A.D[b];
             const LevelT<MT> P0 = Dz.M.lv[0];
-            const double alpha = S.dq[b] != 0.0 ? S.rz[b] / S.dq[b] : 0.0;
+            const double alpha = S.alpha[b];
             const int it1 = (S.it[b] + 1) & 1;
             if constexpr (fp32) {
                 const float s_r2 = pb_update_start<D, float, float>(P0, Dz.x32, Dz.d32[it1], Dz.q32, Dz.rbuf[rin],
                                                                     Dz.rbuf[rout], (float)alpha, t0, TT);
+                pb_mark(A, PH_B0_LOOP);
                 pb_partial(Dz.part, QB_RR, s_r2);
+                pb_mark(A, PH_B0_PART);
             } else {
                 const Fields& F = Dz.F;
                 const double s_r2 = pb_update_start<D, double, double>(P0, F.pn, F.d[it1], F.q, Dz.rbuf[rin],
@@ -776,6 +817,7 @@ __global__ void __launch_bounds__(1024, 1) k_pressure_pcg(PcgbArgs<MT> A) {
             if (threadIdx.x == 0) {
                 S.rzp[b] = S.rz[b];
                 S.rz[b] = rz;
+                S.beta[b] = rz / S.rzp[b];
                 S.it[b] += 1;
                 if (!(S.rr[b] > S.tol2[b]) || S.it[b] >= A.maxit) S.done[b] = 1;
             }

@@ -31,10 +31,24 @@ __device__ inline double grad_s(const Grid& g, const double* x, uint16_t f, doub
     return (hi - lo) * g.iD[d];
 }
 
-__device__ inline double sst_F2(double kk, double ww, double y, double nu) {
+// tanh of x >= 0: 1 for x >= 19.5, where tanh(x) = 1 - 2 e^(-2x) + ... is
+// within half an ulp of 1 and rounds to 1 (the call is skipped there)
+__device__ inline double tanh_pos(double x) { return x >= 19.5 ? 1.0 : tanh(x); }
+
+// Menter's F2 from k, 1/omega and 1/y (reciprocals shared with the caller:
+// an FP64 division is many FP64 operations on this GPU)
+__device__ inline double sst_F2(double kk, double iw, double iy, double nu) {
     double sk = sqrt(kk);
-    double arg2 = fmin(fmax(2.0 * sk / (SST_BSTAR * ww * y), 500.0 * nu / (y * y * ww)), 100.0);
-    return tanh(arg2 * arg2);
+    double arg2 = fmin(fmax(2.0 * sk * iw * iy * (1.0 / SST_BSTAR), 500.0 * nu * iy * iy * iw), 100.0);
+    return tanh_pos(arg2 * arg2);
+}
+
+__global__ void k_inv_wall_distance(Grid g, Fields F) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < g.N) F.iyw[c] = 1.0 / fmax(F.ywall[c], 1e-3 * g.h);
+}
+void launch_inv_wall_distance(const Grid& g, const Fields& F, cudaStream_t s) {
+    k_inv_wall_distance<<<nblocks(g.N), BLOCK, 0, s>>>(g, F);
 }
 
 // ---------------------------------------------------------------- a9 production
@@ -44,15 +58,21 @@ __device__ __forceinline__ void b_turb_prep(Pos pos, const Grid& g, const Params
     int i, j, k;
     cell_ijk(g, c, i, j, k);
     uint16_t f = F.flags[c];
-    double S2 = 0.0;
+    // S2 = 2 S:S with S = (G + G^T)/2: the diagonal gives 2 G_aa^2, each
+    // off-diagonal pair (G_ab + G_ba)^2 (a third of the FP64 operations of
+    // the full double sum)
+    double Sd = 0.0, So = 0.0;
     #pragma unroll
-    for (int a = 0; a < 3 && a < g.dims; ++a)
+    for (int a = 0; a < 3 && a < g.dims; ++a) {
+        const double gaa = F.G[(long long)(4 * a) * g.N + c];
+        Sd += gaa * gaa;
         #pragma unroll
-        for (int b = 0; b < 3 && b < g.dims; ++b) {
-            double s = 0.5 * (F.G[(long long)(3 * a + b) * g.N + c] + F.G[(long long)(3 * b + a) * g.N + c]);
-            S2 += s * s;
+        for (int b = a + 1; b < 3 && b < g.dims; ++b) {
+            const double o = F.G[(long long)(3 * a + b) * g.N + c] + F.G[(long long)(3 * b + a) * g.N + c];
+            So += o * o;
         }
-    S2 = 2.0 * S2;
+    }
+    const double S2 = 2.0 * Sd + So;
     double nut = F.nut[c];
     double Pk = tag_of(f) == TAG_IC ? 0.0 : nut * S2;
     F.S2[c] = S2;
@@ -61,10 +81,10 @@ __device__ __forceinline__ void b_turb_prep(Pos pos, const Grid& g, const Params
     double V = g.V;
     if (P.model == HFDIB_KEPSILON) {
         double ratio = wold / fmax(kold, K_MIN);
-        F.gam[c] = g.nu + nut / KE_SIGE;
+        F.gam[c] = g.nu + nut * (1.0 / KE_SIGE);
         F.sp[c] = KE_C2 * ratio * V;
         F.src[c] = KE_C1 * (nut * S2) * ratio * V;
-        F.gamk[c] = g.nu + nut / KE_SIGK;
+        F.gamk[c] = g.nu + nut * (1.0 / KE_SIGK);
         if (F.mixed) { F.gam32[c] = (float)F.gam[c]; F.gamk32[c] = (float)F.gamk[c]; }
     } else if (P.model == HFDIB_KOMEGA) {
         // Eq. hfdibkomega: omega source C_alpha1 (omega/k) P_k, sink C_beta1 omega^2
@@ -106,29 +126,29 @@ __device__ __forceinline__ void b_turb_prep(Pos pos, const Grid& g, const Params
         double kk = fmax(kold, K_MIN);
         double eta = S * kk / wold;
         double C1 = fmax(0.43, eta / (eta + 5.0));
-        F.gam[c] = g.nu + nut / RKE_SIGE;
+        F.gam[c] = g.nu + nut * (1.0 / RKE_SIGE);
         F.sp[c] = RKE_C2 * wold / (kk + sqrt(g.nu * wold)) * V;
         F.src[c] = C1 * S * wold * V;
-        F.gamk[c] = g.nu + nut / RKE_SIGK;
+        F.gamk[c] = g.nu + nut * (1.0 / RKE_SIGK);
         if (F.mixed) { F.gam32[c] = (float)F.gam[c]; F.gamk32[c] = (float)F.gamk[c]; }
     } else {
         double gk = 0.0;
         #pragma unroll
         for (int d = 0; d < 3 && d < g.dims; ++d)
             gk += grad_s(g, F.k, f, P.k_in, c, d, i, j, k) * grad_s(g, F.w, f, P.w_in, c, d, i, j, k);
-        double y = fmax(F.ywall[c], 1e-3 * g.h);
         double kk = fmax(kold, K_MIN), ww = wold;
-        // reciprocals once: FP64 division is many FP64 operations on this GPU
-        double iw = 1.0 / ww, iy = 1.0 / y;
+        // reciprocals once (1/y is stored): FP64 division is many FP64
+        // operations on this GPU
+        double iw = 1.0 / ww, iy = F.iyw[c];
         double CDkw = 2.0 * SST_AW2 * gk * iw;
         double CDp = fmax(CDkw, 1e-10);
         double sk = sqrt(kk);
         double t_k = sk * iw * iy * (1.0 / SST_BSTAR);     // sqrt(k) / (beta* omega y)
         double t_nu = 500.0 * g.nu * iy * iy * iw;          // 500 nu / (y^2 omega)
         double arg1 = fmin(fmax(t_k, t_nu), 4.0 * SST_AW2 * kk * iy * iy / CDp);
-        double F1 = tanh(arg1 * arg1 * arg1 * arg1);
+        double F1 = tanh_pos(arg1 * arg1 * arg1 * arg1);
         double arg2 = fmin(fmax(2.0 * t_k, t_nu), 100.0);   // F2 of the same k, omega, y
-        double F2 = tanh(arg2 * arg2);
+        double F2 = tanh_pos(arg2 * arg2);
         double gamma = F1 * SST_G1 + (1.0 - F1) * SST_G2;
         double beta = F1 * SST_B1 + (1.0 - F1) * SST_B2;
         double GbyNu = fmin(S2, (SST_C1 / SST_A1) * SST_BSTAR * wold * fmax(SST_A1 * wold, SST_BB1 * F2 * sqrt(S2)));
@@ -185,6 +205,7 @@ __device__ inline bool scal_row_fixed(const Grid& g, const Fields& F, int eq, lo
 template <typename T>
 struct ScalRowT {
     T aP, bnd;
+    T aPi;        // the interior-face part of aP (= -sum a)
     T a[6];
     long long nb[6];
     bool has[6];
@@ -197,35 +218,40 @@ template <typename T>
 __device__ void scal_row_t(const Grid& g, T* const* phi, const T* gam, double xin, long long c, int i, int j,
                            int k, uint16_t f, ScalRowT<T>& R) {
     T gP = gam[c];
-    R.aP = T(0);
+    T aPi = T(0), aPb = T(0);
     R.bnd = T(0);
     #pragma unroll
     for (int d = 0; d < 3 && d < g.dims; ++d) {
         long long fl = face_lo(g, d, i, j, k);
         long long fs = face_stride(g, d);
+        const T hSoD = (T)(0.5 * g.SoD[d]);
         for (int side = 0; side < 2; ++side) {
             int s = 2 * d + side;
             T Fb = phi[d][fl + side * fs];
             T Fout = side ? Fb : -Fb;
             if (interior_t(g, d, side, i, j, k)) {
                 long long nc = side ? c + g.stride[d] : c - g.stride[d];
-                T Dif = T(0.5) * (gP + gam[nc]) * (T)g.SoD[d];
+                // Dif = (gamma_P + gamma_N)/2 S/Delta; aP gains
+                // max(-Fout, 0) + Dif = -a (five operations a face)
+                T Dif = (gP + gam[nc]) * hSoD;
                 R.a[s] = fmin(Fout, T(0)) - Dif;
                 R.nb[s] = nc;
                 R.has[s] = true;
-                R.aP += fmax(-Fout, T(0)) + Dif;
+                aPi -= R.a[s];
             } else {
                 R.a[s] = T(0);
                 R.nb[s] = c;
                 R.has[s] = false;
                 if (scal_fixed(g, f, s)) {
                     T coef = gP * (T)g.SoHD[d] + fmax(-Fout, T(0));
-                    R.aP += coef;
+                    aPb += coef;
                     R.bnd += coef * (T)xin;
                 }
             }
         }
     }
+    R.aPi = aPi;
+    R.aP = aPi + aPb;
 }
 
 __device__ inline void scal_row(const Grid& g, const Fields& F, const double* gam, double xin, long long c, int i,
@@ -258,14 +284,15 @@ __device__ __forceinline__ void b_scal_asm(Pos pos, const Grid& g, const Params&
             x[c] = fv;
             if (F.mixed) F.r32[0][c] = 0.0f;
         } else {
-            double Ax = aP * xold, A1 = aP;
+            double Ax = aP * xold;
+            // row sum: aP + sum a = aP - aPi (the interior part cancels)
+            const double A1 = aP - R.aPi;
             #pragma unroll
             for (int s = 0; s < 6 && s < 2 * g.dims; ++s) {
                 if (!R.has[s]) continue;
                 double xN;
                 if (!scal_row_fixed(g, F, eq, R.nb[s], xN)) xN = x[R.nb[s]];
                 Ax += R.a[s] * xN;
-                A1 += R.a[s];
             }
             double xbar = F.scal[eq == 0 ? SC_SUM_W : SC_SUM_K] * g.iN;
             red[0] += fabs(b - Ax);
@@ -388,8 +415,7 @@ __device__ __forceinline__ void b_turb_final(Pos pos, const Grid& g, const Param
         nut = k / w;
         F.w2[c] = C_MU * k * w;
     } else {
-        double y = fmax(F.ywall[c], 1e-3 * g.h);
-        double F2 = sst_F2(fmax(k, K_MIN), w, y, g.nu);
+        double F2 = sst_F2(fmax(k, K_MIN), 1.0 / w, F.iyw[c], g.nu);
         nut = SST_A1 * k / fmax(SST_A1 * w, SST_BB1 * F2 * sqrt(F.S2[c]));
         F.w2[c] = C_MU * k * w;
     }

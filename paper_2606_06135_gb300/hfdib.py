@@ -31,7 +31,7 @@ OBJECTIVES = {"pressure_drop": 0, "drag": 1}
 PRESSURE_PHASES = ("start", "build0", "coarsen", "r0", "vc_smooth0", "vc_restrict", "vc_smooth", "vc_tail",
                    "vc_prolong", "vc_upsmooth", "vc_final", "cg_product", "cg_update", "end",
                    "b0_r0_share", "b0_tail_table", "b0_tail_level", "b0_tail_in", "b0_tail_done",
-                   "b0_tail_down", "b0_tail_coarse", "b0_tail_up")
+                   "b0_tail_down", "b0_tail_coarse", "b0_tail_up", "b0_loop", "b0_part")
 WALL_SIDES = ("xmin", "xmax", "ymin", "ymax", "zmin", "zmax")
 
 ERR_NOT_CONVERGED = -4
