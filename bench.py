@@ -68,13 +68,13 @@ def replica_rate(units_per_rank, world, seconds):
 # name), from an ncu capture of the kernel as it is now
 # (dram__bytes_read.sum + dram__bytes_write.sum); absent once the kernel
 # changed after the capture.
-TRAFFIC = {}
+TRAFFIC = {("pcg", "mixed", "bfs"): 11.760384e6 + 0.487936e6}   # k_pressure_pcg<float, 2>, 1024 x 256
 
 # FP64 flops of one launch of the FP64 assembly kernels on this workload
 # (ncu: 2 x DFMA + DADD + DMUL thread instructions).  These kernels are bound
 # by FP64 arithmetic, so their roofline is the FP64 rate.  Only the profiling
 # classes that time exactly one kernel are listed.
-FP64_FLOPS = {"mom_asm": 4.7356e7, "turb_final": 3.1783e7, "scal_asm": 1.5748e7}
+FP64_FLOPS = {"mom_asm": 3.7358e7, "turb_final": 2.2377e7, "scal_asm": 1.2334e7}
 FP64_PEAK_GFLOPS = 1250.0   # nominal GB300 FP64 rate (no measured FP64 peak is available)
 
 def class_bytes_per_sweep(dims, mixed, model, piters, n_u=2, n_turb=2):
