@@ -325,6 +325,13 @@ print(json.dumps({"seconds": time.perf_counter() - t0}))
 NACA_NX, NACA_NY, NACA_AOAS = 2048, 1024, 16   # batched multi-lambda workload (16 angles of attack)
 ADJ_DESIGNS = 2                                # random-obstacle designs for the adjoint leg
 C5_DESIGNS = 32                                # random-obstacle designs of the batched-gradient leg (--c5)
+BSOLVE_DESIGNS = 16                            # designs of the batched time-to-1e-6 leg (--batch-solve)
+
+
+def G_SIZE(b):
+    sys.path.insert(0, ROOT)
+    from paper_2606_06135_gb300 import geometry as G
+    return G.grf_design_size(b)
 
 
 def _naca_case(aoa):
@@ -380,19 +387,54 @@ def batch_leg(hfdib, torch, cases, dev, steps, warmup):
             "l2": "working set %.0f MB per field set > L2" % (N * 8 / 1e6)}
 
 
+def batch_solve_leg(hfdib, torch, cases, dev, tol, max_sweeps, opts):
+    """Time to residual tol of B designs: the batched mixed-precision form (one
+    graph launch; the stop test on the device, each design sitting out once it
+    converges) against the plain FP64 GPU SIMPLE solving the same designs one
+    at a time."""
+    import time as _t
+    N = sum(c["grid"]["nx"] * c["grid"]["ny"] for c in cases)
+    bs = hfdib.BatchSolver(cases, device=str(dev), precision=1, **opts)
+    torch.cuda.synchronize(dev)
+    t0 = _t.perf_counter()
+    rc, its, res = bs.solve(tol=tol, max_iter=max_sweeps)
+    torch.cuda.synchronize(dev)
+    tb = _t.perf_counter() - t0
+    bs.close()
+    t64, s64, ok64 = 0.0, [], []
+    for c in cases:
+        s = hfdib.Solver(c, device=str(dev), precision=0, **opts)
+        torch.cuda.synchronize(dev)
+        t0 = _t.perf_counter()
+        rc1, it1, r1 = s.solve(tol=tol, max_iter=max_sweeps, check_every=100, raise_on_fail=False)
+        torch.cuda.synchronize(dev)
+        t64 += _t.perf_counter() - t0
+        s64.append(int(it1))
+        ok64.append(rc1 == 0)
+        s.close()
+    return {"workload": "grf_channel_keps_%d_designs_256x128_to_%dx%d" % ((len(cases),) + G_SIZE(len(cases) - 1)),
+            "designs": len(cases), "cells": N, "tol": tol,
+            "batched_mixed": {"converged": rc == 0, "seconds": tb, "solves_per_s": len(cases) / tb,
+                              "sweeps": [int(v) for v in its], "max_residual": float(res[:, :6].max())},
+            "fp64_one_by_one": {"converged": all(ok64), "seconds": t64, "solves_per_s": len(cases) / t64,
+                                "sweeps": s64},
+            "speedup": t64 / tb}
+
+
 def c5_leg(torch, cases, dev):
     """32 random-obstacle designs of uneven size (256 x 128 ... 512 x 256,
     k-epsilon, Re 1000) through the batched autograd path: the forward pass
-    converges all steady states as one batch (mixed precision, the stop test
-    on the device), the backward pass runs each design's frozen-turbulence
-    adjoint of the pressure drop."""
+    converges all steady states to 1e-10 as one batch (FP64, the stop test on
+    the device: the mixed form's FP32 inner solves stalled some designs above
+    1e-10 within 40 000 sweeps), the backward pass runs each design's
+    frozen-turbulence adjoint of the pressure drop."""
     import time as _t
     from paper_2606_06135_gb300.autograd import pressure_drops
     lams = [torch.tensor(c["lam"], dtype=torch.float64, device=dev, requires_grad=True) for c in cases]
     torch.cuda.synchronize(dev)
     t0 = _t.perf_counter()
-    J = pressure_drops(lams, cases, solve_tol=1e-10, max_sweeps=40000, adj_tol=1e-9, adj_max_iter=40000,
-                       precision=1)
+    J = pressure_drops(lams, cases, solve_tol=1e-10, max_sweeps=60000, adj_tol=1e-9, adj_max_iter=40000,
+                       precision=0)
     torch.cuda.synchronize(dev)
     t1 = _t.perf_counter()
     J.sum().backward()
@@ -446,6 +488,9 @@ def main():
     ap.add_argument("--no-c4", action="store_true", help="skip the 3D Ahmed-body leg")
     ap.add_argument("--no-c1", action="store_true", help="skip the 128 x 64 cylinder leg")
     ap.add_argument("--c5", action="store_true", help="run the 32-design batched-gradient leg (minutes)")
+    ap.add_argument("--batch-solve", action="store_true",
+                    help="time 16 random-obstacle designs to residual 1e-6: batched mixed against FP64 one by one "
+                         "(minutes)")
     ap.add_argument("--only", choices=["c2", "c4"], default=None,
                     help="profiling aid: run only the mixed timed sweeps of the 1024 x 256 step (c2) or of "
                          "the 3D Ahmed-like body (c4), print that leg's numbers and stop")
@@ -460,8 +505,8 @@ def main():
 
     # geometry of the extra legs, generated by spawned workers while the
     # GPU legs run (the pool starts before the first CUDA call)
-    pool, fut_naca, fut_grf, fut_c5 = None, [], [], []
-    if rank == 0 and not args.only and (not args.no_batch or not args.no_adjoint or args.c5):
+    pool, fut_naca, fut_grf, fut_c5, fut_bs = None, [], [], [], []
+    if rank == 0 and not args.only and (not args.no_batch or not args.no_adjoint or args.c5 or args.batch_solve):
         import multiprocessing as mp
         from concurrent.futures import ProcessPoolExecutor
         pool = ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1), mp_context=mp.get_context("spawn"))
@@ -471,6 +516,8 @@ def main():
             fut_grf = [pool.submit(_grf_case, b) for b in range(ADJ_DESIGNS)]
         if args.c5:
             fut_c5 = [pool.submit(_grf_case, b) for b in range(C5_DESIGNS)]
+        if args.batch_solve:
+            fut_bs = [pool.submit(_grf_case, b) for b in range(BSOLVE_DESIGNS)]
 
     import numpy as np
     import torch
@@ -671,12 +718,21 @@ def main():
         out["solve"] = lm
         out["fp64"]["solve"] = lf
         out["fp64"]["solves_per_s"] = lf["solves_per_s"]
+    # optional legs: a leg that fails reports its error instead of ending the run
+    def leg(name, fn):
+        try:
+            out[name] = fn()
+        except Exception as e:   # noqa: BLE001 -- reported in the output line
+            out[name] = {"error": "%s: %s" % (type(e).__name__, e)}
+
     if rank == 0 and fut_naca:
-        out["batch"] = batch_leg(hfdib, torch, [f.result() for f in fut_naca], dev, args.steps, args.warmup)
+        leg("batch", lambda: batch_leg(hfdib, torch, [f.result() for f in fut_naca], dev, args.steps, args.warmup))
     if rank == 0 and fut_grf:
-        out["adjoint"] = adjoint_leg(hfdib, torch, [f.result() for f in fut_grf], dev)
+        leg("adjoint", lambda: adjoint_leg(hfdib, torch, [f.result() for f in fut_grf], dev))
+    if rank == 0 and fut_bs:
+        leg("batch_solve", lambda: batch_solve_leg(hfdib, torch, [f.result() for f in fut_bs], dev, 1e-6, 40000, {}))
     if rank == 0 and fut_c5:
-        out["c5"] = c5_leg(torch, [f.result() for f in fut_c5], dev)
+        leg("c5", lambda: c5_leg(torch, [f.result() for f in fut_c5], dev))
     if pool is not None:
         pool.shutdown()
     if rank == 0 and not args.no_cpu:

@@ -112,6 +112,9 @@ struct Ctx {
     long long tail_cells = 0;   // persistent pressure solve: largest level of the one-block tail
     int coarse_sweeps = 20;
     int use_graph = 0;
+    // F.G holds grad u of the current velocity (left by the last sweep's a9;
+    // cleared by anything that writes the state)
+    bool g_cur = false;
     int parity = 0;              // which of the two sweep graphs matches the p / pr buffers
     cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
@@ -281,6 +284,19 @@ cudaEvent_t prof_event(Prof& p) {
     } while (0)
 
 // ---------------------------------------------------------------- sweep schedule
+// grad u from the turbulence step (a9) of the previous sweep serves the
+// next momentum assembly (a3) whenever that step runs
+static bool grad_u_carried(const Ctx* h) { return h->model != HFDIB_LAMINAR && !h->opt.frozen_turbulence; }
+
+// before a sweep: form grad u if no previous sweep left it for this state
+static void ensure_grad_u(Ctx* h) {
+    if (grad_u_carried(h) && !h->g_cur) {
+        PROF(h, HFDIB_K_GRAD_U, launch_grad_u(h->g, h->F, h->stream));
+        h->launches++;
+    }
+    h->g_cur = grad_u_carried(h);   // true again once the sweep's a9 has run
+}
+
 // Part A: a1-a6 of Fig. simplehfdibrans and (with_pressure) the pressure
 // solve or its set-up.
 void enqueue_part_a(Ctx* h, long long* L, bool with_pressure = true) {
@@ -295,8 +311,11 @@ void enqueue_part_a(Ctx* h, long long* L, bool with_pressure = true) {
     PROF(h, HFDIB_K_IMPOSED, launch_imposed(g, h->model, h->opt.freeze_switch, h->bl, F.flags, F.scal, F.u[0], F.u[1],
                                             F.u[2], F.k, F.uib[0], F.uib[1], F.uib[2], F.kib, F.wib, s));
     PROF(h, HFDIB_K_IMPOSED, launch_means(g, P, F, s));
-    // a3: momentum assembly; a4: predictor; a5: correction (imposed rows)
-    PROF(h, HFDIB_K_GRAD_U, launch_grad_u(g, F, s));
+    // a3: momentum assembly; a4: predictor; a5: correction (imposed rows).
+    // With the turbulence step on, grad u of this velocity was formed by the
+    // last sweep's a9 (the velocity does not change in between): the caller
+    // makes sure of it (ensure_grad_u), so it is not formed again here.
+    if (!grad_u_carried(h)) PROF(h, HFDIB_K_GRAD_U, launch_grad_u(g, F, s));
     if (g.conv == 3) { PROF(h, HFDIB_K_GRAD_U, launch_conv_limit(g, F, s)); (*L)++; }
     PROF(h, HFDIB_K_MOM_ASM, launch_mom_asm(g, P, F, s));
     *L += 4;
@@ -408,6 +427,7 @@ void enqueue_part_b(Ctx* h, long long* L) {
 int run_sweep_host(Ctx* h) {
     long long L = 0;
     cudaGraphConditionalHandle none = 0;
+    ensure_grad_u(h);
     enqueue_part_a(h, &L);
     if (h->pblocks == 0) PROF(h, HFDIB_K_PCG, enqueue_pcg_start(h, none, 0, &L));
     int check = h->opt.p_check;
@@ -502,6 +522,7 @@ int run_sweep(Ctx* h) {
             return run_sweep_host(h);
         }
     }
+    ensure_grad_u(h);
     CK(cudaGraphLaunch(h->gexec[h->parity], h->stream));
     std::swap(h->F.p, h->F.pr);
     h->parity ^= 1;
@@ -663,8 +684,9 @@ void batch_enqueue(BatchCtx* b, int skip) {
     if (turb) launchb_max_not_ic(T, tot, s);
     launchb_imposed(T, tot, s);
     launchb_means(T, tot, s);
-    // a3 assembly, a4/a5 predictor with the imposed rows
-    launchb_grad_u(T, tot, s);
+    // a3 assembly (grad u carried from the last sweep's a9 when that step
+    // runs: batch_ensure_grad_u), a4/a5 predictor with the imposed rows
+    if (!turb_b) launchb_grad_u(T, tot, s);
     if (h0->g.conv == 3) launchb_conv_limit(T, tot, s);
     launchb_mom_asm(T, tot, s);
     for (int n = 0; n < h0->opt.n_u; ++n) {
@@ -719,6 +741,18 @@ void batch_enqueue(BatchCtx* b, int skip) {
     launchb_sweep_end(T, tot, s);
 }
 
+// before sweeps of a batch: form grad u for every problem unless each has it
+// from its last sweep (problems that sat out keep theirs: their velocity did
+// not change)
+void batch_ensure_grad_u(BatchCtx* b) {
+    const Ctx* h0 = b->d[0];
+    const bool carried = grad_u_carried(h0);
+    bool cur = true;
+    for (const Ctx* h : b->d) cur = cur && h->g_cur;
+    if (carried && !cur) launchb_grad_u(batch_tab(b, 0), b->tot, b->stream);
+    for (Ctx* h : b->d) h->g_cur = carried;
+}
+
 int batch_sweep_once(BatchCtx* b) {
     if (b->use_graph && !b->gexec) {
         cudaGraph_t g = nullptr;
@@ -738,6 +772,7 @@ int batch_sweep_once(BatchCtx* b) {
             b->gexec = ex;
         }
     }
+    batch_ensure_grad_u(b);
     if (b->use_graph) CK(cudaGraphLaunch(b->gexec, b->stream));
     else batch_enqueue(b, 0);
     CK(cudaGetLastError());
@@ -1448,17 +1483,24 @@ int hfdib_create(const hfdib_grid* grid, const double* lambda, const double* ywa
         size_t dsz = pcgb_desc_size(F.mixed);
         for (int q = 0; q < 2 && !rc; ++q) rc = dalloc(h, &h->pdesc[q], dsz);
         // the problem's descriptor of the persistent solve, one per parity of
-        // the p / pr buffers (a batch of one)
-        std::vector<unsigned char> hd(dsz);
+        // the p / pr buffers (a batch of one).  The upload goes on the
+        // handle's stream, after the zero fill that dalloc queued there: a
+        // synchronous copy runs on the legacy default stream, which does not
+        // wait for a non-blocking stream, so the fill could land after it and
+        // leave a zero descriptor (null pointers in the pressure kernel).
+        std::vector<unsigned char> hd(2 * dsz);
         for (int q = 0; q < 2 && !rc; ++q) {
             Fields Fq = F;
             if (q == 1) std::swap(Fq.p, Fq.pr);
-            size_t by = F.mixed ? pcgb_describe32(hd.data(), g, Fq, h->mg, h->mg32, h->ppart, h->tail_cells,
-                                                  PT_SMEM_BUDGET)
-                                : pcgb_describe64(hd.data(), g, Fq, h->mg, h->ppart, h->tail_cells, PT_SMEM_BUDGET);
+            unsigned char* hq = hd.data() + q * dsz;
+            size_t by = F.mixed ? pcgb_describe32(hq, g, Fq, h->mg, h->mg32, h->ppart, h->tail_cells, PT_SMEM_BUDGET)
+                                : pcgb_describe64(hq, g, Fq, h->mg, h->ppart, h->tail_cells, PT_SMEM_BUDGET);
             h->psmem = by;
-            if (cudaMemcpy(h->pdesc[q], hd.data(), dsz, cudaMemcpyHostToDevice) != cudaSuccess) rc = HFDIB_ERR_CUDA;
+            if (cudaMemcpyAsync(h->pdesc[q], hq, dsz, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+                rc = HFDIB_ERR_CUDA;
         }
+        // (hd must outlive the copies)
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = HFDIB_ERR_CUDA;
         int bps = 0;
         if (!rc && (pcgb_fits(F.mixed, g.dims, PT_THREADS, h->psmem, &bps) != 0 || bps < 1)) rc = HFDIB_ERR_CUDA;
     }
@@ -1576,6 +1618,7 @@ int hfdib_set_field(hfdib_handle hh, int field, const double* srcp) {
     if (!dst) return HFDIB_ERR_INVALID_ARG;
     CK(cudaMemcpyAsync(dst, srcp, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     refresh_mirrors(h);
+    h->g_cur = false;
     return HFDIB_OK;
 }
 
@@ -1676,6 +1719,7 @@ int hfdib_set_state(hfdib_handle hh, const void* buf, size_t bytes) {
     CK(cudaMemcpyAsync(h->F.scal + SC_NSWEEP, &ns, sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->sweeps = hd[5];
+    h->g_cur = false;
     return HFDIB_OK;
 }
 
@@ -1709,7 +1753,7 @@ int hfdib_get_launch_counts(hfdib_handle hh, int64_t* per_sweep, int64_t* per_pc
     bool turb = h->model != HFDIB_LAMINAR;
     int jac = h->opt.precond == 0;
     int tf = h->tail_from;
-    La = (turb ? 1 : 0) + 4 + (h->g.conv == 3 ? 1 : 0) + 2 * h->opt.n_u + 2 +
+    La = (turb ? 1 : 0) + (grad_u_carried(h) ? 3 : 4) + (h->g.conv == 3 ? 1 : 0) + 2 * h->opt.n_u + 2 +
          (h->pblocks > 0 ? 1 : (1 + (tf - 1) + (tf < h->mg.nl ? 1 : 0)) + 1 + (jac ? 0 : 5 * tf + 1) + 1);
     bool turb_b = turb && !h->opt.frozen_turbulence;
     Lb = 1 + (turb_b ? 4 + 2 * h->opt.n_turb + 2 + 2 * h->opt.n_turb + 1 : 0) + 1;
@@ -2111,6 +2155,7 @@ int hfdib_batch_solve_steady(hfdib_batch bb, double tol, int max_iter, int check
     }
     long long ran = 0;
     if (max_iter > 0) {
+        batch_ensure_grad_u(b);
         if (b->use_graph && !b->sgexec) {
             if (batch_build_solve_graph(b) != HFDIB_OK) {
                 cudaStreamCaptureStatus st;
