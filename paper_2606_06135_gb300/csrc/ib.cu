@@ -431,8 +431,11 @@ void launch_imposed(const Grid& g, int model, int freeze, const BcList& bl, uint
                     const double* uy, const double* uz, const double* k, double* uibx, double* uiby,
                     double* uibz, double* kib, double* wib, cudaStream_t s) {
     if (bl.nbc == 0) return;
-    k_imposed<<<nblocks(bl.nbc), BLOCK, 0, s>>>(g, model, freeze, bl, flags, scal, ux, uy, uz, k, uibx, uiby, uibz,
-                                                kib, wib);
+    // one warp per block: a few thousand bc cells of a few hundred FP64
+    // operations each spread over as many SMs as there are warps (full
+    // blocks would leave the work to a handful of SMs' FP64 units)
+    k_imposed<<<(unsigned int)((bl.nbc + 31) / 32), 32, 0, s>>>(g, model, freeze, bl, flags, scal, ux, uy, uz, k, uibx,
+                                                               uiby, uibz, kib, wib);
 }
 void launch_export_bc(const BcList& bl, long long* ints, long long* ints2, double* reals, cudaStream_t s) {
     if (bl.nbc == 0) return;

@@ -432,7 +432,8 @@ void launch_turb_prep(const Grid& g, const Params& P, const Fields& F, cudaStrea
 }
 void launch_bc_prod(const Grid& g, const BcList& bl, const Fields& F, cudaStream_t s) {
     if (bl.nbc == 0) return;
-    k_bc_prod<<<nblocks(bl.nbc), BLOCK, 0, s>>>(g, bl, F);
+    // one warp per block, as for the imposed fields (FP64 work per bc cell)
+    k_bc_prod<<<(unsigned int)((bl.nbc + 31) / 32), 32, 0, s>>>(g, bl, F);
 }
 void launch_scal_asm(const Grid& g, const Params& P, const Fields& F, int eq, cudaStream_t s) {
     k_scal_asm<<<rblocks(g.N), BLOCK, 0, s>>>(g, P, F, eq);
