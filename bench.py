@@ -102,10 +102,20 @@ def class_bytes_per_sweep(dims, mixed, model, piters, n_u=2, n_turb=2):
     b["mom_smooth"] = 2 * n_u * one
     # HbyA: rows, b, p, u* (+ FP32 correction) -> HbyA, rAU; phiHbyA: HbyA -> faces
     b["hbya"] = (fl + (3 * D + D + 1 + D) * f8 + (D * f4 if mixed else 0) + (D + 1) * f8) + (fl + 2 * D * f8)
-    # per CG iteration: FP64 CG vectors (13 words) and the V-cycle (26 words
-    # in the preconditioner type, x 4/3 (2D) or 8/7 (3D) for the coarse levels)
-    coarse = 4.0 / 3.0 if D == 2 else 8.0 / 7.0
-    b["pcg"] = (13 * f8 + 26 * w * coarse) * max(float(piters), 1.0)
+    # the persistent pressure solve.  Per CG iteration, level-0 words in the
+    # solve's type (FP32 correction CG on the mixed path, FP64 otherwise):
+    # product (z, D face coefficients, diag, d_old, q; d, q out: D + 6),
+    # update with level 0's two half sweeps (x, d, q, r_old, 1/diag, D
+    # coefficients; x, r_new, z out: D + 8), restriction (r, z, diag, D
+    # coefficients: D + 3.5), prolongation (D + 5.25), last red half sweep
+    # (D + 4); the coarse levels add a third of the V-cycle's (4D + 16)
+    # words (2D; a seventh in 3D).  Per solve: the FP64 level-0 operator from
+    # rAU and its FP32 copy, the FP64 defect r0, pn = p + x.
+    coarse = 1.0 / 3.0 if D == 2 else 1.0 / 7.0
+    per_it = (5 * D + 26.75 + (4 * D + 16) * coarse) * w
+    setup = (8 + 8 * D + 16 + (4 * (D + 2) if mixed else 0)) + (D * f8 + fl + 3 * f8 + D * f8 + 3 * w) + \
+            (f8 + w + f8)
+    b["pcg"] = setup + per_it * max(float(piters), 1.0)
     # phiH, pn, p, HbyA, rAU, level-0 coefficients -> phi (+FP32), u, relaxed p
     b["update"] = fl + (D + 1 + 1 + D + 1 + D) * f8 + (D + D + 1) * f8 + (D * f4 if mixed else 0)
     if turb:
@@ -348,7 +358,7 @@ def _grf_case(b):
     return G.case_grf(nx, ny, seed=b)
 
 
-def batch_leg(hfdib, torch, cases, dev, steps, warmup):
+def batch_leg(hfdib, torch, cases, dev, steps, warmup, peak):
     """B lambda fields advanced together (one batched persistent pressure
     launch per sweep) against the same designs solved one at a time."""
     N = sum(c["grid"]["nx"] * c["grid"]["ny"] for c in cases)
@@ -365,6 +375,11 @@ def batch_leg(hfdib, torch, cases, dev, steps, warmup):
     t = e0.elapsed_time(e1) / 1e3
     res = bs.sweep(1)
     bs.close()
+    # roofline of the batched sweep: every class's algorithmic bytes per cell
+    # (2D, mixed, SST, the batch's mean CG iterations) over the sweep time
+    piters = float(res[:, 7].mean())
+    bpc = sum(class_bytes_per_sweep(2, True, "komegasst", piters).values())
+    gbs = N * bpc / (t / steps) / 1e9
     one = 0.0
     n1 = 0
     for c in cases[:2]:
@@ -384,6 +399,9 @@ def batch_leg(hfdib, torch, cases, dev, steps, warmup):
             "ms_per_batched_sweep": 1e3 * t / steps, "precision": "mixed",
             "one_by_one": {"designs": 2, "value": n1 * steps / one, "unit": "cell-updates/s"},
             "autotune": tune, "max_residual_after": float(max(res[:, :6].max(), 0.0)),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak[0], "unit": "GB/s",
+                         "frac": gbs / peak[0], "peak_source": peak[1],
+                         "algorithmic_bytes_per_cell_and_sweep": bpc, "pcg_iters_mean": piters},
             "l2": "working set %.0f MB per field set > L2" % (N * 8 / 1e6)}
 
 
@@ -726,7 +744,8 @@ def main():
             out[name] = {"error": "%s: %s" % (type(e).__name__, e)}
 
     if rank == 0 and fut_naca:
-        leg("batch", lambda: batch_leg(hfdib, torch, [f.result() for f in fut_naca], dev, args.steps, args.warmup))
+        leg("batch", lambda: batch_leg(hfdib, torch, [f.result() for f in fut_naca], dev, args.steps, args.warmup,
+                                       (peak, peak_kind)))
     if rank == 0 and fut_grf:
         leg("adjoint", lambda: adjoint_leg(hfdib, torch, [f.result() for f in fut_grf], dev))
     if rank == 0 and fut_bs:
