@@ -543,7 +543,9 @@ __device__ __forceinline__ void b_mom_smooth32(Pos pos, const Grid& g, const Par
         if (finalize) F.us[q][c] += (double)dq;
     }
 }
-__global__ void k_mom_smooth32(Grid g, Params P, Fields F, int colour, int zero_init, int finalize) {
+// six resident blocks per SM (40 registers): the half sweeps are bound by
+// the latency of their global loads, so more warps in flight pay
+__global__ void __launch_bounds__(BLOCK, 6) k_mom_smooth32(Grid g, Params P, Fields F, int colour, int zero_init, int finalize) {
     b_mom_smooth32(grid_pos(), g, P, F, colour, zero_init, finalize);
 }
 

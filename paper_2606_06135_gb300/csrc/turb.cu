@@ -362,7 +362,9 @@ __device__ __forceinline__ void b_scal_smooth32(Pos pos, const Grid& g, const Pa
             if (R.has[s]) acc -= R.a[s] * F.d32[0][R.nb[s]];
     F.d32[0][c] = acc / F.diag32[c];
 }
-__global__ void k_scal_smooth32(Grid g, Params P, Fields F, int eq, int colour, int zero_init) {
+// six resident blocks per SM (40 registers): the half sweeps are bound by
+// the latency of their global loads, so more warps in flight pay
+__global__ void __launch_bounds__(BLOCK, 6) k_scal_smooth32(Grid g, Params P, Fields F, int eq, int colour, int zero_init) {
     b_scal_smooth32(grid_pos(), g, P, F, eq, colour, zero_init);
 }
 
