@@ -40,6 +40,7 @@ TAG_CASES = {
     "grf": lambda: G.case_grf(64, 32, seed=3),
     "box15": lambda: G.case_rotated_box(15.0, 48),
     "box45": lambda: G.case_rotated_box(45.0, 48),
+    "misaligned30": lambda: G.case_misaligned_box(30.0, 96, L=6.0),
     "naca4": lambda: G.case_naca(256, 128, aoa_deg=4.0),
     "ahmed_small": lambda: G.case_ahmed(64, 24, 24),
 }
@@ -99,6 +100,8 @@ SWEEP_CASES = {
     # odd sizes: the last x-pair of a row holds one cell, coarse levels round up
     "cylinder_keps_odd": lambda: G.case_cylinder(45, 23),
     "bfs_sst_odd": lambda: G.case_bfs(63, 17),
+    # inflow through two sides at 30 degrees (x- and y- inlets)
+    "misaligned30_keps": lambda: G.case_misaligned_box(30.0, 48, L=4.0, Re=1e4),
 }
 
 EXACT = dict(n_u=600, n_turb=600, p_reltol=1e-15, p_maxiter=4000)
