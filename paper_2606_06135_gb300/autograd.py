@@ -80,7 +80,11 @@ class SteadyRANSBatch(torch.autograd.Function):
         rc, its, res = bs.solve(tol=solve_tol, max_iter=max_sweeps)
         if rc != 0:
             bs.close()
-            raise RuntimeError("batch solve did not reach %g in %d sweeps (status %d)" % (solve_tol, max_sweeps, rc))
+            worst = res[:, :6].max(axis=1)
+            late = ", ".join("%d: %.1e after %d" % (i, worst[i], its[i]) for i in range(len(cs))
+                             if not worst[i] <= solve_tol)
+            raise RuntimeError("batch solve did not reach %g in %d sweeps (status %d); design: max scaled "
+                               "residual after sweeps -- %s" % (solve_tol, max_sweeps, rc, late))
         ctx.batch = bs
         ctx.adj = (adj_tol, adj_max_iter, objective)
         ctx.shapes = [l.shape for l in lams]
