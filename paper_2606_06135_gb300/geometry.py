@@ -6,7 +6,7 @@ fluid, negative in solid, Sec. 2.3), the lambda indicator of Eq. (lambda)
 made from them, the wall distance the k-omega SST blending functions need,
 and the boundary/flow description of the benchmark-shaped workloads
 (cylinder, backward-facing step, NACA 0012, Ahmed-like body, random
-obstacles).  No step of the SIMPLE sweep lives here; both the CUDA path and
+obstacles, a rectangle misaligned with the mesh).  No step of the SIMPLE sweep lives here; both the CUDA path and
 the CPU oracle take these dictionaries as plain inputs.
 
 A case is a dict with keys
