@@ -91,8 +91,9 @@ def class_bytes_per_sweep(dims, mixed, model, piters, n_u=2, n_turb=2):
     b = {}
     # a1 max over bc u fc (flags, w); residual means (flags, u, p, k, w)
     b["imposed"] = (fl + f8 if turb else 0) + fl + (D + 1 + (2 if turb else 0)) * f8
-    # flags, u -> grad u (D x D), once for the momentum rows and once for production
-    b["grad_u"] = (2 if turb else 1) * (fl + D * f8 + D * D * f8)
+    # flags, u -> grad u (D x D), once per sweep: the gradient formed after the
+    # velocity update feeds the production and the next sweep's momentum rows
+    b["grad_u"] = fl + D * f8 + D * D * f8
     # flags, u, p, nut, phi, grad u -> rows (aP per component, 2D neighbours),
     # b, u*, FP32 defect (mixed)
     b["mom_asm"] = fl + (D + 1 + 1 + D + D * D) * f8 + (D + 2 * D + D + D) * f8 + (D * f4 if mixed else 0)
@@ -209,22 +210,29 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], None, set()
-        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 7:
-                continue
-            try:
-                sm.append(float(parts[0]))
-                smax = float(parts[1])
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[3:7]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return parse_clock_lines(self.lines)
+
+
+def parse_clock_lines(lines):
+    """Median SM clock, the maximum clock and the throttle reasons seen in
+    nvidia-smi CSV lines of ClockSampler.FIELDS (no header, no units):
+    sm, max sm, power, then four reasons as "Active" / "Not Active"."""
+    sm, smax, reasons = [], None, set()
+    names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+    for ln in lines:
+        parts = [p.strip() for p in ln.split(",")]
+        if len(parts) < 7:
+            continue
+        try:
+            sm.append(float(parts[0]))
+            smax = float(parts[1])
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[3:7]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+            "reasons": sorted(reasons), "samples": len(sm)}
 
 
 # ---------------------------------------------------------------- CPU oracle
