@@ -427,8 +427,13 @@ int hfdib_get_history(hfdib_handle h, int count, double* host, int* n_out);
 
 /* Checkpoint: the complete FP64 state (u, p, phi, k, eps, omega, nu_t and the
  * sweep counter).  hfdib_get_state with buf == NULL returns the size in
- * *bytes.  Buffers are host memory.  Resuming from a saved state reproduces
- * the uninterrupted run bit for bit. */
+ * *bytes.  Buffers are host memory, caller-owned; both calls wait for the
+ * handle's stream.  Resuming from a saved state reproduces the uninterrupted
+ * run bit for bit.  Layout: eight int64 header words (magic, nx, ny, nz,
+ * model, sweep counter, total bytes, 0), then the arrays in the order above.
+ * Errors: INVALID_ARG (NULL; get_state with *bytes below the size),
+ * STATE_MISMATCH (set_state with a size, magic word, grid or model other
+ * than the handle's; the size is checked before the header is read), CUDA. */
 int hfdib_get_state(hfdib_handle h, void* buf, size_t* bytes);
 int hfdib_set_state(hfdib_handle h, const void* buf, size_t bytes);
 
@@ -507,16 +512,26 @@ int hfdib_classify_noalloc(const hfdib_grid* grid, const double* lambda, uint8_t
  * do not sweep them individually. */
 typedef struct hfdib_batch_ctx* hfdib_batch;
 
+/* hfdib_create_batch -- B problems created as hfdib_create would create
+ * them, on one stream (stream NULL: the batch creates and owns a
+ * non-blocking stream).  *out is NULL on failure.  Errors: INVALID_ARG (NULL
+ * out, grids, lambdas, Re or bcs; B < 1 or B > 64; precond != 1; p_cg32 != 0;
+ * 2D and 3D grids mixed; or an error of hfdib_create for one problem, whose
+ * status is returned), TOO_LARGE (B above the GPU's SM count: problem b's
+ * coarse tail runs on block b), OOM, CUDA. */
 int hfdib_create_batch(int B, const hfdib_grid* grids, const double* const* lambdas, const double* const* ywalls,
                        int model, const double* Re, const hfdib_bc* bcs, const hfdib_options* opt, void* stream,
                        hfdib_batch* out);
-/* residuals: host, B * HFDIB_NRES doubles (nullable). */
+/* residuals: host, B * HFDIB_NRES doubles (nullable).  Errors: INVALID_ARG
+ * (NULL, n_sweeps < 0), DIVERGED (a non-finite residual), TIMEOUT, CUDA. */
 int hfdib_batch_sweep(hfdib_batch b, int n_sweeps, double* residuals);
 /* Sweep until every problem's largest scaled residual is <= tol (or
  * max_iter); iters_out (host, B ints) receives the sweep at which each
  * problem first met tol; final_res host B * HFDIB_NRES (both nullable). */
 int hfdib_batch_solve_steady(hfdib_batch b, double tol, int max_iter, int check_every, int* iters_out,
                              double* final_res);
+/* The handle of problem i (0 <= i < B, else INVALID_ARG).  It belongs to
+ * the batch and lives until hfdib_destroy_batch: do not destroy it. */
 int hfdib_batch_handle(hfdib_batch b, int i, hfdib_handle* out);
 
 /* Autotuner of the batched pressure kernel: threads per block {512, 1024},
@@ -534,9 +549,16 @@ typedef struct {
 int hfdib_batch_autotune(hfdib_batch b, int trial_sweeps, hfdib_tune* best);
 /* the batch's barrier poll budget, as hfdib_set_barrier_polls */
 int hfdib_batch_set_barrier_polls(hfdib_batch b, int64_t polls);
+/* Waits for the batch's stream, destroys its problem handles and releases
+ * every block through the allocator the batch was created with; NULL is a
+ * no-op. */
 void hfdib_destroy_batch(hfdib_batch b);
 
+/* A static description of a status code ("unknown error" for any other
+ * value); never NULL. */
 const char* hfdib_error_string(int code);
+/* Waits for the handle's stream and releases all its device memory through
+ * the allocator it was created with; NULL is a no-op. */
 void hfdib_destroy(hfdib_handle h);
 
 #ifdef __cplusplus
